@@ -1,0 +1,526 @@
+"""Benchmark of the strategy-preserving map/reduce hot path on GB300.
+
+Default workload (one step): the bandwidth set at n = 2^26 float32 (256 MiB
+per vector), inputs x, y ~ U[-1, 1) from seed 1:
+    asum(x)  -- one strategy reduction, 256 MiB read
+    scal(1.5, x) -> y'  -- a map, 256 MiB read + 256 MiB write
+    dot(x, y)  -- one strategy reduction, 512 MiB read
+Split sizes are chosen per op by the autotuner from the sweep 1024..65536
+(untimed, before warm-up); the sweep table is printed in the JSON line.
+
+Prints ONE JSON line: value = algorithmic bytes of the step / device time of
+the step (GB/s), whole job over all ranks. Other workloads (``--workload
+dot|gemv|gemm|batched``) print their own line with their own metric.
+
+``--impl reference`` times the CPU oracle (the paper has no runnable
+reference; the oracle is the plain CPU evaluation of the same strategy trees)
+on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import signal
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILES = os.path.join(ROOT, "profiles")
+FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+METRIC = "HBM GB/s (dot/asum/GEMV) and TFLOP/s (GEMM) vs GB300 roofline; batched vs per-launch"
+
+
+# ---------------------------------------------------------------------------
+# process group (one rank per GPU; replicas of the workload)
+# ---------------------------------------------------------------------------
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+
+    ws, rank, _ = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if ws > 1 else None
+
+
+def reduce_max(dist, value: float, device=None) -> float:
+    """Max of a float over ranks (identity with one rank)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# peaks, clocks, profiles
+# ---------------------------------------------------------------------------
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", FALLBACK_HBM_GBS), d.get("bf16_tflops", FALLBACK_BF16_TFLOPS), \
+            d.get("bf16_tflops_sustained"), "measured"
+    except (OSError, ValueError):
+        return FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        load = [v for v in sm if mx and v > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "window": "warm-up + timed steps"}
+
+
+def source_digest(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(summary: str, sources):
+    """Per-launch DRAM bytes recorded in a profiles/ summary, if it was taken on
+    the current kernel sources (its 'source_digest' matches); else None."""
+    path = os.path.join(PROFILES, summary)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    d = re.search(r"source_digest:\s*([0-9a-f]+)", text)
+    if not m or not d or d.group(1) != source_digest(sources):
+        return None
+    return float(m.group(1))
+
+
+REDUCE_SOURCES = ["paper_1710_08332_gb300/csrc/k_reduce.cu", "paper_1710_08332_gb300/csrc/device_common.cuh"]
+
+
+# ---------------------------------------------------------------------------
+# timing helpers
+# ---------------------------------------------------------------------------
+
+
+class Timeline:
+    """CUDA events around each kernel call of each step, on the launch stream."""
+
+    def __init__(self, names, stream):
+        import torch
+
+        self.torch = torch
+        self.stream = stream
+        self.names = names
+        self.events = {n: [] for n in names}
+
+    def call(self, name, fn):
+        E = self.torch.cuda.Event
+        a, b = E(enable_timing=True), E(enable_timing=True)
+        a.record(self.stream)
+        fn()
+        b.record(self.stream)
+        self.events[name].append((a, b))
+
+    def avg_ms(self, name):
+        ev = self.events[name]
+        return sum(a.elapsed_time(b) for a, b in ev) / max(len(ev), 1)
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+
+def _default_bw_strategy():
+    from paper_1710_08332_gb300.strategy import ReduceStrategy
+
+    return ReduceStrategy(split=16384, threads=256, vec=4, second="tree", threads2=256)
+
+
+DEFAULT_BW_STRATEGY = None  # set in main() after the package is importable
+
+
+def profile_case(args):
+    """A small case of one kernel, launched args.reps times after one warm-up."""
+    import torch
+
+    import paper_1710_08332_gb300 as dpia
+    from synth import workloads as W
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    st = _default_bw_strategy()
+    n = args.n
+    if args.profile in ("dot", "asum", "scal"):
+        x, y = W.bandwidth(dev, n=n)
+        out = torch.empty(1, device=dev)
+        ws = torch.zeros(dpia.dpia_dot_workspace_size(n, st.with_(pad=n % st.split != 0)), dtype=torch.uint8,
+                         device=dev)
+        st = st.with_(pad=n % st.split != 0)
+        ys = torch.empty_like(x)
+        fn = {"dot": lambda: dpia.dpia_dot_f32(x, y, n, st, out, ws),
+              "asum": lambda: dpia.dpia_asum_f32(x, n, st, out, ws),
+              "scal": lambda: dpia.dpia_scal_f32(W.SCAL_A, x, ys, n, 4)}[args.profile]
+    else:
+        raise SystemExit(f"unknown profile case {args.profile}")
+    for _ in range(1 + args.reps):
+        fn()
+    torch.cuda.synchronize()
+    print(f"profile case {args.profile} n={n} reps={args.reps} done", flush=True)
+    return 0
+
+
+PROFILE_CASES = {"dot", "asum", "scal"}
+
+
+def bandwidth_workload(args, device, dist):
+    import torch
+
+    import paper_1710_08332_gb300 as dpia
+    from paper_1710_08332_gb300 import tune
+    from synth import workloads as W
+
+    n = W.BW_N
+    x, y = W.bandwidth(device)
+    ys = torch.empty_like(x)
+    out_a = torch.empty(1, device=device)
+    out_d = torch.empty(1, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    # autotune split sizes (untimed)
+    if args.no_tune:
+        st_dot = st_asum = DEFAULT_BW_STRATEGY
+        sweep_dot = sweep_asum = {}
+    else:
+        st_dot, sweep_dot = tune.tune_reduce("dot", x, y, reps=5, use_cache=False)
+        st_asum, sweep_asum = tune.tune_reduce("asum", x, reps=5, use_cache=False)
+    ws_d = dpia.workspace(dpia.dpia_dot_workspace_size(n, st_dot), device)
+    ws_a = torch.zeros(dpia.dpia_dot_workspace_size(n, st_asum), dtype=torch.uint8, device=device)
+
+    B_ASUM, B_SCAL, B_DOT = 4 * n, 8 * n, 8 * n
+    step_bytes = B_ASUM + B_SCAL + B_DOT
+
+    def step(tl=None):
+        calls = (("scal", lambda: dpia.dpia_scal_f32(W.SCAL_A, x, ys, n, 4)),
+                 ("asum", lambda: dpia.dpia_asum_f32(x, n, st_asum, out_a, ws_a)),
+                 ("dot", lambda: dpia.dpia_dot_f32(x, y, n, st_dot, out_d, ws_d)))
+        for name, fn in calls:
+            if tl is None:
+                fn()
+            else:
+                tl.call(name, fn)
+
+    clocks = ClockSampler(device.index)
+    clocks.start()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    tl = Timeline(["scal", "asum", "dot"], stream)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(tl)
+    t1.record(stream)
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    ms_total = t0.elapsed_time(t1)
+    ms_total_max = reduce_max(dist, ms_total, device if dist and dist.get_backend() == "nccl" else None)
+    ms_step = ms_total_max / args.steps
+
+    kern = {}
+    for name, b in (("asum", B_ASUM), ("scal", B_SCAL), ("dot", B_DOT)):
+        ms = tl.avg_ms(name)
+        kern[name] = {"avg_us": round(ms * 1e3, 2), "algorithmic_bytes": b, "GB_s": round(b / ms / 1e6, 1)}
+
+    # end to end: pinned host inputs -> device, the three calls, results -> host
+    e2e = e2e_bandwidth(args, device, dist, st_dot, st_asum, x.cpu(), y.cpu(), step_bytes)
+
+    hbm, _, _, src = peaks()
+    dot_ms = tl.avg_ms("dot")
+    achieved = B_DOT / dot_ms / 1e6
+    traffic = profile_traffic("reduce_dot_bandwidth_n2e26.md", REDUCE_SOURCES)
+    world = dist.get_world_size() if dist else 1
+    line = {
+        "metric": METRIC,
+        "value": round(world * step_bytes / (ms_step / 1e3) / 1e9, 1),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "bandwidth set: asum + scal(a=1.5) + dot, n=2^26 f32 (256 MiB per vector), "
+                               "U[-1,1) seed 1, autotuned split (sweep 1024..65536)",
+                   "n": n, "split_dot": st_dot.split, "split_asum": st_asum.split,
+                   "strategy_dot": st_dot.as_dict(), "strategy_asum": st_asum.as_dict(),
+                   "l2": "inputs larger than L2 (256 MiB per vector > 129 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "kernels": kern,
+        "split_sweep_dot_ms": sweep_dot,
+        "split_sweep_asum_ms": sweep_asum,
+        "roofline": {"bound": "hbm", "kernel": "reduce_kernel<DotF32,SumF32,V=4,Block> (dpia_dot_f32)",
+                     "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": traffic,
+                     "peak_source": f"{src} hbm_gbs (copy, burst)",
+                     "algorithmic_bytes_per_launch": B_DOT},
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    return line
+
+
+def e2e_bandwidth(args, device, dist, st_dot, st_asum, hx, hy, step_bytes):
+    """The same step through the public API with pinned host inputs and a host
+    read of the results, copies inside the timed region."""
+    import torch
+
+    import paper_1710_08332_gb300 as dpia
+    from synth import workloads as W
+
+    n = hx.numel()
+    px, py = hx.pin_memory(), hy.pin_memory()
+    host_scal = torch.empty(n, dtype=torch.float32).pin_memory()
+    host_res = torch.empty(2, dtype=torch.float32).pin_memory()
+    dx = torch.empty(n, device=device)
+    dy = torch.empty(n, device=device)
+    ys = torch.empty(n, device=device)
+    res = torch.empty(2, device=device)
+    ws_d = dpia.workspace(dpia.dpia_dot_workspace_size(n, st_dot), device)
+    ws_a = torch.zeros(dpia.dpia_dot_workspace_size(n, st_asum), dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream(device)
+    K = max(3, min(args.steps, 20))
+
+    def one():
+        dx.copy_(px, non_blocking=True)
+        dy.copy_(py, non_blocking=True)
+        dpia.dpia_asum_f32(dx, n, st_asum, res[0:1], ws_a)
+        dpia.dpia_scal_f32(W.SCAL_A, dx, ys, n, 4)
+        dpia.dpia_dot_f32(dx, dy, n, st_dot, res[1:2], ws_d)
+        host_scal.copy_(ys, non_blocking=True)
+        host_res.copy_(res, non_blocking=True)
+
+    for _ in range(2):
+        one()
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(K):
+        one()
+    t1.record(stream)
+    t1.synchronize()
+    ms = reduce_max(dist, t0.elapsed_time(t1) / K, device if dist and dist.get_backend() == "nccl" else None)
+    world = dist.get_world_size() if dist else 1
+    return {"value": round(world * step_bytes / (ms / 1e3) / 1e9, 1), "unit": "GB/s",
+            "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * n + 8, "steps": K,
+            "ms_per_step": round(ms, 3)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the cpu_baseline object and --impl reference)
+# ---------------------------------------------------------------------------
+
+
+def oracle_bandwidth_sample(n_sample: int, reps: int, st_dot=None, st_asum=None):
+    """Time the oracle (C loop nests, one thread) on asum + scal + dot of
+    n_sample elements; returns (GB/s, seconds, description)."""
+    import numpy as np
+
+    from oracle import loopnest
+    from oracle import patterns as P
+    from synth import workloads as W
+
+    x, y = W.bandwidth("cpu", n=n_sample)
+    hx, hy = x.numpy(), y.numpy()
+    od = P.Strategy(s=8192, T=256, V=4, second="tree", T2=256, pad=n_sample % 8192 != 0)
+    if st_dot is not None:
+        od = P.Strategy(s=st_dot.split, T=st_dot.chunk_threads, V=st_dot.vec, thread_map=st_dot.thread_map,
+                        second=st_dot.second, T2=st_dot.threads2, pad=n_sample % st_dot.split != 0)
+    oa = od
+    if st_asum is not None:
+        oa = P.Strategy(s=st_asum.split, T=st_asum.chunk_threads, V=st_asum.vec, thread_map=st_asum.thread_map,
+                        second=st_asum.second, T2=st_asum.threads2, pad=n_sample % st_asum.split != 0)
+    loopnest.lib()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        loopnest.asum_f32(hx, oa)
+        loopnest.scal_f32(W.SCAL_A, hx)
+        loopnest.dot_f32(hx, hy, od)
+    dt = time.perf_counter() - t0
+    step_bytes = 20 * n_sample
+    return reps * step_bytes / dt / 1e9, dt, np.float32(0)
+
+
+def cpu_baseline(st_dot=None, st_asum=None, budget_s: float = 10.0):
+    n_sample = 1 << 24
+    gbs, dt, _ = oracle_bandwidth_sample(n_sample, 1, st_dot, st_asum)
+    reps = max(1, int(budget_s / max(dt, 1e-3)))
+    gbs, dt, _ = oracle_bandwidth_sample(n_sample, reps, st_dot, st_asum)
+    return {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle loop-nest evaluator (C, -O2 -ffp-contract=off, one thread): asum + scal + dot "
+                      f"on n=2^24 of the same distribution with the GPU's strategies, {reps} rep(s), "
+                      f"{dt:.1f} s", "seconds": round(dt, 2)}
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    n_sample = 1 << 22
+    for _ in range(args.warmup):
+        oracle_bandwidth_sample(n_sample, 1)
+    gbs, dt, _ = oracle_bandwidth_sample(n_sample, args.steps)
+    step_bytes = 20 * n_sample
+    ms_step = dt / args.steps * 1e3
+    cb = {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+          "sample": f"each step: oracle asum + scal + dot on n=2^22 (1/16 of the 2^26 workload), one thread"}
+    return {"impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "bandwidth set: asum + scal(a=1.5) + dot, f32, U[-1,1) seed 1 "
+                                   "(oracle sample n=2^22 per step)", "n": n_sample, "bytes_per_step": step_bytes},
+            "cpu_baseline": cb,
+            "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------------------
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["bandwidth"], default="bandwidth")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the split autotuner; use the default strategy (split 16384, tree second level)")
+    ap.add_argument("--profile", choices=sorted(PROFILE_CASES),
+                    help="run a small case of one kernel --reps times (for ncu captures); no JSON line")
+    ap.add_argument("--n", type=int, default=1 << 25, help="elements (or rows x cols) of the --profile case")
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args(argv)
+    if args.profile:
+        return profile_case(args)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        line = reference_arm(args)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+
+    global DEFAULT_BW_STRATEGY
+    DEFAULT_BW_STRATEGY = _default_bw_strategy()
+    world, rank, local = dist_env()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    dist = dist_init("nccl") if world > 1 else None
+    line = bandwidth_workload(args, device, dist)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(_strategy(line, "dot"), _strategy(line, "asum"))
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _strategy(line, op):
+    from paper_1710_08332_gb300.strategy import ReduceStrategy
+
+    return ReduceStrategy(**line["config"][f"strategy_{op}"])
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,220 @@
+/*
+ * dpia.h -- C ABI of the strategy-preserving map/reduce hot path for GB300 (sm_103a).
+ *
+ * Each entry point computes one pattern instance "out := E" (Section 4.1 states
+ * the translation problem as producing a command equal to the assignment of a
+ * functional expression E to an output acceptor) with the parallelisation
+ * strategy passed explicitly, as the strategy-annotated dot product of Section
+ * 2.1 carries it in its split sizes and map levels. Temporaries that the
+ * strategy allocates in global memory are not allocated here: as in Section
+ * 6.4 (allocation hoisting of newGlobal out of parallel loops) they become a
+ * caller-provided workspace of (#chunks x partial) entries.
+ *
+ * Conventions for every call:
+ *   - Pointers are DEVICE pointers owned by the caller, unless stated.
+ *   - Calls are asynchronous on `stream` (NULL = the legacy default stream);
+ *     the library never synchronises and never allocates device memory.
+ *   - All arguments are validated on the host before anything is launched; a
+ *     non-OK status means nothing was enqueued (except DPIA_ERR_CUDA, which
+ *     reports a launch failure). dpia_last_error_message() then describes it.
+ *   - Outputs and workspaces must not overlap inputs (the paper's interference
+ *     control: a parallel loop writes only through its own acceptor). The only
+ *     exception is scal's exact in-place form y == x.
+ *   - A workspace serves one call at a time. It holds completion counters
+ *     and must be zero-filled before its first use (e.g. one memset); every
+ *     call leaves the counters zero again, so it can be reused without a new
+ *     memset. It must be 128-byte aligned.
+ *   - Floating point is IEEE binary32 with round-to-nearest-even, subnormals
+ *     kept; every + and * of a reduction is rounded separately (no contraction),
+ *     so a result is bit-identical to any evaluation of the same strategy tree.
+ */
+#ifndef DPIA_H
+#define DPIA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t / CUstream. */
+typedef struct CUstream_st *dpia_stream_t;
+
+typedef enum {
+  DPIA_OK = 0,
+  DPIA_ERR_NULL = 1,        /* a required pointer is NULL */
+  DPIA_ERR_SHAPE = 2,       /* negative size, split not dividing the length (without pad), ... */
+  DPIA_ERR_ALIGN = 3,       /* pointer or leading dimension not aligned for the requested vector width */
+  DPIA_ERR_STRATEGY = 4,    /* illegal strategy: bad sizes or an illegal nesting of levels */
+  DPIA_ERR_WORKSPACE = 5,   /* workspace NULL or smaller than the *_workspace_size() answer */
+  DPIA_ERR_ALIAS = 6,       /* an output or the workspace overlaps an input */
+  DPIA_ERR_CUDA = 7,        /* the CUDA runtime reported an error at launch */
+  DPIA_ERR_TIMEOUT = 8,     /* a bounded device-side wait gave up (reported via a status word) */
+  DPIA_ERR_UNSUPPORTED = 9  /* a legal strategy this build does not implement */
+} dpia_status;
+
+/*
+ * Levels of the GPU hierarchy a map can run at (Section 6.2: mapGlobal,
+ * mapWorkgroup, mapLocal, mapSeq; WARP is the sm_103a level between a
+ * work-group and a work-item, where reductions use register shuffles).
+ *   GRID   -- mapGlobal: iterations spread over all threads of the grid;
+ *   BLOCK  -- mapWorkgroup: one thread block per iteration;
+ *   WARP   -- one warp (32 threads) per iteration;
+ *   THREAD -- mapLocal: one thread of the enclosing block/warp per iteration;
+ *   SEQ    -- mapSeq: a sequential loop in one thread.
+ * A map nested in another must run at a strictly finer level; a map at GRID
+ * level runs on single threads, so only SEQ may be nested in it (the legality
+ * rule the paper's conclusion asks for: no work-group map inside a local map).
+ */
+typedef enum {
+  DPIA_LVL_GRID = 0,
+  DPIA_LVL_BLOCK = 1,
+  DPIA_LVL_WARP = 2,
+  DPIA_LVL_THREAD = 3,
+  DPIA_LVL_SEQ = 4
+} dpia_level;
+
+enum { DPIA_MAP_INTERLEAVED = 0, DPIA_MAP_CONTIG = 1 };
+enum { DPIA_SECOND_SEQ = 0, DPIA_SECOND_TREE = 1 };
+
+/*
+ * Reduction strategy R (dot, asum, the rows of GEMV):
+ *
+ *   reduce2nd (join (map@map_level (lambda chunk.
+ *       tree (map@inner_level (lambda col. foldV (reduce (+) 0 (map f col)))
+ *                              (columns of (asVector vec chunk)))))
+ *     (split split (input)))
+ *
+ * split       -- s, elements per chunk (Section 2.1's split 2048*128).
+ * threads     -- T, threads per block (power of two, 32..1024; <= 512 when vec >= 8).
+ * vec         -- V in {1,2,4,8,16}: lanes per thread (asVector V, Section 6.2);
+ *                V >= 4 uses 128-bit loads. Inputs must be aligned to
+ *                min(4V, 16) bytes.
+ * map_level   -- level of the map over chunks: BLOCK (a block per chunk,
+ *                inner THREAD: T threads), WARP (a warp per chunk, inner
+ *                THREAD: 32 threads), or GRID (one thread per chunk, inner
+ *                SEQ). These three pairs are implemented.
+ * inner_level -- level of the map over the chunk's columns (see above).
+ * thread_map  -- INTERLEAVED: thread t folds vectors r*Tc + t, r = 0,1,..
+ *                (coalesced); CONTIG: thread t folds vectors t*Rc .. t*Rc+Rc-1
+ *                (the paper's per-thread contiguous sub-chunk). Tc = threads
+ *                per chunk, Rc = s / (Tc*V).
+ * The Tc per-thread results are reduced by a halving tree (lane l adds lane
+ * l+16, l+8, .., l+1 inside each warp, then the same over the warp sums).
+ * second      -- SEQ: the chunk results are folded in chunk order from +0 (the
+ *                final sequential loop of Section 2.2); TREE: they are reduced
+ *                by threads2 threads of one block, thread t folding result
+ *                r*threads2 + t, then the halving tree. threads2 is a power of
+ *                two <= threads. The second level runs in the last block to
+ *                finish (no second launch, no device-side wait).
+ * compensated -- 1: every fold step is a Kahan step on (sum, compensation)
+ *                pairs; tree nodes merge pairs (f32 only).
+ * pad         -- 1: n need not be a multiple of split; the last chunk is
+ *                padded with (+0,+0) items (the reduce's identity). 0: a
+ *                non-dividing split is DPIA_ERR_SHAPE.
+ * grid        -- blocks to launch; 0 = a persistent grid of (SMs x resident
+ *                blocks per SM), capped by the work. The grid never changes
+ *                the result (chunks map to blocks by a grid-stride loop).
+ */
+typedef struct {
+  int64_t split;
+  int32_t threads;
+  int32_t vec;
+  int32_t map_level;
+  int32_t inner_level;
+  int32_t thread_map;
+  int32_t second;
+  int32_t threads2;
+  int32_t compensated;
+  int32_t pad;
+  int32_t grid;
+} dpia_reduce_strategy;
+
+/* Version of this ABI (major*10000 + minor*100 + patch). */
+int32_t dpia_version(void);
+
+/* Description of the last error of the calling host thread ("" if none). */
+const char *dpia_last_error_message(void);
+
+/*
+ * Workspace bytes a dot/asum call with this n and strategy needs: 128 bytes of
+ * counter plus one partial per chunk (4 bytes f32, 8 bytes for a compensated
+ * pair or an int64 partial; the larger is returned). Returns 0 if the
+ * strategy is invalid for n (the call would fail with the same error).
+ */
+size_t dpia_dot_workspace_size(int64_t n, const dpia_reduce_strategy *st);
+
+/*
+ * out[0] := reduce (+) 0 (map (lambda p. fst p * snd p) (zip x y)) under
+ * strategy st (Section 2.1, the dot product and its two-level strategy).
+ * x, y: n floats each; out: one float. n == 0 gives +0.
+ */
+dpia_status dpia_dot_f32(const float *x, const float *y, int64_t n,
+                         const dpia_reduce_strategy *st, float *out, void *ws,
+                         size_t ws_bytes, dpia_stream_t stream);
+
+/*
+ * out[0] := the same reduction on int32 inputs with int64 products and int64
+ * sums (exact, wrapping modulo 2^64 only beyond the int64 range). st as for
+ * dpia_dot_f32 (compensated must be 0).
+ */
+dpia_status dpia_dot_i32(const int32_t *x, const int32_t *y, int64_t n,
+                         const dpia_reduce_strategy *st, int64_t *out, void *ws,
+                         size_t ws_bytes, dpia_stream_t stream);
+
+/* out[0] := reduce (+) 0 (map abs x) under strategy st (asum of Section 7). */
+dpia_status dpia_asum_f32(const float *x, int64_t n, const dpia_reduce_strategy *st,
+                          float *out, void *ws, size_t ws_bytes, dpia_stream_t stream);
+
+/*
+ * y := map (lambda v. a * v) x (scal of Section 7). n floats; vec in
+ * {1,2,4,8,16} is the asVector width of the map (alignment as above). y == x
+ * (in place) is allowed; any other overlap is DPIA_ERR_ALIAS.
+ */
+dpia_status dpia_scal_f32(float a, const float *x, float *y, int64_t n, int32_t vec,
+                          dpia_stream_t stream);
+
+/*
+ * Backward of out = dot(x, y): with g the incoming gradient (ONE float in
+ * device memory), dx := map (lambda v. g * v) y and dy := map (lambda v. g * v) x
+ * (the adjoint of reduce(+) is a broadcast of g, the adjoint of the pointwise
+ * product map multiplies by the other operand). dx or dy may be NULL to skip it.
+ */
+dpia_status dpia_dot_bwd_f32(const float *x, const float *y, const float *g, int64_t n,
+                             float *dx, float *dy, dpia_stream_t stream);
+
+/*
+ * y := map (lambda row. R (zip row x)) A for A of M rows x N columns, row-major
+ * with leading dimension lda >= N (elements). R is the reduction strategy st
+ * applied to each row: map_level BLOCK (a block per row) or WARP (a warp per
+ * row), inner THREAD; split divides N (or pad = 1) and the row's chunk
+ * results are folded in chunk order (second must be SEQ). With V >= 4, A,
+ * lda*4 bytes and x must be 16-byte aligned.
+ */
+dpia_status dpia_gemv_f32(const float *A, int64_t M, int64_t N, int64_t lda, const float *x,
+                          float *y, const dpia_reduce_strategy *st, dpia_stream_t stream);
+
+/* Workspace bytes of dpia_gemv_bwd_f32 for dx: 128 + ceil(M/row_split)*N*4 (+ counters). */
+size_t dpia_gemv_bwd_workspace_size(int64_t M, int64_t N, int64_t row_split);
+
+/*
+ * Backward of y = A x:
+ *   dx := map (lambda col. reduce2nd (map fold (split row_split (zip col dy)))) (transpose A)
+ *         -- each column's rows are split into chunks of row_split rows, each
+ *         chunk folded in row order from +0, the chunk results folded in chunk
+ *         order from +0 (rows past M are the identity);
+ *   dA := map (lambda d. map (lambda v. d * v) x) dy   (dA = dy x^T, ldda >= N).
+ * dx or dA may be NULL to skip it. ws (for dx) as dpia_gemv_bwd_workspace_size.
+ * A, dA, lda*4 and ldda*4 must be 16-byte aligned.
+ */
+dpia_status dpia_gemv_bwd_f32(const float *A, int64_t M, int64_t N, int64_t lda,
+                              const float *x, const float *dy, float *dx, float *dA,
+                              int64_t ldda, int64_t row_split, void *ws, size_t ws_bytes,
+                              dpia_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPIA_H */

@@ -1,0 +1,16 @@
+"""Strategy-preserving map/reduce hot path for GB300 (sm_103a).
+
+The C-ABI library ``libdpia.so`` (include/dpia.h) computes dot, asum, scal,
+GEMV (forward and backward) and GEMM instances of the paper's
+strategy-annotated map/reduce skeleton with hand-written CUDA kernels; this
+package is its Python binding. PyTorch supplies device memory and streams.
+"""
+from . import _native
+from ._native import DPIAError
+from .ops import (asum, dot, dot_bwd, dpia_asum_f32, dpia_dot_bwd_f32, dpia_dot_f32, dpia_dot_i32,
+                  dpia_dot_workspace_size, dpia_gemv_bwd_f32, dpia_gemv_bwd_workspace_size,
+                  dpia_gemv_f32, dpia_last_error_message, dpia_scal_f32, dpia_version, gemv,
+                  gemv_bwd, scal, workspace)
+from .strategy import ReduceStrategy, default_dot_strategy
+
+__all__ = [n for n in dir() if not n.startswith("_")]

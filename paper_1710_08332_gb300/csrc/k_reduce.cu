@@ -1,0 +1,167 @@
+// Strategy reduction kernel: dot (f32, int32) and asum.
+//
+// The split input is mapped chunk by chunk onto the GPU hierarchy the strategy
+// names (Section 6.2's mapWorkgroup / mapLocal / mapGlobal levels, with the
+// warp as the extra sm_103a level):
+//   BLOCK: chunk c -> block (c mod gridDim), Tc = blockDim threads;
+//   WARP : chunk c -> warp  (c mod #warps),   Tc = 32 lanes;
+//   GRID : chunk c -> thread(c mod #threads), Tc = 1 (a sequential fold).
+// Each thread folds its column of the chunk (thread_fold), the Tc results are
+// reduced by the halving tree, and the chunk result goes to partials[c] -- the
+// hoisted global temporary of Section 6.4. The second-level reduce over the C
+// partials runs in the last block to finish: every block fences its partials
+// and takes a ticket; the block that draws the last ticket reduces them. No
+// block ever waits for another.
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace dpia {
+
+namespace {
+
+// Partials written by other blocks are read from L2 (never a stale L1 line).
+template <class A>
+__device__ __forceinline__ typename A::acc_t load_partial(const typename A::acc_t *p, int64_t i) {
+  return __ldcg(p + i);
+}
+
+// Second level over the C chunk partials, run by the last block.
+template <class A>
+__device__ void second_level(const ReduceLaunch &p, typename A::acc_t *sm) {
+  using acc_t = typename A::acc_t;
+  const acc_t *part = static_cast<const acc_t *>(p.partials);
+  acc_t res = A::zero();
+  if (!p.second_tree) {
+    // left fold in chunk order from zero (the final sequential loop)
+    if (threadIdx.x == 0) {
+      acc_t acc = A::zero();
+      int64_t c = 0;
+      for (; c + 8 <= p.C; c += 8) {
+        acc_t b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) b[u] = load_partial<A>(part, c + u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = A::combine(acc, b[u]);
+      }
+      for (; c < p.C; ++c) acc = A::combine(acc, load_partial<A>(part, c));
+      res = acc;
+    }
+  } else {
+    // thread t folds partials r*T2 + t (identity past C), then the tree
+    const int t = threadIdx.x;
+    acc_t acc = A::zero();
+    if (t < p.T2) {
+      const int64_t R2 = ceil_div(p.C, p.T2);
+      for (int64_t r = 0; r < R2; ++r) {
+        const int64_t i = r * p.T2 + t;
+        acc = A::combine(acc, i < p.C ? load_partial<A>(part, i) : A::zero());
+      }
+    }
+    res = block_tree<A>(acc, p.T2, sm);
+  }
+  if (threadIdx.x == 0) {
+    *static_cast<typename A::out_t *>(p.out) = A::result(res);
+    *p.counter = 0u;  // leave the workspace counter zero for the next call
+  }
+}
+
+template <class E, class A, int V, int LEVEL>
+__global__ void __launch_bounds__(max_threads_for_vec(V)) reduce_kernel(const ReduceLaunch p) {
+  using in_t = typename E::in_t;
+  using acc_t = typename A::acc_t;
+  __shared__ acc_t sm[32];
+  __shared__ int is_last;
+  const in_t *x = static_cast<const in_t *>(p.x);
+  const in_t *y = static_cast<const in_t *>(p.y);
+  acc_t *part = static_cast<acc_t *>(p.partials);
+
+  if constexpr (LEVEL == int(ChunkLevel::Block)) {
+    const int t = threadIdx.x;
+    for (int64_t c = blockIdx.x; c < p.C; c += gridDim.x) {
+      const int64_t base = c * p.s + t * p.tstride;
+      const bool full = (c + 1) * p.s <= p.n;
+      acc_t v = thread_fold<E, A, V, false>(x, y, p.n, base, p.Rc, p.step, full);
+      v = block_tree<A>(v, p.Tc, sm);
+      if (t == 0) part[c] = v;
+    }
+  } else if constexpr (LEVEL == int(ChunkLevel::Warp)) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5;
+    const int64_t w0 = blockIdx.x * wpb + (threadIdx.x >> 5);
+    const int64_t nw = gridDim.x * wpb;
+    for (int64_t c = w0; c < p.C; c += nw) {
+      const int64_t base = c * p.s + lane * p.tstride;
+      const bool full = (c + 1) * p.s <= p.n;
+      acc_t v = thread_fold<E, A, V, false>(x, y, p.n, base, p.Rc, p.step, full);
+      v = warp_tree<A>(v, 32);
+      if (lane == 0) part[c] = v;
+    }
+  } else {
+    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ng = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = g0; c < p.C; c += ng) {
+      const bool full = (c + 1) * p.s <= p.n;
+      part[c] = thread_fold<E, A, V, false>(x, y, p.n, c * p.s, p.Rc, p.step, full);
+    }
+  }
+
+  // publish this block's partials, then take a ticket
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned ticket = atomicAdd(p.counter, 1u);
+    __threadfence();
+    is_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) second_level<A>(p, sm);
+}
+
+template <class E, class A, int LEVEL>
+const void *pick_v(int V) {
+  switch (V) {
+    case 1: return (const void *)reduce_kernel<E, A, 1, LEVEL>;
+    case 2: return (const void *)reduce_kernel<E, A, 2, LEVEL>;
+    case 4: return (const void *)reduce_kernel<E, A, 4, LEVEL>;
+    case 8: return (const void *)reduce_kernel<E, A, 8, LEVEL>;
+    case 16: return (const void *)reduce_kernel<E, A, 16, LEVEL>;
+  }
+  return nullptr;
+}
+
+template <class E, class A>
+const void *pick_level(ChunkLevel level, int V) {
+  switch (level) {
+    case ChunkLevel::Grid: return pick_v<E, A, 0>(V);
+    case ChunkLevel::Block: return pick_v<E, A, 1>(V);
+    case ChunkLevel::Warp: return pick_v<E, A, 2>(V);
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+int resident_blocks(const void *kernel, int threads);
+
+cudaError_t launch_reduce(ReduceOp op, bool compensated, int V, ChunkLevel level, int threads,
+                          int grid, const ReduceLaunch &p, cudaStream_t stream) {
+  const void *k = nullptr;
+  if (op == ReduceOp::DotF32)
+    k = compensated ? pick_level<DotF32, KahanF32>(level, V) : pick_level<DotF32, SumF32>(level, V);
+  else if (op == ReduceOp::AsumF32)
+    k = compensated ? pick_level<AsumF32, KahanF32>(level, V) : pick_level<AsumF32, SumF32>(level, V);
+  else
+    k = pick_level<DotI32, SumI64>(level, V);
+  if (!k) return cudaErrorInvalidValue;
+  int64_t units_per_block = level == ChunkLevel::Block ? 1 : level == ChunkLevel::Warp ? threads / 32 : threads;
+  int64_t need = ceil_div(p.C, units_per_block);
+  if (grid <= 0) {
+    int64_t cap = (int64_t)sm_count() * resident_blocks(k, threads);
+    grid = (int)(need < cap ? need : cap);
+    if (grid < 1) grid = 1;
+  }
+  void *args[] = {const_cast<ReduceLaunch *>(&p)};
+  return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, 0, stream);
+}
+
+}  // namespace dpia

@@ -1,0 +1,72 @@
+// Host-side launch interface between the C ABI layer (abi.cu) and the kernel
+// translation units. Arguments arrive here already validated.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dpia {
+
+enum class ReduceOp { DotF32 = 0, AsumF32 = 1, DotI32 = 2 };
+enum class ChunkLevel { Grid = 0, Block = 1, Warp = 2 };
+
+struct ReduceLaunch {
+  const void *x;
+  const void *y;
+  int64_t n;
+  int64_t s;        // chunk elements
+  int64_t C;        // chunks
+  int64_t Rc;       // fold steps per thread per chunk: s / (Tc * V)
+  int64_t step;     // elements between a thread's successive fold steps
+  int64_t tstride;  // elements between the first items of neighbouring threads
+  int Tc;           // threads per chunk
+  int second_tree;  // 0 seq, 1 tree
+  int T2;           // threads of the tree second level
+  void *partials;   // C (or padded) partials
+  unsigned *counter;
+  void *out;
+};
+
+// Launch the reduction; returns cudaSuccess or the launch error. `grid` = 0
+// picks a persistent grid.
+cudaError_t launch_reduce(ReduceOp op, bool compensated, int V, ChunkLevel level, int threads,
+                          int grid, const ReduceLaunch &p, cudaStream_t stream);
+
+struct GemvLaunch {
+  const float *A;
+  int64_t M, N, lda;
+  const float *x;
+  float *y;
+  int64_t s;        // row chunk elements
+  int64_t Crow;     // chunks per row
+  int64_t Rc;       // fold steps per thread per chunk
+  int64_t step;
+  int64_t tstride;
+  int Tc;
+};
+cudaError_t launch_gemv(bool compensated, int V, ChunkLevel level, int threads, int grid,
+                        const GemvLaunch &p, cudaStream_t stream);
+
+cudaError_t launch_scal(float a, const float *x, float *y, int64_t n, int V, cudaStream_t stream);
+cudaError_t launch_dot_bwd(const float *x, const float *y, const float *g, int64_t n, float *dx,
+                           float *dy, cudaStream_t stream);
+cudaError_t launch_outer(const float *x, const float *dy, int64_t M, int64_t N, float *dA,
+                         int64_t ldda, cudaStream_t stream);
+
+struct GemvBwdLaunch {
+  const float *A;
+  int64_t M, N, lda;
+  const float *dy;
+  float *dx;
+  int64_t Rs;        // rows per chunk
+  int64_t Cr;        // row chunks
+  float *partials;   // Cr x Npad
+  int64_t Npad;
+  unsigned *counters;  // one per column tile
+};
+cudaError_t launch_gemv_bwd_dx(const GemvBwdLaunch &p, cudaStream_t stream);
+
+// Device properties cached per device.
+int sm_count();
+
+}  // namespace dpia

@@ -1,0 +1,201 @@
+"""Python binding of the C ABI: one function per entry point, same names.
+
+The ``dpia_*`` functions only marshal torch tensors (device pointers, sizes,
+the current CUDA stream) into the C call and raise ``DPIAError`` on a non-OK
+status; every step of the computation runs in the library's kernels. The
+short names (``dot``, ``asum``, ...) additionally allocate outputs and
+workspaces with torch.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import _native as N
+from .strategy import ReduceStrategy, default_dot_strategy
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("dpia: tensors must be CUDA tensors (device memory)")
+
+
+def _st(st: ReduceStrategy):
+    return ctypes.byref(st.to_c())
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as include/dpia.h)
+# ---------------------------------------------------------------------------
+
+
+def dpia_version() -> int:
+    return N.lib().dpia_version()
+
+
+def dpia_last_error_message() -> str:
+    return N.lib().dpia_last_error_message().decode(errors="replace")
+
+
+def dpia_dot_workspace_size(n: int, st: ReduceStrategy) -> int:
+    return int(N.lib().dpia_dot_workspace_size(int(n), _st(st)))
+
+
+def dpia_dot_f32(x, y, n, st, out, ws, stream=None):
+    _need_cuda(x, y, out, ws)
+    N.check(N.lib().dpia_dot_f32(_ptr(x), _ptr(y), int(n), _st(st), _ptr(out), _ptr(ws),
+                                 ws.numel() * ws.element_size() if ws is not None else 0,
+                                 _stream(stream)), "dpia_dot_f32")
+
+
+def dpia_dot_i32(x, y, n, st, out, ws, stream=None):
+    _need_cuda(x, y, out, ws)
+    N.check(N.lib().dpia_dot_i32(_ptr(x), _ptr(y), int(n), _st(st), _ptr(out), _ptr(ws),
+                                 ws.numel() * ws.element_size() if ws is not None else 0,
+                                 _stream(stream)), "dpia_dot_i32")
+
+
+def dpia_asum_f32(x, n, st, out, ws, stream=None):
+    _need_cuda(x, out, ws)
+    N.check(N.lib().dpia_asum_f32(_ptr(x), int(n), _st(st), _ptr(out), _ptr(ws),
+                                  ws.numel() * ws.element_size() if ws is not None else 0,
+                                  _stream(stream)), "dpia_asum_f32")
+
+
+def dpia_scal_f32(a, x, y, n, vec=4, stream=None):
+    _need_cuda(x, y)
+    N.check(N.lib().dpia_scal_f32(ctypes.c_float(a), _ptr(x), _ptr(y), int(n), int(vec),
+                                  _stream(stream)), "dpia_scal_f32")
+
+
+def dpia_dot_bwd_f32(x, y, g, n, dx, dy, stream=None):
+    _need_cuda(x, y, g, dx, dy)
+    N.check(N.lib().dpia_dot_bwd_f32(_ptr(x), _ptr(y), _ptr(g), int(n), _ptr(dx), _ptr(dy),
+                                     _stream(stream)), "dpia_dot_bwd_f32")
+
+
+def dpia_gemv_f32(A, M, N_, lda, x, y, st, stream=None):
+    _need_cuda(A, x, y)
+    N.check(N.lib().dpia_gemv_f32(_ptr(A), int(M), int(N_), int(lda), _ptr(x), _ptr(y), _st(st),
+                                  _stream(stream)), "dpia_gemv_f32")
+
+
+def dpia_gemv_bwd_workspace_size(M, N_, row_split) -> int:
+    return int(N.lib().dpia_gemv_bwd_workspace_size(int(M), int(N_), int(row_split)))
+
+
+def dpia_gemv_bwd_f32(A, M, N_, lda, x, dy, dx, dA, ldda, row_split, ws, stream=None):
+    _need_cuda(A, x, dy, dx, dA, ws)
+    N.check(N.lib().dpia_gemv_bwd_f32(_ptr(A), int(M), int(N_), int(lda), _ptr(x), _ptr(dy),
+                                      _ptr(dx), _ptr(dA), int(ldda), int(row_split), _ptr(ws),
+                                      ws.numel() * ws.element_size() if ws is not None else 0,
+                                      _stream(stream)), "dpia_gemv_bwd_f32")
+
+
+# ---------------------------------------------------------------------------
+# workspaces: zero-filled once, reused (each call leaves its counters zero)
+# ---------------------------------------------------------------------------
+
+_ws_lock = threading.Lock()
+_ws_cache: dict = {}
+
+
+def workspace(nbytes: int, device=None, stream=None) -> torch.Tensor:
+    """A zero-initialised workspace of >= nbytes for calls on ``stream``.
+
+    One buffer per (device, stream) is kept and grown on demand; calls on one
+    stream are ordered, so they can share it.
+    """
+    device = torch.device(device) if device is not None else torch.device("cuda")
+    if device.index is None:
+        device = torch.device("cuda", torch.cuda.current_device())
+    stream = stream or torch.cuda.current_stream(device)
+    key = (device.index, stream.cuda_stream)
+    nbytes = max(int(nbytes), 128)
+    with _ws_lock:
+        buf = _ws_cache.get(key)
+        if buf is None or buf.numel() < nbytes:
+            size = 1 << (nbytes - 1).bit_length()
+            with torch.cuda.stream(stream):
+                buf = torch.zeros(size, dtype=torch.uint8, device=device)
+            _ws_cache[key] = buf
+    return buf
+
+
+# ---------------------------------------------------------------------------
+# convenience API
+# ---------------------------------------------------------------------------
+
+
+def dot(x, y, strategy: ReduceStrategy | None = None, out=None):
+    """dot(x, y) under a reduction strategy (float32 or int32 inputs)."""
+    n = x.numel()
+    st = strategy or default_dot_strategy(n)
+    if x.dtype == torch.int32:
+        out = out if out is not None else torch.empty(1, dtype=torch.int64, device=x.device)
+        ws = workspace(dpia_dot_workspace_size(n, st), x.device)
+        dpia_dot_i32(x, y, n, st, out, ws)
+        return out[0]
+    out = out if out is not None else torch.empty(1, dtype=torch.float32, device=x.device)
+    ws = workspace(dpia_dot_workspace_size(n, st), x.device)
+    dpia_dot_f32(x, y, n, st, out, ws)
+    return out[0]
+
+
+def asum(x, strategy: ReduceStrategy | None = None, out=None):
+    n = x.numel()
+    st = strategy or default_dot_strategy(n)
+    out = out if out is not None else torch.empty(1, dtype=torch.float32, device=x.device)
+    ws = workspace(dpia_dot_workspace_size(n, st), x.device)
+    dpia_asum_f32(x, n, st, out, ws)
+    return out[0]
+
+
+def scal(a: float, x, out=None, vec: int = 4):
+    y = out if out is not None else torch.empty_like(x)
+    dpia_scal_f32(a, x, y, x.numel(), vec)
+    return y
+
+
+def default_gemv_strategy(N_: int) -> ReduceStrategy:
+    if N_ >= 1024:
+        s = N_ if N_ % 1024 == 0 else ((N_ + 1023) // 1024) * 1024
+        return ReduceStrategy(split=s, threads=256, vec=4, pad=N_ % 1024 != 0)
+    s = ((N_ + 127) // 128) * 128
+    return ReduceStrategy(split=s, threads=128, vec=4, map_level="warp", pad=N_ % 128 != 0)
+
+
+def gemv(A, x, strategy: ReduceStrategy | None = None, out=None):
+    M, N_ = A.shape
+    st = strategy or default_gemv_strategy(N_)
+    y = out if out is not None else torch.empty(M, dtype=torch.float32, device=A.device)
+    dpia_gemv_f32(A, M, N_, A.stride(0), x, y, st)
+    return y
+
+
+def gemv_bwd(A, x, dy, need_dx=True, need_dA=True, row_split=64):
+    M, N_ = A.shape
+    dx = torch.empty(N_, dtype=torch.float32, device=A.device) if need_dx else None
+    dA = torch.empty(M, N_, dtype=torch.float32, device=A.device) if need_dA else None
+    ws = workspace(dpia_gemv_bwd_workspace_size(M, N_, row_split), A.device) if need_dx else None
+    dpia_gemv_bwd_f32(A, M, N_, A.stride(0), x, dy, dx, dA, N_, row_split, ws)
+    return dx, dA
+
+
+def dot_bwd(x, y, g):
+    dx, dy = torch.empty_like(x), torch.empty_like(y)
+    dpia_dot_bwd_f32(x, y, g, x.numel(), dx, dy)
+    return dx, dy

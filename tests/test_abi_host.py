@@ -1,0 +1,125 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+symbol include/dpia.h declares, and rejects bad arguments on the host before
+any CUDA call (null pointers, shapes, alignment, illegal level nestings,
+small workspaces, aliasing). Pointers here are fake host addresses: validation
+never dereferences them and fails before anything is launched."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1710_08332_gb300 as dpia
+from paper_1710_08332_gb300 import _native as N
+from paper_1710_08332_gb300.strategy import ReduceStrategy
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "dpia.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dpia_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = N.lib()
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(L, name), f"{name} declared in dpia.h but not exported"
+    assert set(names) == set(N.SIGNATURES), "binding signatures out of sync with dpia.h"
+
+
+def test_version_and_empty_error():
+    assert dpia.dpia_version() == 10000
+    assert isinstance(dpia.dpia_last_error_message(), str)
+
+
+def _call_dot(st, n=1 << 20, x=0x10000, y=0x20000000, out=0x7000000000, ws=0x7100000000,
+              ws_bytes=1 << 20):
+    L = N.lib()
+    return L.dpia_dot_f32(ctypes.c_void_p(x), ctypes.c_void_p(y), n, ctypes.byref(st.to_c()),
+                          ctypes.c_void_p(out), ctypes.c_void_p(ws), ws_bytes, None)
+
+
+BASE = ReduceStrategy(split=8192, threads=256, vec=4)
+
+
+@pytest.mark.parametrize("bad,code", [
+    (BASE.with_(threads=48), N.ERR_STRATEGY),
+    (BASE.with_(threads=2048), N.ERR_STRATEGY),
+    (BASE.with_(vec=3), N.ERR_STRATEGY),
+    (BASE.with_(vec=16, threads=1024), N.ERR_STRATEGY),
+    (BASE.with_(split=1000), N.ERR_STRATEGY),
+    (BASE.with_(split=3 * 8192), N.ERR_SHAPE),
+    (BASE.with_(map_level="thread", inner_level="seq"), N.ERR_STRATEGY),
+    (BASE.with_(map_level="warp", inner_level="block"), N.ERR_STRATEGY),
+    (BASE.with_(map_level="grid", inner_level="thread"), N.ERR_STRATEGY),
+    (BASE.with_(map_level="block", inner_level="block"), N.ERR_STRATEGY),
+    (BASE.with_(map_level="block", inner_level="seq"), N.ERR_UNSUPPORTED),
+    (BASE.with_(map_level="block", inner_level="warp"), N.ERR_UNSUPPORTED),
+    (BASE.with_(second="tree", threads2=512), N.ERR_STRATEGY),
+    (BASE.with_(second="tree", threads2=24), N.ERR_STRATEGY),
+    (BASE.with_(grid=-1), N.ERR_STRATEGY),
+])
+def test_strategy_validation(bad, code):
+    assert _call_dot(bad) == code
+    assert dpia.dpia_last_error_message()
+
+
+def test_hierarchy_legality_message():
+    _call_dot(BASE.with_(map_level="warp", inner_level="block"))
+    assert "not finer" in dpia.dpia_last_error_message()
+
+
+def test_pointer_shape_alias_workspace_errors():
+    assert _call_dot(BASE, x=0) == N.ERR_NULL
+    assert _call_dot(BASE, out=0) == N.ERR_NULL
+    assert _call_dot(BASE, n=-5) == N.ERR_SHAPE
+    assert _call_dot(BASE, x=0x10004) == N.ERR_ALIGN          # not 16-byte aligned for vec=4
+    assert _call_dot(BASE.with_(vec=1), x=0x10004) != N.ERR_ALIGN
+    assert _call_dot(BASE, out=0x10000 + 64) == N.ERR_ALIAS  # out inside x
+    assert _call_dot(BASE, ws=0) == N.ERR_WORKSPACE
+    need = dpia.dpia_dot_workspace_size(1 << 20, BASE)
+    assert need == 128 + 128 * 8
+    assert _call_dot(BASE, ws_bytes=need - 1) == N.ERR_WORKSPACE
+    assert _call_dot(BASE, ws=0x20000000 + 4096) == N.ERR_ALIAS  # workspace inside y
+    assert _call_dot(BASE, ws=0x7100000040) == N.ERR_ALIGN      # workspace not 128-byte aligned
+
+
+def test_workspace_size_matches_chunks():
+    for n, s in ((1 << 26, 1024), (1 << 26, 65536), (12345, 1024)):
+        st = BASE.with_(split=s, pad=True)
+        C = -(-n // s)
+        assert dpia.dpia_dot_workspace_size(n, st) == 128 + -(-C * 8 // 128) * 128
+    assert dpia.dpia_dot_workspace_size(100, BASE.with_(threads=7)) == 0
+
+
+def test_int32_rejects_compensated():
+    L = N.lib()
+    st = BASE.with_(compensated=True)
+    rc = L.dpia_dot_i32(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000000), 1 << 20,
+                        ctypes.byref(st.to_c()), ctypes.c_void_p(0x7000000000),
+                        ctypes.c_void_p(0x7100000000), 1 << 20, None)
+    assert rc == N.ERR_STRATEGY
+
+
+def test_scal_and_gemv_validation():
+    L = N.lib()
+    p = ctypes.c_void_p
+    assert L.dpia_scal_f32(1.5, p(0x10000), p(0x10000 + 8), 1000, 4, None) in (N.ERR_ALIAS, N.ERR_ALIGN)
+    assert L.dpia_scal_f32(1.5, p(0x10000), p(0x10000 + 16), 1000, 4, None) == N.ERR_ALIAS
+    assert L.dpia_scal_f32(1.5, p(0x10000), p(0x20000), 1000, 5, None) == N.ERR_STRATEGY
+    assert L.dpia_scal_f32(1.5, p(0x10000), p(0x20000), -1, 4, None) == N.ERR_SHAPE
+    st = ReduceStrategy(split=8192, threads=256, vec=4, second="tree", threads2=256)
+    assert L.dpia_gemv_f32(p(0x10000000), 64, 8192, 8192, p(0x20000), p(0x30000), ctypes.byref(st.to_c()),
+                           None) == N.ERR_UNSUPPORTED
+    st = ReduceStrategy(split=8192, threads=256, vec=4)
+    assert L.dpia_gemv_f32(p(0x10000000), 64, 8192, 100, p(0x20000), p(0x30000), ctypes.byref(st.to_c()),
+                           None) == N.ERR_SHAPE
+    assert L.dpia_gemv_f32(p(0x10000000), 64, 8192, 8193, p(0x20000), p(0x30000), ctypes.byref(st.to_c()),
+                           None) == N.ERR_ALIGN
+    assert L.dpia_gemv_bwd_f32(p(0x10000000), 1 << 20, 64, 64, p(0x20000), p(0x30000), p(0x40000), None, 64, 8,
+                               p(0x50000000), 1 << 30, None) == N.ERR_STRATEGY  # > 65535 row chunks
+    assert dpia.dpia_gemv_bwd_workspace_size(8192, 8192, 64) == 128 + 1024 + 128 * 8192 * 4
