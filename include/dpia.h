@@ -213,6 +213,31 @@ dpia_status dpia_gemv_bwd_f32(const float *A, int64_t M, int64_t N, int64_t lda,
                               int64_t ldda, int64_t row_split, void *ws, size_t ws_bytes,
                               dpia_stream_t stream);
 
+/*
+ * Allocation-free dot product. The paper has no counterpart: this entry exists
+ * for callers that cannot allocate device memory -- e.g. a plugin inside a
+ * host framework that owns all device memory and offers it no allocator, or a
+ * latency-critical path that cannot afford cudaMalloc's possible device
+ * synchronisation. It computes exactly what dpia_dot_f32 computes (same
+ * strategy, same bits) but takes no workspace: its scratch (the per-chunk
+ * partials and the completion counter) is a static device array of
+ * DPIA_NOALLOC_SCRATCH_BYTES (1 MiB) that every GPU loading the library keeps
+ * until the process exits, so at most (1 MiB - 128) / 8 = 131056 chunks
+ * (n / split, rounded up) are allowed; larger requests return
+ * DPIA_ERR_WORKSPACE with an explanation and enqueue nothing.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address; make that first call before any stream capture.
+ *   - Every call clears the array's counter (an asynchronous memset on
+ *     `stream`) and then reuses the array: calls whose executions overlap on
+ *     the GPU race on it and must be ordered by the caller.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.
+ * Arguments and errors otherwise as dpia_dot_f32.
+ */
+#define DPIA_NOALLOC_SCRATCH_BYTES (1u << 20)
+dpia_status dpia_dot_f32_noalloc(const float *x, const float *y, int64_t n,
+                                 const dpia_reduce_strategy *st, float *out,
+                                 dpia_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,7 @@ SIGNATURES = {
     "dpia_gemv_f32": (_I32, [_P, _I64, _I64, _I64, _P, _P, _SP, _P]),
     "dpia_gemv_bwd_workspace_size": (_SZ, [_I64, _I64, _I64]),
     "dpia_gemv_bwd_f32": (_I32, [_P, _I64, _I64, _I64, _P, _P, _P, _P, _I64, _I64, _P, _SZ, _P]),
+    "dpia_dot_f32_noalloc": (_I32, [_P, _P, _I64, _SP, _P, _P]),
 }
 
 

@@ -202,6 +202,17 @@ dpia_status run_reduce(const char *fn, ReduceOp op, const void *x, const void *y
 
 }  // namespace
 
+namespace dpia {
+void set_last_error(const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+}  // namespace dpia
+
 extern "C" {
 
 int32_t dpia_version(void) { return 10000; }

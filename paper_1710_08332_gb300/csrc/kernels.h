@@ -69,4 +69,7 @@ cudaError_t launch_gemv_bwd_dx(const GemvBwdLaunch &p, cudaStream_t stream);
 // Device properties cached per device.
 int sm_count();
 
+// Set the calling host thread's dpia_last_error_message() text (printf format).
+void set_last_error(const char *fmt, ...);
+
 }  // namespace dpia

@@ -105,6 +105,15 @@ def dpia_gemv_bwd_f32(A, M, N_, lda, x, dy, dx, dA, ldda, row_split, ws, stream=
                                       _stream(stream)), "dpia_gemv_bwd_f32")
 
 
+def dpia_dot_f32_noalloc(x, y, n, st, out, stream=None):
+    """dpia_dot_f32 without a workspace argument, for callers that cannot
+    allocate device memory: the scratch is the library's static 1 MiB device
+    array (calls that overlap on the GPU race on it)."""
+    _need_cuda(x, y, out)
+    N.check(N.lib().dpia_dot_f32_noalloc(_ptr(x), _ptr(y), int(n), _st(st), _ptr(out), _stream(stream)),
+            "dpia_dot_f32_noalloc")
+
+
 # ---------------------------------------------------------------------------
 # workspaces: zero-filled once, reused (each call leaves its counters zero)
 # ---------------------------------------------------------------------------
