@@ -213,6 +213,62 @@ dpia_status dpia_gemv_bwd_f32(const float *A, int64_t M, int64_t N, int64_t lda,
                               int64_t ldda, int64_t row_split, void *ws, size_t ws_bytes,
                               dpia_stream_t stream);
 
+enum { DPIA_CONTRACT_OFF = 0, DPIA_CONTRACT_FMA = 1 };
+
+/*
+ * GEMM strategy. contract: how the FP32 fold rounds each step (OFF: a
+ * separately rounded multiply and add; FMA: one fused multiply-add, the
+ * contraction declared explicitly -- the paper's num is abstract, so the
+ * rounding of a step is part of the strategy). tile_m/n/k: 0 for the
+ * implemented tiles (FP32: 128 x 128 x 16; BF16: 128 x 256 x 64) or exactly
+ * those values. grid: CTAs of the persistent BF16 kernel (0 = one per SM).
+ */
+typedef struct {
+  int32_t contract;
+  int32_t tile_m;
+  int32_t tile_n;
+  int32_t tile_k;
+  int32_t grid;
+} dpia_gemm_strategy;
+
+/*
+ * C := map (lambda a. map (lambda b. fold_k (a_k * b_k)) (transpose op(B))) op(A)
+ * in FP32 on the CUDA cores: op(A) is M x K (A stored M x K row-major with
+ * lda, or K x M when transA = 1), op(B) is K x N (B stored K x N with ldb, or
+ * N x K when transB = 1), C is M x N with ldc (f32). Each C_ij is one
+ * sequential fold over k = 0..K-1 from +0 (Section 4.2's reduceI), so the
+ * result is bit-identical to a plain loop with the same contraction. No
+ * alignment is required; 16-byte alignment with leading dimensions a multiple
+ * of 4 enables 128-bit loads. K == 0 gives C = +0.
+ */
+dpia_status dpia_gemm_f32(const float *A, const float *B, float *C, int64_t M, int64_t N, int64_t K,
+                          int64_t lda, int64_t ldb, int64_t ldc, int32_t transA, int32_t transB,
+                          const dpia_gemm_strategy *st, dpia_stream_t stream);
+
+/*
+ * The same map of maps of reduce with bf16 operands (raw bit patterns,
+ * uint16) and f32 accumulation on the tensor cores (tcgen05.mma, TMA, tensor
+ * memory). Layout arguments as dpia_gemm_f32 (transA = 1 / transB = 0 are the
+ * MN-major operand layouts, read directly). A and B must be 16-byte aligned
+ * and lda, ldb multiples of 8 (TMA). The order of the accumulation inside the
+ * tensor core is fixed by the hardware, so results are defined up to the
+ * f32 rounding of a k-reduction (checked against FP64 by tolerance).
+ */
+dpia_status dpia_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N,
+                           int64_t K, int64_t lda, int64_t ldb, int64_t ldc, int32_t transA,
+                           int32_t transB, const dpia_gemm_strategy *st, dpia_stream_t stream);
+
+/* y := map bf16_round_nearest_even x (n floats to n bf16 bit patterns); x 16-byte, y 8-byte aligned. */
+dpia_status dpia_cast_f32_bf16(const float *x, uint16_t *y, int64_t n, dpia_stream_t stream);
+
+/*
+ * Synchronous: writes to *status DPIA_ERR_TIMEOUT if a bounded device-side wait
+ * of any kernel of this library gave up since the previous poll on the
+ * current device (the kernel then returned early, leaving its output
+ * undefined), else DPIA_OK; clears the flag.
+ */
+dpia_status dpia_poll_device_status(int32_t *status);
+
 /*
  * Allocation-free dot product. The paper has no counterpart: this entry exists
  * for callers that cannot allocate device memory -- e.g. a plugin inside a

@@ -33,6 +33,11 @@ class DPIAError(RuntimeError):
         self.status = status
 
 
+class GemmStrategyC(ctypes.Structure):
+    _fields_ = [("contract", ctypes.c_int32), ("tile_m", ctypes.c_int32), ("tile_n", ctypes.c_int32),
+                ("tile_k", ctypes.c_int32), ("grid", ctypes.c_int32)]
+
+
 class ReduceStrategyC(ctypes.Structure):
     _fields_ = [
         ("split", ctypes.c_int64),
@@ -54,6 +59,7 @@ _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
 _SZ = ctypes.c_size_t
 _SP = ctypes.POINTER(ReduceStrategyC)
+_GP = ctypes.POINTER(GemmStrategyC)
 
 # name -> (restype, argtypes); kept in the order of include/dpia.h
 SIGNATURES = {
@@ -68,6 +74,10 @@ SIGNATURES = {
     "dpia_gemv_f32": (_I32, [_P, _I64, _I64, _I64, _P, _P, _SP, _P]),
     "dpia_gemv_bwd_workspace_size": (_SZ, [_I64, _I64, _I64]),
     "dpia_gemv_bwd_f32": (_I32, [_P, _I64, _I64, _I64, _P, _P, _P, _P, _I64, _I64, _P, _SZ, _P]),
+    "dpia_gemm_f32": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I64, _I64, _I64, _I32, _I32, _GP, _P]),
+    "dpia_gemm_bf16": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I64, _I64, _I64, _I32, _I32, _GP, _P]),
+    "dpia_cast_f32_bf16": (_I32, [_P, _P, _I64, _P]),
+    "dpia_poll_device_status": (_I32, [ctypes.POINTER(ctypes.c_int32)]),
     "dpia_dot_f32_noalloc": (_I32, [_P, _P, _I64, _SP, _P, _P]),
 }
 

@@ -1,0 +1,417 @@
+// BF16 GEMM on the 5th-generation tensor cores: C (f32) = op(A) op(B) with
+// bf16 operands and f32 accumulation in tensor memory.
+//
+// The same map-of-maps-of-reduce as the FP32 fold (each C_ij is a reduce over
+// k of a_ik * b_kj), but the reduce is carried by tcgen05.mma, whose internal
+// accumulation order is fixed by the hardware: results are checked against
+// FP64 by tolerance, not bit for bit.
+//
+// Structure (one CTA per SM, persistent over 128 x 256 output tiles):
+//   warp 0     -- TMA producer: cp.async.bulk.tensor loads of the A (128 x 64)
+//                 and B (256 x 64) k-slices into a 4-stage shared-memory ring,
+//                 128-byte swizzled, completion counted on mbarriers;
+//   warp 1     -- allocates 512 TMEM columns (two 128 x 256 f32 accumulators);
+//                 one thread issues tcgen05.mma (M=128, N=256, K=16) and
+//                 commits each stage back to the producer and each finished
+//                 accumulator to the epilogue;
+//   warps 2..5 -- epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//                 lanes 32*(w%4) .. +31, i.e. its 32 rows), then f32 stores.
+// The two accumulators let the epilogue of tile i overlap the MMAs of tile
+// i+1. Operands may be K-major or MN-major (transposed) independently: the
+// shared-memory descriptors select the canonical 128-byte-swizzle layout of
+// either major-ness, so the transposes of the backward pass need no copies.
+//
+// Every mbarrier wait is bounded by the global timer. A wait that runs out
+// sets the CTA's abort flag and the library's device status word
+// (dpia_poll_device_status reports it), the CTA drains what it has in flight,
+// frees its tensor memory and returns; nothing spins forever.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "../../include/dpia.h"
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace dpia {
+
+__device__ unsigned g_device_status;  // sticky DPIA_ERR_TIMEOUT flag, read by dpia_poll_device_status
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;             // 16 KiB
+constexpr int B_BYTES = BN * BK * 2;             // 32 KiB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 48 KiB
+constexpr int NUM_THREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint64_t kTimeoutNs = 2000000000ull;   // 2 s
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+
+struct Params {
+  float *C;
+  int64_t M, N, K, ldc;
+  int tiles_n, num_tiles, k_blocks;
+  int a_mn, b_mn, vec_ok;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on a phase parity; false if it timed out or the CTA aborted.
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > kTimeoutNs) {
+        *abort_flag = 1;
+        atomicExch(&g_device_status, (unsigned)DPIA_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint64_t *bar, void *dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: start address, leading/stride byte
+// offsets, descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: f32 accumulator, bf16 A and B,
+// operand major-ness, N >> 3 and M >> 4.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    gemm_bf16_tcgen05_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b,
+                             const Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+  uint64_t *empty = full + STAGES;
+  uint64_t *tfull = empty + STAGES;
+  uint64_t *tempty = tfull + 2;
+  uint64_t *drain = tempty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tma_a)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tma_b)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    uint32_t stage = 0, phase = 0;
+    int pending[STAGES] = {0, 0, 0, 0};
+    uint32_t pend_phase[STAGES] = {0, 0, 0, 0};
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
+      const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
+      for (int kb = 0; kb < p.k_blocks; ++kb) {
+        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        pending[stage] = 0;  // the previous load of this stage was consumed
+        mbar_expect_tx(&full[stage], STAGE_BYTES);
+        uint8_t *sa = smem + stage * STAGE_BYTES;
+        uint8_t *sb = sa + A_BYTES;
+        if (!p.a_mn) {
+          tma_load_2d(&tma_a, &full[stage], sa, kb * BK, tm * BM);
+        } else {
+          tma_load_2d(&tma_a, &full[stage], sa, tm * BM, kb * BK);
+          tma_load_2d(&tma_a, &full[stage], sa + 8192, tm * BM + 64, kb * BK);
+        }
+        if (!p.b_mn) {
+          tma_load_2d(&tma_b, &full[stage], sb, kb * BK, tn * BN);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) tma_load_2d(&tma_b, &full[stage], sb + j * 8192, tn * BN + 64 * j, kb * BK);
+        }
+        pending[stage] = 1;
+        pend_phase[stage] = phase;
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+    if (!ok) {
+      // drain copies still in flight before the CTA's shared memory goes away
+      for (int s = 0; s < STAGES; ++s) {
+        if (!pending[s]) continue;
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(&full[s], pend_phase[s]) && globaltimer() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    const uint32_t idesc = idesc_bf16(BM, BN, p.a_mn, p.b_mn);
+    uint32_t stage = 0, phase = 0;
+    bool ok = true;
+    int iter = 0;
+    for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x, ++iter) {
+      const int buf = iter & 1;
+      const uint32_t use = (iter >> 1) & 1;
+      if (!mbar_wait(&tempty[buf], use ^ 1, abort_flag)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+      const uint32_t d_tmem = tmem_base + buf * BN;
+      for (int kb = 0; kb < p.k_blocks; ++kb) {
+        if (!mbar_wait(&full[stage], phase, abort_flag)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t a0 = smem_u32(smem + stage * STAGE_BYTES);
+        const uint32_t b0 = a0 + A_BYTES;
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint64_t da = p.a_mn ? sdesc(a0 + k * 2048, 8192, 1024) : sdesc(a0 + k * 32, 16, 1024);
+          const uint64_t db = p.b_mn ? sdesc(b0 + k * 2048, 8192, 1024) : sdesc(b0 + k * 32, 16, 1024);
+          umma(d_tmem, da, db, idesc, (kb | k) != 0);
+        }
+        umma_commit(&empty[stage]);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (ok) umma_commit(&tfull[buf]);
+    }
+    // every MMA of this CTA has completed once this commit arrives
+    umma_commit(drain);
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    int iter = 0;
+    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++iter) {
+      const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
+      const int buf = iter & 1;
+      const uint32_t use = (iter >> 1) & 1;
+      if (!mbar_wait(&tfull[buf], use, abort_flag)) break;
+      fence_after();
+      const int64_t row = (int64_t)tm * BM + 32 * q + lane;
+      float *crow = p.C + row * p.ldc;
+      const uint32_t tbase = tmem_base + buf * BN + ((uint32_t)(32 * q) << 16);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        tmem_ld32(tbase + c, r);
+        if (c == BN - 32) {
+          fence_before();
+          mbar_arrive(&tempty[buf]);
+        }
+        if (row < p.M) {
+          const int64_t col0 = (int64_t)tn * BN + c;
+          if (p.vec_ok && col0 + 32 <= p.N) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4 *>(crow + col0 + j) =
+                  make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                              __uint_as_float(r[j + 3]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (col0 + j < p.N) crow[col0 + j] = __uint_as_float(r[j]);
+          }
+        }
+      }
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+// 2-D bf16 tensor map of a row-major matrix rows x cols (leading dimension ld
+// elements), box {box_inner (along cols), box_outer (along rows)}, 128B swizzle.
+bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_inner,
+              int box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int resident_blocks(const void *kernel, int threads);
+
+// op(A) is M x K: A stored M x K (transA = 0, K-major) or K x M (transA = 1,
+// MN-major). op(B) is K x N: B stored K x N (transB = 0, MN-major) or N x K
+// (transB = 1, K-major).
+cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,
+                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid,
+                             int vec_ok, cudaStream_t stream) {
+  static bool attr_set = false;
+  const void *kfn = reinterpret_cast<const void *>(gemm_bf16_tcgen05_kernel);
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  alignas(64) CUtensorMap ma, mb;
+  bool ok = transA ? make_map(&ma, A, K, M, lda, 64, 64) : make_map(&ma, A, M, K, lda, 64, 128);
+  ok = ok && (transB ? make_map(&mb, B, N, K, ldb, 64, 256) : make_map(&mb, B, K, N, ldb, 64, 64));
+  if (!ok) return cudaErrorInvalidValue;
+  Params p;
+  p.C = C;
+  p.M = M;
+  p.N = N;
+  p.K = K;
+  p.ldc = ldc;
+  p.tiles_n = (int)ceil_div(N, BN);
+  p.num_tiles = (int)(ceil_div(M, BM) * p.tiles_n);
+  p.k_blocks = (int)ceil_div(K, BK);
+  p.a_mn = transA ? 1 : 0;
+  p.b_mn = transB ? 0 : 1;
+  p.vec_ok = vec_ok;
+  if (grid <= 0) grid = sm_count();
+  if (grid > p.num_tiles) grid = p.num_tiles;
+  void *args[] = {&ma, &mb, &p};
+  return cudaLaunchKernel(kfn, dim3(grid), dim3(NUM_THREADS), args, SMEM_BYTES, stream);
+}
+
+cudaError_t poll_device_status(unsigned *out) {
+  unsigned zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_device_status, sizeof(unsigned));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(g_device_status, &zero, sizeof(unsigned));
+}
+
+}  // namespace dpia

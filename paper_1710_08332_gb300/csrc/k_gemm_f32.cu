@@ -1,0 +1,201 @@
+// FP32 GEMM on the CUDA cores: C = op(A) op(B) as
+//   map (lambda a. map (lambda b. fold_k (a_k * b_k)) (transpose B)) A,
+// each C_ij folded over k = 0..K-1 in order from +0, either with fmaf (the
+// contraction declared) or with a separately rounded multiply and add.
+//
+// The map over C is split into 128 x 128 tiles (a block each); inside a tile,
+// 256 threads own 8 x 8 elements each. k advances in slices of 16 staged in
+// shared memory (double-buffered, the next slice prefetched through registers
+// while the current one is consumed). Every element's fold stays one
+// sequential chain in k, so the result is bit-identical to the oracle's loop.
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace dpia {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 16, NT = 256;
+
+template <bool FMA>
+__device__ __forceinline__ float madd(float a, float b, float acc) {
+  if constexpr (FMA) return __fmaf_rn(a, b, acc);
+  else return __fadd_rn(acc, __fmul_rn(a, b));
+}
+
+struct GemmArgs {
+  const float *A, *B;
+  float *C;
+  int64_t M, N, K, lda, ldb, ldc;
+};
+
+// op(A)[m][k] and op(B)[k][n] element loads with bounds (0 outside).
+template <bool TA>
+__device__ __forceinline__ float a_at(const GemmArgs &g, int64_t m, int64_t k) {
+  if (m >= g.M || k >= g.K) return 0.0f;
+  return TA ? g.A[k * g.lda + m] : g.A[m * g.lda + k];
+}
+template <bool TB>
+__device__ __forceinline__ float b_at(const GemmArgs &g, int64_t k, int64_t n) {
+  if (k >= g.K || n >= g.N) return 0.0f;
+  return TB ? g.B[n * g.ldb + k] : g.B[k * g.ldb + n];
+}
+
+// Load the (m0, k0) A slice and (k0, n0) B slice into registers: 8 + 8 floats
+// per thread; `vec` selects 128-bit loads (interior, aligned tiles).
+template <bool TA, bool TB>
+__device__ __forceinline__ void load_slices(const GemmArgs &g, int64_t m0, int64_t n0, int64_t k0,
+                                            bool vec, float (&ra)[8], float (&rb)[8]) {
+  const int tid = threadIdx.x;
+  if (vec) {
+    if (!TA) {  // A[m][k]: thread -> row m = tid/2, k = (tid%2)*8 .. +7
+      const float *p = g.A + (m0 + tid / 2) * g.lda + k0 + (tid % 2) * 8;
+      float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p + 4));
+      ra[0] = u.x; ra[1] = u.y; ra[2] = u.z; ra[3] = u.w; ra[4] = v.x; ra[5] = v.y; ra[6] = v.z; ra[7] = v.w;
+    } else {  // A[k][m]: thread -> k = tid/16, m = (tid%16)*8 .. +7
+      const float *p = g.A + (k0 + tid / 16) * g.lda + m0 + (tid % 16) * 8;
+      float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p + 4));
+      ra[0] = u.x; ra[1] = u.y; ra[2] = u.z; ra[3] = u.w; ra[4] = v.x; ra[5] = v.y; ra[6] = v.z; ra[7] = v.w;
+    }
+    if (!TB) {  // B[k][n]: thread -> k = tid/16, n = (tid%16)*8 .. +7
+      const float *p = g.B + (k0 + tid / 16) * g.ldb + n0 + (tid % 16) * 8;
+      float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p + 4));
+      rb[0] = u.x; rb[1] = u.y; rb[2] = u.z; rb[3] = u.w; rb[4] = v.x; rb[5] = v.y; rb[6] = v.z; rb[7] = v.w;
+    } else {  // B[n][k]: thread -> n = tid/2, k = (tid%2)*8 .. +7
+      const float *p = g.B + (n0 + tid / 2) * g.ldb + k0 + (tid % 2) * 8;
+      float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p + 4));
+      rb[0] = u.x; rb[1] = u.y; rb[2] = u.z; rb[3] = u.w; rb[4] = v.x; rb[5] = v.y; rb[6] = v.z; rb[7] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (!TA) ra[j] = a_at<TA>(g, m0 + tid / 2, k0 + (tid % 2) * 8 + j);
+      else ra[j] = a_at<TA>(g, m0 + (tid % 16) * 8 + j, k0 + tid / 16);
+      if (!TB) rb[j] = b_at<TB>(g, k0 + tid / 16, n0 + (tid % 16) * 8 + j);
+      else rb[j] = b_at<TB>(g, k0 + (tid % 2) * 8 + j, n0 + tid / 2);
+    }
+  }
+}
+
+// Registers -> shared slices As[k][m], Bs[k][n].
+template <bool TA, bool TB>
+__device__ __forceinline__ void store_slices(float (*As)[BM], float (*Bs)[BN], const float (&ra)[8],
+                                             const float (&rb)[8]) {
+  const int tid = threadIdx.x;
+  if (!TA) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) As[(tid % 2) * 8 + j][tid / 2] = ra[j];
+  } else {
+    *reinterpret_cast<float4 *>(&As[tid / 16][(tid % 16) * 8]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+    *reinterpret_cast<float4 *>(&As[tid / 16][(tid % 16) * 8 + 4]) = make_float4(ra[4], ra[5], ra[6], ra[7]);
+  }
+  if (!TB) {
+    *reinterpret_cast<float4 *>(&Bs[tid / 16][(tid % 16) * 8]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    *reinterpret_cast<float4 *>(&Bs[tid / 16][(tid % 16) * 8 + 4]) = make_float4(rb[4], rb[5], rb[6], rb[7]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) Bs[(tid % 2) * 8 + j][tid / 2] = rb[j];
+  }
+}
+
+template <bool TA, bool TB, bool FMA>
+__global__ void __launch_bounds__(NT) sgemm_fold_kernel(const GemmArgs g, int vec_ok) {
+  __shared__ __align__(16) float As[2][BK][BM];
+  __shared__ __align__(16) float Bs[2][BK][BN];
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const bool interior_mn = m0 + BM <= g.M && n0 + BN <= g.N;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+
+  const int64_t nk = ceil_div(g.K, BK);
+  float ra[8], rb[8];
+  load_slices<TA, TB>(g, m0, n0, 0, vec_ok && interior_mn && BK <= g.K, ra, rb);
+  store_slices<TA, TB>(As[0], Bs[0], ra, rb);
+  __syncthreads();
+  for (int64_t kt = 0; kt < nk; ++kt) {
+    const int buf = kt & 1;
+    const int64_t k0 = kt * BK;
+    if (kt + 1 < nk) {
+      const int64_t k1 = k0 + BK;
+      load_slices<TA, TB>(g, m0, n0, k1, vec_ok && interior_mn && k1 + BK <= g.K, ra, rb);
+    }
+    const int kcount = g.K - k0 < BK ? (int)(g.K - k0) : BK;
+    if (kcount == BK) {
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+        float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+        float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+        float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = madd<FMA>(a[i], b[j], acc[i][j]);
+      }
+    } else {
+      for (int kk = 0; kk < kcount; ++kk) {  // k tail: exactly K terms, no padded ones
+        float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+        float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+        float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+        float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = madd<FMA>(a[i], b[j], acc[i][j]);
+      }
+    }
+    if (kt + 1 < nk) {
+      store_slices<TA, TB>(As[buf ^ 1], Bs[buf ^ 1], ra, rb);
+    }
+    __syncthreads();
+  }
+  // epilogue: rows ty*4 + i (i<4) and 64 + ty*4 + (i-4); columns likewise
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (m >= g.M) continue;
+    float *crow = g.C + m * g.ldc;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t n = n0 + h * 64 + tx * 4;
+      if (vec_ok && n + 4 <= g.N) {
+        *reinterpret_cast<float4 *>(crow + n) =
+            make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (n + j < g.N) crow[n + j] = acc[i][4 * h + j];
+      }
+    }
+  }
+}
+
+template <bool FMA>
+const void *pick(int ta, int tb) {
+  if (!ta && !tb) return (const void *)sgemm_fold_kernel<false, false, FMA>;
+  if (!ta && tb) return (const void *)sgemm_fold_kernel<false, true, FMA>;
+  if (ta && !tb) return (const void *)sgemm_fold_kernel<true, false, FMA>;
+  return (const void *)sgemm_fold_kernel<true, true, FMA>;
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_f32(const float *A, const float *B, float *C, int64_t M, int64_t N, int64_t K,
+                            int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int fma,
+                            int vec_ok, cudaStream_t stream) {
+  GemmArgs g{A, B, C, M, N, K, lda, ldb, ldc};
+  const void *k = fma ? pick<true>(transA, transB) : pick<false>(transA, transB);
+  dim3 grid((unsigned)ceil_div(N, BN), (unsigned)ceil_div(M, BM));
+  void *args[] = {&g, &vec_ok};
+  return cudaLaunchKernel(k, grid, dim3(NT), args, 0, stream);
+}
+
+}  // namespace dpia

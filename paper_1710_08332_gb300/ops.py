@@ -105,6 +105,36 @@ def dpia_gemv_bwd_f32(A, M, N_, lda, x, dy, dx, dA, ldda, row_split, ws, stream=
                                       _stream(stream)), "dpia_gemv_bwd_f32")
 
 
+def _gst(contract="fma", grid=0):
+    return ctypes.byref(N.GemmStrategyC(1 if contract == "fma" else 0, 0, 0, 0, int(grid)))
+
+
+def dpia_gemm_f32(A, B, C, M, N_, K, lda, ldb, ldc, transA=0, transB=0, contract="fma", stream=None):
+    _need_cuda(A, B, C)
+    N.check(N.lib().dpia_gemm_f32(_ptr(A), _ptr(B), _ptr(C), int(M), int(N_), int(K), int(lda), int(ldb),
+                                  int(ldc), int(transA), int(transB), _gst(contract), _stream(stream)),
+            "dpia_gemm_f32")
+
+
+def dpia_gemm_bf16(A, B, C, M, N_, K, lda, ldb, ldc, transA=0, transB=0, grid=0, stream=None):
+    """A, B: torch.bfloat16 (or int16/uint16 bit patterns) device tensors; C float32."""
+    _need_cuda(A, B, C)
+    N.check(N.lib().dpia_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), int(M), int(N_), int(K), int(lda), int(ldb),
+                                   int(ldc), int(transA), int(transB), _gst("fma", grid), _stream(stream)),
+            "dpia_gemm_bf16")
+
+
+def dpia_cast_f32_bf16(x, y, n, stream=None):
+    _need_cuda(x, y)
+    N.check(N.lib().dpia_cast_f32_bf16(_ptr(x), _ptr(y), int(n), _stream(stream)), "dpia_cast_f32_bf16")
+
+
+def dpia_poll_device_status() -> int:
+    v = ctypes.c_int32(-1)
+    N.check(N.lib().dpia_poll_device_status(ctypes.byref(v)), "dpia_poll_device_status")
+    return int(v.value)
+
+
 def dpia_dot_f32_noalloc(x, y, n, st, out, stream=None):
     """dpia_dot_f32 without a workspace argument, for callers that cannot
     allocate device memory: the scratch is the library's static 1 MiB device
@@ -208,3 +238,36 @@ def dot_bwd(x, y, g):
     dx, dy = torch.empty_like(x), torch.empty_like(y)
     dpia_dot_bwd_f32(x, y, g, x.numel(), dx, dy)
     return dx, dy
+
+
+def _op_shape(t, trans):
+    r, c = t.shape
+    return (c, r) if trans else (r, c)
+
+
+def gemm(A, B, transA=False, transB=False, precision="f32", contract="fma", out=None):
+    """C = op(A) op(B). precision "f32": the FP32 fold on CUDA cores (bit-exact
+    against a sequential k loop); "bf16": A and B (float32 or bfloat16) are
+    rounded to bf16 and multiplied on the tensor cores with f32 accumulation."""
+    M, K = _op_shape(A, transA)
+    K2, N_ = _op_shape(B, transB)
+    if K != K2:
+        raise ValueError(f"inner dimensions differ: {K} vs {K2}")
+    C = out if out is not None else torch.empty(M, N_, dtype=torch.float32, device=A.device)
+    if precision == "f32":
+        dpia_gemm_f32(A, B, C, M, N_, K, A.stride(0), B.stride(0), C.stride(0), int(transA), int(transB), contract)
+    elif precision == "bf16":
+        Ab, Bb = to_bf16(A), to_bf16(B)
+        dpia_gemm_bf16(Ab, Bb, C, M, N_, K, Ab.stride(0), Bb.stride(0), C.stride(0), int(transA), int(transB))
+    else:
+        raise ValueError(precision)
+    return C
+
+
+def to_bf16(x):
+    """x as bfloat16 (round to nearest even by the library's cast kernel)."""
+    if x.dtype == torch.bfloat16:
+        return x
+    y = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
+    dpia_cast_f32_bf16(x.contiguous(), y, x.numel())
+    return y

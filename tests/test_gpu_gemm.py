@@ -1,0 +1,150 @@
+"""GPU parity of the GEMM instances.
+
+FP32 fold: bit-identical to the oracle's sequential k loop (both contractions,
+all four operand layouts, ragged shapes, and sampled entries at 4096^3).
+BF16 tensor cores: the cast is bit-exact against round-to-nearest-even; the
+product is checked against FP64 of the bf16-rounded inputs (||C - C64||_F /
+||C64||_F <= 1e-4, and per element within the f32 accumulation bound) and
+against FP64 of the original FP32 inputs (<= 2e-2).
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1710_08332_gb300 as dpia
+from oracle import loopnest, naive64
+from synth import workloads as W
+from tests.helpers import assert_bits_equal, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _store(op, trans):
+    """The stored matrix whose op() is `op` (row-major)."""
+    return np.ascontiguousarray(op.T) if trans else np.ascontiguousarray(op)
+
+
+@pytest.mark.parametrize("contract", ["fma", "off"])
+@pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("M,N,K", [(256, 384, 80), (300, 257, 70), (1, 129, 3), (128, 128, 16)])
+def test_gemm_f32_bits(cuda_device, contract, tA, tB, M, N, K):
+    g = torch.Generator().manual_seed(M * 7 + N + K)
+    opA = torch.randn(M, K, generator=g).numpy()
+    opB = torch.randn(K, N, generator=g).numpy()
+    A, B = _store(opA, tA), _store(opB, tB)
+    C = torch.full((M, N), float("nan"), device="cuda")
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dpia.dpia_gemm_f32(Ad, Bd, C, M, N, K, A.shape[1], B.shape[1], N, tA, tB, contract)
+    want = loopnest.gemm_f32(A, B, bool(tA), bool(tB), contract == "fma")
+    assert_bits_equal(host(C), want, f"gemm f32 {contract} tA={tA} tB={tB} {M}x{N}x{K}")
+
+
+def test_gemm_f32_unaligned_leading_dims(cuda_device):
+    M, N, K = 70, 90, 33
+    g = torch.Generator().manual_seed(3)
+    A = torch.randn(M, K + 3, generator=g)
+    B = torch.randn(K, N + 1, generator=g)
+    C = torch.zeros(M, N + 2, device="cuda")
+    dpia.dpia_gemm_f32(A.cuda(), B.cuda(), C, M, N, K, K + 3, N + 1, N + 2, 0, 0, "fma")
+    want = loopnest.gemm_f32(A[:, :K].contiguous().numpy(), B[:, :N].contiguous().numpy(), False, False, True)
+    assert_bits_equal(host(C)[:, :N], want, "unaligned")
+
+
+@pytest.fixture(scope="module")
+def gemm_inputs():
+    A, B, dC = W.gemm("cuda")
+    return A, B, dC
+
+
+def test_gemm_f32_4096_sampled(cuda_device, gemm_inputs):
+    A, B, _ = gemm_inputs
+    n = W.GEMM_MNK
+    C = torch.empty(n, n, device="cuda")
+    dpia.dpia_gemm_f32(A, B, C, n, n, n, n, n, n, 0, 0, "fma")
+    rows = np.array([0, 1, 127, 128, 2047, 4000, 4095])
+    cols = np.array([0, 5, 255, 256, 1023, 3071, 4095])
+    hA, hB = host(A), host(B)
+    want = loopnest.gemm_f32_sample(hA, hB, False, False, True, rows, cols)
+    assert_bits_equal(host(C)[np.ix_(rows, cols)], want, "gemm f32 4096 sample")
+    ref = hA[rows].astype(np.float64) @ hB.astype(np.float64)
+    scale = np.abs(hA[rows]).astype(np.float64) @ np.abs(hB).astype(np.float64)
+    assert np.all(np.abs(host(C)[rows] - ref) <= (n + 1) * 2.0 ** -24 * scale)
+
+
+def test_cast_bf16_exact(cuda_device):
+    x = torch.randn(1 << 20, device="cuda") * 3
+    x[:6] = torch.tensor([0.0, -0.0, 1e-40, -3e38, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8])
+    y = torch.empty(x.numel() + 3, dtype=torch.bfloat16, device="cuda")[:x.numel()]
+    dpia.dpia_cast_f32_bf16(x, y, x.numel())
+    want = naive64.bf16_round(host(x))
+    assert np.array_equal(host(y.float()).astype(np.float64), want)
+    assert np.array_equal(np.signbit(host(y.float())), np.signbit(want))
+
+
+def _bf16_check(C, opA, opB, what):
+    """C against FP64 of the bf16-rounded operands (tight) and of the f32 ones (loose)."""
+    a16 = naive64.bf16_round(opA)
+    b16 = naive64.bf16_round(opB)
+    ref16 = a16 @ b16
+    rel = np.linalg.norm(C - ref16) / np.linalg.norm(ref16)
+    assert rel <= 1e-4, f"{what}: rel err vs bf16 inputs {rel}"
+    K = opA.shape[1]
+    bound = (K + 2) * 2.0 ** -23 * (np.abs(a16) @ np.abs(b16)) + 1e-30
+    worst = np.max(np.abs(C - ref16) / bound)
+    assert worst <= 1.0, f"{what}: elementwise error {worst} x the f32 accumulation bound"
+    ref = opA.astype(np.float64) @ opB.astype(np.float64)
+    rel32 = np.linalg.norm(C - ref) / np.linalg.norm(ref)
+    assert rel32 <= 2e-2, f"{what}: rel err vs f32 inputs {rel32}"
+    return rel, rel32
+
+
+@pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("M,N,K", [(256, 512, 256), (200, 300, 136), (384, 256, 64), (128, 768, 1024)])
+def test_gemm_bf16_tolerance(cuda_device, tA, tB, M, N, K):
+    g = torch.Generator().manual_seed(M + 3 * N + 7 * K + tA + 2 * tB)
+    opA = torch.randn(M, K, generator=g).numpy()
+    opB = torch.randn(K, N, generator=g).numpy()
+    A, B = _store(opA, tA), _store(opB, tB)
+    # leading dimensions padded to multiples of 8 elements (16 bytes), as TMA requires
+    lda = (A.shape[1] + 7) // 8 * 8
+    ldb = (B.shape[1] + 7) // 8 * 8
+    Ad = torch.zeros(A.shape[0], lda, device="cuda")
+    Ad[:, :A.shape[1]] = torch.from_numpy(A)
+    Bd = torch.zeros(B.shape[0], ldb, device="cuda")
+    Bd[:, :B.shape[1]] = torch.from_numpy(B)
+    Ab, Bb = dpia.to_bf16(Ad), dpia.to_bf16(Bd)
+    C = torch.full((M, N), float("nan"), device="cuda")
+    dpia.dpia_gemm_bf16(Ab, Bb, C, M, N, K, lda, ldb, N, tA, tB)
+    torch.cuda.synchronize()
+    _bf16_check(host(C).astype(np.float64), opA, opB, f"bf16 tA={tA} tB={tB} {M}x{N}x{K}")
+    assert dpia.dpia_poll_device_status() == 0
+
+
+def test_gemm_bf16_4096(cuda_device, gemm_inputs):
+    """The GEMM workload (4096^3): forward and both backward products."""
+    A, B, dC = gemm_inputs
+    n = W.GEMM_MNK
+    Ab, Bb, dCb = dpia.to_bf16(A), dpia.to_bf16(B), dpia.to_bf16(dC)
+    rows = np.arange(0, n, 97)[:40]
+    hA, hB, hdC = host(A), host(B), host(dC)
+    C = torch.empty(n, n, device="cuda")
+    dpia.dpia_gemm_bf16(Ab, Bb, C, n, n, n, n, n, n, 0, 0)            # C = A B
+    _bf16_check(host(C)[rows].astype(np.float64), hA[rows], hB, "C = A B")
+    dA = torch.empty(n, n, device="cuda")
+    dpia.dpia_gemm_bf16(dCb, Bb, dA, n, n, n, n, n, n, 0, 1)          # dA = dC B^T
+    _bf16_check(host(dA)[rows].astype(np.float64), hdC[rows], hB.T, "dA = dC B^T")
+    dB = torch.empty(n, n, device="cuda")
+    dpia.dpia_gemm_bf16(Ab, dCb, dB, n, n, n, n, n, n, 1, 0)          # dB = A^T dC
+    _bf16_check(host(dB)[rows].astype(np.float64), hA.T[rows], hdC, "dB = A^T dC")
+    assert dpia.dpia_poll_device_status() == 0
+
+
+def test_gemm_validation(cuda_device):
+    A = torch.zeros(64, 64, dtype=torch.bfloat16, device="cuda")
+    C = torch.zeros(64, 64, device="cuda")
+    with pytest.raises(dpia.DPIAError, match="ALIGN"):
+        dpia.dpia_gemm_bf16(A, A, C, 60, 60, 60, 60, 64, 64, 0, 0)  # lda not a multiple of 8
+    with pytest.raises(dpia.DPIAError, match="ALIAS"):
+        dpia.dpia_gemm_f32(C, C, C, 64, 64, 64, 64, 64, 64, 0, 0)
+    with pytest.raises(dpia.DPIAError, match="SHAPE"):
+        dpia.dpia_gemm_f32(C, C, torch.zeros(4, device="cuda"), 64, 64, 64, 32, 64, 64, 0, 0)
