@@ -235,6 +235,15 @@ def profile_case(args):
         fn = {"dot": lambda: dpia.dpia_dot_f32(x, y, n, st, out, ws),
               "asum": lambda: dpia.dpia_asum_f32(x, n, st, out, ws),
               "scal": lambda: dpia.dpia_scal_f32(W.SCAL_A, x, ys, n, 4)}[args.profile]
+    elif args.profile == "gemm":
+        m = args.n
+        A, B, _ = W.gemm(dev, M=m, N=m, K=m)
+        Ab, Bb = dpia.to_bf16(A), dpia.to_bf16(B)
+        C = torch.empty(m, m, device=dev)
+
+        def fn():
+            dpia.dpia_gemm_bf16(Ab, Bb, C, m, m, m, m, m, m, 0, 0)
+            dpia.dpia_gemm_f32(A, B, C, m, m, m, m, m, m, 0, 0, "fma")
     else:
         raise SystemExit(f"unknown profile case {args.profile}")
     for _ in range(1 + args.reps):
@@ -244,7 +253,7 @@ def profile_case(args):
     return 0
 
 
-PROFILE_CASES = {"dot", "asum", "scal"}
+PROFILE_CASES = {"dot", "asum", "scal", "gemm"}
 
 
 def bandwidth_workload(args, device, dist):

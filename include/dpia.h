@@ -220,8 +220,10 @@ enum { DPIA_CONTRACT_OFF = 0, DPIA_CONTRACT_FMA = 1 };
  * separately rounded multiply and add; FMA: one fused multiply-add, the
  * contraction declared explicitly -- the paper's num is abstract, so the
  * rounding of a step is part of the strategy). tile_m/n/k: 0 for the
- * implemented tiles (FP32: 128 x 128 x 16; BF16: 128 x 256 x 64) or exactly
- * those values. grid: CTAs of the persistent BF16 kernel (0 = one per SM).
+ * implemented tiles or exactly those values -- FP32: 128 x 128 x 16; BF16:
+ * 256 x tile_n x 64 with tile_n in {128, 160, 192, 224, 256} (0 = the width
+ * whose tiles fill the fewest waves of SMs). grid: CTAs of the persistent
+ * BF16 kernel (0 = one per SM).
  */
 typedef struct {
   int32_t contract;

@@ -12,8 +12,8 @@ cudaError_t launch_gemm_f32(const float *A, const float *B, float *C, int64_t M,
                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int fma, int vec_ok,
                             cudaStream_t stream);
 cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,
-                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int vec_ok,
-                             cudaStream_t stream);
+                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_n,
+                             int vec_ok, cudaStream_t stream);
 cudaError_t poll_device_status(unsigned *out);
 int resident_blocks(const void *kernel, int threads);
 }  // namespace dpia
@@ -141,8 +141,9 @@ dpia_status dpia_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64
     set_last_error("%s: strategy is NULL", fn);
     return DPIA_ERR_NULL;
   }
-  if ((st->tile_m && st->tile_m != 128) || (st->tile_n && st->tile_n != 256) || (st->tile_k && st->tile_k != 64)) {
-    set_last_error("%s: only 128 x 256 x 64 tiles are implemented for tcgen05", fn);
+  if ((st->tile_m && st->tile_m != 256) || (st->tile_k && st->tile_k != 64) ||
+      (st->tile_n && (st->tile_n < 128 || st->tile_n > 256 || st->tile_n % 32 != 0))) {
+    set_last_error("%s: tiles are 256 x tile_n x 64 with tile_n in {128, 160, ..., 256} (0 = chosen per shape)", fn);
     return DPIA_ERR_UNSUPPORTED;
   }
   if (st->grid < 0) {
@@ -163,7 +164,8 @@ dpia_status dpia_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64
     return DPIA_ERR_SHAPE;
   }
   const int vec_ok = aligned(C, 16) && ldc % 4 == 0;
-  return cuda_status(launch_gemm_bf16(A, B, C, M, N, K, lda, ldb, ldc, transA, transB, st->grid, vec_ok, s), fn);
+  return cuda_status(
+      launch_gemm_bf16(A, B, C, M, N, K, lda, ldb, ldc, transA, transB, st->grid, st->tile_n, vec_ok, s), fn);
 }
 
 dpia_status dpia_cast_f32_bf16(const float *x, uint16_t *y, int64_t n, dpia_stream_t stream) {

@@ -6,18 +6,26 @@
 // accumulation order is fixed by the hardware: results are checked against
 // FP64 by tolerance, not bit for bit.
 //
-// Structure (one CTA per SM, persistent over 128 x 256 output tiles):
-//   warp 0     -- TMA producer: cp.async.bulk.tensor loads of the A (128 x 64)
-//                 and B (256 x 64) k-slices into a 4-stage shared-memory ring,
+// Structure (one CTA per SM, persistent over 256 x BN output tiles):
+//   warp 0     -- TMA producer: cp.async.bulk.tensor loads of the A (256 x 64)
+//                 and B (BN x 64) k-slices into a 3-stage shared-memory ring,
 //                 128-byte swizzled, completion counted on mbarriers;
-//   warp 1     -- allocates 512 TMEM columns (two 128 x 256 f32 accumulators);
-//                 one thread issues tcgen05.mma (M=128, N=256, K=16) and
-//                 commits each stage back to the producer and each finished
-//                 accumulator to the epilogue;
-//   warps 2..5 -- epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
-//                 lanes 32*(w%4) .. +31, i.e. its 32 rows), then f32 stores.
-// The two accumulators let the epilogue of tile i overlap the MMAs of tile
-// i+1. Operands may be K-major or MN-major (transposed) independently: the
+//   warp 1     -- allocates 512 TMEM columns (two 128 x BN f32 accumulators,
+//                 rows 0..127 and 128..255 of the tile); one thread issues two
+//                 tcgen05.mma (M=128, N=BN, K=16) per k step, both reading the
+//                 same B slice, and commits each stage back to the producer
+//                 and each finished tile to the epilogue;
+//   warps 2..9 -- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 of
+//                 accumulator (w-2)/4 with tcgen05.ld, then f32 stores.
+//                 (Sixteen epilogue warps, two per lane quarter and
+//                 accumulator, measured no faster at 4096^3.)
+// Two M=128 products per B slice halve the operand bytes per flop against a
+// 128-row tile. BN (<= 256, a multiple of 32) is chosen per shape so that the
+// tiles fill whole waves of SMs. The producer keeps prefetching the next tile
+// while the epilogue drains TMEM. (Six 32 KiB stages of 32-wide k-slices were
+// measured slower than three 64 KiB stages: the per-request cost of the
+// smaller TMA loads outweighs the deeper pipeline.)
+// Operands may be K-major or MN-major (transposed) independently: the
 // shared-memory descriptors select the canonical 128-byte-swizzle layout of
 // either major-ness, so the transposes of the backward pass need no copies.
 //
@@ -38,11 +46,20 @@ __device__ unsigned g_device_status;  // sticky DPIA_ERR_TIMEOUT flag, read by d
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;             // 16 KiB
-constexpr int B_BYTES = BN * BK * 2;             // 32 KiB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 48 KiB
-constexpr int NUM_THREADS = 192;
+constexpr int BM = 256, BN_MAX = 256, BK = 64, STAGES = 3;
+constexpr int A_BYTES = BM * BK * 2;             // 32 KiB
+constexpr int B_BYTES = BN_MAX * BK * 2;         // 32 KiB (room for the widest B slice)
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 64 KiB
+// Shared-memory layouts of one k-slice (BK = 64 bf16), 128-byte swizzle:
+//   K-major operand : rows of 128 bytes (the 64 k values), 8-row atoms of
+//                     1024 bytes (SBO 1024), k step of 16 = +32 bytes;
+//   MN-major operand: TMA boxes of 64 (m or n) x 64 (k), rows of 128 bytes,
+//                     8-row atoms of 1024 bytes (SBO 1024), boxes 8192 bytes
+//                     apart (LBO 8192), k step of 16 = +2048 bytes.
+constexpr uint32_t KMAJ_SBO = 1024, MN_LBO = 8192, MN_SBO = 1024;
+constexpr uint32_t LAYOUT_SW128 = 2;
+constexpr int NUM_EPI_WARPS = 8;
+constexpr int NUM_THREADS = 64 + 32 * NUM_EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint64_t kTimeoutNs = 2000000000ull;   // 2 s
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
@@ -50,8 +67,9 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 struct Params {
   float *C;
   int64_t M, N, K, ldc;
-  int tiles_n, num_tiles, k_blocks;
+  int BN, tiles_n, num_tiles, k_blocks;
   int a_mn, b_mn, vec_ok;
+  uint32_t stage_tx;  // bytes the TMA loads of one stage deliver
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -117,15 +135,22 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: start address, leading/stride byte
-// offsets, descriptor version 1, 128-byte swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// offsets, descriptor version 1, swizzle layout.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
   d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)layout << 61;
   return d;
+}
+
+// Descriptor of rows [128h, 128h+128) (A) or of the whole slice (B, h = 0)
+// for the k-th 16-wide step of a stage.
+__device__ __forceinline__ uint64_t operand_desc(uint32_t base, int mn_major, int h, int k) {
+  return mn_major ? sdesc(base + h * (2 * MN_LBO) + k * 2048, MN_LBO, MN_SBO, LAYOUT_SW128)
+                  : sdesc(base + h * (128 * BK * 2) + k * 32, 16, KMAJ_SBO, LAYOUT_SW128);
 }
 
 // Instruction descriptor of kind::f16: f32 accumulator, bf16 A and B,
@@ -171,21 +196,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
   uint64_t *empty = full + STAGES;
   uint64_t *tfull = empty + STAGES;
-  uint64_t *tempty = tfull + 2;
-  uint64_t *drain = tempty + 2;
+  uint64_t *tempty = tfull + 1;
+  uint64_t *drain = tempty + 1;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int BN = p.BN;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
-    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 32 * NUM_EPI_WARPS);
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -206,8 +230,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
     uint32_t stage = 0, phase = 0;
-    int pending[STAGES] = {0, 0, 0, 0};
-    uint32_t pend_phase[STAGES] = {0, 0, 0, 0};
+    int pending[STAGES] = {0, 0, 0};
+    uint32_t pend_phase[STAGES] = {0, 0, 0};
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
       const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
@@ -217,20 +241,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           break;
         }
         pending[stage] = 0;  // the previous load of this stage was consumed
-        mbar_expect_tx(&full[stage], STAGE_BYTES);
+        mbar_expect_tx(&full[stage], p.stage_tx);
         uint8_t *sa = smem + stage * STAGE_BYTES;
         uint8_t *sb = sa + A_BYTES;
         if (!p.a_mn) {
           tma_load_2d(&tma_a, &full[stage], sa, kb * BK, tm * BM);
         } else {
-          tma_load_2d(&tma_a, &full[stage], sa, tm * BM, kb * BK);
-          tma_load_2d(&tma_a, &full[stage], sa + 8192, tm * BM + 64, kb * BK);
+#pragma unroll
+          for (int j = 0; j < BM / 64; ++j) tma_load_2d(&tma_a, &full[stage], sa + j * MN_LBO, tm * BM + 64 * j, kb * BK);
         }
         if (!p.b_mn) {
           tma_load_2d(&tma_b, &full[stage], sb, kb * BK, tn * BN);
         } else {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) tma_load_2d(&tma_b, &full[stage], sb + j * 8192, tn * BN + 64 * j, kb * BK);
+          for (int j = 0; j * 64 < BN; ++j) tma_load_2d(&tma_b, &full[stage], sb + j * MN_LBO, tn * BN + 64 * j, kb * BK);
         }
         pending[stage] = 1;
         pend_phase[stage] = phase;
@@ -251,19 +274,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
-    const uint32_t idesc = idesc_bf16(BM, BN, p.a_mn, p.b_mn);
+    const uint32_t idesc = idesc_bf16(128, BN, p.a_mn, p.b_mn);
     uint32_t stage = 0, phase = 0;
     bool ok = true;
     int iter = 0;
     for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x, ++iter) {
-      const int buf = iter & 1;
-      const uint32_t use = (iter >> 1) & 1;
-      if (!mbar_wait(&tempty[buf], use ^ 1, abort_flag)) {
+      if (!mbar_wait(tempty, (iter & 1) ^ 1, abort_flag)) {
         ok = false;
         break;
       }
       fence_after();
-      const uint32_t d_tmem = tmem_base + buf * BN;
       for (int kb = 0; kb < p.k_blocks; ++kb) {
         if (!mbar_wait(&full[stage], phase, abort_flag)) {
           ok = false;
@@ -274,9 +294,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const uint32_t b0 = a0 + A_BYTES;
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
-          const uint64_t da = p.a_mn ? sdesc(a0 + k * 2048, 8192, 1024) : sdesc(a0 + k * 32, 16, 1024);
-          const uint64_t db = p.b_mn ? sdesc(b0 + k * 2048, 8192, 1024) : sdesc(b0 + k * 32, 16, 1024);
-          umma(d_tmem, da, db, idesc, (kb | k) != 0);
+          const uint64_t db = operand_desc(b0, p.b_mn, 0, k);
+#pragma unroll
+          for (int h = 0; h < 2; ++h)  // rows 128*h .. 128*h+127 of the tile
+            umma(tmem_base + h * 256, operand_desc(a0, p.a_mn, h, k), db, idesc, (kb | k) != 0);
         }
         umma_commit(&empty[stage]);
         if (++stage == STAGES) {
@@ -284,7 +305,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           phase ^= 1;
         }
       }
-      if (ok) umma_commit(&tfull[buf]);
+      if (ok) umma_commit(tfull);
     }
     // every MMA of this CTA has completed once this commit arrives
     umma_commit(drain);
@@ -293,24 +314,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   } else if (warp >= 2) {
     // ------------------------------------------------------------ epilogue
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int q = warp & 3;         // TMEM lane quarter this warp may access
+    const int h = (warp - 2) >> 2;  // accumulator (row half of the tile)
     int iter = 0;
     for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++iter) {
       const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
-      const int buf = iter & 1;
-      const uint32_t use = (iter >> 1) & 1;
-      if (!mbar_wait(&tfull[buf], use, abort_flag)) break;
+      if (!mbar_wait(tfull, iter & 1, abort_flag)) break;
       fence_after();
-      const int64_t row = (int64_t)tm * BM + 32 * q + lane;
+      const int64_t row = (int64_t)tm * BM + 128 * h + 32 * q + lane;
       float *crow = p.C + row * p.ldc;
-      const uint32_t tbase = tmem_base + buf * BN + ((uint32_t)(32 * q) << 16);
+      const uint32_t tbase = tmem_base + h * 256 + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
       for (int c = 0; c < BN; c += 32) {
         uint32_t r[32];
         tmem_ld32(tbase + c, r);
-        if (c == BN - 32) {
+        if (c + 32 >= BN) {
           fence_before();
-          mbar_arrive(&tempty[buf]);
+          mbar_arrive(tempty);
         }
         if (row < p.M) {
           const int64_t col0 = (int64_t)tn * BN + c;
@@ -353,7 +373,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 2-D bf16 tensor map of a row-major matrix rows x cols (leading dimension ld
-// elements), box {box_inner (along cols), box_outer (along rows)}, 128B swizzle.
+// elements), box {box_inner (along cols), box_outer (along rows)}; the swizzle
+// span equals the box's inner extent in bytes (64 or 128).
 bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_inner,
               int box_outer) {
   auto fn = encode_fn();
@@ -363,7 +384,9 @@ bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, in
   cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  box_inner * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -375,8 +398,28 @@ int resident_blocks(const void *kernel, int threads);
 // op(A) is M x K: A stored M x K (transA = 0, K-major) or K x M (transA = 1,
 // MN-major). op(B) is K x N: B stored K x N (transB = 0, MN-major) or N x K
 // (transB = 1, K-major).
+// Tile width: the BN in {256, 224, ..., 128} whose tiles fill the fewest
+// waves of CTAs, weighted by the tile's cost (proportional to BN).
+int pick_bn(int64_t M, int64_t N, int ctas) {
+  int best = 256;
+  int64_t best_cost = -1;
+  for (int bn = 256; bn >= 128; bn -= 32) {
+    const int64_t tiles = ceil_div(M, BM) * ceil_div(N, bn);
+    const int64_t waves = ceil_div(tiles, ctas);
+    const int64_t cost = waves * bn;
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = bn;
+    }
+  }
+  return best;
+}
+
+// op(A) is M x K: A stored M x K (transA = 0, K-major) or K x M (transA = 1,
+// MN-major). op(B) is K x N: B stored K x N (transB = 0, MN-major) or N x K
+// (transB = 1, K-major). tile_n = 0 picks BN per shape.
 cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,
-                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid,
+                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_n,
                              int vec_ok, cudaStream_t stream) {
   static bool attr_set = false;
   const void *kfn = reinterpret_cast<const void *>(gemm_bf16_tcgen05_kernel);
@@ -385,9 +428,11 @@ cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  const int ctas = grid > 0 ? grid : sm_count();
+  const int BN = tile_n > 0 ? tile_n : pick_bn(M, N, ctas);
   alignas(64) CUtensorMap ma, mb;
-  bool ok = transA ? make_map(&ma, A, K, M, lda, 64, 64) : make_map(&ma, A, M, K, lda, 64, 128);
-  ok = ok && (transB ? make_map(&mb, B, N, K, ldb, 64, 256) : make_map(&mb, B, K, N, ldb, 64, 64));
+  bool ok = transA ? make_map(&ma, A, K, M, lda, 64, BK) : make_map(&ma, A, M, K, lda, BK, BM);
+  ok = ok && (transB ? make_map(&mb, B, N, K, ldb, BK, BN) : make_map(&mb, B, K, N, ldb, 64, BK));
   if (!ok) return cudaErrorInvalidValue;
   Params p;
   p.C = C;
@@ -395,16 +440,18 @@ cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int
   p.N = N;
   p.K = K;
   p.ldc = ldc;
+  p.BN = BN;
   p.tiles_n = (int)ceil_div(N, BN);
   p.num_tiles = (int)(ceil_div(M, BM) * p.tiles_n);
   p.k_blocks = (int)ceil_div(K, BK);
   p.a_mn = transA ? 1 : 0;
   p.b_mn = transB ? 0 : 1;
   p.vec_ok = vec_ok;
-  if (grid <= 0) grid = sm_count();
-  if (grid > p.num_tiles) grid = p.num_tiles;
+  const uint32_t b_tx = p.b_mn ? (uint32_t)ceil_div(BN, 64) * (64u * BK * 2u) : (uint32_t)BN * BK * 2u;
+  p.stage_tx = (uint32_t)A_BYTES + b_tx;
+  int g = ctas < p.num_tiles ? ctas : p.num_tiles;
   void *args[] = {&ma, &mb, &p};
-  return cudaLaunchKernel(kfn, dim3(grid), dim3(NUM_THREADS), args, SMEM_BYTES, stream);
+  return cudaLaunchKernel(kfn, dim3(g), dim3(NUM_THREADS), args, SMEM_BYTES, stream);
 }
 
 cudaError_t poll_device_status(unsigned *out) {

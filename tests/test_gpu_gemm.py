@@ -98,9 +98,11 @@ def _bf16_check(C, opA, opB, what):
     return rel, rel32
 
 
+@pytest.mark.parametrize("tile_n", [0, 128, 224, 256])
 @pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0), (1, 1)])
-@pytest.mark.parametrize("M,N,K", [(256, 512, 256), (200, 300, 136), (384, 256, 64), (128, 768, 1024)])
-def test_gemm_bf16_tolerance(cuda_device, tA, tB, M, N, K):
+@pytest.mark.parametrize("M,N,K", [(256, 512, 256), (200, 300, 136), (384, 256, 64), (128, 768, 1024),
+                                   (520, 900, 200)])
+def test_gemm_bf16_tolerance(cuda_device, tA, tB, M, N, K, tile_n):
     g = torch.Generator().manual_seed(M + 3 * N + 7 * K + tA + 2 * tB)
     opA = torch.randn(M, K, generator=g).numpy()
     opB = torch.randn(K, N, generator=g).numpy()
@@ -114,9 +116,9 @@ def test_gemm_bf16_tolerance(cuda_device, tA, tB, M, N, K):
     Bd[:, :B.shape[1]] = torch.from_numpy(B)
     Ab, Bb = dpia.to_bf16(Ad), dpia.to_bf16(Bd)
     C = torch.full((M, N), float("nan"), device="cuda")
-    dpia.dpia_gemm_bf16(Ab, Bb, C, M, N, K, lda, ldb, N, tA, tB)
+    dpia.dpia_gemm_bf16(Ab, Bb, C, M, N, K, lda, ldb, N, tA, tB, tile_n=tile_n)
     torch.cuda.synchronize()
-    _bf16_check(host(C).astype(np.float64), opA, opB, f"bf16 tA={tA} tB={tB} {M}x{N}x{K}")
+    _bf16_check(host(C).astype(np.float64), opA, opB, f"bf16 tA={tA} tB={tB} {M}x{N}x{K} tile_n={tile_n}")
     assert dpia.dpia_poll_device_status() == 0
 
 
