@@ -362,6 +362,248 @@ def bandwidth_workload(args, device, dist):
     return line
 
 
+class L2Flush:
+    """Reads a buffer larger than L2 (256 MiB) between timed steps, leaving L2
+    full of clean lines (a write would leave dirty lines for the next kernel
+    to write back)."""
+
+    def __init__(self, device):
+        import torch
+
+        self.buf = torch.ones(64 << 20, dtype=torch.float32, device=device)
+
+    def __call__(self):
+        self.buf.sum()
+
+
+def timed_steps(args, device, dist, names, step, flush=None):
+    """W warm-up steps, then K timed steps with CUDA events around every kernel
+    call (flush, if given, runs before each step outside the events). Returns
+    (per-kernel avg ms, per-step kernel ms max over ranks, clocks)."""
+    import torch
+
+    stream = torch.cuda.current_stream(device)
+    clocks = ClockSampler(device.index)
+    clocks.start()
+    for _ in range(args.warmup):
+        if flush:
+            flush()
+        step(None)
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    tl = Timeline(names, stream)
+    for _ in range(args.steps):
+        if flush:
+            flush()
+        step(tl)
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    clk = clocks.stop()
+    per = {n: tl.avg_ms(n) for n in names}
+    step_ms = reduce_max(dist, sum(per.values()), device if dist and dist.get_backend() == "nccl" else None)
+    return per, step_ms, clk
+
+
+def _line(args, dist, metric_value, unit, step_ms, dtype, config, kernels, roofline, clk, launches, extra=None):
+    world = dist.get_world_size() if dist else 1
+    d = {"metric": METRIC, "value": metric_value, "unit": unit, "n_gpus": world, "steps": args.steps,
+         "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
+         "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config, "kernels": kernels,
+         "roofline": roofline, "gpu_launches": launches, "clocks": clk}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def dot_workload(args, device, dist):
+    """n = 2^20 dot, split 8192 (128 chunks), block per chunk, sequential second
+    level over the 128 partials; f32 and int32. The inputs (8 MiB) fit in L2,
+    so L2 is flushed before every step, outside the kernel events."""
+    import torch
+
+    import paper_1710_08332_gb300 as dpia
+    from synth import workloads as W
+
+    x, y = W.dot_f32(device)
+    xi, yi = W.dot_i32(device)
+    n = x.numel()
+    st = dpia.ReduceStrategy(split=W.DOT_SPLIT, threads=256, vec=4)
+    ws = torch.zeros(dpia.dpia_dot_workspace_size(n, st), dtype=torch.uint8, device=device)
+    wsi = torch.zeros_like(ws)
+    out = torch.empty(1, device=device)
+    outi = torch.empty(1, dtype=torch.int64, device=device)
+
+    def step(tl):
+        calls = (("dot_f32", lambda: dpia.dpia_dot_f32(x, y, n, st, out, ws)),
+                 ("dot_i32", lambda: dpia.dpia_dot_i32(xi, yi, n, st, outi, wsi)))
+        for name, fn in calls:
+            fn() if tl is None else tl.call(name, fn)
+
+    per, step_ms, clk = timed_steps(args, device, dist, ["dot_f32", "dot_i32"], step, L2Flush(device))
+    hbm = peaks()[0]
+    b = 8 * n
+    kern = {k: {"avg_us": round(v * 1e3, 2), "algorithmic_bytes": b, "GB_s": round(b / v / 1e6, 1)}
+            for k, v in per.items()}
+    achieved = b / per["dot_f32"] / 1e6
+    world = dist.get_world_size() if dist else 1
+    roof = {"bound": "hbm", "kernel": "reduce_kernel<DotF32,SumF32,V=4,Block> (dpia_dot_f32)",
+            "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+            "traffic": None, "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": b,
+            "note": "8 MiB per launch: launch latency and the 128-partial sequential second level dominate"}
+    cfg = {"workload": "dot f32 and int32, n=2^20, U[-1,1) / U{-100..100} seed 0, split 8192 (128 chunks), "
+                       "block per chunk, sequential second level", "n": n, "strategy": st.as_dict(),
+           "l2": "flushed before every step (256 MiB read), outside the kernel events"}
+    return _line(args, dist, round(world * 2 * b / (step_ms / 1e3) / 1e9, 1), "GB/s", step_ms, "f32",
+                 cfg, kern, roof, clk, 2 * args.steps)
+
+
+def gemv_workload(args, device, dist):
+    """GEMV 8192 x 8192: forward y = A x, backward dx = A^T dy and dA = dy x^T."""
+    import torch
+
+    import paper_1710_08332_gb300 as dpia
+    from synth import workloads as W
+
+    A, x, dy = W.gemv(device)
+    M, N = A.shape
+    st = dpia.ReduceStrategy(split=N, threads=128, vec=4)  # a block of 128 per row (best of the GEMV sweep)
+    rs = 256
+    y = torch.empty(M, device=device)
+    dx = torch.empty(N, device=device)
+    dA = torch.empty(M, N, device=device)
+    ws = torch.zeros(dpia.dpia_gemv_bwd_workspace_size(M, N, rs), dtype=torch.uint8, device=device)
+
+    def step(tl):
+        calls = (("gemv_fwd", lambda: dpia.dpia_gemv_f32(A, M, N, N, x, y, st)),
+                 ("gemv_bwd_dx", lambda: dpia.dpia_gemv_bwd_f32(A, M, N, N, x, dy, dx, None, N, rs, ws)),
+                 ("gemv_bwd_dA", lambda: dpia.dpia_gemv_bwd_f32(A, M, N, N, x, dy, None, dA, N, rs, ws)))
+        for name, fn in calls:
+            fn() if tl is None else tl.call(name, fn)
+
+    per, step_ms, clk = timed_steps(args, device, dist, ["gemv_fwd", "gemv_bwd_dx", "gemv_bwd_dA"], step)
+    hbm = peaks()[0]
+    bytes_ = {"gemv_fwd": 4 * M * N + 4 * N + 4 * M,
+              "gemv_bwd_dx": 4 * M * N + 4 * M + 4 * N,
+              "gemv_bwd_dA": 4 * M * N + 4 * M + 4 * N}
+    kern = {k: {"avg_us": round(v * 1e3, 2), "algorithmic_bytes": bytes_[k], "GB_s": round(bytes_[k] / v / 1e6, 1)}
+            for k, v in per.items()}
+    achieved = bytes_["gemv_fwd"] / per["gemv_fwd"] / 1e6
+    world = dist.get_world_size() if dist else 1
+    roof = {"bound": "hbm", "kernel": "gemv_kernel<SumF32,V=4,Block> (dpia_gemv_f32)", "achieved": round(achieved, 1),
+            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+            "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": bytes_["gemv_fwd"]}
+    cfg = {"workload": "GEMV 8192x8192 f32, A ~ N(0,1/8192), x, dy ~ U[-1,1) seed 2: forward + backward (dx, dA)",
+           "M": M, "N": N, "strategy": st.as_dict(), "row_split": rs,
+           "l2": "inputs larger than L2 (A is 256 MiB)"}
+    total = sum(bytes_.values())
+    return _line(args, dist, round(world * total / (step_ms / 1e3) / 1e9, 1), "GB/s", step_ms, "f32", cfg, kern,
+                 roof, clk, 3 * args.steps)
+
+
+def gemm_workload(args, device, dist):
+    """GEMM 4096^3: BF16 tensor-core forward C = A B and backward dA = dC B^T,
+    dB = A^T dC (f32 accumulate), plus the FP32 CUDA-core fold forward."""
+    import torch
+
+    import paper_1710_08332_gb300 as dpia
+    from synth import workloads as W
+
+    A, B, dC = W.gemm(device)
+    n = A.shape[0]
+    Ab, Bb, dCb = dpia.to_bf16(A), dpia.to_bf16(B), dpia.to_bf16(dC)
+    C = torch.empty(n, n, device=device)
+    gA = torch.empty(n, n, device=device)
+    gB = torch.empty(n, n, device=device)
+    Cf = torch.empty(n, n, device=device)
+
+    def step(tl):
+        calls = (("bf16_fwd", lambda: dpia.dpia_gemm_bf16(Ab, Bb, C, n, n, n, n, n, n, 0, 0)),
+                 ("bf16_bwd_dA", lambda: dpia.dpia_gemm_bf16(dCb, Bb, gA, n, n, n, n, n, n, 0, 1)),
+                 ("bf16_bwd_dB", lambda: dpia.dpia_gemm_bf16(Ab, dCb, gB, n, n, n, n, n, n, 1, 0)))
+        for name, fn in calls:
+            fn() if tl is None else tl.call(name, fn)
+
+    per, step_ms, clk = timed_steps(args, device, dist, ["bf16_fwd", "bf16_bwd_dA", "bf16_bwd_dB"], step,
+                                    L2Flush(device))
+    fl = 2 * n ** 3
+    _, bf16_peak, bf16_sust, src = peaks()
+    kern = {k: {"avg_us": round(v * 1e3, 2), "flops": fl, "TFLOP_s": round(fl / v / 1e9, 1)} for k, v in per.items()}
+    # FP32 fold forward, a few launches (it runs on the FMA pipes, not the tensor cores)
+    f32_ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dpia.dpia_gemm_f32(A, B, Cf, n, n, n, n, n, n, 0, 0, "fma")
+        e1.record()
+        e1.synchronize()
+        f32_ms.append(e0.elapsed_time(e1))
+    f32 = min(f32_ms)
+    sm_mhz = (clk or {}).get("sm_mhz") or 1900.0
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    fma_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    kern["f32_fold_fwd"] = {"avg_us": round(f32 * 1e3, 1), "flops": fl, "TFLOP_s": round(fl / f32 / 1e9, 2),
+                            "bound": "alu", "peak_TFLOP_s": round(fma_peak, 1),
+                            "peak_source": f"{sms} SMs x 128 FP32 FMA lanes x 2 flops x {sm_mhz:.0f} MHz (median "
+                                           "clock under load)", "frac": round(fl / f32 / 1e9 / fma_peak, 4)}
+    dominant = max(per, key=per.get)  # the launch with the largest time share
+    achieved = fl / per[dominant] / 1e9
+    world = dist.get_world_size() if dist else 1
+    total = 3 * fl
+    layouts = {"bf16_fwd": "C = A B, B MN-major", "bf16_bwd_dA": "dA = dC B^T, both K-major",
+               "bf16_bwd_dB": "dB = A^T dC, both MN-major"}
+    roof = {"bound": "tensor", "kernel": f"gemm_bf16_tcgen05_kernel ({dominant}: {layouts[dominant]})",
+            "achieved": round(achieved, 1), "peak": bf16_peak, "unit": "TFLOP/s", "frac": round(achieved / bf16_peak, 4),
+            "traffic": None, "peak_source": f"{src} bf16_tflops (cuBLAS burst)",
+            "frac_per_launch": {k: round(fl / v / 1e9 / bf16_peak, 4) for k, v in per.items()}}
+    cfg = {"workload": "GEMM 4096^3, A, B, dC ~ N(0,1) seed 4, BF16 inputs (RNE cast outside the timed kernels), "
+                       "f32 accumulate: forward and backward; FP32 fold forward timed separately",
+           "M": n, "N": n, "K": n, "l2": "flushed before every step (256 MiB read), outside the kernel events"}
+    return _line(args, dist, round(world * total / (step_ms / 1e3) / 1e12, 1), "TFLOP/s", step_ms, "bf16", cfg,
+                 kern, roof, clk, 3 * args.steps)
+
+
+def cpu_baseline_for(workload):
+    """Oracle timings for the secondary workloads (one thread, bounded samples)."""
+    import numpy as np
+
+    from oracle import loopnest
+    from oracle import patterns as P
+    from synth import workloads as W
+
+    t0 = time.perf_counter()
+    if workload == "dot":
+        x, y = W.dot_f32("cpu")
+        reps = 0
+        while time.perf_counter() - t0 < 5.0:
+            loopnest.dot_f32(x.numpy(), y.numpy(), P.Strategy(s=8192, T=256, V=4))
+            reps += 1
+        dt = time.perf_counter() - t0
+        return {"value": round(reps * 8 * x.numel() / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                "sample": f"oracle dot (same strategy) on the full n=2^20 input, {reps} reps, {dt:.1f} s"}
+    if workload == "gemv":
+        A, x, dy = W.gemv("cpu", M=1024)
+        hA, hx, hdy = A.numpy(), x.numpy(), dy.numpy()
+        reps = 0
+        while time.perf_counter() - t0 < 10.0:
+            loopnest.gemv_f32(hA, hx, P.Strategy(s=8192, T=256, V=4))
+            loopnest.gemv_bwd_dx_f32(hA, hdy, 64)
+            loopnest.gemv_bwd_dA_f32(hx, hdy)
+            reps += 1
+        dt = time.perf_counter() - t0
+        b = 3 * 4 * hA.size
+        return {"value": round(reps * b / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                "sample": f"oracle GEMV forward + dx + dA on 1024 of the 8192 rows, {reps} reps, {dt:.1f} s"}
+    if workload == "gemm":
+        A, B, _ = W.gemm("cpu", M=64)
+        rows = np.arange(64)
+        cols = np.arange(4096)
+        loopnest.gemm_f32_sample(A.numpy(), B.numpy(), False, False, True, rows, cols)
+        dt = time.perf_counter() - t0
+        return {"value": round(2 * 64 * 4096 * 4096 / dt / 1e12, 5), "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                "sample": f"oracle FP32 fold (FMA) for 64 of the 4096 rows of C = A B, {dt:.1f} s"}
+    return None
+
+
 def e2e_bandwidth(args, device, dist, st_dot, st_asum, hx, hy, step_bytes):
     """The same step through the public API with pinned host inputs and a host
     read of the results, copies inside the timed region."""
@@ -487,7 +729,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["bandwidth"], default="bandwidth")
+    ap.add_argument("--workload", choices=["bandwidth", "dot", "gemv", "gemm"], default="bandwidth",
+                    help="bandwidth (default: the headline step); dot (n=2^20, split 8192), gemv (8192^2 "
+                         "forward + backward), gemm (4096^3 BF16 forward + backward, FP32 fold forward)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the split autotuner; use the default strategy (split 16384, tree second level)")
@@ -515,10 +759,16 @@ def main(argv=None):
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     dist = dist_init("nccl") if world > 1 else None
-    line = bandwidth_workload(args, device, dist)
+    if args.workload == "bandwidth":
+        line = bandwidth_workload(args, device, dist)
+    else:
+        line = {"dot": dot_workload, "gemv": gemv_workload, "gemm": gemm_workload}[args.workload](args, device, dist)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(_strategy(line, "dot"), _strategy(line, "asum"))
+            if args.workload == "bandwidth":
+                line["cpu_baseline"] = cpu_baseline(_strategy(line, "dot"), _strategy(line, "asum"))
+            else:
+                line["cpu_baseline"] = cpu_baseline_for(args.workload)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -23,7 +23,10 @@
  *   - A workspace serves one call at a time. It holds completion counters
  *     and must be zero-filled before its first use (e.g. one memset); every
  *     call leaves the counters zero again, so it can be reused without a new
- *     memset. It must be 128-byte aligned.
+ *     memset by calls with the same counter layout: dot / asum / int32-dot
+ *     calls of any shape keep theirs in the first 128 bytes; a GEMV backward's
+ *     counters depend on (M, N, row_split), so reuse its workspace only for
+ *     that shape (or zero it again). It must be 128-byte aligned.
  *   - Floating point is IEEE binary32 with round-to-nearest-even, subnormals
  *     kept; every + and * of a reduction is rounded separately (no contraction),
  *     so a result is bit-identical to any evaluation of the same strategy tree.
@@ -206,7 +209,8 @@ size_t dpia_gemv_bwd_workspace_size(int64_t M, int64_t N, int64_t row_split);
  *         order from +0 (rows past M are the identity);
  *   dA := map (lambda d. map (lambda v. d * v) x) dy   (dA = dy x^T, ldda >= N).
  * dx or dA may be NULL to skip it. ws (for dx) as dpia_gemv_bwd_workspace_size.
- * A, dA, lda*4 and ldda*4 must be 16-byte aligned.
+ * Pointers 4-byte aligned; 16-byte alignment of A, dA, x with lda and ldda
+ * multiples of 4 enables 128-bit loads and stores (the values do not change).
  */
 dpia_status dpia_gemv_bwd_f32(const float *A, int64_t M, int64_t N, int64_t lda,
                               const float *x, const float *dy, float *dx, float *dA,
@@ -270,6 +274,84 @@ dpia_status dpia_cast_f32_bf16(const float *x, uint16_t *y, int64_t n, dpia_stre
  * undefined), else DPIA_OK; clears the flag.
  */
 dpia_status dpia_poll_device_status(int32_t *status);
+
+/*
+ * Batches of uneven instances in one persistent launch.
+ *
+ * Thousands of dot products and GEMVs of different lengths are packed into
+ * shared arrays (each instance at its own offset) and computed by a single
+ * persistent kernel: the plan lists every instance with its own reduction
+ * strategy (Section 2.1's split sizes chosen per instance) and a work table
+ * of (instance, chunk) and (instance, row group) items, longest first, that
+ * the blocks walk in a grid-stride loop. Each instance's second-level reduce
+ * runs in the block that finishes its last chunk (a per-instance ticket; no
+ * block waits). The backward launch covers dx = g*y, dy = g*x of every dot and
+ * dA = dy x^T, dx = A^T dy of every GEMV the same way.
+ *
+ * Instance strategies: dots at BLOCK level (threads = the batch's threads,
+ * vec 4), any split (a multiple of threads*4), interleaved or contiguous,
+ * SEQ or TREE second level, pad implied; GEMV rows at WARP level (a warp per
+ * row, vec 4), split a multiple of 128, the row's chunks folded in order, and
+ * a backward row_split. Offsets are in elements; every instance must start on
+ * a 16-byte boundary (offsets multiples of 4) and GEMV rows too (lda a
+ * multiple of 4).
+ */
+typedef struct {
+  int64_t off;                /* offset of x_i (and y_i) in the packed arrays */
+  int64_t n;                  /* length */
+  dpia_reduce_strategy st;    /* BLOCK / THREAD, vec 4, threads = the batch's */
+} dpia_dot_instance;
+
+typedef struct {
+  int64_t a_off;              /* offset of A_i (M x N, row-major, lda) in the packed A array */
+  int64_t x_off;              /* offset of x_i (N) in the packed x array (and of dx_i in dx) */
+  int64_t y_off;              /* offset of y_i (M) in the packed y array (and of dy_i in dy) */
+  int64_t M, N, lda;
+  dpia_reduce_strategy st;    /* WARP / THREAD rows, vec 4 */
+  int64_t row_split;          /* backward: rows per chunk of dx = A^T dy */
+} dpia_gemv_instance;
+
+/*
+ * Bytes of the plan of a batch (0 if an instance is invalid). threads: the
+ * block size of the batched launches (a multiple of 32, <= 1024).
+ */
+size_t dpia_batch_plan_size(int32_t n_dots, const dpia_dot_instance *dots, int32_t n_gemvs,
+                            const dpia_gemv_instance *gemvs, int32_t threads);
+
+/*
+ * Build the plan in host memory (plan_bytes from dpia_batch_plan_size),
+ * validating every instance. The plan is plain data: copy it to device
+ * memory once (cudaMemcpy) and pass both copies to the launches below; it is
+ * reused for every launch with the same shapes.
+ */
+dpia_status dpia_batch_plan(int32_t n_dots, const dpia_dot_instance *dots, int32_t n_gemvs,
+                            const dpia_gemv_instance *gemvs, int32_t threads, void *plan_host,
+                            size_t plan_bytes);
+
+/* Workspace bytes the batched launches of this plan need (zero-filled once). */
+size_t dpia_batch_workspace_size(const void *plan_host);
+
+/*
+ * Forward of every instance in one launch: dot_out[i] := dot_i(xs, ys) and
+ * gy_i := A_i gx_i. Pointers of a kind (dots or GEMVs) may be NULL when the
+ * plan has no instance of that kind. grid = 0: one persistent grid.
+ */
+dpia_status dpia_batch_forward_f32(const void *plan_dev, const void *plan_host, const float *xs,
+                                   const float *ys, float *dot_out, const float *As,
+                                   const float *gx, float *gy, void *ws, size_t ws_bytes,
+                                   int32_t grid, dpia_stream_t stream);
+
+/*
+ * Backward of every instance in one launch: for each dot, with g = dot_g[i],
+ * dxs_i := g * y_i and dys_i := g * x_i; for each GEMV, with dy_i in gdy,
+ * dA_i := dy_i x_i^T (stored with the instance's lda in dAs) and
+ * dgx_i := A_i^T dy_i (row chunks of row_split folded in order).
+ */
+dpia_status dpia_batch_backward_f32(const void *plan_dev, const void *plan_host, const float *xs,
+                                    const float *ys, const float *dot_g, float *dxs, float *dys,
+                                    const float *As, const float *gx, const float *gdy, float *dAs,
+                                    float *dgx, void *ws, size_t ws_bytes, int32_t grid,
+                                    dpia_stream_t stream);
 
 /*
  * Allocation-free dot product. The paper has no counterpart: this entry exists

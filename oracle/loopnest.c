@@ -340,10 +340,10 @@ void oracle_dot_bwd_f32(const float *x, const float *y, float g, int64_t n, floa
 /* ------------------------------------------------------------------------ */
 
 int oracle_gemv_f32(const float *A, int64_t M, int64_t N, int64_t lda, const float *x, float *y,
-                    int64_t s, int T, int V, int interleaved, int compensated) {
+                    int64_t s, int T, int V, int interleaved, int compensated, int pad) {
   if (!A || !x || !y || M < 0 || N < 0 || lda < N) return BAD_ARGS;
   for (int64_t i = 0; i < M; ++i) {
-    int rc = reduce_f32(0, A + i * lda, x, N, s, T, V, interleaved, 0, 1, compensated, 0, y + i);
+    int rc = reduce_f32(0, A + i * lda, x, N, s, T, V, interleaved, 0, 1, compensated, pad, y + i);
     if (rc) return rc;
   }
   return OK;

@@ -61,7 +61,7 @@ def _declare(L):
     L.oracle_scal_f32.restype = None
     L.oracle_dot_bwd_f32.argtypes = [_f, _f, ctypes.c_float, _L, _f, _f]
     L.oracle_dot_bwd_f32.restype = None
-    L.oracle_gemv_f32.argtypes = [_f, _L, _L, _L, _f, _f, _L, _I, _I, _I, _I]
+    L.oracle_gemv_f32.argtypes = [_f, _L, _L, _L, _f, _f, _L, _I, _I, _I, _I, _I]
     L.oracle_gemv_bwd_dx_f32.argtypes = [_f, _L, _L, _L, _f, _L, _f]
     L.oracle_gemv_bwd_dA_f32.argtypes = [_f, _f, _L, _L, _f, _L]
     L.oracle_gemv_bwd_dA_f32.restype = None
@@ -143,13 +143,14 @@ def dot_bwd_f32(x, y, g):
 
 
 def gemv_f32(A, x, st) -> np.ndarray:
-    """Rows of A (M x N, row-major) each reduced with ``st`` (second level seq)."""
+    """Rows of A (M x N, row-major) each reduced with ``st`` (second level seq;
+    with st.pad a ragged row's last chunk takes identity items)."""
     A, x = _c32(A), _c32(x)
     M, N = A.shape
     y = np.zeros(M, np.float32)
     _check(lib().oracle_gemv_f32(_fp(A), M, N, N, _fp(x), _fp(y), int(st.s), int(st.T),
                                  int(st.V), 1 if st.thread_map == "interleaved" else 0,
-                                 1 if st.compensated else 0), "gemv_f32")
+                                 1 if st.compensated else 0, 1 if st.pad else 0), "gemv_f32")
     return y
 
 

@@ -54,6 +54,16 @@ class ReduceStrategyC(ctypes.Structure):
     ]
 
 
+class DotInstanceC(ctypes.Structure):
+    _fields_ = [("off", ctypes.c_int64), ("n", ctypes.c_int64), ("st", ReduceStrategyC)]
+
+
+class GemvInstanceC(ctypes.Structure):
+    _fields_ = [("a_off", ctypes.c_int64), ("x_off", ctypes.c_int64), ("y_off", ctypes.c_int64),
+                ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("lda", ctypes.c_int64), ("st", ReduceStrategyC),
+                ("row_split", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
@@ -78,6 +88,12 @@ SIGNATURES = {
     "dpia_gemm_bf16": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I64, _I64, _I64, _I32, _I32, _GP, _P]),
     "dpia_cast_f32_bf16": (_I32, [_P, _P, _I64, _P]),
     "dpia_poll_device_status": (_I32, [ctypes.POINTER(ctypes.c_int32)]),
+    "dpia_batch_plan_size": (_SZ, [_I32, ctypes.POINTER(DotInstanceC), _I32, ctypes.POINTER(GemvInstanceC), _I32]),
+    "dpia_batch_plan": (_I32, [_I32, ctypes.POINTER(DotInstanceC), _I32, ctypes.POINTER(GemvInstanceC), _I32, _P,
+                               _SZ]),
+    "dpia_batch_workspace_size": (_SZ, [_P]),
+    "dpia_batch_forward_f32": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _I32, _P]),
+    "dpia_batch_backward_f32": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _I32, _P]),
     "dpia_dot_f32_noalloc": (_I32, [_P, _P, _I64, _SP, _P, _P]),
 }
 

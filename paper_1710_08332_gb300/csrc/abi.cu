@@ -354,15 +354,14 @@ dpia_status dpia_gemv_bwd_f32(const float *A, int64_t M, int64_t N, int64_t lda,
   if (dA && (overlap(dA, dabytes, A, abytes) || overlap(dA, dabytes, dy, M * 4) || overlap(dA, dabytes, x, N * 4)))
     return fail(DPIA_ERR_ALIAS, "%s: dA overlaps an input", fn);
   if (dA && M > 0) {
-    if (!aligned(dA, 16) || (ldda * 4) % 16 != 0 || !aligned(x, 16))
-      return fail(DPIA_ERR_ALIGN, "%s: dA, ldda*4 and x must be 16-byte aligned", fn);
-    cudaError_t e = launch_outer(x, dy, M, N, dA, ldda, s);
+    if (!aligned(dA, 4) || !aligned(x, 4)) return fail(DPIA_ERR_ALIGN, "%s: dA and x must be 4-byte aligned", fn);
+    const int vec = aligned(dA, 16) && (ldda * 4) % 16 == 0 && aligned(x, 16);
+    cudaError_t e = launch_outer(x, dy, M, N, dA, ldda, vec, s);
     if (e != cudaSuccess) return cuda_status(e, fn);
   }
   if (dx) {
     if (M == 0) return cuda_status(cudaMemsetAsync(dx, 0, (size_t)N * 4, s), fn);
-    if (!aligned(A, 16) || (lda * 4) % 16 != 0)
-      return fail(DPIA_ERR_ALIGN, "%s: A and lda*4 must be 16-byte aligned", fn);
+    if (!aligned(A, 4)) return fail(DPIA_ERR_ALIGN, "%s: A must be 4-byte aligned", fn);
     const int64_t need = (int64_t)dpia_gemv_bwd_workspace_size(M, N, row_split);
     if (!ws || (int64_t)ws_bytes < need)
       return fail(DPIA_ERR_WORKSPACE, "%s: workspace of %zu bytes, %lld needed", fn, ws_bytes, (long long)need);
@@ -383,6 +382,7 @@ dpia_status dpia_gemv_bwd_f32(const float *A, int64_t M, int64_t N, int64_t lda,
     const int64_t counters = round_up(((N + 31) / 32) * 4, 128);
     p.counters = reinterpret_cast<unsigned *>(static_cast<char *>(ws) + kCounterBytes);
     p.partials = reinterpret_cast<float *>(static_cast<char *>(ws) + kCounterBytes + counters);
+    p.vec = aligned(A, 16) && (lda * 4) % 16 == 0;
     return cuda_status(launch_gemv_bwd_dx(p, s), fn);
   }
   return DPIA_OK;

@@ -1,0 +1,606 @@
+// Batches of uneven dot and GEMV instances: host planner and the two
+// persistent kernels (forward, backward).
+//
+// The planner (plain host C++) validates every instance, turns its strategy
+// into launch constants (the same ones the single-instance kernels use) and
+// lists the work items -- dot chunks and groups of GEMV rows for the forward;
+// ranges of dot gradients, groups of dA rows and (column tile, row chunk)
+// pieces of dx for the backward -- sorted longest first. The kernels walk
+// the item list with a grid-stride loop, so every block gets a similar mix.
+//
+// Every value is computed exactly as the single-instance kernels compute it
+// (same fold, same trees, same second levels), so each instance's result is
+// bit-identical to the oracle's evaluation of its own strategy.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "../../include/dpia.h"
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace dpia {
+
+int resident_blocks(const void *kernel, int threads);
+void set_last_error(const char *fmt, ...);
+
+namespace {
+
+constexpr uint32_t kPlanMagic = 0x44504942u;  // "DPIB"
+constexpr int V = 4;
+
+enum ItemType : int32_t { DOT_CHUNK = 0, GEMV_ROWS = 1, DOT_BWD = 2, GEMV_DA = 3, GEMV_DX = 4 };
+
+struct PlanHeader {
+  uint32_t magic;
+  int32_t threads;
+  int32_t n_dots, n_gemvs;
+  int64_t n_fwd, n_bwd;
+  int64_t dots_off, gemvs_off, fwd_off, bwd_off;  // byte offsets inside the plan
+  int64_t dot_partials, dx_partials;              // floats of workspace
+  int64_t dx_tiles;                               // dx tile counters
+  int64_t xs_extent, as_extent, gx_extent, gy_extent;  // elements the packed arrays must hold
+  int64_t bwd_elems_per_item, rows_per_item, da_rows_per_item;
+  int64_t total_bytes;
+};
+
+struct DotDesc {
+  int64_t off, n, s, C, Rc, step, tstride, part_base;
+  int32_t second_tree, T2, pad0, pad1;
+};
+
+struct GemvDesc {
+  int64_t a_off, x_off, y_off, M, N, lda;
+  int64_t s, Crow, Rc, step, tstride;  // forward row strategy (a warp per row)
+  int64_t Rs, Cr, Npad, part_base;     // backward dx: rows per chunk, chunks, padded width, partial offset
+  int32_t tiles, tile_cnt;             // dx column tiles and the index of the first tile's counter
+};
+
+struct Item {
+  int32_t type, inst;
+  int64_t a;
+};
+
+struct WsLayout {
+  unsigned *dot_cnt;
+  unsigned *dx_cnt;
+  float *dot_part;
+  float *dx_part;
+};
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int64_t ws_bytes_of(const PlanHeader &h) {
+  return 128 + round_up((int64_t)h.n_dots * 4, 128) + round_up(h.dx_tiles * 4, 128) +
+         round_up(h.dot_partials * 4, 128) + round_up(h.dx_partials * 4, 128);
+}
+
+WsLayout ws_layout(const PlanHeader &h, void *ws) {
+  char *p = static_cast<char *>(ws) + 128;
+  WsLayout L;
+  L.dot_cnt = reinterpret_cast<unsigned *>(p);
+  p += round_up((int64_t)h.n_dots * 4, 128);
+  L.dx_cnt = reinterpret_cast<unsigned *>(p);
+  p += round_up(h.dx_tiles * 4, 128);
+  L.dot_part = reinterpret_cast<float *>(p);
+  p += round_up(h.dot_partials * 4, 128);
+  L.dx_part = reinterpret_cast<float *>(p);
+  return L;
+}
+
+struct Built {
+  PlanHeader h;
+  std::vector<DotDesc> dots;
+  std::vector<GemvDesc> gemvs;
+  std::vector<Item> fwd, bwd;
+};
+
+// Validate and plan; returns DPIA_OK and fills b.
+dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, const dpia_gemv_instance *gemvs,
+                       int32_t T, Built &b) {
+  if (nd < 0 || ng < 0) {
+    set_last_error("dpia_batch_plan: negative instance count");
+    return DPIA_ERR_SHAPE;
+  }
+  if ((nd > 0 && !dots) || (ng > 0 && !gemvs)) {
+    set_last_error("dpia_batch_plan: instance array is NULL");
+    return DPIA_ERR_NULL;
+  }
+  if (!is_pow2(T) || T < 32 || T > 512) {
+    set_last_error("dpia_batch_plan: threads=%d must be a power of two in [32, 512]", T);
+    return DPIA_ERR_STRATEGY;
+  }
+  PlanHeader &h = b.h;
+  std::memset(&h, 0, sizeof h);
+  h.magic = kPlanMagic;
+  h.threads = T;
+  h.n_dots = nd;
+  h.n_gemvs = ng;
+  h.rows_per_item = T / 32;          // a warp per row
+  h.da_rows_per_item = 8;
+  h.bwd_elems_per_item = 4 * (int64_t)T * 8;
+  std::vector<std::pair<int64_t, Item>> fwd, bwd;  // (cost, item)
+  for (int32_t i = 0; i < nd; ++i) {
+    const dpia_dot_instance &in = dots[i];
+    const dpia_reduce_strategy &st = in.st;
+    if (in.n < 0 || in.off < 0 || in.off % 4) {
+      set_last_error("dpia_batch_plan: dot %d: bad offset %lld or length %lld (offsets must be multiples of 4)", i,
+                     (long long)in.off, (long long)in.n);
+      return DPIA_ERR_SHAPE;
+    }
+    if (st.map_level != DPIA_LVL_BLOCK || st.inner_level != DPIA_LVL_THREAD || st.threads != T || st.vec != V ||
+        st.compensated || st.split <= 0 || st.split % ((int64_t)T * V) ||
+        (st.thread_map != DPIA_MAP_INTERLEAVED && st.thread_map != DPIA_MAP_CONTIG) ||
+        (st.second == DPIA_SECOND_TREE && (!is_pow2(st.threads2) || st.threads2 > T)) ||
+        (st.second != DPIA_SECOND_SEQ && st.second != DPIA_SECOND_TREE)) {
+      set_last_error("dpia_batch_plan: dot %d: strategy must be BLOCK/THREAD, threads %d, vec 4, split a multiple "
+                     "of %d, plain (not compensated), threads2 a power of two <= threads", i, T, T * V);
+      return DPIA_ERR_STRATEGY;
+    }
+    DotDesc d{};
+    d.off = in.off;
+    d.n = in.n;
+    d.s = st.split;
+    d.C = in.n > 0 ? (in.n + d.s - 1) / d.s : 1;  // an empty dot is one all-identity chunk: +0
+    d.Rc = d.s / ((int64_t)T * V);
+    if (st.thread_map == DPIA_MAP_INTERLEAVED) {
+      d.step = (int64_t)T * V;
+      d.tstride = V;
+    } else {
+      d.step = V;
+      d.tstride = d.Rc * V;
+    }
+    d.part_base = h.dot_partials;
+    d.second_tree = st.second == DPIA_SECOND_TREE;
+    d.T2 = d.second_tree ? st.threads2 : 1;
+    h.dot_partials += d.C;
+    h.xs_extent = std::max(h.xs_extent, in.off + in.n);
+    b.dots.push_back(d);
+    for (int64_t c = 0; c < d.C; ++c) fwd.push_back({8 * d.s, Item{DOT_CHUNK, i, c}});
+    for (int64_t e = 0; e < in.n; e += h.bwd_elems_per_item) bwd.push_back({16 * h.bwd_elems_per_item, Item{DOT_BWD, i, e}});
+  }
+  for (int32_t i = 0; i < ng; ++i) {
+    const dpia_gemv_instance &in = gemvs[i];
+    const dpia_reduce_strategy &st = in.st;
+    if (in.M < 0 || in.N < 1 || in.lda < in.N || in.lda % 4 || in.a_off < 0 || in.a_off % 4 || in.x_off < 0 ||
+        in.x_off % 4 || in.y_off < 0 || in.row_split < 1) {
+      set_last_error("dpia_batch_plan: gemv %d: bad shape or offsets (offsets and lda must be multiples of 4, "
+                     "N >= 1, row_split >= 1)", i);
+      return DPIA_ERR_SHAPE;
+    }
+    if (st.map_level != DPIA_LVL_WARP || st.inner_level != DPIA_LVL_THREAD || st.vec != V || st.compensated ||
+        st.split <= 0 || st.split % (32 * V) || st.second != DPIA_SECOND_SEQ ||
+        (st.thread_map != DPIA_MAP_INTERLEAVED && st.thread_map != DPIA_MAP_CONTIG)) {
+      set_last_error("dpia_batch_plan: gemv %d: row strategy must be WARP/THREAD, vec 4, split a multiple of 128, "
+                     "SEQ second level, plain", i);
+      return DPIA_ERR_STRATEGY;
+    }
+    GemvDesc g{};
+    g.a_off = in.a_off;
+    g.x_off = in.x_off;
+    g.y_off = in.y_off;
+    g.M = in.M;
+    g.N = in.N;
+    g.lda = in.lda;
+    g.s = st.split;
+    g.Crow = (in.N + g.s - 1) / g.s;
+    g.Rc = g.s / (32 * V);
+    if (st.thread_map == DPIA_MAP_INTERLEAVED) {
+      g.step = 32 * V;
+      g.tstride = V;
+    } else {
+      g.step = V;
+      g.tstride = g.Rc * V;
+    }
+    g.Rs = in.row_split;
+    g.Cr = (in.M + g.Rs - 1) / g.Rs;
+    g.Npad = round_up(in.N, 4);
+    g.part_base = h.dx_partials;
+    g.tiles = (int32_t)((in.N + 4 * (int64_t)T - 1) / (4 * (int64_t)T));
+    g.tile_cnt = (int32_t)h.dx_tiles;
+    h.dx_partials += g.Cr * g.Npad;
+    h.dx_tiles += g.tiles;
+    h.as_extent = std::max(h.as_extent, in.M > 0 ? in.a_off + (in.M - 1) * in.lda + in.N : in.a_off);
+    h.gx_extent = std::max(h.gx_extent, in.x_off + in.N);
+    h.gy_extent = std::max(h.gy_extent, in.y_off + in.M);
+    b.gemvs.push_back(g);
+    for (int64_t r = 0; r < in.M; r += h.rows_per_item)
+      fwd.push_back({4 * std::min<int64_t>(h.rows_per_item, in.M - r) * in.N, Item{GEMV_ROWS, i, r}});
+    for (int64_t r = 0; r < in.M; r += h.da_rows_per_item)
+      bwd.push_back({4 * std::min<int64_t>(h.da_rows_per_item, in.M - r) * in.N, Item{GEMV_DA, i, r}});
+    for (int64_t t = 0; t < g.tiles; ++t)
+      for (int64_t c = 0; c < g.Cr; ++c)
+        bwd.push_back({4 * std::min<int64_t>(g.Rs, in.M - c * g.Rs) * std::min<int64_t>(4 * T, in.N - t * 4 * T),
+                       Item{GEMV_DX, i, t * g.Cr + c}});
+  }
+  auto by_cost = [](const std::pair<int64_t, Item> &a, const std::pair<int64_t, Item> &b) { return a.first > b.first; };
+  std::stable_sort(fwd.begin(), fwd.end(), by_cost);
+  std::stable_sort(bwd.begin(), bwd.end(), by_cost);
+  for (auto &p : fwd) b.fwd.push_back(p.second);
+  for (auto &p : bwd) b.bwd.push_back(p.second);
+  h.n_fwd = (int64_t)b.fwd.size();
+  h.n_bwd = (int64_t)b.bwd.size();
+  int64_t off = round_up(sizeof(PlanHeader), 128);
+  h.dots_off = off;
+  off += round_up((int64_t)b.dots.size() * sizeof(DotDesc), 128);
+  h.gemvs_off = off;
+  off += round_up((int64_t)b.gemvs.size() * sizeof(GemvDesc), 128);
+  h.fwd_off = off;
+  off += round_up(h.n_fwd * (int64_t)sizeof(Item), 128);
+  h.bwd_off = off;
+  off += round_up(h.n_bwd * (int64_t)sizeof(Item), 128);
+  h.total_bytes = off;
+  return DPIA_OK;
+}
+
+struct FwdArgs {
+  const char *plan;
+  const float *xs, *ys;
+  float *dot_out;
+  const float *As, *gx;
+  float *gy;
+  WsLayout ws;
+};
+
+struct BwdArgs {
+  const char *plan;
+  const float *xs, *ys, *dot_g;
+  float *dxs, *dys;
+  const float *As, *gx, *gdy;
+  float *dAs, *dgx;
+  WsLayout ws;
+};
+
+__global__ void __launch_bounds__(512) batch_fwd_kernel(const FwdArgs a) {
+  __shared__ float sm[32];
+  __shared__ int last;
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(a.plan);
+  const DotDesc *dots = reinterpret_cast<const DotDesc *>(a.plan + h->dots_off);
+  const GemvDesc *gemvs = reinterpret_cast<const GemvDesc *>(a.plan + h->gemvs_off);
+  const Item *items = reinterpret_cast<const Item *>(a.plan + h->fwd_off);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t n_items = h->n_fwd;
+  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const Item w = items[it];
+    if (w.type == DOT_CHUNK) {
+      const DotDesc d = dots[w.inst];
+      const float *x = a.xs + d.off, *y = a.ys + d.off;
+      const int64_t c = w.a;
+      const bool full = (c + 1) * d.s <= d.n;
+      float v = thread_fold<DotF32, SumF32, V, false>(x, y, d.n, c * d.s + t * d.tstride, d.Rc, d.step, full);
+      v = block_tree<SumF32>(v, blockDim.x, sm);
+      if (t == 0) a.ws.dot_part[d.part_base + c] = v;
+      __threadfence();
+      __syncthreads();
+      if (t == 0) {
+        const unsigned ticket = atomicAdd(a.ws.dot_cnt + w.inst, 1u);
+        __threadfence();
+        last = ticket == d.C - 1;
+      }
+      __syncthreads();
+      if (last) {  // this block finished the instance's last chunk: second level
+        const float *part = a.ws.dot_part + d.part_base;
+        float res = 0.0f;
+        if (!d.second_tree) {
+          if (t == 0) {
+            int64_t k = 0;
+            for (; k + 8 <= d.C; k += 8) {
+              float b8[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) b8[u] = __ldcg(part + k + u);
+#pragma unroll
+              for (int u = 0; u < 8; ++u) res = __fadd_rn(res, b8[u]);
+            }
+            for (; k < d.C; ++k) res = __fadd_rn(res, __ldcg(part + k));
+          }
+        } else {
+          float acc = 0.0f;
+          if (t < d.T2) {
+            const int64_t R2 = ceil_div(d.C, d.T2);
+            for (int64_t r = 0; r < R2; ++r) {
+              const int64_t i = r * d.T2 + t;
+              acc = __fadd_rn(acc, i < d.C ? __ldcg(part + i) : 0.0f);
+            }
+          }
+          res = block_tree<SumF32>(acc, d.T2, sm);
+        }
+        if (t == 0) {
+          a.dot_out[w.inst] = res;
+          a.ws.dot_cnt[w.inst] = 0u;
+        }
+      }
+      __syncthreads();
+    } else {  // GEMV_ROWS: a warp per row, the row's chunks folded in order
+      const GemvDesc g = gemvs[w.inst];
+      const int64_t r = w.a + warp;
+      if (r < g.M && r < w.a + h->rows_per_item) {
+        const float *row = a.As + g.a_off + r * g.lda;
+        const float *x = a.gx + g.x_off;
+        float acc = 0.0f;
+        for (int64_t c = 0; c < g.Crow; ++c) {
+          const bool full = (c + 1) * g.s <= g.N;
+          float v = thread_fold<DotF32, SumF32, V, true>(row, x, g.N, c * g.s + lane * g.tstride, g.Rc, g.step, full);
+          v = warp_tree<SumF32>(v, 32);
+          if (lane == 0) acc = __fadd_rn(acc, v);
+        }
+        if (lane == 0) a.gy[g.y_off + r] = acc;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(512) batch_bwd_kernel(const BwdArgs a) {
+  __shared__ int last;
+  const PlanHeader *h = reinterpret_cast<const PlanHeader *>(a.plan);
+  const DotDesc *dots = reinterpret_cast<const DotDesc *>(a.plan + h->dots_off);
+  const GemvDesc *gemvs = reinterpret_cast<const GemvDesc *>(a.plan + h->gemvs_off);
+  const Item *items = reinterpret_cast<const Item *>(a.plan + h->bwd_off);
+  const int t = threadIdx.x;
+  const int T = blockDim.x;
+  const int64_t n_items = h->n_bwd;
+  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const Item w = items[it];
+    if (w.type == DOT_BWD) {  // dx = g*y, dy = g*x over [e0, e1)
+      const DotDesc d = dots[w.inst];
+      const float gv = __ldg(a.dot_g + w.inst);
+      const int64_t e0 = w.a;
+      const int64_t e1 = e0 + h->bwd_elems_per_item < d.n ? e0 + h->bwd_elems_per_item : d.n;
+      const float *x = a.xs + d.off, *y = a.ys + d.off;
+      float *dx = a.dxs + d.off, *dy = a.dys + d.off;
+      const int64_t v1 = e0 + (e1 - e0) / 4 * 4;
+      for (int64_t e = e0 + 4 * t; e < v1; e += 4 * T) {
+        const float4 yv = ld_stream_v4(y + e), xv = ld_stream_v4(x + e);
+        *reinterpret_cast<float4 *>(dx + e) =
+            make_float4(__fmul_rn(gv, yv.x), __fmul_rn(gv, yv.y), __fmul_rn(gv, yv.z), __fmul_rn(gv, yv.w));
+        *reinterpret_cast<float4 *>(dy + e) =
+            make_float4(__fmul_rn(gv, xv.x), __fmul_rn(gv, xv.y), __fmul_rn(gv, xv.z), __fmul_rn(gv, xv.w));
+      }
+      for (int64_t e = v1 + t; e < e1; e += T) {
+        dx[e] = __fmul_rn(gv, y[e]);
+        dy[e] = __fmul_rn(gv, x[e]);
+      }
+    } else if (w.type == GEMV_DA) {  // dA rows = dy_r * x
+      const GemvDesc g = gemvs[w.inst];
+      const float *x = a.gx + g.x_off;
+      const int64_t r1 = w.a + h->da_rows_per_item < g.M ? w.a + h->da_rows_per_item : g.M;
+      const int64_t nv = g.N / 4;
+      for (int64_t r = w.a; r < r1; ++r) {
+        const float d = __ldg(a.gdy + g.y_off + r);
+        float *row = a.dAs + g.a_off + r * g.lda;
+        for (int64_t j = t; j < nv; j += T) {
+          const float4 xv = ld_cached_v4(x + 4 * j);
+          *reinterpret_cast<float4 *>(row + 4 * j) =
+              make_float4(__fmul_rn(d, xv.x), __fmul_rn(d, xv.y), __fmul_rn(d, xv.z), __fmul_rn(d, xv.w));
+        }
+        for (int64_t j = nv * 4 + t; j < g.N; j += T) row[j] = __fmul_rn(d, __ldg(x + j));
+      }
+    } else {  // GEMV_DX: column tile x row chunk, partials, last block of the tile folds them
+      const GemvDesc g = gemvs[w.inst];
+      const int64_t tile = w.a / g.Cr, chunk = w.a % g.Cr;
+      const int64_t j0 = tile * 4 * T + 4 * t;
+      const int64_t r0 = chunk * g.Rs;
+      const int64_t r1 = r0 + g.Rs < g.M ? r0 + g.Rs : g.M;
+      const float *A = a.As + g.a_off;
+      const float *dyv = a.gdy + g.y_off;
+      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      if (j0 + 4 <= g.N) {
+        int64_t i = r0;
+        for (; i + 4 <= r1; i += 4) {
+          float4 av[4];
+          float dv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            av[u] = ld_stream_v4(A + (i + u) * g.lda + j0);
+            dv[u] = __ldg(dyv + i + u);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            acc[0] = __fadd_rn(acc[0], __fmul_rn(av[u].x, dv[u]));
+            acc[1] = __fadd_rn(acc[1], __fmul_rn(av[u].y, dv[u]));
+            acc[2] = __fadd_rn(acc[2], __fmul_rn(av[u].z, dv[u]));
+            acc[3] = __fadd_rn(acc[3], __fmul_rn(av[u].w, dv[u]));
+          }
+        }
+        for (; i < r1; ++i) {
+          const float4 av = ld_stream_v4(A + i * g.lda + j0);
+          const float dv = __ldg(dyv + i);
+          acc[0] = __fadd_rn(acc[0], __fmul_rn(av.x, dv));
+          acc[1] = __fadd_rn(acc[1], __fmul_rn(av.y, dv));
+          acc[2] = __fadd_rn(acc[2], __fmul_rn(av.z, dv));
+          acc[3] = __fadd_rn(acc[3], __fmul_rn(av.w, dv));
+        }
+      } else if (j0 < g.N) {
+        for (int64_t i = r0; i < r1; ++i) {
+          const float dv = __ldg(dyv + i);
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (j0 + v < g.N) acc[v] = __fadd_rn(acc[v], __fmul_rn(A[i * g.lda + j0 + v], dv));
+        }
+      }
+      float *part = a.ws.dx_part + g.part_base + chunk * g.Npad;
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (j0 + v < g.N) part[j0 + v] = acc[v];
+      __threadfence();
+      __syncthreads();
+      if (t == 0) {
+        const unsigned ticket = atomicAdd(a.ws.dx_cnt + g.tile_cnt + tile, 1u);
+        __threadfence();
+        last = ticket == g.Cr - 1;
+      }
+      __syncthreads();
+      if (last) {
+        float res[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const float *pb = a.ws.dx_part + g.part_base;
+        for (int64_t c = 0; c < g.Cr; ++c)
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (j0 + v < g.N) res[v] = __fadd_rn(res[v], __ldcg(pb + c * g.Npad + j0 + v));
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (j0 + v < g.N) a.dgx[g.x_off + j0 + v] = res[v];
+        if (t == 0) a.ws.dx_cnt[g.tile_cnt + tile] = 0u;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+const PlanHeader *check_plan(const char *fn, const void *plan_dev, const void *plan_host) {
+  if (!plan_dev || !plan_host) {
+    set_last_error("%s: plan is NULL", fn);
+    return nullptr;
+  }
+  const PlanHeader *h = static_cast<const PlanHeader *>(plan_host);
+  if (h->magic != kPlanMagic) {
+    set_last_error("%s: not a batch plan (bad magic)", fn);
+    return nullptr;
+  }
+  if (reinterpret_cast<uintptr_t>(plan_dev) % 128) {
+    set_last_error("%s: device plan must be 128-byte aligned", fn);
+    return nullptr;
+  }
+  return h;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+int persistent(const void *k, int threads, int64_t items) {
+  int64_t cap = (int64_t)sm_count() * resident_blocks(k, threads);
+  int64_t g = items < cap ? items : cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+}  // namespace dpia
+
+using namespace dpia;
+
+extern "C" {
+
+size_t dpia_batch_plan_size(int32_t n_dots, const dpia_dot_instance *dots, int32_t n_gemvs,
+                            const dpia_gemv_instance *gemvs, int32_t threads) {
+  Built b;
+  if (build_plan(n_dots, dots, n_gemvs, gemvs, threads, b) != DPIA_OK) return 0;
+  return (size_t)b.h.total_bytes;
+}
+
+dpia_status dpia_batch_plan(int32_t n_dots, const dpia_dot_instance *dots, int32_t n_gemvs,
+                            const dpia_gemv_instance *gemvs, int32_t threads, void *plan_host, size_t plan_bytes) {
+  set_last_error("");
+  Built b;
+  dpia_status rc = build_plan(n_dots, dots, n_gemvs, gemvs, threads, b);
+  if (rc) return rc;
+  if (!plan_host) {
+    set_last_error("dpia_batch_plan: plan_host is NULL");
+    return DPIA_ERR_NULL;
+  }
+  if ((int64_t)plan_bytes < b.h.total_bytes) {
+    set_last_error("dpia_batch_plan: plan buffer of %zu bytes, %lld needed", plan_bytes, (long long)b.h.total_bytes);
+    return DPIA_ERR_WORKSPACE;
+  }
+  char *p = static_cast<char *>(plan_host);
+  std::memset(p, 0, (size_t)b.h.total_bytes);
+  std::memcpy(p, &b.h, sizeof b.h);
+  if (!b.dots.empty()) std::memcpy(p + b.h.dots_off, b.dots.data(), b.dots.size() * sizeof(DotDesc));
+  if (!b.gemvs.empty()) std::memcpy(p + b.h.gemvs_off, b.gemvs.data(), b.gemvs.size() * sizeof(GemvDesc));
+  if (!b.fwd.empty()) std::memcpy(p + b.h.fwd_off, b.fwd.data(), b.fwd.size() * sizeof(Item));
+  if (!b.bwd.empty()) std::memcpy(p + b.h.bwd_off, b.bwd.data(), b.bwd.size() * sizeof(Item));
+  return DPIA_OK;
+}
+
+size_t dpia_batch_workspace_size(const void *plan_host) {
+  if (!plan_host) return 0;
+  const PlanHeader *h = static_cast<const PlanHeader *>(plan_host);
+  if (h->magic != kPlanMagic) return 0;
+  return (size_t)ws_bytes_of(*h);
+}
+
+dpia_status dpia_batch_forward_f32(const void *plan_dev, const void *plan_host, const float *xs, const float *ys,
+                                   float *dot_out, const float *As, const float *gx, float *gy, void *ws,
+                                   size_t ws_bytes, int32_t grid, dpia_stream_t stream) {
+  const char *fn = "dpia_batch_forward_f32";
+  set_last_error("");
+  const PlanHeader *h = check_plan(fn, plan_dev, plan_host);
+  if (!h) return DPIA_ERR_NULL;
+  if (h->n_fwd == 0) return DPIA_OK;
+  if (h->n_dots > 0 && (!xs || !ys || !dot_out)) {
+    set_last_error("%s: dot arrays are NULL", fn);
+    return DPIA_ERR_NULL;
+  }
+  if (h->n_gemvs > 0 && (!As || !gx || !gy)) {
+    set_last_error("%s: GEMV arrays are NULL", fn);
+    return DPIA_ERR_NULL;
+  }
+  if ((xs && !aligned16(xs)) || (ys && !aligned16(ys)) || (As && !aligned16(As)) || (gx && !aligned16(gx))) {
+    set_last_error("%s: packed inputs must be 16-byte aligned", fn);
+    return DPIA_ERR_ALIGN;
+  }
+  if (!ws || (int64_t)ws_bytes < ws_bytes_of(*h) || reinterpret_cast<uintptr_t>(ws) % 128) {
+    set_last_error("%s: workspace NULL, unaligned or smaller than %lld bytes", fn, (long long)ws_bytes_of(*h));
+    return DPIA_ERR_WORKSPACE;
+  }
+  if (grid < 0) {
+    set_last_error("%s: grid=%d", fn, grid);
+    return DPIA_ERR_STRATEGY;
+  }
+  FwdArgs a{static_cast<const char *>(plan_dev), xs, ys, dot_out, As, gx, gy, ws_layout(*h, ws)};
+  const void *k = (const void *)batch_fwd_kernel;
+  const int g = grid > 0 ? grid : persistent(k, h->threads, h->n_fwd);
+  void *args[] = {&a};
+  cudaError_t e = cudaLaunchKernel(k, dim3(g), dim3(h->threads), args, 0, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    set_last_error("%s: CUDA error %d (%s)", fn, (int)e, cudaGetErrorString(e));
+    return DPIA_ERR_CUDA;
+  }
+  return DPIA_OK;
+}
+
+dpia_status dpia_batch_backward_f32(const void *plan_dev, const void *plan_host, const float *xs, const float *ys,
+                                    const float *dot_g, float *dxs, float *dys, const float *As, const float *gx,
+                                    const float *gdy, float *dAs, float *dgx, void *ws, size_t ws_bytes, int32_t grid,
+                                    dpia_stream_t stream) {
+  const char *fn = "dpia_batch_backward_f32";
+  set_last_error("");
+  const PlanHeader *h = check_plan(fn, plan_dev, plan_host);
+  if (!h) return DPIA_ERR_NULL;
+  if (h->n_bwd == 0) return DPIA_OK;
+  if (h->n_dots > 0 && (!xs || !ys || !dot_g || !dxs || !dys)) {
+    set_last_error("%s: dot arrays are NULL", fn);
+    return DPIA_ERR_NULL;
+  }
+  if (h->n_gemvs > 0 && (!As || !gx || !gdy || !dAs || !dgx)) {
+    set_last_error("%s: GEMV arrays are NULL", fn);
+    return DPIA_ERR_NULL;
+  }
+  const void *vp[] = {xs, ys, dxs, dys, As, gx, dAs};
+  for (const void *p : vp)
+    if (p && !aligned16(p)) {
+      set_last_error("%s: packed arrays must be 16-byte aligned", fn);
+      return DPIA_ERR_ALIGN;
+    }
+  if (!ws || (int64_t)ws_bytes < ws_bytes_of(*h) || reinterpret_cast<uintptr_t>(ws) % 128) {
+    set_last_error("%s: workspace NULL, unaligned or smaller than %lld bytes", fn, (long long)ws_bytes_of(*h));
+    return DPIA_ERR_WORKSPACE;
+  }
+  if (grid < 0) {
+    set_last_error("%s: grid=%d", fn, grid);
+    return DPIA_ERR_STRATEGY;
+  }
+  BwdArgs a{static_cast<const char *>(plan_dev), xs, ys, dot_g, dxs, dys, As, gx, gdy, dAs, dgx, ws_layout(*h, ws)};
+  const void *k = (const void *)batch_bwd_kernel;
+  const int g = grid > 0 ? grid : persistent(k, h->threads, h->n_bwd);
+  void *args[] = {&a};
+  cudaError_t e = cudaLaunchKernel(k, dim3(g), dim3(h->threads), args, 0, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    set_last_error("%s: CUDA error %d (%s)", fn, (int)e, cudaGetErrorString(e));
+    return DPIA_ERR_CUDA;
+  }
+  return DPIA_OK;
+}
+
+}  // extern "C"

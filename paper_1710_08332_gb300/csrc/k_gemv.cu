@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kBwdThreads) gemv_bwd_dx_kernel(const GemvBwdL
   const int64_t r0 = chunk * p.Rs;
   const int64_t r1 = r0 + p.Rs < p.M ? r0 + p.Rs : p.M;
   float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  if (j0 + 4 <= p.N) {
+  if (p.vec && j0 + 4 <= p.N) {
     int64_t i = r0;
     for (; i + 4 <= r1; i += 4) {
       float4 a[4];
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kBwdThreads) gemv_bwd_dx_kernel(const GemvBwdL
       acc[2] = __fadd_rn(acc[2], __fmul_rn(a.z, d));
       acc[3] = __fadd_rn(acc[3], __fmul_rn(a.w, d));
     }
-  } else if (j0 < p.N) {
+  } else if (j0 < p.N) {  // ragged last columns, or a leading dimension not fit for 128-bit loads
     for (int64_t i = r0; i < r1; ++i) {
       const float d = __ldg(p.dy + i);
 #pragma unroll
@@ -131,13 +131,35 @@ __global__ void __launch_bounds__(kBwdThreads) gemv_bwd_dx_kernel(const GemvBwdL
   }
   __syncthreads();
   if (!is_last) return;
-  // fold the tile's partials over the row chunks in chunk order from zero
+  // fold the tile's partials over the row chunks in chunk order from zero;
+  // loads run 8 chunks ahead of the dependent adds
   float res[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  for (int64_t c = 0; c < p.Cr; ++c) {
-    const float *pc = p.partials + c * p.Npad;
+  if (j0 < p.N) {
+    const bool full4 = j0 + 4 <= p.N;
+    int64_t c = 0;
+    for (; c + 8 <= p.Cr; c += 8) {
+      float4 b[8];
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
-      if (j0 + v < p.N) res[v] = __fadd_rn(res[v], __ldcg(pc + j0 + v));
+      for (int u = 0; u < 8; ++u) {
+        const float *pc = p.partials + (c + u) * p.Npad + j0;
+        b[u] = full4 ? __ldcg(reinterpret_cast<const float4 *>(pc))
+                     : make_float4(__ldcg(pc), j0 + 1 < p.N ? __ldcg(pc + 1) : 0.0f,
+                                   j0 + 2 < p.N ? __ldcg(pc + 2) : 0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        res[0] = __fadd_rn(res[0], b[u].x);
+        res[1] = __fadd_rn(res[1], b[u].y);
+        res[2] = __fadd_rn(res[2], b[u].z);
+        res[3] = __fadd_rn(res[3], b[u].w);
+      }
+    }
+    for (; c < p.Cr; ++c) {
+      const float *pc = p.partials + c * p.Npad;
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (j0 + v < p.N) res[v] = __fadd_rn(res[v], __ldcg(pc + j0 + v));
+    }
   }
 #pragma unroll
   for (int v = 0; v < 4; ++v)

@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(256) dot_bwd_kernel(const float *x, const floa
 
 // dA[i][j] = dy[i] * x[j]: one block per row (grid-stride), x from L1/L2.
 __global__ void __launch_bounds__(256) outer_kernel(const float *x, const float *dy, int64_t M,
-                                                    int64_t N, float *dA, int64_t ldda) {
-  const int64_t nv = N / 4;
+                                                    int64_t N, float *dA, int64_t ldda, int vec) {
+  const int64_t nv = vec ? N / 4 : 0;
   for (int64_t i = blockIdx.x; i < M; i += gridDim.x) {
     const float d = __ldg(dy + i);
     float *row = dA + i * ldda;
@@ -134,12 +134,12 @@ cudaError_t launch_dot_bwd(const float *x, const float *y, const float *g, int64
 }
 
 cudaError_t launch_outer(const float *x, const float *dy, int64_t M, int64_t N, float *dA,
-                         int64_t ldda, cudaStream_t stream) {
+                         int64_t ldda, int vec, cudaStream_t stream) {
   const int threads = 256;
   int64_t cap = (int64_t)sm_count() * resident_blocks((const void *)outer_kernel, threads);
   int64_t grid = M < cap ? M : cap;
   if (grid < 1) grid = 1;
-  outer_kernel<<<(unsigned)grid, threads, 0, stream>>>(x, dy, M, N, dA, ldda);
+  outer_kernel<<<(unsigned)grid, threads, 0, stream>>>(x, dy, M, N, dA, ldda, vec);
   return cudaGetLastError();
 }
 

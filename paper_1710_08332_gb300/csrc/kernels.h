@@ -51,7 +51,7 @@ cudaError_t launch_scal(float a, const float *x, float *y, int64_t n, int V, cud
 cudaError_t launch_dot_bwd(const float *x, const float *y, const float *g, int64_t n, float *dx,
                            float *dy, cudaStream_t stream);
 cudaError_t launch_outer(const float *x, const float *dy, int64_t M, int64_t N, float *dA,
-                         int64_t ldda, cudaStream_t stream);
+                         int64_t ldda, int vec, cudaStream_t stream);
 
 struct GemvBwdLaunch {
   const float *A;
@@ -63,6 +63,7 @@ struct GemvBwdLaunch {
   float *partials;   // Cr x Npad
   int64_t Npad;
   unsigned *counters;  // one per column tile
+  int vec;             // A 16-byte aligned and lda a multiple of 4: 128-bit loads
 };
 cudaError_t launch_gemv_bwd_dx(const GemvBwdLaunch &p, cudaStream_t stream);
 

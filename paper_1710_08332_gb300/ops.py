@@ -152,17 +152,20 @@ _ws_lock = threading.Lock()
 _ws_cache: dict = {}
 
 
-def workspace(nbytes: int, device=None, stream=None) -> torch.Tensor:
+def workspace(nbytes: int, device=None, stream=None, kind="reduce") -> torch.Tensor:
     """A zero-initialised workspace of >= nbytes for calls on ``stream``.
 
-    One buffer per (device, stream) is kept and grown on demand; calls on one
-    stream are ordered, so they can share it.
+    One buffer per (device, stream, kind) is kept and grown on demand; calls on
+    one stream are ordered, so they can share it. Workspaces may only be shared
+    by calls with the same counter layout: every dot / asum / int32-dot call
+    keeps its counter in the first 128 bytes (kind "reduce", any shape), while a
+    GEMV backward's counters depend on its shape, so its kind is the shape.
     """
     device = torch.device(device) if device is not None else torch.device("cuda")
     if device.index is None:
         device = torch.device("cuda", torch.cuda.current_device())
     stream = stream or torch.cuda.current_stream(device)
-    key = (device.index, stream.cuda_stream)
+    key = (device.index, stream.cuda_stream, kind)
     nbytes = max(int(nbytes), 128)
     with _ws_lock:
         buf = _ws_cache.get(key)
@@ -209,27 +212,34 @@ def scal(a: float, x, out=None, vec: int = 4):
     return y
 
 
-def default_gemv_strategy(N_: int) -> ReduceStrategy:
+def default_gemv_strategy(N_: int, lda: int | None = None, aligned16: bool = True) -> ReduceStrategy:
+    """One chunk per row: a block per row for long rows, a warp per row for
+    short ones; the vector width is the widest the row alignment allows."""
+    lda = N_ if lda is None else lda
+    V = 4 if (aligned16 and lda % 4 == 0) else 2 if lda % 2 == 0 else 1
     if N_ >= 1024:
-        s = N_ if N_ % 1024 == 0 else ((N_ + 1023) // 1024) * 1024
-        return ReduceStrategy(split=s, threads=256, vec=4, pad=N_ % 1024 != 0)
-    s = ((N_ + 127) // 128) * 128
-    return ReduceStrategy(split=s, threads=128, vec=4, map_level="warp", pad=N_ % 128 != 0)
+        q = 128 * V
+        s = ((N_ + q - 1) // q) * q
+        return ReduceStrategy(split=s, threads=128, vec=V, pad=N_ % q != 0)
+    q = 32 * V
+    s = ((max(N_, 1) + q - 1) // q) * q
+    return ReduceStrategy(split=s, threads=128, vec=V, map_level="warp", pad=N_ % q != 0)
 
 
 def gemv(A, x, strategy: ReduceStrategy | None = None, out=None):
     M, N_ = A.shape
-    st = strategy or default_gemv_strategy(N_)
+    st = strategy or default_gemv_strategy(N_, A.stride(0), A.data_ptr() % 16 == 0 and x.data_ptr() % 16 == 0)
     y = out if out is not None else torch.empty(M, dtype=torch.float32, device=A.device)
     dpia_gemv_f32(A, M, N_, A.stride(0), x, y, st)
     return y
 
 
-def gemv_bwd(A, x, dy, need_dx=True, need_dA=True, row_split=64):
+def gemv_bwd(A, x, dy, need_dx=True, need_dA=True, row_split=256):
     M, N_ = A.shape
     dx = torch.empty(N_, dtype=torch.float32, device=A.device) if need_dx else None
     dA = torch.empty(M, N_, dtype=torch.float32, device=A.device) if need_dA else None
-    ws = workspace(dpia_gemv_bwd_workspace_size(M, N_, row_split), A.device) if need_dx else None
+    ws = workspace(dpia_gemv_bwd_workspace_size(M, N_, row_split), A.device,
+                   kind=("gemv_bwd", M, N_, row_split)) if need_dx else None
     dpia_gemv_bwd_f32(A, M, N_, A.stride(0), x, dy, dx, dA, N_, row_split, ws)
     return dx, dA
 

@@ -410,6 +410,11 @@ def test_gemv_pins():
     A = rng.integers(-5, 6, (M, N)).astype(np.float32)
     xi = rng.integers(-5, 6, N).astype(np.float32)
     assert np.array_equal(loopnest.gemv_f32(A, xi, st), (A.astype(np.int64) @ xi.astype(np.int64)).astype(np.float32))
+    # ragged rows with padding: each row is the padded dot of the pattern evaluator
+    Ar = rng.normal(0, 1, (5, 200)).astype(np.float32)
+    xr = rng.uniform(-1, 1, 200).astype(np.float32)
+    stp = P.Strategy(s=128, T=32, V=4, pad=True)
+    assert np.array(P.gemv_R(Ar, list(xr), stp), np.float32).tobytes() == loopnest.gemv_f32(Ar, xr, stp).tobytes()
     A = rng.normal(0, 1, (M, N)).astype(np.float32)
     c1 = np.array(P.gemv_R(A, list(x), st), np.float32)
     c2 = loopnest.gemv_f32(A, x, st)
