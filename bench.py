@@ -562,6 +562,113 @@ def gemm_workload(args, device, dist):
                  kern, roof, clk, 3 * args.steps)
 
 
+def batched_workload(args, device, dist):
+    """4096 dots + 512 GEMVs, uneven sizes (seed 3), forward and backward: the
+    batched persistent launch against one launch per instance (eager and under
+    a CUDA graph). value = per-launch (eager) time / batched time."""
+    import math
+
+    import torch
+
+    from paper_1710_08332_gb300 import tune
+    from synth import generator
+    from synth import workloads as W
+
+    dl, rows, cols = W.batched_shapes()
+    dots, gemvs = dl.tolist(), list(zip(rows.tolist(), cols.tolist()))
+
+    def make_inputs(b):
+        g = generator(3, device)
+        xs = torch.rand(b.xs_len, generator=g, device=device).mul_(2).sub_(1)
+        ys = torch.rand(b.xs_len, generator=g, device=device).mul_(2).sub_(1)
+        As = torch.randn(b.as_len, generator=g, device=device)
+        for i, (_, n) in enumerate(b.gemv_shapes):
+            b.a_view(As, i).mul_(1.0 / math.sqrt(n))
+        gx = torch.rand(b.gx_len, generator=g, device=device).mul_(2).sub_(1)
+        dot_g = torch.rand(len(b.dot_lengths), generator=g, device=device).mul_(2).sub_(1)
+        gdy = torch.rand(b.gy_len, generator=g, device=device).mul_(2).sub_(1)
+        return xs, ys, As, gx, dot_g, gdy
+
+    b, tune_ms = tune.tune_batch(dots, gemvs, make_inputs)
+    xs, ys, As, gx, dot_g, gdy = make_inputs(b)
+    dot_out = torch.empty(len(dots), device=device)
+    gy = torch.empty(b.gy_len, device=device)
+    dxs, dys, dAs, dgx = torch.empty_like(xs), torch.empty_like(ys), torch.empty_like(As), torch.empty_like(gx)
+    pl_ws = b.per_launch_workspace()
+    pl_bws = b.per_launch_bwd_workspaces()
+    stream = torch.cuda.current_stream(device)
+
+    def graph_of(fn):
+        s = torch.cuda.Stream(device)
+        s.wait_stream(stream)
+        with torch.cuda.stream(s):
+            fn()
+        stream.wait_stream(s)
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            fn()
+        return gr
+
+    fwd_b = lambda: b.forward(xs, ys, dot_out, As, gx, gy)
+    bwd_b = lambda: b.backward(xs, ys, dot_g, dxs, dys, As, gx, gdy, dAs, dgx)
+    fwd_p = lambda: b.per_launch_forward(xs, ys, dot_out, As, gx, gy, pl_ws)
+    bwd_p = lambda: b.per_launch_backward(xs, ys, dot_g, dxs, dys, As, gx, gdy, dAs, dgx, pl_bws)
+    g_fwd_b, g_bwd_b, g_fwd_p, g_bwd_p = graph_of(fwd_b), graph_of(bwd_b), graph_of(fwd_p), graph_of(bwd_p)
+
+    names = ["batched_fwd", "batched_bwd", "graph_batched_fwd", "graph_batched_bwd",
+             "per_launch_fwd", "per_launch_bwd", "graph_per_launch_fwd", "graph_per_launch_bwd"]
+    fns = [fwd_b, bwd_b, g_fwd_b.replay, g_bwd_b.replay, fwd_p, bwd_p, g_fwd_p.replay, g_bwd_p.replay]
+
+    def step(tl):
+        for name, fn in zip(names, fns):
+            fn() if tl is None else tl.call(name, fn)
+
+    per, _, clk = timed_steps(args, device, dist, names, step)
+    # subsets (forward, batched launch each): dots only and GEMVs only
+    from paper_1710_08332_gb300.batch import Batch
+    bd = Batch(dots, [], policy=b.policy)
+    bg = Batch([], gemvs, policy=b.policy)
+    sub = {}
+    for label, bb, f in (("dots", bd, lambda bb: bb.forward(xs, ys, dot_out, None, None, None)),
+                         ("gemvs", bg, lambda bb: bb.forward(None, None, None, As, gx, gy))):
+        sub[label + "_batched_fwd_us"] = round(tune.time_call(lambda: f(bb), reps=5) * 1e3, 1)
+    for label, bb, f in (("dots", bd, lambda bb: bb.per_launch_forward(xs, ys, dot_out, None, None, None, pl_ws)),
+                         ("gemvs", bg, lambda bb: bb.per_launch_forward(None, None, None, As, gx, gy, pl_ws))):
+        gr = graph_of(lambda: f(bb))
+        sub[label + "_graph_per_launch_fwd_us"] = round(tune.time_call(gr.replay, reps=5) * 1e3, 1)
+
+    n_dot = int(sum(dots))
+    mn = int(sum(m * n for m, n in gemvs))
+    fwd_bytes = 8 * n_dot + 4 * mn
+    bwd_bytes = 16 * n_dot + 8 * mn
+    hbm = peaks()[0]
+    kern = {k: {"avg_ms": round(v, 4)} for k, v in per.items()}
+    kern["batched_fwd"]["GB_s"] = round(fwd_bytes / per["batched_fwd"] / 1e6, 1)
+    kern["batched_bwd"]["GB_s"] = round(bwd_bytes / per["batched_bwd"] / 1e6, 1)
+    speed_eager = (per["per_launch_fwd"] + per["per_launch_bwd"]) / (per["batched_fwd"] + per["batched_bwd"])
+    speed_graph = (per["graph_per_launch_fwd"] + per["graph_per_launch_bwd"]) / \
+        (per["graph_batched_fwd"] + per["graph_batched_bwd"])
+    achieved = fwd_bytes / per["batched_fwd"] / 1e6
+    roof = {"bound": "hbm", "kernel": "batch_fwd_kernel (dpia_batch_forward_f32)", "achieved": round(achieved, 1),
+            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+            "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": fwd_bytes,
+            "bwd_frac": round(bwd_bytes / per["batched_bwd"] / 1e6 / hbm, 4)}
+    cfg = {"workload": "batched uneven instances: 4096 f32 dots (lengths log-uniform [256, 65536]) + 512 GEMVs "
+                       "(rows log-uniform [256, 65536], cols [256, 4096]), seed 3, packed with offsets, forward + "
+                       "backward; one persistent launch per direction vs one launch per instance",
+           "dots": len(dots), "gemvs": len(gemvs), "dot_elements": n_dot, "gemv_elements": mn,
+           "policy": b.policy.__dict__, "tuned_ms": tune_ms,
+           "l2": "inputs larger than L2 (tens of GB)"}
+    world = dist.get_world_size() if dist else 1
+    extra = {"speedup_eager": round(speed_eager, 2), "speedup_graph": round(speed_graph, 2), "subsets": sub}
+    line = _line(args, dist, round(speed_graph, 2),
+                 "x (per-launch time / batched time, forward + backward, both as CUDA graphs)",
+                 per["batched_fwd"] + per["batched_bwd"], "f32", cfg, kern, roof, clk,
+                 (2 + 2 + 2 * (len(dots) + len(gemvs)) * 2) * args.steps, extra)
+    line["higher_is_better"] = True
+    return line
+
+
 def cpu_baseline_for(workload):
     """Oracle timings for the secondary workloads (one thread, bounded samples)."""
     import numpy as np
@@ -593,6 +700,21 @@ def cpu_baseline_for(workload):
         b = 3 * 4 * hA.size
         return {"value": round(reps * b / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                 "sample": f"oracle GEMV forward + dx + dA on 1024 of the 8192 rows, {reps} reps, {dt:.1f} s"}
+    if workload == "batched":
+        dl, _, _ = W.batched_shapes()
+        g = torch_gen = None
+        import torch
+
+        lens = dl.tolist()[:64]
+        reps = 0
+        t0 = time.perf_counter()
+        xs = [torch.rand(n) for n in lens]
+        t0 = time.perf_counter()
+        for x in xs:
+            loopnest.dot_f32(x.numpy(), x.numpy(), P.Strategy(s=8192, T=256, V=4, second="tree", T2=256, pad=True))
+        dt = time.perf_counter() - t0
+        return {"value": round(8 * sum(lens) / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                "sample": f"oracle dots of the first 64 batch instances ({sum(lens)} elements), {dt:.2f} s"}
     if workload == "gemm":
         A, B, _ = W.gemm("cpu", M=64)
         rows = np.arange(64)
@@ -729,9 +851,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["bandwidth", "dot", "gemv", "gemm"], default="bandwidth",
+    ap.add_argument("--workload", choices=["bandwidth", "dot", "gemv", "gemm", "batched"], default="bandwidth",
                     help="bandwidth (default: the headline step); dot (n=2^20, split 8192), gemv (8192^2 "
-                         "forward + backward), gemm (4096^3 BF16 forward + backward, FP32 fold forward)")
+                         "forward + backward), gemm (4096^3 BF16 forward + backward, FP32 fold forward), batched "
+                         "(4096 dots + 512 GEMVs of uneven sizes, one launch vs one launch per instance)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the split autotuner; use the default strategy (split 16384, tree second level)")
@@ -762,7 +885,8 @@ def main(argv=None):
     if args.workload == "bandwidth":
         line = bandwidth_workload(args, device, dist)
     else:
-        line = {"dot": dot_workload, "gemv": gemv_workload, "gemm": gemm_workload}[args.workload](args, device, dist)
+        line = {"dot": dot_workload, "gemv": gemv_workload, "gemm": gemm_workload,
+                "batched": batched_workload}[args.workload](args, device, dist)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             if args.workload == "bandwidth":

@@ -196,7 +196,7 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
       g.tstride = g.Rc * V;
     }
     g.Rs = in.row_split;
-    g.Cr = (in.M + g.Rs - 1) / g.Rs;
+    g.Cr = in.M > 0 ? (in.M + g.Rs - 1) / g.Rs : 1;  // no rows: one empty chunk, so dx = +0 is written
     g.Npad = round_up(in.N, 4);
     g.part_base = h.dx_partials;
     g.tiles = (int32_t)((in.N + 4 * (int64_t)T - 1) / (4 * (int64_t)T));

@@ -113,3 +113,42 @@ def tune_reduce(op: str, x, y=None, candidates=None, reps: int = 10, use_cache: 
 def _label(st: ReduceStrategy) -> str:
     return (f"{st.map_level}:s{st.split}:T{st.threads}:V{st.vec}:{st.second}"
             f"{st.threads2 if st.second == 'tree' else ''}")
+
+
+def batch_candidates():
+    """Policies the batch autotuner tries (block size, dot split cap, GEMV row
+    split cap, backward row split)."""
+    from .batch import BatchPolicy
+
+    out = []
+    for T in (256, 512):
+        for cap in (4096, 8192, 16384):
+            out.append(BatchPolicy(threads=T, dot_split_cap=cap, gemv_split_cap=4096, row_split=256))
+    out.append(BatchPolicy(threads=256, dot_split_cap=8192, gemv_split_cap=4096, row_split=128))
+    out.append(BatchPolicy(threads=256, dot_split_cap=8192, gemv_split_cap=4096, row_split=512))
+    return out
+
+
+def tune_batch(dot_lengths, gemv_shapes, make_inputs, candidates=None, reps: int = 3):
+    """Fastest policy for a batch: each candidate is planned and its forward and
+    backward launches are timed on the data make_inputs(batch) returns
+    (xs, ys, As, gx, dot_g, gdy). Returns (Batch, {label: ms})."""
+    from .batch import Batch
+
+    timings, best, best_ms = {}, None, float("inf")
+    for pol in candidates or batch_candidates():
+        b = Batch(dot_lengths, gemv_shapes, policy=pol)
+        xs, ys, As, gx, dot_g, gdy = make_inputs(b)
+        dot_out = torch.empty(max(len(dot_lengths), 1), device=b.device)
+        gy = torch.empty(b.gy_len, device=b.device)
+        dxs, dys = torch.empty_like(xs), torch.empty_like(ys)
+        dAs, dgx = torch.empty_like(As), torch.empty_like(gx)
+        ms = time_call(lambda: (b.forward(xs, ys, dot_out, As, gx, gy),
+                                b.backward(xs, ys, dot_g, dxs, dys, As, gx, gdy, dAs, dgx)), reps=reps, warmup=1)
+        label = f"T{pol.threads}:dotcap{pol.dot_split_cap}:rs{pol.row_split}"
+        timings[label] = ms
+        del xs, ys, As, gx, dot_g, gdy, dxs, dys, dAs, dgx
+        if ms < best_ms:
+            best, best_ms = pol, ms
+        torch.cuda.empty_cache()
+    return Batch(dot_lengths, gemv_shapes, policy=best), timings
