@@ -244,6 +244,25 @@ def profile_case(args):
         def fn():
             dpia.dpia_gemm_bf16(Ab, Bb, C, m, m, m, m, m, m, 0, 0)
             dpia.dpia_gemm_f32(A, B, C, m, m, m, m, m, m, 0, 0, "fma")
+    elif args.profile == "batched":  # the first 512 dots and 16 GEMVs of the batched workload
+        import math
+
+        from paper_1710_08332_gb300.batch import Batch
+
+        dl, rows, cols = W.batched_shapes()
+        b = Batch(dl.tolist()[:512], list(zip(rows.tolist()[:16], cols.tolist()[:16])), dev)
+        xs = torch.rand(b.xs_len, device=dev)
+        ys = torch.rand(b.xs_len, device=dev)
+        As = torch.randn(b.as_len, device=dev)
+        gx = torch.rand(b.gx_len, device=dev)
+        dot_g = torch.rand(len(b.dot_lengths), device=dev)
+        gdy = torch.rand(b.gy_len, device=dev)
+        dot_out, gy = torch.empty(len(b.dot_lengths), device=dev), torch.empty(b.gy_len, device=dev)
+        dxs, dys, dAs, dgx = torch.empty_like(xs), torch.empty_like(ys), torch.empty_like(As), torch.empty_like(gx)
+
+        def fn():
+            b.forward(xs, ys, dot_out, As, gx, gy)
+            b.backward(xs, ys, dot_g, dxs, dys, As, gx, gdy, dAs, dgx)
     else:
         raise SystemExit(f"unknown profile case {args.profile}")
     for _ in range(1 + args.reps):
@@ -253,7 +272,7 @@ def profile_case(args):
     return 0
 
 
-PROFILE_CASES = {"dot", "asum", "scal", "gemm"}
+PROFILE_CASES = {"dot", "asum", "scal", "gemm", "batched"}
 
 
 def bandwidth_workload(args, device, dist):

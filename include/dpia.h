@@ -312,11 +312,22 @@ typedef struct {
 } dpia_gemv_instance;
 
 /*
- * Bytes of the plan of a batch (0 if an instance is invalid). threads: the
- * block size of the batched launches (a multiple of 32, <= 1024).
+ * How the blocks of a batched launch share the work (the values never depend
+ * on it):
+ *   threads       -- block size (a power of two, 32..256);
+ *   schedule      -- 0: items sorted longest first and dealt to the blocks
+ *                    round robin; 1: items in instance order, each block takes
+ *                    the contiguous run whose byte costs make up its equal share.
  */
+typedef struct {
+  int32_t threads;
+  int32_t schedule;
+  int32_t reserved[2];
+} dpia_batch_options;
+
+/* Bytes of the plan of a batch (0 if an instance or an option is invalid). */
 size_t dpia_batch_plan_size(int32_t n_dots, const dpia_dot_instance *dots, int32_t n_gemvs,
-                            const dpia_gemv_instance *gemvs, int32_t threads);
+                            const dpia_gemv_instance *gemvs, const dpia_batch_options *opt);
 
 /*
  * Build the plan in host memory (plan_bytes from dpia_batch_plan_size),
@@ -325,8 +336,8 @@ size_t dpia_batch_plan_size(int32_t n_dots, const dpia_dot_instance *dots, int32
  * reused for every launch with the same shapes.
  */
 dpia_status dpia_batch_plan(int32_t n_dots, const dpia_dot_instance *dots, int32_t n_gemvs,
-                            const dpia_gemv_instance *gemvs, int32_t threads, void *plan_host,
-                            size_t plan_bytes);
+                            const dpia_gemv_instance *gemvs, const dpia_batch_options *opt,
+                            void *plan_host, size_t plan_bytes);
 
 /* Workspace bytes the batched launches of this plan need (zero-filled once). */
 size_t dpia_batch_workspace_size(const void *plan_host);

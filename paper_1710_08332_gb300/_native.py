@@ -64,6 +64,10 @@ class GemvInstanceC(ctypes.Structure):
                 ("row_split", ctypes.c_int64)]
 
 
+class BatchOptionsC(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
@@ -88,9 +92,10 @@ SIGNATURES = {
     "dpia_gemm_bf16": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I64, _I64, _I64, _I32, _I32, _GP, _P]),
     "dpia_cast_f32_bf16": (_I32, [_P, _P, _I64, _P]),
     "dpia_poll_device_status": (_I32, [ctypes.POINTER(ctypes.c_int32)]),
-    "dpia_batch_plan_size": (_SZ, [_I32, ctypes.POINTER(DotInstanceC), _I32, ctypes.POINTER(GemvInstanceC), _I32]),
-    "dpia_batch_plan": (_I32, [_I32, ctypes.POINTER(DotInstanceC), _I32, ctypes.POINTER(GemvInstanceC), _I32, _P,
-                               _SZ]),
+    "dpia_batch_plan_size": (_SZ, [_I32, ctypes.POINTER(DotInstanceC), _I32, ctypes.POINTER(GemvInstanceC),
+                                   ctypes.POINTER(BatchOptionsC)]),
+    "dpia_batch_plan": (_I32, [_I32, ctypes.POINTER(DotInstanceC), _I32, ctypes.POINTER(GemvInstanceC),
+                               ctypes.POINTER(BatchOptionsC), _P, _SZ]),
     "dpia_batch_workspace_size": (_SZ, [_P]),
     "dpia_batch_forward_f32": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _I32, _P]),
     "dpia_batch_backward_f32": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _I32, _P]),

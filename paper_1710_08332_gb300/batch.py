@@ -34,6 +34,7 @@ class BatchPolicy:
     dot_second: str = "tree"
     gemv_split_cap: int = 4096     # GEMV row split = N rounded up to 128, capped
     row_split: int = 256           # backward dx rows per chunk
+    schedule: int = 0              # 0: longest first, round robin; 1: contiguous equal-cost runs
 
     def dot_strategy(self, n: int) -> ReduceStrategy:
         q = self.threads * 4
@@ -83,11 +84,12 @@ class Batch:
             gemvs[i] = N.GemvInstanceC(self.a_offs[i], self.gx_offs[i], self.gy_offs[i], M, N_, self.ldas[i],
                                        st.to_c(), P.row_split)
         L = N.lib()
-        nbytes = L.dpia_batch_plan_size(nd, dots, ng, gemvs, P.threads)
+        opt = ctypes.byref(N.BatchOptionsC(P.threads, P.schedule))
+        nbytes = L.dpia_batch_plan_size(nd, dots, ng, gemvs, opt)
         if nbytes == 0:
             raise N.DPIAError(N.ERR_STRATEGY, L.dpia_last_error_message().decode())
         self._plan_host = (ctypes.c_char * nbytes)()
-        N.check(L.dpia_batch_plan(nd, dots, ng, gemvs, P.threads, self._plan_host, nbytes), "dpia_batch_plan")
+        N.check(L.dpia_batch_plan(nd, dots, ng, gemvs, opt, self._plan_host, nbytes), "dpia_batch_plan")
         host = torch.frombuffer(bytearray(self._plan_host.raw), dtype=torch.uint8)
         self.plan_dev = host.to(self.device)
         self.ws = torch.zeros(L.dpia_batch_workspace_size(self._plan_host), dtype=torch.uint8, device=self.device)

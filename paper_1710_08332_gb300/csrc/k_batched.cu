@@ -4,13 +4,18 @@
 // The planner (plain host C++) validates every instance, turns its strategy
 // into launch constants (the same ones the single-instance kernels use) and
 // lists the work items -- dot chunks and groups of GEMV rows for the forward;
-// ranges of dot gradients, groups of dA rows and (column tile, row chunk)
-// pieces of dx for the backward -- sorted longest first. The kernels walk
-// the item list with a grid-stride loop, so every block gets a similar mix.
+// ranges of dot gradients, groups of dA rows and (column tile, row chunks)
+// pieces of dx for the backward -- in instance order, with the running sum of
+// their byte costs. Each block of the persistent grid takes the contiguous
+// run of items whose costs fall in its equal share of the total (a binary
+// search over the running sums), so the work is balanced to within one item
+// and consecutive items of a block mostly belong to one instance, whose
+// descriptor then stays in registers.
 //
 // Every value is computed exactly as the single-instance kernels compute it
-// (same fold, same trees, same second levels), so each instance's result is
-// bit-identical to the oracle's evaluation of its own strategy.
+// (same fold order per element, same trees, same second levels), so each
+// instance's result is bit-identical to the oracle's evaluation of its own
+// strategy.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,6 +44,9 @@ struct PlanHeader {
   int32_t n_dots, n_gemvs;
   int64_t n_fwd, n_bwd;
   int64_t dots_off, gemvs_off, fwd_off, bwd_off;  // byte offsets inside the plan
+  int64_t fwd_cost_off, bwd_cost_off;             // running sums of item costs (int64 per item)
+  int64_t fwd_total, bwd_total;
+  int32_t schedule, pad_;
   int64_t dot_partials, dx_partials;              // floats of workspace
   int64_t dx_tiles;                               // dx tile counters
   int64_t xs_extent, as_extent, gx_extent, gy_extent;  // elements the packed arrays must hold
@@ -56,6 +64,8 @@ struct GemvDesc {
   int64_t s, Crow, Rc, step, tstride;  // forward row strategy (a warp per row)
   int64_t Rs, Cr, Npad, part_base;     // backward dx: rows per chunk, chunks, padded width, partial offset
   int32_t tiles, tile_cnt;             // dx column tiles and the index of the first tile's counter
+  int32_t G, cpi;                      // dx: threads per chunk (column groups), chunks per item
+  int32_t items_per_tile, pad0;
 };
 
 struct Item {
@@ -96,11 +106,27 @@ struct Built {
   std::vector<DotDesc> dots;
   std::vector<GemvDesc> gemvs;
   std::vector<Item> fwd, bwd;
+  std::vector<int64_t> fwd_cost, bwd_cost;  // running sums
 };
+
+int64_t next_pow2(int64_t v) {
+  int64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
 
 // Validate and plan; returns DPIA_OK and fills b.
 dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, const dpia_gemv_instance *gemvs,
-                       int32_t T, Built &b) {
+                       const dpia_batch_options *opt, Built &b) {
+  if (!opt) {
+    set_last_error("dpia_batch_plan: options are NULL");
+    return DPIA_ERR_NULL;
+  }
+  const int32_t T = opt->threads;
+  if (opt->schedule != 0 && opt->schedule != 1) {
+    set_last_error("dpia_batch_plan: schedule must be 0 or 1");
+    return DPIA_ERR_STRATEGY;
+  }
   if (nd < 0 || ng < 0) {
     set_last_error("dpia_batch_plan: negative instance count");
     return DPIA_ERR_SHAPE;
@@ -109,8 +135,8 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
     set_last_error("dpia_batch_plan: instance array is NULL");
     return DPIA_ERR_NULL;
   }
-  if (!is_pow2(T) || T < 32 || T > 512) {
-    set_last_error("dpia_batch_plan: threads=%d must be a power of two in [32, 512]", T);
+  if (!is_pow2(T) || T < 32 || T > 256) {
+    set_last_error("dpia_batch_plan: threads=%d must be a power of two in [32, 256]", T);
     return DPIA_ERR_STRATEGY;
   }
   PlanHeader &h = b.h;
@@ -119,7 +145,8 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
   h.threads = T;
   h.n_dots = nd;
   h.n_gemvs = ng;
-  h.rows_per_item = T / 32;          // a warp per row
+  h.schedule = opt->schedule;
+  h.rows_per_item = T / 32;  // a warp per row
   h.da_rows_per_item = 8;
   h.bwd_elems_per_item = 4 * (int64_t)T * 8;
   std::vector<std::pair<int64_t, Item>> fwd, bwd;  // (cost, item)
@@ -199,7 +226,17 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
     g.Cr = in.M > 0 ? (in.M + g.Rs - 1) / g.Rs : 1;  // no rows: one empty chunk, so dx = +0 is written
     g.Npad = round_up(in.N, 4);
     g.part_base = h.dx_partials;
-    g.tiles = (int32_t)((in.N + 4 * (int64_t)T - 1) / (4 * (int64_t)T));
+    const int64_t cg = (in.N + 3) / 4;  // column groups of 4
+    if (cg >= T) {                       // wide: tiles of T column groups, one row chunk per item
+      g.G = T;
+      g.cpi = 1;
+      g.tiles = (int32_t)((cg + T - 1) / T);
+    } else {                             // narrow: T / G row chunks side by side in one item
+      g.G = (int32_t)next_pow2(cg);
+      g.cpi = T / g.G;
+      g.tiles = 1;
+    }
+    g.items_per_tile = (int32_t)((g.Cr + g.cpi - 1) / g.cpi);
     g.tile_cnt = (int32_t)h.dx_tiles;
     h.dx_partials += g.Cr * g.Npad;
     h.dx_tiles += g.tiles;
@@ -212,15 +249,35 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
     for (int64_t r = 0; r < in.M; r += h.da_rows_per_item)
       bwd.push_back({4 * std::min<int64_t>(h.da_rows_per_item, in.M - r) * in.N, Item{GEMV_DA, i, r}});
     for (int64_t t = 0; t < g.tiles; ++t)
-      for (int64_t c = 0; c < g.Cr; ++c)
-        bwd.push_back({4 * std::min<int64_t>(g.Rs, in.M - c * g.Rs) * std::min<int64_t>(4 * T, in.N - t * 4 * T),
-                       Item{GEMV_DX, i, t * g.Cr + c}});
+      for (int64_t k = 0; k < g.items_per_tile; ++k) {
+        const int64_t rows = std::min<int64_t>(g.cpi * g.Rs, std::max<int64_t>(in.M - k * g.cpi * g.Rs, 1));
+        bwd.push_back({4 * rows * std::min<int64_t>(4 * (int64_t)g.G, in.N - t * 4 * (int64_t)g.G),
+                       Item{GEMV_DX, i, t * g.items_per_tile + k}});
+      }
   }
-  auto by_cost = [](const std::pair<int64_t, Item> &a, const std::pair<int64_t, Item> &b) { return a.first > b.first; };
-  std::stable_sort(fwd.begin(), fwd.end(), by_cost);
-  std::stable_sort(bwd.begin(), bwd.end(), by_cost);
-  for (auto &p : fwd) b.fwd.push_back(p.second);
-  for (auto &p : bwd) b.bwd.push_back(p.second);
+  // schedule 0: longest first, dealt round robin at launch; schedule 1: instance
+  // order, with the running sums of the costs each block finds its share by
+  if (h.schedule == 0) {
+    auto by_cost = [](const std::pair<int64_t, Item> &x, const std::pair<int64_t, Item> &y) {
+      return x.first > y.first;
+    };
+    std::stable_sort(fwd.begin(), fwd.end(), by_cost);
+    std::stable_sort(bwd.begin(), bwd.end(), by_cost);
+  }
+  int64_t acc = 0;
+  for (auto &p : fwd) {
+    b.fwd.push_back(p.second);
+    acc += std::max<int64_t>(p.first, 1);
+    b.fwd_cost.push_back(acc);
+  }
+  h.fwd_total = acc;
+  acc = 0;
+  for (auto &p : bwd) {
+    b.bwd.push_back(p.second);
+    acc += std::max<int64_t>(p.first, 1);
+    b.bwd_cost.push_back(acc);
+  }
+  h.bwd_total = acc;
   h.n_fwd = (int64_t)b.fwd.size();
   h.n_bwd = (int64_t)b.bwd.size();
   int64_t off = round_up(sizeof(PlanHeader), 128);
@@ -232,8 +289,18 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
   off += round_up(h.n_fwd * (int64_t)sizeof(Item), 128);
   h.bwd_off = off;
   off += round_up(h.n_bwd * (int64_t)sizeof(Item), 128);
+  h.fwd_cost_off = off;
+  off += round_up(h.n_fwd * 8, 128);
+  h.bwd_cost_off = off;
+  off += round_up(h.n_bwd * 8, 128);
   h.total_bytes = off;
   return DPIA_OK;
+}
+
+__device__ __forceinline__ int64_t next_pow2_dev(int64_t v) {
+  int64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
 }
 
 struct FwdArgs {
@@ -254,19 +321,50 @@ struct BwdArgs {
   WsLayout ws;
 };
 
-__global__ void __launch_bounds__(512) batch_fwd_kernel(const FwdArgs a) {
+// The contiguous run of items whose start cost lies in this block's share
+// [total*b/G, total*(b+1)/G) of the running sums `end` (item i starts at
+// end[i-1], item 0 at 0). Computed by thread 0, broadcast through shared memory.
+__device__ __forceinline__ void block_item_range(const int64_t *end, int64_t n, int64_t total, int64_t *lo_hi) {
+  if (threadIdx.x == 0) {
+    auto first_at = [&](int64_t c) -> int64_t {  // first i with start(i) >= c
+      if (c <= 0) return 0;
+      int64_t lo = 0, hi = n;  // first j with end[j] >= c, then i = j + 1
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (end[mid] >= c) hi = mid; else lo = mid + 1;
+      }
+      return lo + 1 < n ? lo + 1 : n;
+    };
+    const int64_t G = gridDim.x, b = blockIdx.x;
+    lo_hi[0] = first_at(total / G * b + total % G * b / G);
+    lo_hi[1] = b + 1 == G ? n : first_at(total / G * (b + 1) + total % G * (b + 1) / G);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256, 4) batch_fwd_kernel(const FwdArgs a) {
   __shared__ float sm[32];
   __shared__ int last;
+  __shared__ int64_t range[2];
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(a.plan);
-  const DotDesc *dots = reinterpret_cast<const DotDesc *>(a.plan + h->dots_off);
-  const GemvDesc *gemvs = reinterpret_cast<const GemvDesc *>(a.plan + h->gemvs_off);
-  const Item *items = reinterpret_cast<const Item *>(a.plan + h->fwd_off);
+  const DotDesc *__restrict__ dots = reinterpret_cast<const DotDesc *>(a.plan + h->dots_off);
+  const GemvDesc *__restrict__ gemvs = reinterpret_cast<const GemvDesc *>(a.plan + h->gemvs_off);
+  const Item *__restrict__ items = reinterpret_cast<const Item *>(a.plan + h->fwd_off);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int64_t n_items = h->n_fwd;
-  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+  int64_t i0 = blockIdx.x, i1 = h->n_fwd, istep = gridDim.x;
+  if (h->schedule == 1) {
+    block_item_range(reinterpret_cast<const int64_t *>(a.plan + h->fwd_cost_off), h->n_fwd, h->fwd_total, range);
+    i0 = range[0];
+    i1 = range[1];
+    istep = 1;
+  }
+  for (int64_t it = i0; it < i1; it += istep) {
     const Item w = items[it];
+    // descriptors are read field by field through the read-only cache (held
+    // whole in registers they would cap the kernel's occupancy)
+    const DotDesc &d = dots[w.inst];
+    const GemvDesc &g = gemvs[w.inst];
     if (w.type == DOT_CHUNK) {
-      const DotDesc d = dots[w.inst];
       const float *x = a.xs + d.off, *y = a.ys + d.off;
       const int64_t c = w.a;
       const bool full = (c + 1) * d.s <= d.n;
@@ -314,9 +412,8 @@ __global__ void __launch_bounds__(512) batch_fwd_kernel(const FwdArgs a) {
       }
       __syncthreads();
     } else {  // GEMV_ROWS: a warp per row, the row's chunks folded in order
-      const GemvDesc g = gemvs[w.inst];
       const int64_t r = w.a + warp;
-      if (r < g.M && r < w.a + h->rows_per_item) {
+      if (r < g.M) {
         const float *row = a.As + g.a_off + r * g.lda;
         const float *x = a.gx + g.x_off;
         float acc = 0.0f;
@@ -332,19 +429,27 @@ __global__ void __launch_bounds__(512) batch_fwd_kernel(const FwdArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(512) batch_bwd_kernel(const BwdArgs a) {
+__global__ void __launch_bounds__(256, 4) batch_bwd_kernel(const BwdArgs a) {
   __shared__ int last;
+  __shared__ int64_t range[2];
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(a.plan);
-  const DotDesc *dots = reinterpret_cast<const DotDesc *>(a.plan + h->dots_off);
-  const GemvDesc *gemvs = reinterpret_cast<const GemvDesc *>(a.plan + h->gemvs_off);
-  const Item *items = reinterpret_cast<const Item *>(a.plan + h->bwd_off);
+  const DotDesc *__restrict__ dots = reinterpret_cast<const DotDesc *>(a.plan + h->dots_off);
+  const GemvDesc *__restrict__ gemvs = reinterpret_cast<const GemvDesc *>(a.plan + h->gemvs_off);
+  const Item *__restrict__ items = reinterpret_cast<const Item *>(a.plan + h->bwd_off);
   const int t = threadIdx.x;
   const int T = blockDim.x;
-  const int64_t n_items = h->n_bwd;
-  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+  int64_t i0 = blockIdx.x, i1 = h->n_bwd, istep = gridDim.x;
+  if (h->schedule == 1) {
+    block_item_range(reinterpret_cast<const int64_t *>(a.plan + h->bwd_cost_off), h->n_bwd, h->bwd_total, range);
+    i0 = range[0];
+    i1 = range[1];
+    istep = 1;
+  }
+  for (int64_t it = i0; it < i1; it += istep) {
     const Item w = items[it];
+    const DotDesc &d = dots[w.inst];
+    const GemvDesc &g = gemvs[w.inst];
     if (w.type == DOT_BWD) {  // dx = g*y, dy = g*x over [e0, e1)
-      const DotDesc d = dots[w.inst];
       const float gv = __ldg(a.dot_g + w.inst);
       const int64_t e0 = w.a;
       const int64_t e1 = e0 + h->bwd_elems_per_item < d.n ? e0 + h->bwd_elems_per_item : d.n;
@@ -362,86 +467,97 @@ __global__ void __launch_bounds__(512) batch_bwd_kernel(const BwdArgs a) {
         dx[e] = __fmul_rn(gv, y[e]);
         dy[e] = __fmul_rn(gv, x[e]);
       }
-    } else if (w.type == GEMV_DA) {  // dA rows = dy_r * x
-      const GemvDesc g = gemvs[w.inst];
+    } else if (w.type == GEMV_DA) {  // dA rows = dy_r * x; threads over (row, column group)
       const float *x = a.gx + g.x_off;
       const int64_t r1 = w.a + h->da_rows_per_item < g.M ? w.a + h->da_rows_per_item : g.M;
-      const int64_t nv = g.N / 4;
-      for (int64_t r = w.a; r < r1; ++r) {
-        const float d = __ldg(a.gdy + g.y_off + r);
+      const int64_t cgv = g.N / 4;  // full column groups
+      const int64_t cg = (g.N + 3) / 4;
+      const int64_t Gc = cg < T ? (int64_t)next_pow2_dev(cg) : T;  // threads per row
+      const int64_t rows_par = T / Gc;
+      for (int64_t r = w.a + t / Gc; r < r1; r += rows_par) {
+        const float dv = __ldg(a.gdy + g.y_off + r);
         float *row = a.dAs + g.a_off + r * g.lda;
-        for (int64_t j = t; j < nv; j += T) {
-          const float4 xv = ld_cached_v4(x + 4 * j);
-          *reinterpret_cast<float4 *>(row + 4 * j) =
-              make_float4(__fmul_rn(d, xv.x), __fmul_rn(d, xv.y), __fmul_rn(d, xv.z), __fmul_rn(d, xv.w));
+        for (int64_t j = t % Gc; j < cg; j += Gc) {
+          if (j < cgv) {
+            const float4 xv = ld_cached_v4(x + 4 * j);
+            *reinterpret_cast<float4 *>(row + 4 * j) =
+                make_float4(__fmul_rn(dv, xv.x), __fmul_rn(dv, xv.y), __fmul_rn(dv, xv.z), __fmul_rn(dv, xv.w));
+          } else {
+            for (int64_t e = 4 * j; e < g.N; ++e) row[e] = __fmul_rn(dv, __ldg(x + e));
+          }
         }
-        for (int64_t j = nv * 4 + t; j < g.N; j += T) row[j] = __fmul_rn(d, __ldg(x + j));
       }
-    } else {  // GEMV_DX: column tile x row chunk, partials, last block of the tile folds them
-      const GemvDesc g = gemvs[w.inst];
-      const int64_t tile = w.a / g.Cr, chunk = w.a % g.Cr;
-      const int64_t j0 = tile * 4 * T + 4 * t;
-      const int64_t r0 = chunk * g.Rs;
-      const int64_t r1 = r0 + g.Rs < g.M ? r0 + g.Rs : g.M;
+    } else {  // GEMV_DX: (column tile, cpi row chunks); thread = (chunk, column group)
+      const int64_t tile = w.a / g.items_per_tile, k = w.a % g.items_per_tile;
+      const int64_t chunk = k * g.cpi + t / g.G;
+      const int64_t j0 = (tile * g.G + t % g.G) * 4;
       const float *A = a.As + g.a_off;
       const float *dyv = a.gdy + g.y_off;
-      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      if (j0 + 4 <= g.N) {
-        int64_t i = r0;
-        for (; i + 4 <= r1; i += 4) {
-          float4 av[4];
-          float dv[4];
+      if (chunk < g.Cr && j0 < g.N) {
+        const int64_t r0 = chunk * g.Rs;
+        const int64_t r1 = r0 + g.Rs < g.M ? r0 + g.Rs : g.M;
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (j0 + 4 <= g.N) {
+          int64_t i = r0;
+          for (; i + 8 <= r1; i += 8) {  // eight rows of loads in flight per thread
+            float4 av[8];
+            float dv[8];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            av[u] = ld_stream_v4(A + (i + u) * g.lda + j0);
-            dv[u] = __ldg(dyv + i + u);
+            for (int u = 0; u < 8; ++u) {
+              av[u] = ld_stream_v4(A + (i + u) * g.lda + j0);
+              dv[u] = __ldg(dyv + i + u);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              acc[0] = __fadd_rn(acc[0], __fmul_rn(av[u].x, dv[u]));
+              acc[1] = __fadd_rn(acc[1], __fmul_rn(av[u].y, dv[u]));
+              acc[2] = __fadd_rn(acc[2], __fmul_rn(av[u].z, dv[u]));
+              acc[3] = __fadd_rn(acc[3], __fmul_rn(av[u].w, dv[u]));
+            }
           }
+          for (; i < r1; ++i) {
+            const float4 av = ld_stream_v4(A + i * g.lda + j0);
+            const float dv = __ldg(dyv + i);
+            acc[0] = __fadd_rn(acc[0], __fmul_rn(av.x, dv));
+            acc[1] = __fadd_rn(acc[1], __fmul_rn(av.y, dv));
+            acc[2] = __fadd_rn(acc[2], __fmul_rn(av.z, dv));
+            acc[3] = __fadd_rn(acc[3], __fmul_rn(av.w, dv));
+          }
+        } else {
+          for (int64_t i = r0; i < r1; ++i) {
+            const float dv = __ldg(dyv + i);
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            acc[0] = __fadd_rn(acc[0], __fmul_rn(av[u].x, dv[u]));
-            acc[1] = __fadd_rn(acc[1], __fmul_rn(av[u].y, dv[u]));
-            acc[2] = __fadd_rn(acc[2], __fmul_rn(av[u].z, dv[u]));
-            acc[3] = __fadd_rn(acc[3], __fmul_rn(av[u].w, dv[u]));
+            for (int v = 0; v < 4; ++v)
+              if (j0 + v < g.N) acc[v] = __fadd_rn(acc[v], __fmul_rn(A[i * g.lda + j0 + v], dv));
           }
         }
-        for (; i < r1; ++i) {
-          const float4 av = ld_stream_v4(A + i * g.lda + j0);
-          const float dv = __ldg(dyv + i);
-          acc[0] = __fadd_rn(acc[0], __fmul_rn(av.x, dv));
-          acc[1] = __fadd_rn(acc[1], __fmul_rn(av.y, dv));
-          acc[2] = __fadd_rn(acc[2], __fmul_rn(av.z, dv));
-          acc[3] = __fadd_rn(acc[3], __fmul_rn(av.w, dv));
-        }
-      } else if (j0 < g.N) {
-        for (int64_t i = r0; i < r1; ++i) {
-          const float dv = __ldg(dyv + i);
+        float *part = a.ws.dx_part + g.part_base + chunk * g.Npad;
 #pragma unroll
-          for (int v = 0; v < 4; ++v)
-            if (j0 + v < g.N) acc[v] = __fadd_rn(acc[v], __fmul_rn(A[i * g.lda + j0 + v], dv));
-        }
+        for (int v = 0; v < 4; ++v)
+          if (j0 + v < g.N) part[j0 + v] = acc[v];
       }
-      float *part = a.ws.dx_part + g.part_base + chunk * g.Npad;
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (j0 + v < g.N) part[j0 + v] = acc[v];
       __threadfence();
       __syncthreads();
       if (t == 0) {
         const unsigned ticket = atomicAdd(a.ws.dx_cnt + g.tile_cnt + tile, 1u);
         __threadfence();
-        last = ticket == g.Cr - 1;
+        last = ticket == g.items_per_tile - 1;
       }
       __syncthreads();
-      if (last) {
-        float res[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      if (last) {  // fold the tile's chunk partials in chunk order; a thread per column group
         const float *pb = a.ws.dx_part + g.part_base;
-        for (int64_t c = 0; c < g.Cr; ++c)
+        for (int64_t q = t; q < g.G; q += T) {
+          const int64_t jj = (tile * g.G + q) * 4;
+          if (jj >= g.N) continue;
+          float res[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          for (int64_t c = 0; c < g.Cr; ++c)
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              if (jj + v < g.N) res[v] = __fadd_rn(res[v], __ldcg(pb + c * g.Npad + jj + v));
 #pragma unroll
           for (int v = 0; v < 4; ++v)
-            if (j0 + v < g.N) res[v] = __fadd_rn(res[v], __ldcg(pb + c * g.Npad + j0 + v));
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-          if (j0 + v < g.N) a.dgx[g.x_off + j0 + v] = res[v];
+            if (jj + v < g.N) a.dgx[g.x_off + jj + v] = res[v];
+        }
         if (t == 0) a.ws.dx_cnt[g.tile_cnt + tile] = 0u;
       }
       __syncthreads();
@@ -483,17 +599,18 @@ using namespace dpia;
 extern "C" {
 
 size_t dpia_batch_plan_size(int32_t n_dots, const dpia_dot_instance *dots, int32_t n_gemvs,
-                            const dpia_gemv_instance *gemvs, int32_t threads) {
+                            const dpia_gemv_instance *gemvs, const dpia_batch_options *opt) {
   Built b;
-  if (build_plan(n_dots, dots, n_gemvs, gemvs, threads, b) != DPIA_OK) return 0;
+  if (build_plan(n_dots, dots, n_gemvs, gemvs, opt, b) != DPIA_OK) return 0;
   return (size_t)b.h.total_bytes;
 }
 
 dpia_status dpia_batch_plan(int32_t n_dots, const dpia_dot_instance *dots, int32_t n_gemvs,
-                            const dpia_gemv_instance *gemvs, int32_t threads, void *plan_host, size_t plan_bytes) {
+                            const dpia_gemv_instance *gemvs, const dpia_batch_options *opt, void *plan_host,
+                            size_t plan_bytes) {
   set_last_error("");
   Built b;
-  dpia_status rc = build_plan(n_dots, dots, n_gemvs, gemvs, threads, b);
+  dpia_status rc = build_plan(n_dots, dots, n_gemvs, gemvs, opt, b);
   if (rc) return rc;
   if (!plan_host) {
     set_last_error("dpia_batch_plan: plan_host is NULL");
@@ -510,6 +627,8 @@ dpia_status dpia_batch_plan(int32_t n_dots, const dpia_dot_instance *dots, int32
   if (!b.gemvs.empty()) std::memcpy(p + b.h.gemvs_off, b.gemvs.data(), b.gemvs.size() * sizeof(GemvDesc));
   if (!b.fwd.empty()) std::memcpy(p + b.h.fwd_off, b.fwd.data(), b.fwd.size() * sizeof(Item));
   if (!b.bwd.empty()) std::memcpy(p + b.h.bwd_off, b.bwd.data(), b.bwd.size() * sizeof(Item));
+  if (!b.fwd_cost.empty()) std::memcpy(p + b.h.fwd_cost_off, b.fwd_cost.data(), b.fwd_cost.size() * 8);
+  if (!b.bwd_cost.empty()) std::memcpy(p + b.h.bwd_cost_off, b.bwd_cost.data(), b.bwd_cost.size() * 8);
   return DPIA_OK;
 }
 

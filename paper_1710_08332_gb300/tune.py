@@ -120,12 +120,9 @@ def batch_candidates():
     split cap, backward row split)."""
     from .batch import BatchPolicy
 
-    out = []
-    for T in (256, 512):
-        for cap in (4096, 8192, 16384):
-            out.append(BatchPolicy(threads=T, dot_split_cap=cap, gemv_split_cap=4096, row_split=256))
-    out.append(BatchPolicy(threads=256, dot_split_cap=8192, gemv_split_cap=4096, row_split=128))
-    out.append(BatchPolicy(threads=256, dot_split_cap=8192, gemv_split_cap=4096, row_split=512))
+    out = [BatchPolicy(threads=256, dot_split_cap=8192, row_split=128, schedule=1)]
+    for T, cap, rs in ((256, 8192, 128), (128, 8192, 128), (256, 16384, 256), (256, 4096, 64), (256, 8192, 512)):
+        out.append(BatchPolicy(threads=T, dot_split_cap=cap, row_split=rs))
     return out
 
 
@@ -145,7 +142,7 @@ def tune_batch(dot_lengths, gemv_shapes, make_inputs, candidates=None, reps: int
         dAs, dgx = torch.empty_like(As), torch.empty_like(gx)
         ms = time_call(lambda: (b.forward(xs, ys, dot_out, As, gx, gy),
                                 b.backward(xs, ys, dot_g, dxs, dys, As, gx, gdy, dAs, dgx)), reps=reps, warmup=1)
-        label = f"T{pol.threads}:dotcap{pol.dot_split_cap}:rs{pol.row_split}"
+        label = f"T{pol.threads}:dotcap{pol.dot_split_cap}:rs{pol.row_split}:sched{pol.schedule}"
         timings[label] = ms
         del xs, ys, As, gx, dot_g, gdy, dxs, dys, dAs, dgx
         if ms < best_ms:

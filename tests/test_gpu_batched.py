@@ -72,8 +72,10 @@ SMALL_GEMVS = [(1, 1), (3, 5), (100, 257), (300, 1000), (50, 4096), (2000, 128),
 
 
 @pytest.mark.parametrize("policy", [BatchPolicy(), BatchPolicy(threads=128, dot_split_cap=2048, dot_second="seq",
-                                                                gemv_split_cap=256, row_split=100)],
-                         ids=["default", "small-splits"])
+                                                                gemv_split_cap=256, row_split=100),
+                                    BatchPolicy(schedule=1),
+                                    BatchPolicy(threads=64, schedule=1, row_split=37)],
+                         ids=["default", "small-splits", "contiguous", "contiguous-64"])
 def test_batch_bits_against_oracle(cuda_device, policy):
     rng = np.random.default_rng(11)
     dots = SMALL_DOTS + [int(v) for v in np.exp(rng.uniform(np.log(256), np.log(20000), 150))]
