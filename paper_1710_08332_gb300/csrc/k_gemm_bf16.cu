@@ -69,6 +69,7 @@ struct Params {
   int64_t M, N, K, ldc;
   int BN, tiles_n, num_tiles, k_blocks;
   int a_mn, b_mn, vec_ok;
+  int a_3d;           // MN-major A loaded as one 3-D box {64 m, 64 k, 4 m-blocks}
   uint32_t stage_tx;  // bytes the TMA loads of one stage deliver
 };
 
@@ -128,6 +129,14 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint64_t *ba
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(const CUtensorMap *map, uint64_t *bar, void *dst, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
 
@@ -246,6 +255,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         uint8_t *sb = sa + A_BYTES;
         if (!p.a_mn) {
           tma_load_2d(&tma_a, &full[stage], sa, kb * BK, tm * BM);
+        } else if (p.a_3d) {
+          tma_load_3d(&tma_a, &full[stage], sa, 0, kb * BK, tm * (BM / 64));
         } else {
 #pragma unroll
           for (int j = 0; j < BM / 64; ++j) tma_load_2d(&tma_a, &full[stage], sa + j * MN_LBO, tm * BM + 64 * j, kb * BK);
@@ -359,6 +370,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
 }
 
+// 3-D view of a row-major K x M bf16 matrix (M contiguous) as {64 m, K, M/64
+// blocks}: a box {64, 64, 4} lands in shared memory as four [64 k][64 m]
+// blocks, the MN-major layout the descriptors read, in one copy. Needs M a
+// multiple of 64 (the view never reads past a row).
+bool make_map_mn3d(CUtensorMap *map, const void *base, int64_t K, int64_t M, int64_t ld);
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -387,6 +404,19 @@ bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, in
                   CU_TENSOR_MAP_INTERLEAVE_NONE,
                   box_inner * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool make_map_mn3d(CUtensorMap *map, const void *base, int64_t K, int64_t M, int64_t ld) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {64, (cuuint64_t)K, (cuuint64_t)(M / 64)};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, 128};
+  cuuint32_t box[3] = {64, (cuuint32_t)BK, (cuuint32_t)(BM / 64)};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -431,7 +461,9 @@ cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int
   const int ctas = grid > 0 ? grid : sm_count();
   const int BN = tile_n > 0 ? tile_n : pick_bn(M, N, ctas);
   alignas(64) CUtensorMap ma, mb;
-  bool ok = transA ? make_map(&ma, A, K, M, lda, 64, BK) : make_map(&ma, A, M, K, lda, BK, BM);
+  const int a_3d = transA && M % 64 == 0;
+  bool ok = transA ? (a_3d ? make_map_mn3d(&ma, A, K, M, lda) : make_map(&ma, A, K, M, lda, 64, BK))
+                   : make_map(&ma, A, M, K, lda, BK, BM);
   ok = ok && (transB ? make_map(&mb, B, N, K, ldb, BK, BN) : make_map(&mb, B, K, N, ldb, 64, BK));
   if (!ok) return cudaErrorInvalidValue;
   Params p;
@@ -447,6 +479,7 @@ cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int
   p.a_mn = transA ? 1 : 0;
   p.b_mn = transB ? 0 : 1;
   p.vec_ok = vec_ok;
+  p.a_3d = a_3d;
   const uint32_t b_tx = p.b_mn ? (uint32_t)ceil_div(BN, 64) * (64u * BK * 2u) : (uint32_t)BN * BK * 2u;
   p.stage_tx = (uint32_t)A_BYTES + b_tx;
   int g = ctas < p.num_tiles ? ctas : p.num_tiles;
