@@ -235,6 +235,28 @@ def profile_case(args):
         fn = {"dot": lambda: dpia.dpia_dot_f32(x, y, n, st, out, ws),
               "asum": lambda: dpia.dpia_asum_f32(x, n, st, out, ws),
               "scal": lambda: dpia.dpia_scal_f32(W.SCAL_A, x, ys, n, 4)}[args.profile]
+    elif args.profile == "dot1m":  # the n = 2^20 dot: split 8192, 128 chunks, sequential second level
+        x, y = W.dot_f32(dev)
+        n = x.numel()
+        st = dpia.ReduceStrategy(split=W.DOT_SPLIT, threads=256, vec=4)
+        out = torch.empty(1, device=dev)
+        ws = torch.zeros(dpia.dpia_dot_workspace_size(n, st), dtype=torch.uint8, device=dev)
+
+        def fn():
+            dpia.dpia_dot_f32(x, y, n, st, out, ws)
+    elif args.profile == "gemv":  # GEMV 8192 x 8192 forward, dx, dA
+        A, xv, dy = W.gemv(dev)
+        M, N_ = A.shape
+        st = dpia.ReduceStrategy(split=N_, threads=128, vec=4)
+        yv = torch.empty(M, device=dev)
+        dx = torch.empty(N_, device=dev)
+        dA = torch.empty(M, N_, device=dev)
+        ws = torch.zeros(dpia.dpia_gemv_bwd_workspace_size(M, N_, 256), dtype=torch.uint8, device=dev)
+
+        def fn():
+            dpia.dpia_gemv_f32(A, M, N_, N_, xv, yv, st)
+            dpia.dpia_gemv_bwd_f32(A, M, N_, N_, xv, dy, dx, None, N_, 256, ws)
+            dpia.dpia_gemv_bwd_f32(A, M, N_, N_, xv, dy, None, dA, N_, 256, ws)
     elif args.profile == "gemm":
         m = args.n
         A, B, _ = W.gemm(dev, M=m, N=m, K=m)
@@ -272,7 +294,7 @@ def profile_case(args):
     return 0
 
 
-PROFILE_CASES = {"dot", "asum", "scal", "gemm", "batched"}
+PROFILE_CASES = {"dot", "asum", "scal", "gemm", "batched", "dot1m", "gemv"}
 
 
 def bandwidth_workload(args, device, dist):
@@ -339,6 +361,22 @@ def bandwidth_workload(args, device, dist):
         ms = tl.avg_ms(name)
         kern[name] = {"avg_us": round(ms * 1e3, 2), "algorithmic_bytes": b, "GB_s": round(b / ms / 1e6, 1)}
 
+    # the compensated (Kahan) variants of the two reductions, same strategies,
+    # timed after the step (not part of it)
+    variants = {}
+    for name, b, fn in (
+            ("dot_compensated", B_DOT, lambda st: dpia.dpia_dot_f32(x, y, n, st, out_d, ws_d)),
+            ("asum_compensated", B_ASUM, lambda st: dpia.dpia_asum_f32(x, n, st, out_a, ws_a))):
+        base = st_dot if name.startswith("dot") else st_asum
+        stk = base.with_(compensated=True)
+        need = dpia.dpia_dot_workspace_size(n, stk)
+        if need > (ws_d.numel() if name.startswith("dot") else ws_a.numel()):
+            continue
+        ms = tune.time_call(lambda: fn(stk), reps=20, warmup=3)
+        ms0 = tune.time_call(lambda: fn(base), reps=20, warmup=3)
+        variants[name] = {"avg_us": round(ms * 1e3, 2), "GB_s": round(b / ms / 1e6, 1),
+                          "plain_avg_us": round(ms0 * 1e3, 2), "time_ratio": round(ms / ms0, 3)}
+
     # end to end: pinned host inputs -> device, the three calls, results -> host
     e2e = e2e_bandwidth(args, device, dist, st_dot, st_asum, x.cpu(), y.cpu(), step_bytes)
 
@@ -367,6 +405,7 @@ def bandwidth_workload(args, device, dist):
                    "l2": "inputs larger than L2 (256 MiB per vector > 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "kernels": kern,
+        "variants": variants,
         "split_sweep_dot_ms": sweep_dot,
         "split_sweep_asum_ms": sweep_asum,
         "roofline": {"bound": "hbm", "kernel": "reduce_kernel<DotF32,SumF32,V=4,Block> (dpia_dot_f32)",
@@ -443,10 +482,16 @@ def dot_workload(args, device, dist):
     import paper_1710_08332_gb300 as dpia
     from synth import workloads as W
 
+    from paper_1710_08332_gb300 import tune
+
     x, y = W.dot_f32(device)
     xi, yi = W.dot_i32(device)
     n = x.numel()
-    st = dpia.ReduceStrategy(split=W.DOT_SPLIT, threads=256, vec=4)
+    # the workload fixes split 8192 (128 chunks), a block per chunk and the
+    # sequential second level; the block size and vector width are tuned
+    cands = [dpia.ReduceStrategy(split=W.DOT_SPLIT, threads=T, vec=V)
+             for T in (256, 512, 1024) for V in (4, 8) if T * V <= W.DOT_SPLIT and not (V == 8 and T > 512)]
+    st, sweep = tune.tune_reduce("dot", x, y, candidates=cands, reps=10, use_cache=False)
     ws = torch.zeros(dpia.dpia_dot_workspace_size(n, st), dtype=torch.uint8, device=device)
     wsi = torch.zeros_like(ws)
     out = torch.empty(1, device=device)
@@ -471,6 +516,7 @@ def dot_workload(args, device, dist):
             "note": "8 MiB per launch: launch latency and the 128-partial sequential second level dominate"}
     cfg = {"workload": "dot f32 and int32, n=2^20, U[-1,1) / U{-100..100} seed 0, split 8192 (128 chunks), "
                        "block per chunk, sequential second level", "n": n, "strategy": st.as_dict(),
+           "tuned_ms": sweep,
            "l2": "flushed before every step (256 MiB read), outside the kernel events"}
     return _line(args, dist, round(world * 2 * b / (step_ms / 1e3) / 1e9, 1), "GB/s", step_ms, "f32",
                  cfg, kern, roof, clk, 2 * args.steps)

@@ -342,8 +342,11 @@ __device__ __forceinline__ void block_item_range(const int64_t *end, int64_t n, 
   __syncthreads();
 }
 
+constexpr int kSeqStage = 1024;
+
 __global__ void __launch_bounds__(256, 4) batch_fwd_kernel(const FwdArgs a) {
   __shared__ float sm[32];
+  __shared__ float stage[kSeqStage];
   __shared__ int last;
   __shared__ int64_t range[2];
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(a.plan);
@@ -382,17 +385,14 @@ __global__ void __launch_bounds__(256, 4) batch_fwd_kernel(const FwdArgs a) {
       if (last) {  // this block finished the instance's last chunk: second level
         const float *part = a.ws.dot_part + d.part_base;
         float res = 0.0f;
-        if (!d.second_tree) {
-          if (t == 0) {
-            int64_t k = 0;
-            for (; k + 8 <= d.C; k += 8) {
-              float b8[8];
-#pragma unroll
-              for (int u = 0; u < 8; ++u) b8[u] = __ldcg(part + k + u);
-#pragma unroll
-              for (int u = 0; u < 8; ++u) res = __fadd_rn(res, b8[u]);
-            }
-            for (; k < d.C; ++k) res = __fadd_rn(res, __ldcg(part + k));
+        if (!d.second_tree) {  // stage the partials with one parallel load, fold them in order
+          for (int64_t k0 = 0; k0 < d.C; k0 += kSeqStage) {
+            const int cnt = d.C - k0 < kSeqStage ? (int)(d.C - k0) : kSeqStage;
+            for (int i = t; i < cnt; i += blockDim.x) stage[i] = __ldcg(part + k0 + i);
+            __syncthreads();
+            if (t == 0)
+              for (int i = 0; i < cnt; ++i) res = __fadd_rn(res, stage[i]);
+            __syncthreads();
           }
         } else {
           float acc = 0.0f;

@@ -25,27 +25,29 @@ __device__ __forceinline__ typename A::acc_t load_partial(const typename A::acc_
   return __ldcg(p + i);
 }
 
+// Partials staged per tile of the sequential second level.
+constexpr int kSeqTile = 2048;
+
 // Second level over the C chunk partials, run by the last block.
 template <class A>
-__device__ void second_level(const ReduceLaunch &p, typename A::acc_t *sm) {
+__device__ void second_level(const ReduceLaunch &p, typename A::acc_t *sm, typename A::acc_t *stage) {
   using acc_t = typename A::acc_t;
   const acc_t *part = static_cast<const acc_t *>(p.partials);
   acc_t res = A::zero();
   if (!p.second_tree) {
-    // left fold in chunk order from zero (the final sequential loop)
-    if (threadIdx.x == 0) {
-      acc_t acc = A::zero();
-      int64_t c = 0;
-      for (; c + 8 <= p.C; c += 8) {
-        acc_t b[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) b[u] = load_partial<A>(part, c + u);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc = A::combine(acc, b[u]);
-      }
-      for (; c < p.C; ++c) acc = A::combine(acc, load_partial<A>(part, c));
-      res = acc;
+    // left fold in chunk order from zero (the final sequential loop): the
+    // block stages a tile of partials in shared memory with one parallel load,
+    // then thread 0 folds the tile in order
+    acc_t acc = A::zero();
+    for (int64_t k0 = 0; k0 < p.C; k0 += kSeqTile) {
+      const int cnt = p.C - k0 < kSeqTile ? (int)(p.C - k0) : kSeqTile;
+      for (int i = threadIdx.x; i < cnt; i += blockDim.x) stage[i] = load_partial<A>(part, k0 + i);
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int i = 0; i < cnt; ++i) acc = A::combine(acc, stage[i]);
+      __syncthreads();
     }
+    res = acc;
   } else {
     // thread t folds partials r*T2 + t (identity past C), then the tree
     const int t = threadIdx.x;
@@ -70,6 +72,7 @@ __global__ void __launch_bounds__(max_threads_for_vec(V)) reduce_kernel(const Re
   using in_t = typename E::in_t;
   using acc_t = typename A::acc_t;
   __shared__ acc_t sm[32];
+  __shared__ acc_t stage[kSeqTile];
   __shared__ int is_last;
   const in_t *x = static_cast<const in_t *>(p.x);
   const in_t *y = static_cast<const in_t *>(p.y);
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(max_threads_for_vec(V)) reduce_kernel(const Re
     is_last = (ticket == gridDim.x - 1);
   }
   __syncthreads();
-  if (is_last) second_level<A>(p, sm);
+  if (is_last) second_level<A>(p, sm, stage);
 }
 
 template <class E, class A, int LEVEL>

@@ -1,0 +1,61 @@
+"""Host logic of bench.py's multi-rank path on the CPU: two gloo ranks, a
+barrier, and the max of the per-rank times (the whole-job time of a replica
+run). No GPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, results):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+
+    ws, r, local = bench.dist_env()
+    assert (ws, r, local) == (world, rank, rank)
+    dist = bench.dist_init("gloo")
+    bench.barrier(dist)
+    got = bench.reduce_max(dist, 10.0 + 3.5 * rank)
+    results[rank] = got
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_max_time():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        results = m.dict()
+        procs = [ctx.Process(target=_rank_main, args=(r, world, port, results)) for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+        assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+        assert dict(results) == {0: 13.5, 1: 13.5}
+
+
+def test_single_rank_identity():
+    import bench
+
+    assert bench.reduce_max(None, 4.25) == 4.25
+    bench.barrier(None)
+
+
+def test_reference_arm_prints_only_on_rank0(monkeypatch, capsys):
+    import bench
+
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"]) == 0
+    assert capsys.readouterr().out == ""
