@@ -169,6 +169,9 @@ def profile_traffic(summary: str, sources):
 
 
 REDUCE_SOURCES = ["paper_1710_08332_gb300/csrc/k_reduce.cu", "paper_1710_08332_gb300/csrc/device_common.cuh"]
+GEMV_SOURCES = ["paper_1710_08332_gb300/csrc/k_gemv.cu", "paper_1710_08332_gb300/csrc/device_common.cuh",
+                "paper_1710_08332_gb300/csrc/k_maps.cu"]
+GEMM_SOURCES = ["paper_1710_08332_gb300/csrc/k_gemm_bf16.cu"]
 
 
 # ---------------------------------------------------------------------------
@@ -555,7 +558,8 @@ def gemv_workload(args, device, dist):
     achieved = bytes_["gemv_fwd"] / per["gemv_fwd"] / 1e6
     world = dist.get_world_size() if dist else 1
     roof = {"bound": "hbm", "kernel": "gemv_kernel<SumF32,V=4,Block> (dpia_gemv_f32)", "achieved": round(achieved, 1),
-            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+            "traffic": profile_traffic("gemv_8192.md", GEMV_SOURCES),
             "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": bytes_["gemv_fwd"]}
     cfg = {"workload": "GEMV 8192x8192 f32, A ~ N(0,1/8192), x, dy ~ U[-1,1) seed 2: forward + backward (dx, dA)",
            "M": M, "N": N, "strategy": st.as_dict(), "row_split": rs,
@@ -618,7 +622,9 @@ def gemm_workload(args, device, dist):
                "bf16_bwd_dB": "dB = A^T dC, both MN-major"}
     roof = {"bound": "tensor", "kernel": f"gemm_bf16_tcgen05_kernel ({dominant}: {layouts[dominant]})",
             "achieved": round(achieved, 1), "peak": bf16_peak, "unit": "TFLOP/s", "frac": round(achieved / bf16_peak, 4),
-            "traffic": None, "peak_source": f"{src} bf16_tflops (cuBLAS burst)",
+            "traffic": profile_traffic("gemm_bf16_tcgen05_4096.md", GEMM_SOURCES),
+            "traffic_note": "DRAM bytes of one forward launch of the same kernel (ncu)",
+            "peak_source": f"{src} bf16_tflops (cuBLAS burst)",
             "frac_per_launch": {k: round(fl / v / 1e9 / bf16_peak, 4) for k, v in per.items()}}
     cfg = {"workload": "GEMM 4096^3, A, B, dC ~ N(0,1) seed 4, BF16 inputs (RNE cast outside the timed kernels), "
                        "f32 accumulate: forward and backward; FP32 fold forward timed separately",
