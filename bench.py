@@ -228,16 +228,16 @@ def profile_case(args):
     torch.cuda.set_device(dev)
     st = _default_bw_strategy()
     n = args.n
-    if args.profile in ("dot", "asum", "scal"):
+    if args.profile in ("dot", "asum", "scal", "dot_local", "asum_local"):
         x, y = W.bandwidth(dev, n=n)
         out = torch.empty(1, device=dev)
-        ws = torch.zeros(dpia.dpia_dot_workspace_size(n, st.with_(pad=n % st.split != 0)), dtype=torch.uint8,
-                         device=dev)
-        st = st.with_(pad=n % st.split != 0)
+        st = st.with_(pad=n % st.split != 0,
+                      stage="local" if args.profile.endswith("_local") else "private")
+        ws = torch.zeros(dpia.dpia_dot_workspace_size(n, st), dtype=torch.uint8, device=dev)
         ys = torch.empty_like(x)
         fn = {"dot": lambda: dpia.dpia_dot_f32(x, y, n, st, out, ws),
               "asum": lambda: dpia.dpia_asum_f32(x, n, st, out, ws),
-              "scal": lambda: dpia.dpia_scal_f32(W.SCAL_A, x, ys, n, 4)}[args.profile]
+              "scal": lambda: dpia.dpia_scal_f32(W.SCAL_A, x, ys, n, 4)}[args.profile.split("_")[0]]
     elif args.profile == "dot1m":  # the n = 2^20 dot: split 8192, 128 chunks, sequential second level
         x, y = W.dot_f32(dev)
         n = x.numel()
@@ -297,7 +297,7 @@ def profile_case(args):
     return 0
 
 
-PROFILE_CASES = {"dot", "asum", "scal", "gemm", "batched", "dot1m", "gemv"}
+PROFILE_CASES = {"dot", "asum", "scal", "dot_local", "asum_local", "gemm", "batched", "dot1m", "gemv"}
 
 
 def bandwidth_workload(args, device, dist):
@@ -347,6 +347,7 @@ def bandwidth_workload(args, device, dist):
     tl = Timeline(["scal", "asum", "dot"], stream)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    tune.hold_device(stream, 200.0 * args.steps)  # the host enqueues ahead of the device
     t0.record(stream)
     for _ in range(args.steps):
         step(tl)
@@ -380,6 +381,11 @@ def bandwidth_workload(args, device, dist):
         variants[name] = {"avg_us": round(ms * 1e3, 2), "GB_s": round(b / ms / 1e6, 1),
                           "plain_avg_us": round(ms0 * 1e3, 2), "time_ratio": round(ms / ms0, 3)}
 
+    alone = standalone_us({"scal": lambda: dpia.dpia_scal_f32(W.SCAL_A, x, ys, n, 4),
+                           "asum": lambda: dpia.dpia_asum_f32(x, n, st_asum, out_a, ws_a),
+                           "dot": lambda: dpia.dpia_dot_f32(x, y, n, st_dot, out_d, ws_d)},
+                          {"scal": B_SCAL, "asum": B_ASUM, "dot": B_DOT})
+
     # end to end: pinned host inputs -> device, the three calls, results -> host
     e2e = e2e_bandwidth(args, device, dist, st_dot, st_asum, x.cpu(), y.cpu(), step_bytes)
 
@@ -408,6 +414,9 @@ def bandwidth_workload(args, device, dist):
                    "l2": "inputs larger than L2 (256 MiB per vector > 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "kernels": kern,
+        "kernels_alone": alone,
+        "kernels_note": "in a step, asum follows scal and pays for writing back the dirty lines of scal's "
+                        "256 MiB of stores still in L2; kernels_alone times each kernel by itself",
         "variants": variants,
         "split_sweep_dot_ms": sweep_dot,
         "split_sweep_asum_ms": sweep_asum,
@@ -443,6 +452,8 @@ def timed_steps(args, device, dist, names, step, flush=None):
     (per-kernel avg ms, per-step kernel ms max over ranks, clocks)."""
     import torch
 
+    from paper_1710_08332_gb300 import tune
+
     stream = torch.cuda.current_stream(device)
     clocks = ClockSampler(device.index)
     clocks.start()
@@ -453,6 +464,9 @@ def timed_steps(args, device, dist, names, step, flush=None):
     torch.cuda.synchronize(device)
     barrier(dist, device)
     tl = Timeline(names, stream)
+    # a device-side delay lets the host enqueue the steps ahead of the device,
+    # so each event pair times its kernel and not the host's launch latency
+    tune.hold_device(stream, 200.0 * args.steps)
     for _ in range(args.steps):
         if flush:
             flush()
@@ -463,6 +477,43 @@ def timed_steps(args, device, dist, names, step, flush=None):
     per = {n: tl.avg_ms(n) for n in names}
     step_ms = reduce_max(dist, sum(per.values()), device if dist and dist.get_backend() == "nccl" else None)
     return per, step_ms, clk
+
+
+def standalone_us(calls, bytes_, flush=None, reps: int = 20):
+    """Each call timed alone (median over reps of back-to-back launches of the
+    same kernel, events on the launch stream, the host enqueuing ahead of the
+    device; with a flush, one launch per event pair and the flush before it,
+    outside the events). In a step
+    a kernel also pays for write-backs of the dirty lines its predecessor left
+    in L2; alone it does not."""
+    import torch
+
+    from paper_1710_08332_gb300 import tune
+
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, fn in calls.items():
+        if flush is None:  # back-to-back launches, several per event pair
+            t = tune.time_call(fn, reps=reps, stream=stream)
+        else:
+            for _ in range(3):
+                fn()
+            stream.synchronize()
+            tune.hold_device(stream, 200.0 * reps)
+            ev = []
+            for _ in range(reps):
+                flush()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                ev.append((a, b))
+            stream.synchronize()
+            t = sorted(a.elapsed_time(b) for a, b in ev)[reps // 2]
+        out[name] = {"median_us": round(t * 1e3, 2)}
+        if bytes_.get(name):
+            out[name]["GB_s"] = round(bytes_[name] / t / 1e6, 1)
+    return out
 
 
 def _line(args, dist, metric_value, unit, step_ms, dtype, config, kernels, roofline, clk, launches, extra=None):
@@ -506,9 +557,17 @@ def dot_workload(args, device, dist):
         for name, fn in calls:
             fn() if tl is None else tl.call(name, fn)
 
-    per, step_ms, clk = timed_steps(args, device, dist, ["dot_f32", "dot_i32"], step, L2Flush(device))
+    flush = L2Flush(device)
+    per, step_ms, clk = timed_steps(args, device, dist, ["dot_f32", "dot_i32"], step, flush)
     hbm = peaks()[0]
     b = 8 * n
+    # context on the same flushed inputs: the library dot (cuBLAS through
+    # torch.dot) and the event-to-event time of a launch that does no work
+    tiny = torch.zeros(4, device=device)
+    context = standalone_us({"dpia_dot_f32": lambda: dpia.dpia_dot_f32(x, y, n, st, out, ws),
+                             "torch_dot_cublas": lambda: torch.dot(x, y),
+                             "empty_launch_floor": lambda: dpia.dpia_scal_f32(1.0, tiny, tiny, 4)},
+                            {"dpia_dot_f32": b, "torch_dot_cublas": b}, flush=flush)
     kern = {k: {"avg_us": round(v * 1e3, 2), "algorithmic_bytes": b, "GB_s": round(b / v / 1e6, 1)}
             for k, v in per.items()}
     achieved = b / per["dot_f32"] / 1e6
@@ -516,13 +575,14 @@ def dot_workload(args, device, dist):
     roof = {"bound": "hbm", "kernel": "reduce_kernel<DotF32,SumF32,V=4,Block> (dpia_dot_f32)",
             "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
             "traffic": None, "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": b,
-            "note": "8 MiB per launch: launch latency and the 128-partial sequential second level dominate"}
+            "note": "8 MiB per launch (2^20 f32 pairs): the event-to-event time of an empty launch "
+                    "(context.empty_launch_floor) is most of it"}
     cfg = {"workload": "dot f32 and int32, n=2^20, U[-1,1) / U{-100..100} seed 0, split 8192 (128 chunks), "
                        "block per chunk, sequential second level", "n": n, "strategy": st.as_dict(),
            "tuned_ms": sweep,
            "l2": "flushed before every step (256 MiB read), outside the kernel events"}
     return _line(args, dist, round(world * 2 * b / (step_ms / 1e3) / 1e9, 1), "GB/s", step_ms, "f32",
-                 cfg, kern, roof, clk, 2 * args.steps)
+                 cfg, kern, roof, clk, 2 * args.steps, {"context": context})
 
 
 def gemv_workload(args, device, dist):
@@ -553,6 +613,10 @@ def gemv_workload(args, device, dist):
     bytes_ = {"gemv_fwd": 4 * M * N + 4 * N + 4 * M,
               "gemv_bwd_dx": 4 * M * N + 4 * M + 4 * N,
               "gemv_bwd_dA": 4 * M * N + 4 * M + 4 * N}
+    alone = standalone_us({"gemv_fwd": lambda: dpia.dpia_gemv_f32(A, M, N, N, x, y, st),
+                           "gemv_bwd_dx": lambda: dpia.dpia_gemv_bwd_f32(A, M, N, N, x, dy, dx, None, N, rs, ws),
+                           "gemv_bwd_dA": lambda: dpia.dpia_gemv_bwd_f32(A, M, N, N, x, dy, None, dA, N, rs, ws)},
+                          bytes_)
     kern = {k: {"avg_us": round(v * 1e3, 2), "algorithmic_bytes": bytes_[k], "GB_s": round(bytes_[k] / v / 1e6, 1)}
             for k, v in per.items()}
     achieved = bytes_["gemv_fwd"] / per["gemv_fwd"] / 1e6
@@ -560,13 +624,16 @@ def gemv_workload(args, device, dist):
     roof = {"bound": "hbm", "kernel": "gemv_kernel<SumF32,V=4,Block> (dpia_gemv_f32)", "achieved": round(achieved, 1),
             "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
             "traffic": profile_traffic("gemv_8192.md", GEMV_SOURCES),
-            "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": bytes_["gemv_fwd"]}
+            "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": bytes_["gemv_fwd"],
+            "frac_alone": round(alone["gemv_fwd"]["GB_s"] / hbm, 4),
+            "note": "achieved is the in-step time, which includes writing back the dirty lines of the previous "
+                    "step's dA (256 MiB of stores) still in L2; frac_alone times the kernel by itself"}
     cfg = {"workload": "GEMV 8192x8192 f32, A ~ N(0,1/8192), x, dy ~ U[-1,1) seed 2: forward + backward (dx, dA)",
            "M": M, "N": N, "strategy": st.as_dict(), "row_split": rs,
            "l2": "inputs larger than L2 (A is 256 MiB)"}
     total = sum(bytes_.values())
     return _line(args, dist, round(world * total / (step_ms / 1e3) / 1e9, 1), "GB/s", step_ms, "f32", cfg, kern,
-                 roof, clk, 3 * args.steps)
+                 roof, clk, 3 * args.steps, {"kernels_alone": alone})
 
 
 def gemm_workload(args, device, dist):
@@ -799,7 +866,10 @@ def cpu_baseline_for(workload):
 
 def e2e_bandwidth(args, device, dist, st_dot, st_asum, hx, hy, step_bytes):
     """The same step through the public API with pinned host inputs and a host
-    read of the results, copies inside the timed region."""
+    read of the results, copies inside the timed region. Steps are pipelined
+    over two device buffer sets: the host-to-device copies run on one stream,
+    the kernels on a second and the device-to-host copies on a third, so one
+    step's copies overlap the previous step's kernels and read-back."""
     import torch
 
     import paper_1710_08332_gb300 as dpia
@@ -807,42 +877,69 @@ def e2e_bandwidth(args, device, dist, st_dot, st_asum, hx, hy, step_bytes):
 
     n = hx.numel()
     px, py = hx.pin_memory(), hy.pin_memory()
-    host_scal = torch.empty(n, dtype=torch.float32).pin_memory()
-    host_res = torch.empty(2, dtype=torch.float32).pin_memory()
-    dx = torch.empty(n, device=device)
-    dy = torch.empty(n, device=device)
-    ys = torch.empty(n, device=device)
-    res = torch.empty(2, device=device)
-    ws_d = dpia.workspace(dpia.dpia_dot_workspace_size(n, st_dot), device)
-    ws_a = torch.zeros(dpia.dpia_dot_workspace_size(n, st_asum), dtype=torch.uint8, device=device)
-    stream = torch.cuda.current_stream(device)
+    host_scal = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(2)]
+    host_res = [torch.empty(2, dtype=torch.float32).pin_memory() for _ in range(2)]
+    E = lambda: torch.cuda.Event()
+    sets = []
+    for _ in range(2):
+        sets.append({"x": torch.empty(n, device=device), "y": torch.empty(n, device=device),
+                     "ys": torch.empty(n, device=device), "res": torch.empty(2, device=device),
+                     "ws_d": dpia.workspace(dpia.dpia_dot_workspace_size(n, st_dot), device),
+                     "ws_a": torch.zeros(dpia.dpia_dot_workspace_size(n, st_asum), dtype=torch.uint8,
+                                         device=device),
+                     "ev_x": E(), "ev_y": E(), "ev_s": E(), "done_comp": E(), "done_out": E()})
+    s_in, s_comp, s_out = (torch.cuda.Stream(device) for _ in range(3))
     K = max(3, min(args.steps, 20))
 
-    def one():
-        dx.copy_(px, non_blocking=True)
-        dy.copy_(py, non_blocking=True)
-        dpia.dpia_asum_f32(dx, n, st_asum, res[0:1], ws_a)
-        dpia.dpia_scal_f32(W.SCAL_A, dx, ys, n, 4)
-        dpia.dpia_dot_f32(dx, dy, n, st_dot, res[1:2], ws_d)
-        host_scal.copy_(ys, non_blocking=True)
-        host_res.copy_(res, non_blocking=True)
+    def one(i):
+        b = sets[i % 2]
+        s_in.wait_event(b["done_comp"])  # the set's previous kernels have read x and y
+        s_in.wait_event(b["done_out"])   # and its previous scal output has been read back
+        with torch.cuda.stream(s_in):
+            b["x"].copy_(px, non_blocking=True)
+            b["ev_x"].record(s_in)
+            b["y"].copy_(py, non_blocking=True)
+            b["ev_y"].record(s_in)
+        s_comp.wait_event(b["ev_x"])
+        s_comp.wait_event(b["done_out"])
+        with torch.cuda.stream(s_comp):
+            dpia.dpia_asum_f32(b["x"], n, st_asum, b["res"][0:1], b["ws_a"])
+            dpia.dpia_scal_f32(W.SCAL_A, b["x"], b["ys"], n, 4)
+            b["ev_s"].record(s_comp)
+            s_comp.wait_event(b["ev_y"])
+            dpia.dpia_dot_f32(b["x"], b["y"], n, st_dot, b["res"][1:2], b["ws_d"])
+            b["done_comp"].record(s_comp)
+        s_out.wait_event(b["ev_s"])
+        with torch.cuda.stream(s_out):
+            host_scal[i % 2].copy_(b["ys"], non_blocking=True)
+            s_out.wait_event(b["done_comp"])
+            host_res[i % 2].copy_(b["res"], non_blocking=True)
+            b["done_out"].record(s_out)
 
-    for _ in range(2):
-        one()
+    for b in sets:  # initial state: nothing in flight
+        for k in ("done_comp", "done_out"):
+            b[k].record(torch.cuda.current_stream(device))
+    for i in range(4):
+        one(i)
     torch.cuda.synchronize(device)
     barrier(dist, device)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(K):
-        one()
-    t1.record(stream)
+    t0.record(s_in)
+    for i in range(K):
+        one(i)
+    cur = torch.cuda.current_stream(device)
+    for st_ in (s_in, s_comp, s_out):
+        cur.wait_stream(st_)
+    t1.record(cur)
     t1.synchronize()
     ms = reduce_max(dist, t0.elapsed_time(t1) / K, device if dist and dist.get_backend() == "nccl" else None)
     world = dist.get_world_size() if dist else 1
     return {"value": round(world * step_bytes / (ms / 1e3) / 1e9, 1), "unit": "GB/s",
             "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * n + 8, "steps": K,
-            "ms_per_step": round(ms, 3)}
+            "ms_per_step": round(ms, 3),
+            "overlap": "two device buffer sets; host-to-device copies, kernels and device-to-host copies "
+                       "on three streams"}
 
 
 # ---------------------------------------------------------------------------

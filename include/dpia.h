@@ -80,6 +80,7 @@ typedef enum {
 
 enum { DPIA_MAP_INTERLEAVED = 0, DPIA_MAP_CONTIG = 1 };
 enum { DPIA_SECOND_SEQ = 0, DPIA_SECOND_TREE = 1 };
+enum { DPIA_STAGE_PRIVATE = 0, DPIA_STAGE_LOCAL = 1 };
 
 /*
  * Reduction strategy R (dot, asum, the rows of GEMV):
@@ -119,6 +120,18 @@ enum { DPIA_SECOND_SEQ = 0, DPIA_SECOND_TREE = 1 };
  * grid        -- blocks to launch; 0 = a persistent grid of (SMs x resident
  *                blocks per SM), capped by the work. The grid never changes
  *                the result (chunks map to blocks by a grid-stride loop).
+ * stage       -- address space the chunk passes through on its way to the
+ *                fold (Section 6.2's toPrivate / toLocal, both the identity on
+ *                values): PRIVATE loads it straight into registers; LOCAL
+ *                copies it tile by tile into shared memory with bulk
+ *                asynchronous copies (a four-stage ring per block), and the
+ *                threads fold from there. LOCAL is implemented for
+ *                dot/asum (f32, int32) with map_level BLOCK, vec 4 and the
+ *                interleaved map (otherwise DPIA_ERR_UNSUPPORTED); a ragged
+ *                last chunk is loaded directly. Every wait on a copy is
+ *                bounded (2 s); one that runs out sets the device status word
+ *                (dpia_poll_device_status), and the call's result is then
+ *                undefined while its workspace stays usable.
  */
 typedef struct {
   int64_t split;
@@ -132,6 +145,7 @@ typedef struct {
   int32_t compensated;
   int32_t pad;
   int32_t grid;
+  int32_t stage;
 } dpia_reduce_strategy;
 
 /* Version of this ABI (major*10000 + minor*100 + patch). */

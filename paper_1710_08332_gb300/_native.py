@@ -25,6 +25,7 @@ STATUS_NAMES = {OK: "OK", ERR_NULL: "NULL", ERR_SHAPE: "SHAPE", ERR_ALIGN: "ALIG
 LVL_GRID, LVL_BLOCK, LVL_WARP, LVL_THREAD, LVL_SEQ = range(5)
 MAP_INTERLEAVED, MAP_CONTIG = 0, 1
 SECOND_SEQ, SECOND_TREE = 0, 1
+STAGE_PRIVATE, STAGE_LOCAL = 0, 1
 
 
 class DPIAError(RuntimeError):
@@ -51,6 +52,7 @@ class ReduceStrategyC(ctypes.Structure):
         ("compensated", ctypes.c_int32),
         ("pad", ctypes.c_int32),
         ("grid", ctypes.c_int32),
+        ("stage", ctypes.c_int32),
     ]
 
 

@@ -70,13 +70,13 @@ int granularity(int lvl) {
 
 struct ReducePlan {
   ChunkLevel level;
-  int threads, V, Tc, T2, second_tree, compensated, grid;
+  int threads, V, Tc, T2, second_tree, compensated, grid, staged;
   int64_t s, C, Rc, step, tstride;
 };
 
 // Validate a reduction strategy for a length n and derive the launch plan.
 dpia_status plan_reduce(const char *fn, int64_t n, const dpia_reduce_strategy *st, bool allow_comp,
-                        bool allow_tree, ReducePlan *pl) {
+                        bool allow_tree, bool allow_stage, ReducePlan *pl) {
   if (!st) return fail(DPIA_ERR_NULL, "%s: strategy is NULL", fn);
   if (n < 0) return fail(DPIA_ERR_SHAPE, "%s: negative length %lld", fn, (long long)n);
   const int T = st->threads, V = st->vec;
@@ -127,6 +127,14 @@ dpia_status plan_reduce(const char *fn, int64_t n, const dpia_reduce_strategy *s
     return fail(DPIA_ERR_STRATEGY, "%s: compensated summation applies to f32 only", fn);
   if (st->pad != 0 && st->pad != 1) return fail(DPIA_ERR_STRATEGY, "%s: pad=%d", fn, st->pad);
   if (st->grid < 0) return fail(DPIA_ERR_STRATEGY, "%s: grid=%d", fn, st->grid);
+  if (st->stage != DPIA_STAGE_PRIVATE && st->stage != DPIA_STAGE_LOCAL)
+    return fail(DPIA_ERR_STRATEGY, "%s: stage=%d", fn, st->stage);
+  if (st->stage == DPIA_STAGE_LOCAL) {
+    if (!allow_stage) return fail(DPIA_ERR_UNSUPPORTED, "%s: stage=LOCAL is not implemented here", fn);
+    if (level != ChunkLevel::Block || V != 4 || st->thread_map != DPIA_MAP_INTERLEAVED)
+      return fail(DPIA_ERR_UNSUPPORTED,
+                  "%s: stage=LOCAL is implemented for map_level BLOCK, vec 4, interleaved thread map", fn);
+  }
   const int64_t s = st->split;
   if (s <= 0 || s % ((int64_t)Tc * V) != 0)
     return fail(DPIA_ERR_STRATEGY, "%s: split=%lld must be a positive multiple of %d threads x vec %d",
@@ -142,6 +150,7 @@ dpia_status plan_reduce(const char *fn, int64_t n, const dpia_reduce_strategy *s
   pl->second_tree = st->second == DPIA_SECOND_TREE;
   pl->compensated = st->compensated;
   pl->grid = st->grid;
+  pl->staged = st->stage == DPIA_STAGE_LOCAL;
   pl->s = s;
   pl->C = (n + s - 1) / s;
   pl->Rc = s / ((int64_t)Tc * V);
@@ -162,7 +171,7 @@ dpia_status run_reduce(const char *fn, ReduceOp op, const void *x, const void *y
                        void *ws, size_t ws_bytes, dpia_stream_t stream) {
   g_err.clear();
   ReducePlan pl;
-  dpia_status rc = plan_reduce(fn, n, st, op != ReduceOp::DotI32, true, &pl);
+  dpia_status rc = plan_reduce(fn, n, st, op != ReduceOp::DotI32, true, true, &pl);
   if (rc) return rc;
   if (!out) return fail(DPIA_ERR_NULL, "%s: out is NULL", fn);
   if (n > 0 && (!x || (op != ReduceOp::AsumF32 && !y))) return fail(DPIA_ERR_NULL, "%s: input is NULL", fn);
@@ -197,6 +206,7 @@ dpia_status run_reduce(const char *fn, ReduceOp op, const void *x, const void *y
   p.counter = static_cast<unsigned *>(ws);
   p.partials = static_cast<char *>(ws) + kCounterBytes;
   p.out = out;
+  if (pl.staged) return cuda_status(launch_reduce_staged(op, pl.compensated, pl.threads, pl.grid, p, s), fn);
   return cuda_status(launch_reduce(op, pl.compensated, pl.V, pl.level, pl.threads, pl.grid, p, s), fn);
 }
 
@@ -222,7 +232,7 @@ const char *dpia_last_error_message(void) { return g_err.c_str(); }
 size_t dpia_dot_workspace_size(int64_t n, const dpia_reduce_strategy *st) {
   ReducePlan pl;
   std::string saved = g_err;
-  dpia_status rc = plan_reduce("dpia_dot_workspace_size", n, st, true, true, &pl);
+  dpia_status rc = plan_reduce("dpia_dot_workspace_size", n, st, true, true, true, &pl);
   if (rc) return 0;
   g_err = saved;
   return (size_t)reduce_ws_bytes(pl);
@@ -288,7 +298,7 @@ dpia_status dpia_gemv_f32(const float *A, int64_t M, int64_t N, int64_t lda, con
   if (M < 0 || N < 0) return fail(DPIA_ERR_SHAPE, "%s: negative shape", fn);
   if (lda < (N > 1 ? N : 1)) return fail(DPIA_ERR_SHAPE, "%s: lda=%lld < N=%lld", fn, (long long)lda, (long long)N);
   ReducePlan pl;
-  dpia_status rc = plan_reduce(fn, N, st, true, false, &pl);
+  dpia_status rc = plan_reduce(fn, N, st, true, false, false, &pl);
   if (rc) return rc;
   if (pl.level == ChunkLevel::Grid)
     return fail(DPIA_ERR_UNSUPPORTED, "%s: rows at GRID level (a thread per row) are not implemented", fn);

@@ -162,24 +162,28 @@ struct SumI64 {
 // per-thread fold of one chunk column
 // ---------------------------------------------------------------------------
 
-// Fold-step loads in flight per thread per operand: 16 elements (64 bytes).
-template <int V>
+// Fold-step loads in flight per thread: 128 bytes of streamed operands, i.e.
+// 16 elements per operand when both operands stream from HBM, 32 when one does
+// (asum, or GEMV whose x is re-read from cache); at most 8 vectors per operand.
+template <int V, int STREAMS>
 struct Unroll {
-  static constexpr int value = V >= 16 ? 1 : 16 / V > 8 ? 8 : 16 / V;
+  static constexpr int elems = 32 / STREAMS;
+  static constexpr int value = V >= elems ? 1 : elems / V > 8 ? 8 : elems / V;
 };
 
 // Thread's column of a chunk: Rc vectors of V items at base, base+step, ...
 // Lanes fold their items in order from zero, then the lanes are folded in lane
 // order (asScalar then reduce). Items at index >= n are the identity items
 // (0, 0): they are still folded in (the padded split of a ragged length).
-template <class E, class A, int V, bool CACHE_Y>
+// STREAMS sets the loads in flight (Unroll); callers short of registers pass 2.
+template <class E, class A, int V, bool CACHE_Y, int STREAMS = (E::kTwo && !CACHE_Y) ? 2 : 1>
 __device__ __forceinline__ typename A::acc_t thread_fold(const typename E::in_t *__restrict__ x,
                                                          const typename E::in_t *__restrict__ y,
                                                          int64_t n, int64_t base, int64_t Rc,
                                                          int64_t step, bool full) {
   using in_t = typename E::in_t;
   using acc_t = typename A::acc_t;
-  constexpr int U = Unroll<V>::value;
+  constexpr int U = Unroll<V, STREAMS>::value;
   acc_t acc[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) acc[v] = A::zero();

@@ -159,12 +159,12 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
       return DPIA_ERR_SHAPE;
     }
     if (st.map_level != DPIA_LVL_BLOCK || st.inner_level != DPIA_LVL_THREAD || st.threads != T || st.vec != V ||
-        st.compensated || st.split <= 0 || st.split % ((int64_t)T * V) ||
+        st.compensated || st.stage != DPIA_STAGE_PRIVATE || st.split <= 0 || st.split % ((int64_t)T * V) ||
         (st.thread_map != DPIA_MAP_INTERLEAVED && st.thread_map != DPIA_MAP_CONTIG) ||
         (st.second == DPIA_SECOND_TREE && (!is_pow2(st.threads2) || st.threads2 > T)) ||
         (st.second != DPIA_SECOND_SEQ && st.second != DPIA_SECOND_TREE)) {
       set_last_error("dpia_batch_plan: dot %d: strategy must be BLOCK/THREAD, threads %d, vec 4, split a multiple "
-                     "of %d, plain (not compensated), threads2 a power of two <= threads", i, T, T * V);
+                     "of %d, plain (not compensated), stage PRIVATE, threads2 a power of two <= threads", i, T, T * V);
       return DPIA_ERR_STRATEGY;
     }
     DotDesc d{};
@@ -199,6 +199,7 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
       return DPIA_ERR_SHAPE;
     }
     if (st.map_level != DPIA_LVL_WARP || st.inner_level != DPIA_LVL_THREAD || st.vec != V || st.compensated ||
+        st.stage != DPIA_STAGE_PRIVATE ||
         st.split <= 0 || st.split % (32 * V) || st.second != DPIA_SECOND_SEQ ||
         (st.thread_map != DPIA_MAP_INTERLEAVED && st.thread_map != DPIA_MAP_CONTIG)) {
       set_last_error("dpia_batch_plan: gemv %d: row strategy must be WARP/THREAD, vec 4, split a multiple of 128, "
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(256, 4) batch_fwd_kernel(const FwdArgs a) {
         float acc = 0.0f;
         for (int64_t c = 0; c < g.Crow; ++c) {
           const bool full = (c + 1) * g.s <= g.N;
-          float v = thread_fold<DotF32, SumF32, V, true>(row, x, g.N, c * g.s + lane * g.tstride, g.Rc, g.step, full);
+          float v = thread_fold<DotF32, SumF32, V, true, 2>(row, x, g.N, c * g.s + lane * g.tstride, g.Rc, g.step, full);
           v = warp_tree<SumF32>(v, 32);
           if (lane == 0) acc = __fadd_rn(acc, v);
         }

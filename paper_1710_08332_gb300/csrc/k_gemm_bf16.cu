@@ -37,6 +37,7 @@
 #include <cudaTypedefs.h>
 
 #include "../../include/dpia.h"
+#include "async_copy.cuh"
 #include "device_common.cuh"
 #include "kernels.h"
 
@@ -61,7 +62,6 @@ constexpr uint32_t LAYOUT_SW128 = 2;
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int NUM_THREADS = 64 + 32 * NUM_EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint64_t kTimeoutNs = 2000000000ull;   // 2 s
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 
 struct Params {
@@ -72,40 +72,6 @@ struct Params {
   int a_3d;           // MN-major A loaded as one 3-D box {64 m, 64 k, 4 m-blocks}
   uint32_t stage_tx;  // bytes the TMA loads of one stage deliver
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n"
-      ".reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 
 // Bounded wait on a phase parity; false if it timed out or the CTA aborted.
 __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
@@ -485,6 +451,18 @@ cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int
   int g = ctas < p.num_tiles ? ctas : p.num_tiles;
   void *args[] = {&ma, &mb, &p};
   return cudaLaunchKernel(kfn, dim3(g), dim3(NUM_THREADS), args, SMEM_BYTES, stream);
+}
+
+unsigned *device_status_word() {
+  static unsigned *addr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
+    addr[dev] = static_cast<unsigned *>(p);
+  }
+  return addr[dev];
 }
 
 cudaError_t poll_device_status(unsigned *out) {

@@ -10,7 +10,8 @@
 //
 // Backward dx = A^T dy: a map over columns of a split-over-rows fold. Block
 // (tile, chunk) owns 4*blockDim consecutive columns (4 per thread) and Rs rows;
-// each thread folds its four columns down the chunk's rows in row order, and
+// each thread folds its four columns down the chunk's rows in row order (8 rows
+// of loads in flight), and
 // writes the four chunk partials. The last block of each column tile (ticket,
 // no waiting) folds the tile's partials in chunk order into dx.
 #include "device_common.cuh"
@@ -73,6 +74,7 @@ const void *gemv_pick_v(int V) {
 }
 
 constexpr int kBwdThreads = 256;  // 1024 columns per tile
+constexpr int kDxRows = 8;        // rows of 128-bit loads in flight per thread
 
 __global__ void __launch_bounds__(kBwdThreads) gemv_bwd_dx_kernel(const GemvBwdLaunch p) {
   __shared__ int is_last;
@@ -84,16 +86,16 @@ __global__ void __launch_bounds__(kBwdThreads) gemv_bwd_dx_kernel(const GemvBwdL
   float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (p.vec && j0 + 4 <= p.N) {
     int64_t i = r0;
-    for (; i + 4 <= r1; i += 4) {
-      float4 a[4];
-      float d[4];
+    for (; i + kDxRows <= r1; i += kDxRows) {
+      float4 a[kDxRows];
+      float d[kDxRows];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kDxRows; ++u) {
         a[u] = ld_stream_v4(p.A + (i + u) * p.lda + j0);
         d[u] = __ldg(p.dy + i + u);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kDxRows; ++u) {
         acc[0] = __fadd_rn(acc[0], __fmul_rn(a[u].x, d[u]));
         acc[1] = __fadd_rn(acc[1], __fmul_rn(a[u].y, d[u]));
         acc[2] = __fadd_rn(acc[2], __fmul_rn(a[u].z, d[u]));

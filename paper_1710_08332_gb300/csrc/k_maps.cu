@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) scal_kernel(float a, const float *x, floa
   const int64_t nv = n / V;
   const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t ng = (int64_t)gridDim.x * blockDim.x;
-  constexpr int U = Unroll<V>::value > 4 ? 4 : Unroll<V>::value;
+  constexpr int U = Unroll<V, 2>::value > 4 ? 4 : Unroll<V, 2>::value;
   int64_t i = g0;
   for (; i + (U - 1) * ng < nv; i += U * ng) {
     float r[U][V];

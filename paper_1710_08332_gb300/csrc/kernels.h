@@ -32,6 +32,15 @@ struct ReduceLaunch {
 cudaError_t launch_reduce(ReduceOp op, bool compensated, int V, ChunkLevel level, int threads,
                           int grid, const ReduceLaunch &p, cudaStream_t stream);
 
+// The same reduction (BLOCK/THREAD, V = 4, interleaved map) with each chunk
+// staged through shared memory by bulk asynchronous copies (toLocal).
+cudaError_t launch_reduce_staged(ReduceOp op, bool compensated, int threads, int grid,
+                                 const ReduceLaunch &p, cudaStream_t stream);
+
+// Device address of the library's sticky device status word (0 = no error;
+// DPIA_ERR_TIMEOUT after a bounded wait ran out), or null.
+unsigned *device_status_word();
+
 struct GemvLaunch {
   const float *A;
   int64_t M, N, lda;
@@ -69,6 +78,10 @@ cudaError_t launch_gemv_bwd_dx(const GemvBwdLaunch &p, cudaStream_t stream);
 
 // Device properties cached per device.
 int sm_count();
+// Resident blocks per SM of a kernel at a block size and dynamic shared memory.
+int resident_blocks_dyn(const void *kernel, int threads, size_t dyn_smem);
+// Allow a kernel `bytes` of dynamic shared memory on the current device.
+bool ensure_dyn_smem(const void *kernel, size_t bytes);
 
 // Set the calling host thread's dpia_last_error_message() text (printf format).
 void set_last_error(const char *fmt, ...);

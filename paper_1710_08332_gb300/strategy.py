@@ -27,6 +27,7 @@ class ReduceStrategy:
     compensated: bool = False
     pad: bool = False
     grid: int = 0
+    stage: str = "private"   # "private" (registers) or "local" (shared memory, bulk copies)
 
     def to_c(self) -> N.ReduceStrategyC:
         return N.ReduceStrategyC(
@@ -34,7 +35,8 @@ class ReduceStrategy:
             LEVELS[self.inner_level],
             N.MAP_INTERLEAVED if self.thread_map == "interleaved" else N.MAP_CONTIG,
             N.SECOND_TREE if self.second == "tree" else N.SECOND_SEQ, int(self.threads2),
-            int(bool(self.compensated)), int(bool(self.pad)), int(self.grid))
+            int(bool(self.compensated)), int(bool(self.pad)), int(self.grid),
+            N.STAGE_LOCAL if self.stage == "local" else N.STAGE_PRIVATE)
 
     @property
     def chunk_threads(self) -> int:

@@ -24,7 +24,8 @@ _lock = threading.Lock()
 
 
 def reduce_candidates(n: int, splits=(1024, 2048, 4096, 8192, 16384, 32768, 65536)):
-    """Block-per-chunk strategies over a split sweep, plus warp-per-chunk ones."""
+    """Block-per-chunk strategies over a split sweep (direct loads, and chunks
+    staged through shared memory), plus warp-per-chunk ones."""
     out = []
     for s in splits:
         for T in (256, 512, 1024):
@@ -33,27 +34,56 @@ def reduce_candidates(n: int, splits=(1024, 2048, 4096, 8192, 16384, 32768, 6553
             for second, T2 in (("tree", min(T, 1024)),):
                 out.append(ReduceStrategy(split=s, threads=T, vec=4, second=second, threads2=T2,
                                           pad=n % s != 0))
+                if T <= 512:  # the same chunks staged through shared memory (toLocal)
+                    out.append(ReduceStrategy(split=s, threads=T, vec=4, second=second, threads2=T2,
+                                              pad=n % s != 0, stage="local"))
         if s % 128 == 0 and s <= 8192:
             out.append(ReduceStrategy(split=s, threads=256, vec=4, map_level="warp", second="tree",
                                       threads2=256, pad=n % s != 0))
     return out
 
 
-def time_call(fn, reps: int = 20, warmup: int = 3, stream=None) -> float:
-    """Median milliseconds of fn() over reps, CUDA events on the stream."""
+def hold_device(stream, us: float) -> None:
+    """Queue a device-side delay of about ``us`` microseconds on the stream, so
+    that the host can enqueue the calls that follow before the device reaches
+    them (an event pair then times the kernel, not the host's launch latency)."""
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(int(us * 2500))  # cycles; >= us at clocks up to 2.5 GHz
+
+
+def time_call(fn, reps: int = 20, warmup: int = 3, stream=None, inner: int | None = None) -> float:
+    """Median milliseconds of one fn() call, CUDA events on the stream.
+
+    Each of the reps samples times ``inner`` back-to-back calls (chosen so that
+    a sample spans about 0.3 ms: the event clock ticks in steps of about 2 us)
+    and divides; all samples are enqueued behind a device-side delay, so the
+    host's launch latency is not timed, then synchronised once."""
     stream = stream or torch.cuda.current_stream()
     for _ in range(warmup):
         fn()
-    times = []
+    stream.synchronize()
+    if inner is None:
+        hold_device(stream, 200.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(4):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        est = max(a.elapsed_time(b) / 4, 1e-4)
+        inner = int(min(64, max(1, round(0.3 / est))))
+    hold_device(stream, min(50.0 * reps * inner, 200000.0))
+    ev = []
     for _ in range(reps):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        fn()
+        for _ in range(inner):
+            fn()
         b.record(stream)
-        b.synchronize()
-        times.append(a.elapsed_time(b))
-    times.sort()
+        ev.append((a, b))
+    stream.synchronize()
+    times = sorted(a.elapsed_time(b) / inner for a, b in ev)
     return times[len(times) // 2]
 
 
@@ -112,7 +142,7 @@ def tune_reduce(op: str, x, y=None, candidates=None, reps: int = 10, use_cache: 
 
 def _label(st: ReduceStrategy) -> str:
     return (f"{st.map_level}:s{st.split}:T{st.threads}:V{st.vec}:{st.second}"
-            f"{st.threads2 if st.second == 'tree' else ''}")
+            f"{st.threads2 if st.second == 'tree' else ''}{':local' if st.stage == 'local' else ''}")
 
 
 def batch_candidates():

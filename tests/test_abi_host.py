@@ -62,6 +62,10 @@ BASE = ReduceStrategy(split=8192, threads=256, vec=4)
     (BASE.with_(second="tree", threads2=512), N.ERR_STRATEGY),
     (BASE.with_(second="tree", threads2=24), N.ERR_STRATEGY),
     (BASE.with_(grid=-1), N.ERR_STRATEGY),
+    (BASE.with_(stage="local", map_level="warp"), N.ERR_UNSUPPORTED),
+    (BASE.with_(stage="local", map_level="grid", inner_level="seq", split=8192), N.ERR_UNSUPPORTED),
+    (BASE.with_(stage="local", vec=8), N.ERR_UNSUPPORTED),
+    (BASE.with_(stage="local", thread_map="contig"), N.ERR_UNSUPPORTED),
 ])
 def test_strategy_validation(bad, code):
     assert _call_dot(bad) == code
@@ -123,3 +127,28 @@ def test_scal_and_gemv_validation():
     assert L.dpia_gemv_bwd_f32(p(0x10000000), 1 << 20, 64, 64, p(0x20000), p(0x30000), p(0x40000), None, 64, 8,
                                p(0x50000000), 1 << 30, None) == N.ERR_STRATEGY  # > 65535 row chunks
     assert dpia.dpia_gemv_bwd_workspace_size(8192, 8192, 64) == 128 + 1024 + 128 * 8192 * 4
+
+
+def test_stage_values():
+    """stage is PRIVATE (0) or LOCAL (1); LOCAL passes validation for the
+    implemented shape (the fake pointers then fail only on alignment), and is
+    not implemented for GEMV rows or batched instances."""
+    L = N.lib()
+    p = ctypes.c_void_p
+    c = BASE.to_c()
+    c.stage = 7
+    rc = L.dpia_dot_f32(p(0x10000), p(0x20000000), 1 << 20, ctypes.byref(c), p(0x7000000000), p(0x7100000000),
+                        1 << 20, None)
+    assert rc == N.ERR_STRATEGY and "stage" in dpia.dpia_last_error_message()
+    assert _call_dot(BASE.with_(stage="local"), x=0x10004) == N.ERR_ALIGN
+    assert dpia.dpia_dot_workspace_size(1 << 20, BASE.with_(stage="local")) == 128 + 128 * 8
+    st = ReduceStrategy(split=8192, threads=256, vec=4, stage="local")
+    assert L.dpia_gemv_f32(p(0x10000000), 64, 8192, 8192, p(0x20000), p(0x30000), ctypes.byref(st.to_c()),
+                           None) == N.ERR_UNSUPPORTED
+    from paper_1710_08332_gb300.batch import BatchPolicy
+    d = (N.DotInstanceC * 1)()
+    d[0] = N.DotInstanceC(0, 4096, BatchPolicy().dot_strategy(4096).with_(stage="local").to_c())
+    g = (N.GemvInstanceC * 1)()
+    opt = ctypes.byref(N.BatchOptionsC(256, 0))
+    assert L.dpia_batch_plan_size(1, d, 0, g, opt) == 0
+    assert "stage" in dpia.dpia_last_error_message()

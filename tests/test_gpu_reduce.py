@@ -119,6 +119,45 @@ def test_strategy_sweep_bits(cuda_device, st, op):
             assert_bits_equal(np.float32(got), np.float32(want), f"{op} n={n}")
 
 
+# toLocal: chunks staged through shared memory by bulk asynchronous copies.
+# Same items, same order: bit-identical to the oracle and to the direct loads.
+SWEEP_LOCAL = [
+    RS(split=8192, threads=256, vec=4, stage="local"),
+    RS(split=4096, threads=1024, vec=4, second="tree", threads2=1024, stage="local"),
+    RS(split=2048, threads=32, vec=4, second="tree", threads2=8, stage="local"),
+    RS(split=3072, threads=256, vec=4, stage="local"),              # 3 rows: tiles of 2 + 1
+    RS(split=3072, threads=128, vec=4, second="tree", threads2=128, stage="local"),  # 6 rows: 4 + 2
+    RS(split=65536, threads=512, vec=4, stage="local"),
+    RS(split=8192, threads=256, vec=4, grid=3, stage="local"),
+    RS(split=8192, threads=256, vec=4, compensated=True, stage="local"),
+]
+
+
+@pytest.mark.parametrize("st", SWEEP_LOCAL, ids=lambda st: "local-" + _sid(st))
+@pytest.mark.parametrize("op", ["dot", "asum", "i32"])
+def test_staged_local_bits(cuda_device, st, op):
+    if op == "i32" and st.compensated:
+        pytest.skip("compensated is f32 only")
+    n_exact = st.split * 41
+    for n, pad in ((n_exact, False), (n_exact - 9, True), (st.split // 2 + 4, True), (st.split, False)):
+        s = st.with_(pad=pad)
+        if op == "i32":
+            x, y = W.dot_i32("cpu", n=n, seed=22)
+        else:
+            x, y = W.dot_f32("cpu", n=n, seed=22)
+            x[::11] *= 1e-3
+        x, y = x.cuda(), y.cuda()
+        got = _run(op, x, y, s)
+        want = _oracle(op, x, y, s)
+        direct = _run(op, x, y, s.with_(stage="private"))
+        if op == "i32":
+            assert int(got) == int(want) == int(direct)
+        else:
+            assert_bits_equal(np.float32(got), np.float32(want), f"{op} n={n}")
+            assert_bits_equal(np.float32(got), np.float32(direct), f"{op} n={n} vs direct")
+    assert dpia.dpia_poll_device_status() == 0  # no bounded wait ran out
+
+
 def test_repeat_and_stream_determinism(cuda_device):
     x, y = W.dot_f32("cuda", n=(1 << 22) + 77, seed=5)
     st = RS(split=4096, threads=256, vec=4, second="tree", threads2=256, pad=True)
@@ -178,7 +217,8 @@ def bw_inputs():
 def test_bandwidth_dot_asum_bits(cuda_device, bw_inputs, split):
     x, y, hx, hy = bw_inputs
     for st in (RS(split=split, threads=256, vec=4, second="tree", threads2=256),
-               RS(split=split, threads=min(1024, split // 4), vec=4, second="seq")):
+               RS(split=split, threads=min(1024, split // 4), vec=4, second="seq"),
+               RS(split=split, threads=256, vec=4, second="tree", threads2=256, stage="local")):
         got = _run("dot", x, y, st)
         assert_bits_equal(np.float32(got), loopnest.dot_f32(hx, hy, oracle_strategy(st)), f"dot s={split}")
         got = _run("asum", x, None, st)
