@@ -290,6 +290,16 @@ dpia_status dpia_cast_f32_bf16(const float *x, uint16_t *y, int64_t n, dpia_stre
 dpia_status dpia_poll_device_status(int32_t *status);
 
 /*
+ * Self-test of the bounded device-side waits (no counterpart in the paper):
+ * launches one block whose wait on an mbarrier that nothing completes gives up
+ * after timeout_us microseconds (1 .. 2,000,000) and records DPIA_ERR_TIMEOUT
+ * in the device status word, which dpia_poll_device_status then reports. No
+ * memory is touched and the context stays usable. Asynchronous on stream;
+ * timeout_us out of range is DPIA_ERR_SHAPE.
+ */
+dpia_status dpia_selftest_bounded_wait(uint32_t timeout_us, dpia_stream_t stream);
+
+/*
  * Batches of uneven instances in one persistent launch.
  *
  * Thousands of dot products and GEMVs of different lengths are packed into

@@ -94,6 +94,7 @@ SIGNATURES = {
     "dpia_gemm_bf16": (_I32, [_P, _P, _P, _I64, _I64, _I64, _I64, _I64, _I64, _I32, _I32, _GP, _P]),
     "dpia_cast_f32_bf16": (_I32, [_P, _P, _I64, _P]),
     "dpia_poll_device_status": (_I32, [ctypes.POINTER(ctypes.c_int32)]),
+    "dpia_selftest_bounded_wait": (_I32, [ctypes.c_uint32, ctypes.c_void_p]),
     "dpia_batch_plan_size": (_SZ, [_I32, ctypes.POINTER(DotInstanceC), _I32, ctypes.POINTER(GemvInstanceC),
                                    ctypes.POINTER(BatchOptionsC)]),
     "dpia_batch_plan": (_I32, [_I32, ctypes.POINTER(DotInstanceC), _I32, ctypes.POINTER(GemvInstanceC),

@@ -15,6 +15,7 @@ cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int
                              int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_n,
                              int vec_ok, cudaStream_t stream);
 cudaError_t poll_device_status(unsigned *out);
+cudaError_t launch_bounded_wait_probe(uint64_t timeout_ns, cudaStream_t stream);
 int resident_blocks(const void *kernel, int threads);
 }  // namespace dpia
 
@@ -194,6 +195,17 @@ dpia_status dpia_cast_f32_bf16(const float *x, uint16_t *y, int64_t n, dpia_stre
   int64_t grid = need < cap ? need : cap;
   cast_bf16_kernel<<<(unsigned)(grid < 1 ? 1 : grid), threads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, y, n);
   return cuda_status(cudaGetLastError(), fn);
+}
+
+dpia_status dpia_selftest_bounded_wait(uint32_t timeout_us, dpia_stream_t stream) {
+  set_last_error("");
+  if (timeout_us < 1 || timeout_us > 2000000u) {
+    set_last_error("dpia_selftest_bounded_wait: timeout_us=%u outside 1 .. 2000000", timeout_us);
+    return DPIA_ERR_SHAPE;
+  }
+  cudaError_t e = launch_bounded_wait_probe((uint64_t)timeout_us * 1000ull, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_status(e, "dpia_selftest_bounded_wait");
+  return DPIA_OK;
 }
 
 dpia_status dpia_poll_device_status(int32_t *status) {

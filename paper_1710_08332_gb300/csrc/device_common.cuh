@@ -53,6 +53,13 @@ __device__ __forceinline__ int32_t ld_stream_1(const int32_t *p) {
   return v;
 }
 
+// Streaming store: written once, evict first.
+__device__ __forceinline__ void st_stream_v4(float *p, float4 v) {
+  asm volatile("st.global.cs.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
+
 // Cached read-only loads (an operand many blocks re-read, e.g. GEMV's x).
 __device__ __forceinline__ float4 ld_cached_v4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 __device__ __forceinline__ float2 ld_cached_v2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
@@ -164,10 +171,11 @@ struct SumI64 {
 
 // Fold-step loads in flight per thread: 128 bytes of streamed operands, i.e.
 // 16 elements per operand when both operands stream from HBM, 32 when one does
-// (asum, or GEMV whose x is re-read from cache); at most 8 vectors per operand.
+// (asum, or GEMV whose x is re-read from cache); at most 8 vectors per operand,
+// and 16 elements for V >= 8 (wider vectors would spill).
 template <int V, int STREAMS>
 struct Unroll {
-  static constexpr int elems = 32 / STREAMS;
+  static constexpr int elems = V >= 8 ? 16 : 32 / STREAMS;
   static constexpr int value = V >= elems ? 1 : elems / V > 8 ? 8 : elems / V;
 };
 

@@ -11,12 +11,6 @@ int resident_blocks(const void *kernel, int threads);
 
 namespace {
 
-__device__ __forceinline__ void st_stream_v4(float *p, float4 v) {
-  asm volatile("st.global.cs.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
-               "f"(v.w)
-               : "memory");
-}
-
 template <int V>
 __device__ __forceinline__ void store_vec(float *p, const float (&r)[V]) {
   if constexpr (V == 1) {

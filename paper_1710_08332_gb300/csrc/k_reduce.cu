@@ -274,6 +274,20 @@ cudaError_t launch_staged(int threads, int grid, const ReduceLaunch &p, cudaStre
   return cudaLaunchKernel(k, dim3(grid), dim3(threads), args, ring, stream);
 }
 
+// Self-test of the bounded waits: one block waits on an mbarrier that nothing
+// completes; the wait gives up after timeout_ns and the block records
+// DPIA_ERR_TIMEOUT in the device status word. No copy is in flight.
+__global__ void bounded_wait_probe_kernel(uint64_t timeout_ns, unsigned *status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const bool done = mbar_wait_bounded(&bar, 0, timeout_ns);
+  if (!done && threadIdx.x == 0 && status) atomicExch(status, (unsigned)DPIA_ERR_TIMEOUT);
+}
+
 template <class E, class A, int LEVEL>
 const void *pick_v(int V) {
   switch (V) {
@@ -299,6 +313,13 @@ const void *pick_level(ChunkLevel level, int V) {
 }  // namespace
 
 int resident_blocks(const void *kernel, int threads);
+
+cudaError_t launch_bounded_wait_probe(uint64_t timeout_ns, cudaStream_t stream) {
+  unsigned *status = device_status_word();
+  if (!status) return cudaErrorInvalidSymbol;
+  bounded_wait_probe_kernel<<<1, 32, 0, stream>>>(timeout_ns, status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_reduce_staged(ReduceOp op, bool compensated, int threads, int grid,
                                  const ReduceLaunch &p, cudaStream_t stream) {

@@ -37,6 +37,10 @@ cudaError_t launch_reduce(ReduceOp op, bool compensated, int V, ChunkLevel level
 cudaError_t launch_reduce_staged(ReduceOp op, bool compensated, int threads, int grid,
                                  const ReduceLaunch &p, cudaStream_t stream);
 
+// One block that waits timeout_ns on an mbarrier nothing completes, then sets
+// the device status word to DPIA_ERR_TIMEOUT.
+cudaError_t launch_bounded_wait_probe(uint64_t timeout_ns, cudaStream_t stream);
+
 // Device address of the library's sticky device status word (0 = no error;
 // DPIA_ERR_TIMEOUT after a bounded wait ran out), or null.
 unsigned *device_status_word();

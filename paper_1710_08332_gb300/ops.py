@@ -135,6 +135,10 @@ def dpia_poll_device_status() -> int:
     return int(v.value)
 
 
+def dpia_selftest_bounded_wait(timeout_us: int, stream=None) -> None:
+    N.check(N.lib().dpia_selftest_bounded_wait(int(timeout_us), _stream(stream)), "dpia_selftest_bounded_wait")
+
+
 def dpia_dot_f32_noalloc(x, y, n, st, out, stream=None):
     """dpia_dot_f32 without a workspace argument, for callers that cannot
     allocate device memory: the scratch is the library's static 1 MiB device

@@ -152,3 +152,10 @@ def test_stage_values():
     opt = ctypes.byref(N.BatchOptionsC(256, 0))
     assert L.dpia_batch_plan_size(1, d, 0, g, opt) == 0
     assert "stage" in dpia.dpia_last_error_message()
+
+
+def test_selftest_bounded_wait_range():
+    L = N.lib()
+    assert L.dpia_selftest_bounded_wait(0, None) == N.ERR_SHAPE
+    assert L.dpia_selftest_bounded_wait(2000001, None) == N.ERR_SHAPE
+    assert "timeout_us" in dpia.dpia_last_error_message()
