@@ -146,8 +146,8 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
   h.n_dots = nd;
   h.n_gemvs = ng;
   h.schedule = opt->schedule;
-  h.rows_per_item = T / 32;  // a warp per row
-  h.da_rows_per_item = 8;
+  h.rows_per_item = T / 32 * 4;  // a warp per row, four rows per warp
+  h.da_rows_per_item = 32;
   h.bwd_elems_per_item = 4 * (int64_t)T * 8;
   std::vector<std::pair<int64_t, Item>> fwd, bwd;  // (cost, item)
   for (int32_t i = 0; i < nd; ++i) {
@@ -417,10 +417,11 @@ __global__ void __launch_bounds__(256, 3) batch_fwd_kernel(const FwdArgs a) {
       }
       __syncthreads();
     } else {  // GEMV_ROWS: a warp per row, the row's chunks folded in order
-      const int64_t r = w.a + warp;
-      if (r < g.M) {
+      const int64_t warps = blockDim.x >> 5;
+      const int64_t r_end = w.a + h->rows_per_item < g.M ? w.a + h->rows_per_item : g.M;
+      const float *x = a.gx + g.x_off;
+      for (int64_t r = w.a + warp; r < r_end; r += warps) {
         const float *row = a.As + g.a_off + r * g.lda;
-        const float *x = a.gx + g.x_off;
         float acc = 0.0f;
         for (int64_t c = 0; c < g.Crow; ++c) {
           const bool full = (c + 1) * g.s <= g.N;
@@ -479,16 +480,29 @@ __global__ void __launch_bounds__(256, 4) batch_bwd_kernel(const BwdArgs a) {
       const int64_t cg = (g.N + 3) / 4;
       const int64_t Gc = cg < T ? (int64_t)next_pow2_dev(cg) : T;  // threads per row
       const int64_t rows_par = T / Gc;
-      for (int64_t r = w.a + t / Gc; r < r1; r += rows_par) {
-        const float dv = __ldg(a.gdy + g.y_off + r);
-        float *row = a.dAs + g.a_off + r * g.lda;
+      // eight rows at a time: their dy values are loaded together, then each
+      // x group is loaded once and stored scaled into the eight rows
+      for (int64_t rb = w.a + t / Gc; rb < r1; rb += 8 * rows_par) {
+        float dv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int64_t r = rb + u * rows_par;
+          dv[u] = r < r1 ? __ldg(a.gdy + g.y_off + r) : 0.0f;
+        }
+        float *row0 = a.dAs + g.a_off + rb * g.lda;
+        const int64_t rstep = rows_par * g.lda;
         for (int64_t j = t % Gc; j < cg; j += Gc) {
           if (j < cgv) {
             const float4 xv = ld_cached_v4(x + 4 * j);
-            st_stream_v4(row + 4 * j,
-                         make_float4(__fmul_rn(dv, xv.x), __fmul_rn(dv, xv.y), __fmul_rn(dv, xv.z), __fmul_rn(dv, xv.w)));
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (rb + u * rows_par < r1)
+                st_stream_v4(row0 + u * rstep + 4 * j, make_float4(__fmul_rn(dv[u], xv.x), __fmul_rn(dv[u], xv.y),
+                                                                   __fmul_rn(dv[u], xv.z), __fmul_rn(dv[u], xv.w)));
           } else {
-            for (int64_t e = 4 * j; e < g.N; ++e) row[e] = __fmul_rn(dv, __ldg(x + e));
+            for (int u = 0; u < 8; ++u)
+              if (rb + u * rows_par < r1)
+                for (int64_t e = 4 * j; e < g.N; ++e) row0[u * rstep + e] = __fmul_rn(dv[u], __ldg(x + e));
           }
         }
       }
