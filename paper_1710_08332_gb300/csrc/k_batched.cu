@@ -564,15 +564,33 @@ __global__ void __launch_bounds__(256, 4) batch_bwd_kernel(const BwdArgs a) {
       }
       __syncthreads();
       if (last) {  // fold the tile's chunk partials in chunk order; a thread per column group
+        // (rows of partials are Npad = N rounded up to 4 floats: 128-bit loads,
+        // eight chunks of loads ahead of the dependent adds)
         const float *pb = a.ws.dx_part + g.part_base;
         for (int64_t q = t; q < g.G; q += T) {
           const int64_t jj = (tile * g.G + q) * 4;
           if (jj >= g.N) continue;
           float res[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-          for (int64_t c = 0; c < g.Cr; ++c)
+          int64_t c = 0;
+          for (; c + 8 <= g.Cr; c += 8) {
+            float4 b[8];
 #pragma unroll
-            for (int v = 0; v < 4; ++v)
-              if (jj + v < g.N) res[v] = __fadd_rn(res[v], __ldcg(pb + c * g.Npad + jj + v));
+            for (int u = 0; u < 8; ++u) b[u] = __ldcg(reinterpret_cast<const float4 *>(pb + (c + u) * g.Npad + jj));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              res[0] = __fadd_rn(res[0], b[u].x);
+              res[1] = __fadd_rn(res[1], b[u].y);
+              res[2] = __fadd_rn(res[2], b[u].z);
+              res[3] = __fadd_rn(res[3], b[u].w);
+            }
+          }
+          for (; c < g.Cr; ++c) {
+            const float4 b = __ldcg(reinterpret_cast<const float4 *>(pb + c * g.Npad + jj));
+            res[0] = __fadd_rn(res[0], b.x);
+            res[1] = __fadd_rn(res[1], b.y);
+            res[2] = __fadd_rn(res[2], b.z);
+            res[3] = __fadd_rn(res[3], b.w);
+          }
 #pragma unroll
           for (int v = 0; v < 4; ++v)
             if (jj + v < g.N) a.dgx[g.x_off + jj + v] = res[v];
