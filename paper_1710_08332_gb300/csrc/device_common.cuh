@@ -184,7 +184,12 @@ struct Unroll {
 // order (asScalar then reduce). Items at index >= n are the identity items
 // (0, 0): they are still folded in (the padded split of a ragged length).
 // STREAMS sets the loads in flight (Unroll); callers short of registers pass 2.
-template <class E, class A, int V, bool CACHE_Y, int STREAMS = (E::kTwo && !CACHE_Y) ? 2 : 1>
+// RAGGED_BATCHED: a chunk reaching past n folds its whole vectors with the
+// batched loads too (for callers whose chunks are often padded: GEMV rows,
+// batched instances); otherwise such a chunk is folded one vector at a time,
+// which keeps the kernel's register count down.
+template <class E, class A, int V, bool CACHE_Y, int STREAMS = (E::kTwo && !CACHE_Y) ? 2 : 1,
+          bool RAGGED_BATCHED = false>
 __device__ __forceinline__ typename A::acc_t thread_fold(const typename E::in_t *__restrict__ x,
                                                          const typename E::in_t *__restrict__ y,
                                                          int64_t n, int64_t base, int64_t Rc,
@@ -195,64 +200,103 @@ __device__ __forceinline__ typename A::acc_t thread_fold(const typename E::in_t 
   acc_t acc[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) acc[v] = A::zero();
-  // vectors r < Rin lie wholly below n; with full, Rin = Rc
-  int64_t Rin = Rc;
-  if (!full) {
-    const int64_t room = n - V - base;  // e0(r) + V <= n  <=>  r * step <= room
-    Rin = room < 0 ? 0 : room / step + 1;
-    if (Rin > Rc) Rin = Rc;
-  }
-  int64_t r = 0;
-  for (; r + U <= Rin; r += U) {
-    in_t xv[U][V], yv[U][V];
+  if (full) {
+    int64_t r = 0;
+    for (; r + U <= Rc; r += U) {
+      in_t xv[U][V], yv[U][V];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      load_vec<V, false>(x + base + (r + u) * step, xv[u]);
-      if constexpr (E::kTwo) load_vec<V, CACHE_Y>(y + base + (r + u) * step, yv[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int v = 0; v < V; ++v)
-        acc[v] = A::step(acc[v], E::elem(xv[u][v], E::kTwo ? yv[u][v] : xv[u][v]));
-  }
-  if constexpr (U >= 4) {
-    constexpr int H = U / 2;
-    if (r + H <= Rin) {  // half a batch left
-      in_t xv[H][V], yv[H][V];
-#pragma unroll
-      for (int u = 0; u < H; ++u) {
+      for (int u = 0; u < U; ++u) {
         load_vec<V, false>(x + base + (r + u) * step, xv[u]);
         if constexpr (E::kTwo) load_vec<V, CACHE_Y>(y + base + (r + u) * step, yv[u]);
       }
 #pragma unroll
-      for (int u = 0; u < H; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int v = 0; v < V; ++v)
           acc[v] = A::step(acc[v], E::elem(xv[u][v], E::kTwo ? yv[u][v] : xv[u][v]));
-      r += H;
     }
-  }
-  for (; r < Rin; ++r) {
-    in_t xv[V], yv[V];
-    load_vec<V, false>(x + base + r * step, xv);
-    if constexpr (E::kTwo) load_vec<V, CACHE_Y>(y + base + r * step, yv);
+    for (; r < Rc; ++r) {
+      in_t xv[V], yv[V];
+      load_vec<V, false>(x + base + r * step, xv);
+      if constexpr (E::kTwo) load_vec<V, CACHE_Y>(y + base + r * step, yv);
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = A::step(acc[v], E::elem(xv[v], E::kTwo ? yv[v] : xv[v]));
-  }
-  // past n (a padded chunk): at most one vector straddles n, the rest are the
-  // identity items (0, 0), folded in all the same
-  for (r = Rin; r < Rc; ++r) {
-    const int64_t e0 = base + r * step;
-    in_t xv[V], yv[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const bool in = e0 + v < n;
-      xv[v] = in ? x[e0 + v] : in_t(0);
-      yv[v] = (E::kTwo && in) ? y[e0 + v] : in_t(0);
+      for (int v = 0; v < V; ++v) acc[v] = A::step(acc[v], E::elem(xv[v], E::kTwo ? yv[v] : xv[v]));
     }
+  } else if constexpr (!RAGGED_BATCHED) {
+    // a chunk reaching past n, one vector at a time: items at index >= n are
+    // the identity items (0, 0), folded in all the same
+    for (int64_t r = 0; r < Rc; ++r) {
+      const int64_t e0 = base + r * step;
+      in_t xv[V], yv[V];
+      if (e0 + V <= n) {
+        load_vec<V, false>(x + e0, xv);
+        if constexpr (E::kTwo) load_vec<V, CACHE_Y>(y + e0, yv);
+      } else {
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = A::step(acc[v], E::elem(xv[v], E::kTwo ? yv[v] : xv[v]));
+        for (int v = 0; v < V; ++v) {
+          const bool in = e0 + v < n;
+          xv[v] = in ? x[e0 + v] : in_t(0);
+          yv[v] = (E::kTwo && in) ? y[e0 + v] : in_t(0);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = A::step(acc[v], E::elem(xv[v], E::kTwo ? yv[v] : xv[v]));
+    }
+  } else {
+    // a chunk reaching past n: vectors r < Rin lie wholly below n and take the
+    // same batched loads; at most one vector straddles n, the rest are the
+    // identity items (0, 0), folded in all the same
+    const int64_t room = n - V - base;  // e0(r) + V <= n  <=>  r * step <= room
+    int64_t Rin = room < 0 ? 0 : room / step + 1;
+    if (Rin > Rc) Rin = Rc;
+    int64_t r = 0;
+    for (; r + U <= Rin; r += U) {
+      in_t xv[U][V], yv[U][V];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        load_vec<V, false>(x + base + (r + u) * step, xv[u]);
+        if constexpr (E::kTwo) load_vec<V, CACHE_Y>(y + base + (r + u) * step, yv[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          acc[v] = A::step(acc[v], E::elem(xv[u][v], E::kTwo ? yv[u][v] : xv[u][v]));
+    }
+    if constexpr (U >= 4) {
+      constexpr int H = U / 2;
+      if (r + H <= Rin) {  // half a batch left
+        in_t xv[H][V], yv[H][V];
+#pragma unroll
+        for (int u = 0; u < H; ++u) {
+          load_vec<V, false>(x + base + (r + u) * step, xv[u]);
+          if constexpr (E::kTwo) load_vec<V, CACHE_Y>(y + base + (r + u) * step, yv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < H; ++u)
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+            acc[v] = A::step(acc[v], E::elem(xv[u][v], E::kTwo ? yv[u][v] : xv[u][v]));
+        r += H;
+      }
+    }
+    for (; r < Rc; ++r) {
+      const int64_t e0 = base + r * step;
+      in_t xv[V], yv[V];
+      if (r < Rin) {
+        load_vec<V, false>(x + e0, xv);
+        if constexpr (E::kTwo) load_vec<V, CACHE_Y>(y + e0, yv);
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const bool in = e0 + v < n;
+          xv[v] = in ? x[e0 + v] : in_t(0);
+          yv[v] = (E::kTwo && in) ? y[e0 + v] : in_t(0);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = A::step(acc[v], E::elem(xv[v], E::kTwo ? yv[v] : xv[v]));
+    }
   }
   acc_t t = A::zero();
 #pragma unroll

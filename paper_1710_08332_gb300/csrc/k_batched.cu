@@ -376,7 +376,8 @@ __global__ void __launch_bounds__(256, 3) batch_fwd_kernel(const FwdArgs a) {
       const float *x = a.xs + d.off, *y = a.ys + d.off;
       const int64_t c = w.a;
       const bool full = (c + 1) * d.s <= d.n;
-      float v = thread_fold<DotF32, SumF32, V, false>(x, y, d.n, c * d.s + t * d.tstride, d.Rc, d.step, full);
+      float v = thread_fold<DotF32, SumF32, V, false, 2, true>(x, y, d.n, c * d.s + t * d.tstride, d.Rc, d.step,
+                                                              full);
       v = block_tree<SumF32>(v, blockDim.x, sm);
       if (t == 0) a.ws.dot_part[d.part_base + c] = v;
       __threadfence();
@@ -425,7 +426,8 @@ __global__ void __launch_bounds__(256, 3) batch_fwd_kernel(const FwdArgs a) {
         float acc = 0.0f;
         for (int64_t c = 0; c < g.Crow; ++c) {
           const bool full = (c + 1) * g.s <= g.N;
-          float v = thread_fold<DotF32, SumF32, V, true>(row, x, g.N, c * g.s + lane * g.tstride, g.Rc, g.step, full);
+          float v = thread_fold<DotF32, SumF32, V, true, 1, true>(row, x, g.N, c * g.s + lane * g.tstride, g.Rc,
+                                                                  g.step, full);
           v = warp_tree<SumF32>(v, 32);
           if (lane == 0) acc = __fadd_rn(acc, v);
         }

@@ -51,8 +51,8 @@ __global__ void __launch_bounds__(max_threads_for_vec(V)) gemv_kernel(const Gemv
       acc_t acc = A::zero();
       for (int64_t c = 0; c < p.Crow; ++c) {
         const bool full = (c + 1) * p.s <= p.N;
-        acc_t v = thread_fold<DotF32, A, V, true, 2>(row, p.x, p.N, c * p.s + lane * p.tstride, p.Rc,
-                                                      p.step, full);
+        acc_t v = thread_fold<DotF32, A, V, true, 2, true>(row, p.x, p.N, c * p.s + lane * p.tstride, p.Rc,
+                                                            p.step, full);
         v = warp_tree<A>(v, 32);
         if (lane == 0) acc = A::combine(acc, v);
       }
