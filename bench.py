@@ -542,13 +542,20 @@ def dot_workload(args, device, dist):
     xi, yi = W.dot_i32(device)
     n = x.numel()
     # the workload fixes split 8192 (128 chunks), a block per chunk and the
-    # sequential second level; the block size and vector width are tuned
+    # sequential second level; the block size and vector width are tuned under
+    # the timed conditions (L2 flushed before every launch)
+    flush = L2Flush(device)
     cands = [dpia.ReduceStrategy(split=W.DOT_SPLIT, threads=T, vec=V)
              for T in (256, 512, 1024) for V in (4, 8) if T * V <= W.DOT_SPLIT and not (V == 8 and T > 512)]
-    st, sweep = tune.tune_reduce("dot", x, y, candidates=cands, reps=10, use_cache=False)
+    out = torch.empty(1, device=device)
+    sweep = {}
+    for c in cands:
+        wsc = torch.zeros(dpia.dpia_dot_workspace_size(n, c), dtype=torch.uint8, device=device)
+        t = standalone_us({"c": lambda: dpia.dpia_dot_f32(x, y, n, c, out, wsc)}, {}, flush=flush, reps=15)
+        sweep[tune._label(c)] = t["c"]["median_us"]
+    st = cands[min(range(len(cands)), key=lambda i: sweep[tune._label(cands[i])])]
     ws = torch.zeros(dpia.dpia_dot_workspace_size(n, st), dtype=torch.uint8, device=device)
     wsi = torch.zeros_like(ws)
-    out = torch.empty(1, device=device)
     outi = torch.empty(1, dtype=torch.int64, device=device)
 
     def step(tl):
@@ -557,7 +564,6 @@ def dot_workload(args, device, dist):
         for name, fn in calls:
             fn() if tl is None else tl.call(name, fn)
 
-    flush = L2Flush(device)
     per, step_ms, clk = timed_steps(args, device, dist, ["dot_f32", "dot_i32"], step, flush)
     hbm = peaks()[0]
     b = 8 * n
@@ -579,7 +585,7 @@ def dot_workload(args, device, dist):
                     "(context.empty_launch_floor) is most of it"}
     cfg = {"workload": "dot f32 and int32, n=2^20, U[-1,1) / U{-100..100} seed 0, split 8192 (128 chunks), "
                        "block per chunk, sequential second level", "n": n, "strategy": st.as_dict(),
-           "tuned_ms": sweep,
+           "tuned_us_flushed": sweep,
            "l2": "flushed before every step (256 MiB read), outside the kernel events"}
     return _line(args, dist, round(world * 2 * b / (step_ms / 1e3) / 1e9, 1), "GB/s", step_ms, "f32",
                  cfg, kern, roof, clk, 2 * args.steps, {"context": context})
@@ -934,10 +940,22 @@ def e2e_bandwidth(args, device, dist, st_dot, st_asum, hx, hy, step_bytes):
     t1.record(cur)
     t1.synchronize()
     ms = reduce_max(dist, t0.elapsed_time(t1) / K, device if dist and dist.get_backend() == "nccl" else None)
+    # context: the link alone, one 256 MiB pinned copy in each direction
+    link = {}
+    for name, fn in (("h2d_GB_s", lambda: sets[0]["x"].copy_(px, non_blocking=True)),
+                     ("d2h_GB_s", lambda: host_scal[0].copy_(sets[0]["ys"], non_blocking=True))):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        a.record()
+        for _ in range(5):
+            fn()
+        b.record()
+        b.synchronize()
+        link[name] = round(5 * 4 * n / (a.elapsed_time(b) / 1e3) / 1e9, 1)
     world = dist.get_world_size() if dist else 1
     return {"value": round(world * step_bytes / (ms / 1e3) / 1e9, 1), "unit": "GB/s",
             "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * n + 8, "steps": K,
-            "ms_per_step": round(ms, 3),
+            "ms_per_step": round(ms, 3), "link_alone": link,
             "overlap": "two device buffer sets; host-to-device copies, kernels and device-to-host copies "
                        "on three streams"}
 

@@ -302,6 +302,30 @@ def test_gemv_ragged_shapes(cuda_device):
         assert_bits_equal(host(dA)[:, :N_], loopnest.gemv_bwd_dA_f32(x.numpy(), dy.numpy()), f"dA {M}x{N_}")
 
 
+@pytest.mark.parametrize("st", [
+    RS(split=256, threads=128, vec=4, map_level="warp", pad=True),
+    RS(split=1024, threads=256, vec=4, map_level="warp", pad=True),
+    RS(split=512, threads=128, vec=4, map_level="warp", thread_map="contig", pad=True),
+    RS(split=1024, threads=128, vec=4, map_level="warp", compensated=True, pad=True),
+    RS(split=1024, threads=256, vec=4, pad=True),
+    RS(split=2048, threads=128, vec=8, pad=True),
+], ids=_sid)
+def test_gemv_padded_row_chunks(cuda_device, st):
+    """Rows whose last chunk reaches past N (identity items), at block and warp
+    level: the whole vectors below N take the batched loads, the rest is the
+    straddling vector and identity items."""
+    for (M, N_) in ((67, 1000), (33, 4097), (9, 129), (130, 3000)):
+        A, x, _ = W.gemv("cpu", M=M, N=N_, seed=N_)
+        ld = (N_ + 7) // 8 * 8
+        Ad = torch.zeros(M, ld, device="cuda")
+        Ad[:, :N_] = A.cuda()
+        xd = torch.zeros(ld, device="cuda")
+        xd[:N_] = x.cuda()
+        y = torch.full((M,), float("nan"), device="cuda")
+        dpia.dpia_gemv_f32(Ad, M, N_, ld, xd, y, st)
+        assert_bits_equal(host(y), loopnest.gemv_f32(A.numpy(), x.numpy(), oracle_strategy(st)), f"{M}x{N_}")
+
+
 def test_dot_bwd_exact(cuda_device):
     x, y = W.dot_f32("cuda", n=(1 << 20) + 3, seed=9)
     g = torch.tensor([0.37], device="cuda")
