@@ -813,6 +813,95 @@ def batched_workload(args, device, dist):
     return line
 
 
+def codegen_workload(args, device, dist):
+    """Kernels produced by the code generator from the paper's phrases, on the
+    bandwidth inputs (n = 2^26) and the GEMV 8192^2 inputs, all reading their
+    streams as asVector 4 (GEMV: scalar): the dot as four generated kernels
+    (per-thread lane partials over 2048 chunks of 2^15 with 256 threads, then
+    three folding stages: 32768 sums of 64, 128 sums of 256, the last 128), the
+    asum partials, scal, and the GEMV partials with the per-row fold; beside
+    them the library's hand-written dot and asum on the same inputs."""
+    import torch
+
+    import paper_1710_08332_gb300 as dpia
+    from paper_1710_08332_gb300 import codegen as G
+    from paper_1710_08332_gb300.codegen import programs as PR
+    from synth import workloads as W
+
+    n = W.BW_N
+    x, y = W.bandwidth(device)
+    # streams read as asVector 4; sequential loops unrolled 4 (the folds 16) so
+    # that loads issue ahead of the dependent steps (a sweep of split, threads,
+    # width and unroll factor chose these)
+    s, Tn, V = 1 << 15, 256, 4
+    m1 = n // s * Tn * V  # lane partials of the first kernel
+    k1 = G.compile_cuda("gen_dot_partials", *PR.dot_partials(n, s, Tn, V=V), unroll=4)
+    k2 = G.compile_cuda("gen_dot_fold64", *PR.fold_rows(m1 // 64, 64), unroll=16)
+    k3 = G.compile_cuda("gen_dot_fold256", *PR.fold_rows(m1 // 64 // 256, 256), unroll=16)
+    k4 = G.compile_cuda("gen_dot_fold", *PR.fold_all(m1 // 64 // 256), unroll=16)
+    ka = G.compile_cuda("gen_asum_partials", *PR.asum_partials(n, s, Tn, V=V), unroll=4)
+    ks = G.compile_cuda("gen_scal", *PR.scal(n, W.SCAL_A, V=V))
+    A, xv, _ = W.gemv(device)
+    M, N_ = A.shape
+    kg = G.compile_cuda("gen_gemv_partials", *PR.gemv_partials(M, N_, 128))
+    kr = G.compile_cuda("gen_gemv_rows", *PR.fold_rows(M, 128), unroll=16)
+    part = torch.empty(m1, device=device)
+    p2 = torch.empty(m1 // 64, device=device)
+    p3 = torch.empty(m1 // 64 // 256, device=device)
+    out = torch.empty(1, device=device)
+    ys = torch.empty_like(x)
+    gpart = torch.empty(M * 128, device=device)
+    yv = torch.empty(M, device=device)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    calls = {
+        "gen_dot_partials": lambda: k1.run(x, y, part),
+        "gen_dot_fold64": lambda: k2.run(part, p2, grid=p2.numel() // 256, block=256),
+        "gen_dot_fold256": lambda: k3.run(p2, p3, grid=1, block=p3.numel()),
+        "gen_dot_fold": lambda: k4.run(p3, out),
+        "gen_asum_partials": lambda: ka.run(x, part),
+        "gen_scal": lambda: ks.run(x, ys, grid=sms * 8, block=256),
+        "gen_gemv_partials": lambda: kg.run(A, xv, gpart),
+        "gen_gemv_rows": lambda: kr.run(gpart, yv, grid=M // 256, block=256),
+    }
+    st = dpia.ReduceStrategy(split=16384, threads=256, vec=4, second="tree", threads2=256)
+    ws = dpia.workspace(dpia.dpia_dot_workspace_size(n, st), device)
+    lib_out = torch.empty(1, device=device)
+    calls["library_dot"] = lambda: dpia.dpia_dot_f32(x, y, n, st, lib_out, ws)
+    calls["library_asum"] = lambda: dpia.dpia_asum_f32(x, n, st, lib_out, ws)
+    bytes_ = {"gen_dot_partials": 8 * n, "gen_asum_partials": 4 * n, "gen_scal": 8 * n,
+              "gen_gemv_partials": 4 * M * N_ + 4 * N_, "library_dot": 8 * n, "library_asum": 4 * n}
+    names = list(calls)
+
+    def step(tl):
+        for name in names:
+            calls[name]() if tl is None else tl.call(name, calls[name])
+
+    per, step_ms, clk = timed_steps(args, device, dist, names, step)
+    alone = standalone_us({k: calls[k] for k in ("gen_dot_partials", "library_dot", "gen_asum_partials",
+                                                  "library_asum", "gen_scal", "gen_gemv_partials")}, bytes_)
+    hbm = peaks()[0]
+    kern = {k: {"avg_us": round(v * 1e3, 2)} for k, v in per.items()}
+    for k, b in bytes_.items():
+        kern[k]["GB_s"] = round(b / per[k] / 1e6, 1)
+    dot_ms = sum(per[k] for k in ("gen_dot_partials", "gen_dot_fold64", "gen_dot_fold256", "gen_dot_fold"))
+    achieved = 8 * n / per["gen_dot_partials"] / 1e6
+    roof = {"bound": "hbm", "kernel": "gen_dot_partials (generated: mapWorkgroup / mapLocal / reduceSeq on "
+                                      "asVector 4)",
+            "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+            "traffic": None, "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": 8 * n,
+            "frac_alone": round(alone["gen_dot_partials"]["GB_s"] / hbm, 4)}
+    cfg = {"workload": "generated kernels: dot n=2^26 (4 kernels), asum partials, scal (a=1.5), GEMV 8192^2 "
+                       "partials + row folds, bandwidth inputs seed 1 / GEMV seed 2, asVector 4 (GEMV scalar), "
+                       "sequential loops unrolled 4 (folds 16); beside them the "
+                       "library's dot and asum (split 16384, tree)",
+           "n": n, "dot_split": s, "threads": Tn, "vec": V, "unroll": 4, "l2": "inputs larger than L2"}
+    world = dist.get_world_size() if dist else 1
+    return _line(args, dist, round(world * 8 * n / (dot_ms / 1e3) / 1e9, 1), "GB/s", dot_ms, "f32", cfg, kern,
+                 roof, clk, len(names) * args.steps,
+                 {"kernels_alone": alone,
+                  "generated_dot_vs_library_dot": round(per["library_dot"] / dot_ms, 3)})
+
+
 def cpu_baseline_for(workload):
     """Oracle timings for the secondary workloads (one thread, bounded samples)."""
     import numpy as np
@@ -1037,10 +1126,12 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["bandwidth", "dot", "gemv", "gemm", "batched"], default="bandwidth",
+    ap.add_argument("--workload", choices=["bandwidth", "dot", "gemv", "gemm", "batched", "codegen"],
+                    default="bandwidth",
                     help="bandwidth (default: the headline step); dot (n=2^20, split 8192), gemv (8192^2 "
                          "forward + backward), gemm (4096^3 BF16 forward + backward, FP32 fold forward), batched "
-                         "(4096 dots + 512 GEMVs of uneven sizes, one launch vs one launch per instance)")
+                         "(4096 dots + 512 GEMVs of uneven sizes, one launch vs one launch per instance), codegen "
+                         "(kernels generated from the paper's phrases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the split autotuner; use the default strategy (split 16384, tree second level)")
@@ -1072,7 +1163,7 @@ def main(argv=None):
         line = bandwidth_workload(args, device, dist)
     else:
         line = {"dot": dot_workload, "gemv": gemv_workload, "gemm": gemm_workload,
-                "batched": batched_workload}[args.workload](args, device, dist)
+                "batched": batched_workload, "codegen": codegen_workload}[args.workload](args, device, dist)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             if args.workload == "bandwidth":

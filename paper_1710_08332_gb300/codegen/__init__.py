@@ -1,0 +1,16 @@
+"""A strategy-preserving code generator: functional phrases over the paper's
+primitives (map at a level of the hierarchy, reduceSeq, zip, split, join,
+transpose, address-space annotations) are translated to an imperative loop
+nest (acceptor- and continuation-passing translations, then the mapI /
+reduceI expansion) and emitted as CUDA C for sm_103a or as C for the host.
+The emitted code evaluates exactly the tree the phrase denotes, so its
+results are bit-identical to any other evaluation of the same phrase.
+"""
+from .build import CFunction, CudaKernel, compile_c, compile_cuda
+from .emit import EmitError, generate
+from .phrase import (F32, I32, I64, Arr, Num, PairT, VecT, abs_, add, arr, asScalar, asVector, fst, inp, join,
+                     lit, mapGlobal, mapLocal, mapSeq, mapWorkgroup, mul, reduceSeq, snd, split, sub, to_global,
+                     to_local, to_private, transpose, vlit, zip_)
+from .translate import TranslationError
+
+__all__ = [n for n in dir() if not n.startswith("_")]

@@ -1,0 +1,490 @@
+"""Stage III (Section 5.3): the loop nest becomes CUDA C (or plain C).
+
+Views are resolved into index arithmetic on the arrays they read: an access
+path (a list of index and projection steps, innermost last) is pushed through
+``split``, ``join``, ``transpose``, ``zip`` and the projections until it
+reaches an input or a temporary, where it becomes a row-major offset. Writes
+through acceptors are resolved the same way. Loops map to the hierarchy:
+
+    global     for (i = blockIdx.x*blockDim.x + threadIdx.x; i < n; i += gridDim.x*blockDim.x)
+    workgroup  for (i = blockIdx.x; i < n; i += gridDim.x)
+    local      for (i = threadIdx.x; i < n; i += blockDim.x)
+    seq        for (i = 0; i < n; ++i)
+
+A statement outside every parallel loop runs in one thread (thread 0 of block
+0, or thread 0 of the workgroup when it sits in a workgroup loop only). Where
+a temporary in local or global memory is in scope, block barriers separate a
+local loop from the statements before and after it and end every iteration of
+a loop that contains a local loop, so no thread reads what another has not
+finished writing, nor overwrites what another still reads (writes through the
+output acceptor go to disjoint places and are never read back). Temporaries:
+private ones are C variables (arrays of the loop body), local ones shared
+arrays, global ones slices of a hoisted buffer, one slice per iteration of the
+parallel loops around them (Section 6.4). In the C backend every loop is
+sequential.
+
+Floating-point + and * are emitted as separately rounded operations
+(``__fadd_rn`` / ``__fmul_rn`` in CUDA, plain float arithmetic compiled
+without contraction in C), so the generated code evaluates exactly the tree
+the phrase denotes.
+"""
+from __future__ import annotations
+
+from . import phrase as P
+from . import translate as T
+
+CTYPE = {"f32": "float", "i32": "int", "i64": "long long"}
+VTYPE = {2: "float2", 4: "float4"}
+LANES = "xyzw"
+
+
+def ctype(t) -> str:
+    """C type of a number or vector."""
+    if isinstance(t, P.VecT):
+        return VTYPE[t.n]
+    return CTYPE[t.dtype]
+
+
+# Lane-wise vector arithmetic, each lane rounded separately.
+CUDA_PRELUDE = """#define DPIA_V4(name, op) __device__ __forceinline__ float4 name(float4 a, float4 b) { \\
+  return make_float4(op(a.x, b.x), op(a.y, b.y), op(a.z, b.z), op(a.w, b.w)); }
+#define DPIA_V2(name, op) __device__ __forceinline__ float2 name(float2 a, float2 b) { \\
+  return make_float2(op(a.x, b.x), op(a.y, b.y)); }
+DPIA_V4(dpia_vadd4, __fadd_rn) DPIA_V4(dpia_vsub4, __fsub_rn) DPIA_V4(dpia_vmul4, __fmul_rn)
+DPIA_V2(dpia_vadd2, __fadd_rn) DPIA_V2(dpia_vsub2, __fsub_rn) DPIA_V2(dpia_vmul2, __fmul_rn)
+__device__ __forceinline__ float dpia_lane4(float4 v, long long l) {
+  return l == 0 ? v.x : l == 1 ? v.y : l == 2 ? v.z : v.w; }
+__device__ __forceinline__ float dpia_lane2(float2 v, long long l) { return l == 0 ? v.x : v.y; }
+__device__ __forceinline__ float4 dpia_vabs4(float4 a) { return make_float4(fabsf(a.x), fabsf(a.y), fabsf(a.z), fabsf(a.w)); }
+__device__ __forceinline__ float2 dpia_vabs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+"""
+
+C_PRELUDE = """#include <math.h>
+typedef struct { float x, y, z, w; } float4;
+typedef struct { float x, y; } float2;
+static inline float4 make_float4(float x, float y, float z, float w) { float4 v = {x, y, z, w}; return v; }
+static inline float2 make_float2(float x, float y) { float2 v = {x, y}; return v; }
+static inline float f_add(float a, float b) { return a + b; }
+static inline float f_sub(float a, float b) { return a - b; }
+static inline float f_mul(float a, float b) { return a * b; }
+#define DPIA_V4(name, op) static inline float4 name(float4 a, float4 b) { \\
+  return make_float4(op(a.x, b.x), op(a.y, b.y), op(a.z, b.z), op(a.w, b.w)); }
+#define DPIA_V2(name, op) static inline float2 name(float2 a, float2 b) { \\
+  return make_float2(op(a.x, b.x), op(a.y, b.y)); }
+DPIA_V4(dpia_vadd4, f_add) DPIA_V4(dpia_vsub4, f_sub) DPIA_V4(dpia_vmul4, f_mul)
+DPIA_V2(dpia_vadd2, f_add) DPIA_V2(dpia_vsub2, f_sub) DPIA_V2(dpia_vmul2, f_mul)
+static inline float dpia_lane4(float4 v, long long l) { return l == 0 ? v.x : l == 1 ? v.y : l == 2 ? v.z : v.w; }
+static inline float dpia_lane2(float2 v, long long l) { return l == 0 ? v.x : v.y; }
+static inline float4 dpia_vabs4(float4 a) { return make_float4(fabsf(a.x), fabsf(a.y), fabsf(a.z), fabsf(a.w)); }
+static inline float2 dpia_vabs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+"""
+
+
+def divisible(i, V: int) -> bool:
+    """True if the index expression is a multiple of V for every value of its variables."""
+    if isinstance(i, T.IConst):
+        return i.v % V == 0
+    if isinstance(i, T.IOp):
+        if i.op == "+":
+            return divisible(i.a, V) and divisible(i.b, V)
+        if i.op == "*":
+            return divisible(i.a, V) or divisible(i.b, V)
+    return False
+
+
+class EmitError(Exception):
+    pass
+
+
+def render_index(i) -> str:
+    if isinstance(i, T.IConst):
+        return str(i.v)
+    if isinstance(i, T.IVar):
+        return i.name
+    if isinstance(i, T.IOp):
+        return f"({render_index(i.a)} {i.op} {render_index(i.b)})"
+    raise EmitError(f"bad index {i!r}")
+
+
+def dims(t) -> list:
+    d = []
+    while isinstance(t, P.Arr):
+        d.append(t.n)
+        t = t.elem
+    return d
+
+
+def linear(idx: list, shape: list):
+    """Row-major offset of idx (len(idx) == len(shape))."""
+    if len(idx) != len(shape):
+        raise EmitError(f"access with {len(idx)} indices into an array of rank {len(shape)}")
+    off = T.IConst(0)
+    for i, n in zip(idx, shape):
+        off = T.iadd(T.imul(off, n), i)
+    return off
+
+
+class Emitter:
+    def __init__(self, backend: str, inputs: list, out: T.AOut, temps: list, unroll: int = 1):
+        if backend not in ("cuda", "c"):
+            raise EmitError(f"unknown backend {backend}")
+        self.backend = backend
+        self.unroll = unroll
+        self.inputs = {p.name: p for p in inputs}
+        self.out = out
+        self.temps = {t.name: t for t in temps}
+        self.lines = []
+        self.shared = []
+        self.private_ctx = {}  # private temp name -> parallel depth where declared
+        # per loop scope: are temporaries shared between the block's threads in
+        # play (then barriers separate thread-level loops from what follows)?
+        self.sync = [False]
+
+    # -- reads ----------------------------------------------------------------
+
+    def access(self, e: P.Phrase, path: list) -> str:
+        """C expression for the number reached from e by path (steps applied in order)."""
+        if isinstance(e, P.Idx):
+            return self.access(e.e, [("i", e.i)] + path)
+        if isinstance(e, P.Proj):
+            return self.access(e.e, [("p", e.k)] + path)
+        if isinstance(e, P.Zip):
+            if len(path) < 2 or path[0][0] != "i" or path[1][0] != "p":
+                raise EmitError("a zipped pair must be indexed and projected")
+            return self.access(e.b if path[1][1] else e.a, [path[0]] + path[2:])
+        if isinstance(e, P.Split):
+            if len(path) < 2 or path[0][0] != "i" or path[1][0] != "i":
+                raise EmitError("split read without two indices")
+            return self.access(e.e, [("i", T.iadd(T.imul(path[0][1], e.n), path[1][1]))] + path[2:])
+        if isinstance(e, P.Join):
+            m = e.e.type.elem.n
+            k = path[0][1]
+            return self.access(e.e, [("i", T.idiv(k, m)), ("i", T.imod(k, m))] + path[1:])
+        if isinstance(e, P.Transpose):
+            if len(path) < 2:
+                raise EmitError("transpose read without two indices")
+            return self.access(e.e, [path[1], path[0]] + path[2:])
+        if isinstance(e, P.To):
+            return self.access(e.e, path)
+        if isinstance(e, P.AsVector):
+            if len(path) != 1 or path[0][0] != "i":
+                raise EmitError("asVector read must select one whole vector")
+            base, off = self.locate(e.e, [("i", T.imul(path[0][1], e.n))])
+            if not divisible(off, e.n):
+                raise EmitError(f"asVector {e.n} access at offset {render_index(off)} is not provably aligned")
+            q = "const " if base in self.inputs else ""
+            return f"reinterpret_cast<{q}{VTYPE[e.n]} *>({base})[{render_index(T.idiv(off, e.n))}]" \
+                if self.backend == "cuda" else f"(({q}{VTYPE[e.n]} *){base})[{render_index(T.idiv(off, e.n))}]"
+        if isinstance(e, P.AsScalar):
+            V = e.e.type.elem.n
+            k = path[0][1]
+            v = self.access(e.e, [("i", T.idiv(k, V))])
+            lane = T.imod(k, V)
+            if isinstance(lane, T.IConst):
+                return f"({v}).{LANES[lane.v]}"
+            return f"dpia_lane{V}({v}, {render_index(lane)})"
+        if isinstance(e, P.Lit):
+            return self.literal(e)
+        if isinstance(e, P.Bin):
+            if path:
+                raise EmitError("index into a number")
+            a, b = self.access(e.a, []), self.access(e.b, [])
+            return self.binop(e.op, a, b, e.type)
+        if isinstance(e, P.Abs):
+            if isinstance(e.type, P.VecT):
+                return f"dpia_vabs{e.type.n}({self.access(e.a, [])})"
+            return f"fabsf({self.access(e.a, [])})"
+        if isinstance(e, P.Ident):
+            return self.base_read(e, path)
+        raise EmitError(f"cannot read a {type(e).__name__} (did a map or reduce escape translation?)")
+
+    def locate(self, e: P.Phrase, path: list):
+        """(array name, offset) of the element of e reached by path. Only views
+        that keep an array's elements adjacent in memory (index, split, join)
+        may lie between asVector and the input it reads."""
+        while True:
+            if isinstance(e, P.Idx):
+                path = [("i", e.i)] + path
+                e = e.e
+            elif isinstance(e, P.Split):
+                path = [("i", T.iadd(T.imul(path[0][1], e.n), path[1][1]))] + path[2:]
+                e = e.e
+            elif isinstance(e, P.Join):
+                m = e.e.type.elem.n
+                k = path[0][1]
+                path = [("i", T.idiv(k, m)), ("i", T.imod(k, m))] + path[1:]
+                e = e.e
+            elif isinstance(e, P.Transpose):
+                # neighbours of a transposed array are a row apart in memory
+                raise EmitError("asVector of a transposed array: its lanes are not adjacent in memory")
+            elif isinstance(e, P.To):
+                e = e.e
+            elif isinstance(e, P.Ident):
+                if e.temp is not None or e.name not in self.inputs:
+                    raise EmitError("asVector reads kernel inputs only")
+                return e.name, linear([s_[1] for s_ in path], dims(e.type))
+            else:
+                raise EmitError(f"asVector of a {type(e).__name__}")
+
+    def base_read(self, e: P.Ident, path: list) -> str:
+        idx = [s[1] for s in path]
+        if any(s[0] != "i" for s in path):
+            raise EmitError("projection of a non-pair")
+        if e.temp is None:
+            if e.name not in self.inputs:
+                raise EmitError(f"unknown input {e.name}")
+            if not idx:
+                return e.name if isinstance(e.type, P.Num) else f"{e.name}[0]"
+            return f"{e.name}[{render_index(linear(idx, dims(e.type)))}]"
+        t = self.temps[e.name]
+        return self.temp_ref(t, idx)
+
+    def temp_ref(self, t: T.Temp, idx: list) -> str:
+        shape = dims(t.type)
+        if t.space == "private":
+            if not shape:
+                return t.name
+            return f"{t.name}[{render_index(linear(idx, shape))}]"
+        off = linear(idx, shape) if shape else T.IConst(0)
+        if t.space == "global" and t.hoist:
+            size = P.scalar_count(t.type)
+            h = linear([v for v, _ in t.hoist], [n for _, n in t.hoist])
+            off = T.iadd(T.imul(h, size), off)
+        return f"{t.name}[{render_index(off)}]"
+
+    def literal(self, e: P.Lit) -> str:
+        if isinstance(e.type, P.VecT):
+            v = self.literal(P.Lit(e.value, e.type.num))
+            return f"make_float{e.type.n}({', '.join([v] * e.type.n)})"
+        if e.type.dtype == "f32":
+            v = float(e.value)
+            return f"{v!r}f" if v == v and abs(v) != float("inf") else "0.0f"
+        return f"(({CTYPE[e.type.dtype]}){int(e.value)})"
+
+    def binop(self, op, a, b, t) -> str:
+        if isinstance(t, P.VecT):
+            fn = {"+": "dpia_vadd", "-": "dpia_vsub", "*": "dpia_vmul"}[op]
+            return f"{fn}{t.n}({a}, {b})"
+        if t.dtype == "f32" and self.backend == "cuda":
+            fn = {"+": "__fadd_rn", "-": "__fsub_rn", "*": "__fmul_rn"}[op]
+            return f"{fn}({a}, {b})"
+        return f"({a} {op} {b})"
+
+    # -- writes ---------------------------------------------------------------
+
+    def write(self, acc: T.Acc, path: list) -> str:
+        if isinstance(acc, T.AIdx):
+            return self.write(acc.acc, [acc.i] + path)
+        if isinstance(acc, T.ASplit):
+            return self.write(acc.acc, [T.idiv(path[0], acc.n), T.imod(path[0], acc.n)] + path[1:])
+        if isinstance(acc, T.AJoin):
+            return self.write(acc.acc, [T.iadd(T.imul(path[0], acc.m), path[1])] + path[2:])
+        if isinstance(acc, T.ATranspose):
+            return self.write(acc.acc, [path[1], path[0]] + path[2:])
+        if isinstance(acc, T.AAsScalar):
+            # element j of the vector array is the V scalars at j*V of acc
+            inner = acc.acc
+            path2 = [T.imul(path[0], acc.V)] + path[1:]
+            while not isinstance(inner, T.AOut):
+                if isinstance(inner, T.AIdx):
+                    path2 = [inner.i] + path2
+                elif isinstance(inner, T.ASplit):
+                    path2 = [T.idiv(path2[0], inner.n), T.imod(path2[0], inner.n)] + path2[1:]
+                elif isinstance(inner, T.AJoin):
+                    path2 = [T.iadd(T.imul(path2[0], inner.m), path2[1])] + path2[2:]
+                else:
+                    raise EmitError("asScalar output through a transposed acceptor")
+                inner = inner.acc
+            if inner.temp is not None:
+                raise EmitError("asScalar into a temporary")
+            off = linear(path2, dims(inner.type))
+            if not divisible(off, acc.V):
+                raise EmitError("asScalar store not provably aligned")
+            vt = VTYPE[acc.V]
+            cast = f"reinterpret_cast<{vt} *>({inner.name})" if self.backend == "cuda" else f"(({vt} *){inner.name})"
+            return f"{cast}[{render_index(T.idiv(off, acc.V))}]"
+        if isinstance(acc, T.AOut):
+            if acc.temp is not None:
+                return self.temp_ref(acc.temp, path)
+            shape = dims(acc.type)
+            if isinstance(P.base_elem(acc.type), P.VecT):
+                vt = ctype(P.base_elem(acc.type))
+                cast = f"reinterpret_cast<{vt} *>({acc.name})" if self.backend == "cuda" else f"(({vt} *){acc.name})"
+                return f"{cast}[{render_index(linear(path, shape)) if shape else '0'}]"
+            if not shape:
+                return f"{acc.name}[0]"
+            return f"{acc.name}[{render_index(linear(path, shape))}]"
+        raise EmitError(f"unknown acceptor {type(acc).__name__}")
+
+    # -- commands -------------------------------------------------------------
+
+    def emit(self, c: T.Comm, ind: int, ctx: tuple):
+        """ctx: the levels of the enclosing loops."""
+        pad = "  " * ind
+        if isinstance(c, T.Seq):
+            for k, x in enumerate(c.cs):
+                local = self.backend == "cuda" and self.sync[-1] and _has_level(x, "local")
+                if local and k > 0:  # what the block's threads read was written by others
+                    self.lines.append(f"{pad}__syncthreads();")
+                self.emit(x, ind, ctx)
+                if local and k + 1 < len(c.cs):  # and the other way round
+                    self.lines.append(f"{pad}__syncthreads();")
+            return
+        if isinstance(c, T.New):
+            t = c.temp
+            if t.space != "private":
+                self.sync[-1] = True
+            if isinstance(P.base_elem(t.type), P.VecT) and (dims(t.type) or t.space != "private"):
+                raise EmitError("vector temporaries are private scalars only")
+            if t.space == "private":
+                ct = ctype(P.base_elem(t.type))
+                shape = dims(t.type)
+                par = sum(1 for l in ctx if l != "seq")
+                self.private_ctx[t.name] = (par, "local" in ctx or "global" in ctx)
+                if shape:
+                    self.lines.append(f"{pad}{ct} {t.name}[{P.scalar_count(t.type)}];")
+                else:
+                    self.lines.append(f"{pad}{ct} {t.name};")
+            elif t.space == "local" and self.backend == "cuda":
+                ct = CTYPE[P.base_num(t.type).dtype]
+                self.shared.append(f"  __shared__ {ct} {t.name}[{P.scalar_count(t.type)}];")
+            elif t.space == "local":
+                ct = CTYPE[P.base_num(t.type).dtype]
+                self.lines.append(f"{pad}{ct} {t.name}[{P.scalar_count(t.type)}];")
+            self.emit(c.body, ind, ctx)
+            return
+        if isinstance(c, T.Assign):
+            self.check_private_reads(c.e, ctx)
+            stmt = f"{self.write(c.acc, [])} = {self.access(c.e, [])};"
+            self.lines.append(f"{pad}{self.guard(ctx)}{stmt}")
+            return
+        if isinstance(c, T.For):
+            v, n = c.var.name, c.n
+            if self.backend == "c" or c.level == "seq":
+                if c.level == "seq" and not self.has_parallel(c.body) and self.guard(ctx):
+                    # a sequential loop outside the thread-level loops runs in one thread
+                    self.lines.append(f"{pad}{self.guard(ctx).strip()} {{")
+                    self.lines.append(f"{pad}  for (long long {v} = 0; {v} < {n}; ++{v}) {{")
+                    self.emit(c.body, ind + 2, ctx + ("seq", "guarded"))
+                    self.lines.append(f"{pad}  }}")
+                    self.lines.append(f"{pad}}}")
+                    return
+                if self.backend == "cuda" and self.unroll > 1 and c.level == "seq" and n > self.unroll:
+                    # a sequential loop's iterations stay in order; unrolling only
+                    # lets their loads be issued ahead of the dependent steps
+                    self.lines.append(f"{pad}#pragma unroll {self.unroll}")
+                self.lines.append(f"{pad}for (long long {v} = 0; {v} < {n}; ++{v}) {{")
+            elif c.level == "workgroup":
+                self.lines.append(f"{pad}for (long long {v} = blockIdx.x; {v} < {n}; {v} += gridDim.x) {{")
+            elif c.level == "local":
+                self.lines.append(f"{pad}for (long long {v} = threadIdx.x; {v} < {n}; {v} += blockDim.x) {{")
+            elif c.level == "global":
+                self.lines.append(f"{pad}for (long long {v} = (long long)blockIdx.x * blockDim.x + threadIdx.x; "
+                                  f"{v} < {n}; {v} += (long long)gridDim.x * blockDim.x) {{")
+            shared = _shares(c.body) or self.sync[-1]
+            self.sync.append(shared)
+            self.emit(c.body, ind + 1, ctx + (c.level,))
+            self.sync.pop()
+            if (self.backend == "cuda" and shared and c.level in ("workgroup", "seq")
+                    and _has_level(c.body, "local")):
+                # the next iteration's thread-level loops overwrite what this one's threads still read
+                self.lines.append(f"{pad}  __syncthreads();")
+            self.lines.append(f"{pad}}}")
+            return
+        raise EmitError(f"unknown command {type(c).__name__}")
+
+    def guard(self, ctx) -> str:
+        if self.backend == "c" or "guarded" in ctx:
+            return ""
+        if "local" in ctx or "global" in ctx:
+            return ""
+        if "workgroup" in ctx:
+            return "if (threadIdx.x == 0) "
+        return "if (blockIdx.x == 0 && threadIdx.x == 0) "
+
+    @staticmethod
+    def has_parallel(c) -> bool:
+        if isinstance(c, T.For):
+            return c.level != "seq" or Emitter.has_parallel(c.body)
+        if isinstance(c, T.Seq):
+            return any(Emitter.has_parallel(x) for x in c.cs)
+        if isinstance(c, T.New):
+            return Emitter.has_parallel(c.body)
+        return False
+
+    def check_private_reads(self, e, ctx):
+        """A private value is visible to its own thread only: one declared where
+        a single thread computes it may not be read inside a thread-level loop."""
+        if self.backend != "cuda":
+            return
+        inside_threads = "local" in ctx or "global" in ctx
+        for name in _idents(e):
+            if name in self.private_ctx:
+                _, declared_inside = self.private_ctx[name]
+                if inside_threads and not declared_inside:
+                    raise EmitError(f"private value {name} is computed by one thread but read by "
+                                    f"all threads of a thread-level map; place it in local memory")
+
+
+def _shares(c) -> bool:
+    """c declares a temporary in local or global memory."""
+    if isinstance(c, T.New):
+        return c.temp.space != "private" or _shares(c.body)
+    if isinstance(c, T.For):
+        return _shares(c.body)
+    if isinstance(c, T.Seq):
+        return any(_shares(x) for x in c.cs)
+    return False
+
+
+def _has_level(c, level) -> bool:
+    if isinstance(c, T.For):
+        return c.level == level or _has_level(c.body, level)
+    if isinstance(c, T.Seq):
+        return any(_has_level(x, level) for x in c.cs)
+    if isinstance(c, T.New):
+        return _has_level(c.body, level)
+    return False
+
+
+def _idents(e):
+    if isinstance(e, P.Ident):
+        yield e.name
+    for c in e.children():
+        yield from _idents(c)
+
+
+def generate(name: str, expr: P.Phrase, inputs: list, backend: str = "cuda", unroll: int = 1) -> dict:
+    """Source of a kernel computing expr into an output array; ``unroll`` > 1
+    asks the CUDA compiler to unroll sequential loops by that factor.
+
+    Returns {"source", "kernel", "params" (name, C type, count, role), "temps"}.
+    """
+    comm, out = T.translate(expr, "out")
+    temps = T.hoist(comm)
+    em = Emitter(backend, inputs, out, temps, unroll)
+    em.emit(comm, 1, ())
+    params = []
+    for p in inputs:
+        ct = CTYPE[P.base_num(p.type).dtype]
+        params.append((p.name, ct, P.scalar_count(p.type) if isinstance(p.type, P.Arr) else 1, "in"))
+    params.append(("out", CTYPE[P.base_num(expr.type).dtype],
+                   P.scalar_count(expr.type) if isinstance(expr.type, P.Arr) else 1, "out"))
+    for t in temps:
+        if t.space == "global":
+            count = P.scalar_count(t.type)
+            for _, n in t.hoist:
+                count *= n
+            params.append((t.name, CTYPE[P.base_num(t.type).dtype], count, "temp"))
+    sig = []
+    for pname, ct, _, role in params:
+        if role == "in":
+            sig.append(f"const {ct} *__restrict__ {pname}")
+        else:
+            sig.append(f"{ct} *__restrict__ {pname}")
+    body = "\n".join(em.shared + em.lines)
+    if backend == "cuda":
+        src = (f"{CUDA_PRELUDE}\nextern \"C\" __global__ void {name}({', '.join(sig)}) {{\n{body}\n}}\n")
+    else:
+        src = f"{C_PRELUDE}\nvoid {name}({', '.join(sig)}) {{\n{body}\n}}\n"
+    return {"source": src, "kernel": name, "params": params, "temps": temps, "comm": comm}

@@ -1,0 +1,547 @@
+"""Functional phrases: the data-parallel primitives of the paper's source
+language (Sections 2.1, 5 and 6.2), with their types.
+
+A phrase is built from inputs (``Ident``), literals, arithmetic on numbers,
+``map`` at a level of the GPU hierarchy (mapGlobal / mapWorkgroup / mapLocal /
+mapSeq), the sequential ``reduce`` (reduceSeq), and the data-layout
+primitives ``zip``, ``fst``, ``snd``, ``split``, ``join``, ``transpose``,
+``asVector`` and ``asScalar`` (vectors num<V> of Section 6.2, + - * lane-wise);
+``to_private`` / ``to_local`` / ``to_global`` choose the address space of a
+map's output when it becomes a temporary (Section 6.2, address spaces).
+Types are checked as the phrase is built: a number type, an array ``n.d`` or
+a pair.
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass, field
+
+LEVELS = ("global", "workgroup", "local", "seq")
+SPACES = ("global", "local", "private")
+
+# ---------------------------------------------------------------------------
+# data types
+# ---------------------------------------------------------------------------
+
+
+@dataclass(frozen=True)
+class Num:
+    dtype: str  # "f32", "i32" or "i64"
+
+    def __post_init__(self):
+        if self.dtype not in ("f32", "i32", "i64"):
+            raise TypeError(f"unknown number type {self.dtype}")
+
+    def __str__(self):
+        return self.dtype
+
+
+@dataclass(frozen=True)
+class Arr:
+    n: int
+    elem: object
+
+    def __post_init__(self):
+        if not isinstance(self.n, int) or self.n < 0:
+            raise TypeError(f"array length must be a natural number, not {self.n!r}")
+
+    def __str__(self):
+        return f"{self.n}.{self.elem}"
+
+
+@dataclass(frozen=True)
+class PairT:
+    a: object
+    b: object
+
+    def __str__(self):
+        return f"({self.a} x {self.b})"
+
+
+@dataclass(frozen=True)
+class VecT:
+    """num<V> (Section 6.2's vector data type): V numbers handled as one value."""
+    n: int
+    num: Num
+
+    def __post_init__(self):
+        if self.n not in (2, 4):
+            raise TypeError(f"vector width {self.n} (2 or 4)")
+        if self.num.dtype != "f32":
+            raise TypeError("vectors of f32 only")
+
+    def __str__(self):
+        return f"{self.num}<{self.n}>"
+
+
+F32, I32, I64 = Num("f32"), Num("i32"), Num("i64")
+
+
+def is_scalar(t) -> bool:
+    """A number or a vector of numbers: a value one thread holds in registers."""
+    return isinstance(t, (Num, VecT))
+
+
+def arr(*dims_and_elem):
+    """arr(n, m, F32) is the type n.m.f32."""
+    *dims, elem = dims_and_elem
+    t = elem
+    for d in reversed(dims):
+        t = Arr(int(d), t)
+    return t
+
+
+def scalar_count(t) -> int:
+    """Numbers in a value of type t (arrays of numbers or vectors)."""
+    if isinstance(t, Num):
+        return 1
+    if isinstance(t, VecT):
+        return t.n
+    if isinstance(t, Arr):
+        return t.n * scalar_count(t.elem)
+    raise TypeError(f"{t} is not an array of numbers")
+
+
+def base_num(t) -> Num:
+    while isinstance(t, Arr):
+        t = t.elem
+    if isinstance(t, VecT):
+        return t.num
+    if not isinstance(t, Num):
+        raise TypeError(f"{t} is not an array of numbers")
+    return t
+
+
+def base_elem(t):
+    """The number or vector type at the bottom of an array type."""
+    while isinstance(t, Arr):
+        t = t.elem
+    return t
+
+
+# ---------------------------------------------------------------------------
+# phrases
+# ---------------------------------------------------------------------------
+
+_names = itertools.count()
+
+
+def fresh(prefix: str) -> str:
+    return f"{prefix}{next(_names)}"
+
+
+class Phrase:
+    type: object
+
+    def children(self):
+        return ()
+
+    def computes(self) -> bool:
+        """True if evaluating the phrase runs a map or a reduce (it is not a
+        pure view of its inputs or arithmetic on numbers)."""
+        return any(c.computes() for c in self.children())
+
+
+@dataclass(eq=False)
+class Ident(Phrase):
+    name: str
+    type: object
+    temp: str | None = None  # address space if the identifier names a temporary
+
+
+@dataclass(eq=False)
+class Lit(Phrase):
+    value: float
+    type: object = F32
+
+
+@dataclass(eq=False)
+class Bin(Phrase):
+    op: str  # "+", "-", "*"
+    a: Phrase
+    b: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        if self.op not in ("+", "-", "*"):
+            raise TypeError(f"unknown operator {self.op}")
+        if not is_scalar(self.a.type) or self.a.type != self.b.type:
+            raise TypeError(f"{self.op} needs two numbers (or vectors) of one type, "
+                            f"not {self.a.type} and {self.b.type}")
+        self.type = self.a.type
+
+    def children(self):
+        return (self.a, self.b)
+
+
+@dataclass(eq=False)
+class Abs(Phrase):
+    a: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        if self.a.type != F32 and not isinstance(self.a.type, VecT):
+            raise TypeError("abs of a non-f32")
+        self.type = self.a.type
+
+    def children(self):
+        return (self.a,)
+
+
+@dataclass(eq=False)
+class Lam:
+    """A function of one or two phrases (the body refers to the parameters)."""
+    params: tuple
+    body: Phrase
+
+
+def lam(param_types, fn):
+    """lam([t1, t2], lambda a, b: ...) builds a function phrase."""
+    params = tuple(Ident(fresh("p"), t) for t in param_types)
+    return Lam(params, fn(*params))
+
+
+@dataclass(eq=False)
+class Map(Phrase):
+    level: str
+    f: Lam
+    e: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        if self.level not in LEVELS:
+            raise TypeError(f"unknown level {self.level}")
+        if not isinstance(self.e.type, Arr):
+            raise TypeError(f"map over a non-array {self.e.type}")
+        if len(self.f.params) != 1 or self.f.params[0].type != self.e.type.elem:
+            raise TypeError(f"map function takes {[p.type for p in self.f.params]}, elements are {self.e.type.elem}")
+        self.type = Arr(self.e.type.n, self.f.body.type)
+
+    def children(self):
+        return (self.e, self.f.body)
+
+    def computes(self):
+        return True
+
+
+@dataclass(eq=False)
+class Reduce(Phrase):
+    """reduceSeq f init e: a left fold, f(element, accumulator) (Section 4.2's reduceI)."""
+    f: Lam
+    init: Phrase
+    e: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        if not isinstance(self.e.type, Arr):
+            raise TypeError(f"reduce over a non-array {self.e.type}")
+        if not is_scalar(self.init.type):
+            raise TypeError("reduce accumulates numbers or vectors")
+        ps = self.f.params
+        if len(ps) != 2 or ps[0].type != self.e.type.elem or ps[1].type != self.init.type:
+            raise TypeError("reduce function must take (element, accumulator)")
+        if self.f.body.type != self.init.type:
+            raise TypeError("reduce function must return the accumulator type")
+        self.type = self.init.type
+
+    def children(self):
+        return (self.init, self.e, self.f.body)
+
+    def computes(self):
+        return True
+
+
+@dataclass(eq=False)
+class Zip(Phrase):
+    a: Phrase
+    b: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        ta, tb = self.a.type, self.b.type
+        if not (isinstance(ta, Arr) and isinstance(tb, Arr) and ta.n == tb.n):
+            raise TypeError(f"zip of {ta} and {tb}")
+        self.type = Arr(ta.n, PairT(ta.elem, tb.elem))
+
+    def children(self):
+        return (self.a, self.b)
+
+
+@dataclass(eq=False)
+class Proj(Phrase):
+    k: int  # 0 = fst, 1 = snd
+    e: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        if not isinstance(self.e.type, PairT):
+            raise TypeError(f"projection of a non-pair {self.e.type}")
+        self.type = self.e.type.a if self.k == 0 else self.e.type.b
+
+    def children(self):
+        return (self.e,)
+
+
+@dataclass(eq=False)
+class Split(Phrase):
+    n: int
+    e: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        t = self.e.type
+        if not isinstance(t, Arr) or self.n <= 0 or t.n % self.n:
+            raise TypeError(f"split {self.n} of {t}")
+        self.type = Arr(t.n // self.n, Arr(self.n, t.elem))
+
+    def children(self):
+        return (self.e,)
+
+
+@dataclass(eq=False)
+class Join(Phrase):
+    e: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        t = self.e.type
+        if not (isinstance(t, Arr) and isinstance(t.elem, Arr)):
+            raise TypeError(f"join of {t}")
+        self.type = Arr(t.n * t.elem.n, t.elem.elem)
+
+    def children(self):
+        return (self.e,)
+
+
+@dataclass(eq=False)
+class Transpose(Phrase):
+    e: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        t = self.e.type
+        if not (isinstance(t, Arr) and isinstance(t.elem, Arr)):
+            raise TypeError(f"transpose of {t}")
+        self.type = Arr(t.elem.n, Arr(t.n, t.elem.elem))
+
+    def children(self):
+        return (self.e,)
+
+
+@dataclass(eq=False)
+class AsVector(Phrase):
+    """asVector V: (mV).num -> m.num<V> (Section 6.2), read as V-wide loads."""
+    n: int
+    e: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        t = self.e.type
+        if not (isinstance(t, Arr) and isinstance(t.elem, Num) and t.n % self.n == 0):
+            raise TypeError(f"asVector {self.n} of {t}")
+        self.type = Arr(t.n // self.n, VecT(self.n, t.elem))
+
+    def children(self):
+        return (self.e,)
+
+
+@dataclass(eq=False)
+class AsScalar(Phrase):
+    """asScalar: m.num<V> -> (mV).num."""
+    e: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        t = self.e.type
+        if not (isinstance(t, Arr) and isinstance(t.elem, VecT)):
+            raise TypeError(f"asScalar of {t}")
+        self.type = Arr(t.n * t.elem.n, t.elem.num)
+
+    def children(self):
+        return (self.e,)
+
+
+@dataclass(eq=False)
+class To(Phrase):
+    """to_global / to_local / to_private: where e's result lives if it becomes a temporary."""
+    space: str
+    e: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        if self.space not in SPACES:
+            raise TypeError(f"unknown address space {self.space}")
+        self.type = self.e.type
+
+    def children(self):
+        return (self.e,)
+
+
+@dataclass(eq=False)
+class Idx(Phrase):
+    """Element i of an array phrase (i an index expression); produced by the translation."""
+    e: Phrase
+    i: object
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        if not isinstance(self.e.type, Arr):
+            raise TypeError(f"index into a non-array {self.e.type}")
+        self.type = self.e.type.elem
+
+    def children(self):
+        return (self.e,)
+
+
+# ---------------------------------------------------------------------------
+# constructors in the paper's notation
+# ---------------------------------------------------------------------------
+
+
+def map_at(level, f, e, *, param_type=None):
+    """map at a level; f is a Python function of one phrase."""
+    t = e.type.elem if isinstance(e.type, Arr) else None
+    return Map(level, lam([param_type or t], f), e)
+
+
+def mapGlobal(f, e):
+    return map_at("global", f, e)
+
+
+def mapWorkgroup(f, e):
+    return map_at("workgroup", f, e)
+
+
+def mapLocal(f, e):
+    return map_at("local", f, e)
+
+
+def mapSeq(f, e):
+    return map_at("seq", f, e)
+
+
+def reduceSeq(f, init, e):
+    """f is a Python function (element, accumulator) -> accumulator."""
+    if not isinstance(init, Phrase):
+        init = Lit(float(init), F32)
+    return Reduce(lam([e.type.elem, init.type], f), init, e)
+
+
+def zip_(a, b):
+    return Zip(a, b)
+
+
+def fst(e):
+    return Proj(0, e)
+
+
+def snd(e):
+    return Proj(1, e)
+
+
+def split(n, e):
+    return Split(int(n), e)
+
+
+def join(e):
+    return Join(e)
+
+
+def transpose(e):
+    return Transpose(e)
+
+
+def asVector(n, e):
+    return AsVector(int(n), e)
+
+
+def asScalar(e):
+    return AsScalar(e)
+
+
+def vlit(v, n=4):
+    """The vector with every lane v."""
+    return Lit(v, VecT(n, F32))
+
+
+def to_private(e):
+    return To("private", e)
+
+
+def to_local(e):
+    return To("local", e)
+
+
+def to_global(e):
+    return To("global", e)
+
+
+def lit(v, t=F32):
+    return Lit(v, t)
+
+
+def add(a, b):
+    return Bin("+", a, b)
+
+
+def mul(a, b):
+    return Bin("*", a, b)
+
+
+def sub(a, b):
+    return Bin("-", a, b)
+
+
+def abs_(a):
+    return Abs(a)
+
+
+def inp(name, t):
+    """A kernel input of type t (an array of numbers, or a number)."""
+    return Ident(name, t)
+
+
+# ---------------------------------------------------------------------------
+# substitution (beta reduction of a function applied to a phrase)
+# ---------------------------------------------------------------------------
+
+
+def subst(p: Phrase, env: dict) -> Phrase:
+    """p with every identifier named in env replaced by env[name]."""
+    if isinstance(p, Ident):
+        return env.get(p.name, p)
+    if isinstance(p, Lit):
+        return p
+    if isinstance(p, Bin):
+        return Bin(p.op, subst(p.a, env), subst(p.b, env))
+    if isinstance(p, Abs):
+        return Abs(subst(p.a, env))
+    if isinstance(p, Map):
+        return Map(p.level, Lam(p.f.params, subst(p.f.body, env)), subst(p.e, env))
+    if isinstance(p, Reduce):
+        return Reduce(Lam(p.f.params, subst(p.f.body, env)), subst(p.init, env), subst(p.e, env))
+    if isinstance(p, Zip):
+        return Zip(subst(p.a, env), subst(p.b, env))
+    if isinstance(p, Proj):
+        return Proj(p.k, subst(p.e, env))
+    if isinstance(p, Split):
+        return Split(p.n, subst(p.e, env))
+    if isinstance(p, Join):
+        return Join(subst(p.e, env))
+    if isinstance(p, Transpose):
+        return Transpose(subst(p.e, env))
+    if isinstance(p, To):
+        return To(p.space, subst(p.e, env))
+    if isinstance(p, AsVector):
+        return AsVector(p.n, subst(p.e, env))
+    if isinstance(p, AsScalar):
+        return AsScalar(subst(p.e, env))
+    if isinstance(p, Idx):
+        return Idx(subst(p.e, env), p.i)
+    raise TypeError(f"cannot substitute into {type(p).__name__}")
+
+
+def apply(f: Lam, *args: Phrase) -> Phrase:
+    if len(args) != len(f.params):
+        raise TypeError("wrong number of arguments")
+    return subst(f.body, {p.name: a for p, a in zip(f.params, args)})

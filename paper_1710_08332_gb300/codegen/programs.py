@@ -1,0 +1,103 @@
+"""The paper's running examples as phrases (Sections 2.1 and 7): each program
+is one or two kernels, the second folding the first one's partial results.
+
+    dot   partials = join (mapWorkgroup (lambda chunk.
+                       mapLocal (lambda col. reduceSeq (+) 0 (map (*) col))
+                                (columns chunk)) (split s (zip x y)))
+          result   = reduceSeq (+) 0 partials
+    asum  the same with map abs
+    scal  mapGlobal (lambda v. a * v) x
+    gemv  partials = join (mapWorkgroup (lambda row.
+                       mapLocal (lambda col. reduceSeq (+) 0 (map (*) col))
+                                (columns (zip row x))) A)
+          y        = mapGlobal (lambda p. reduceSeq (+) 0 p) (split T partials)
+
+With V > 1 the streams are read as ``asVector V`` (128-bit loads at V = 4),
+the fold runs lane-wise on num<V> and each thread's V lane sums are written
+out un-reduced; the next kernel folds them like any other partials.
+``columns`` is the thread mapping: interleaved (``transpose (split T c)``:
+thread t folds items r*T + t) or contiguous (``split (len/T) c``: thread t folds
+items t*R .. t*R + R - 1, the paper's form). The map (*) is fused into the
+fold's step function, as the paper's strategies do.
+"""
+from __future__ import annotations
+
+from . import phrase as P
+
+
+def columns(chunk, T: int, thread_map: str):
+    n = chunk.type.n
+    if n % T:
+        raise ValueError(f"{n} items do not split over {T} threads")
+    if thread_map == "interleaved":
+        return P.transpose(P.split(T, chunk))
+    if thread_map == "contig":
+        return P.split(n // T, chunk)
+    raise ValueError(f"unknown thread map {thread_map}")
+
+
+def _vec(e, V):
+    return e if V == 1 else P.asVector(V, e)
+
+
+def _zero(V):
+    return P.lit(0.0) if V == 1 else P.vlit(0.0, V)
+
+
+def dot_partials(n: int, s: int, T: int, thread_map: str = "interleaved", V: int = 1):
+    """(phrase, inputs): the per-thread partial sums of x . y (C*T of them, C = n/s).
+    With V > 1 the inputs are read as asVector V and each thread keeps V lane
+    sums, written out un-reduced (Section 6's float4 kernel): C*T*V partials."""
+    x, y = P.inp("x", P.arr(n, P.F32)), P.inp("y", P.arr(n, P.F32))
+    e = P.join(P.mapWorkgroup(
+        lambda chunk: P.mapLocal(
+            lambda col: P.reduceSeq(lambda p, acc: P.add(acc, P.mul(P.fst(p), P.snd(p))), _zero(V), col),
+            columns(chunk, T, thread_map)),
+        P.split(s // V, P.zip_(_vec(x, V), _vec(y, V)))))
+    return e, [x, y]
+
+
+def asum_partials(n: int, s: int, T: int, thread_map: str = "interleaved", V: int = 1):
+    x = P.inp("x", P.arr(n, P.F32))
+    e = P.join(P.mapWorkgroup(
+        lambda chunk: P.mapLocal(
+            lambda col: P.reduceSeq(lambda v, acc: P.add(acc, P.abs_(v)), _zero(V), col),
+            columns(chunk, T, thread_map)),
+        P.split(s // V, _vec(x, V))))
+    return e, [x]
+
+
+def fold_all(m: int):
+    """The second kernel: reduceSeq (+) 0 over m partials."""
+    p = P.inp("p", P.arr(m, P.F32))
+    return P.reduceSeq(lambda v, acc: P.add(acc, v), 0.0, p), [p]
+
+
+def scal(n: int, a: float, V: int = 1):
+    x = P.inp("x", P.arr(n, P.F32))
+    if V == 1:
+        return P.mapGlobal(lambda v: P.mul(P.lit(a), v), x), [x]
+    return P.asScalar(P.mapGlobal(lambda v: P.mul(P.vlit(a, V), v), P.asVector(V, x))), [x]
+
+
+def gemv_partials(M: int, N: int, T: int, thread_map: str = "interleaved", V: int = 1):
+    """Per-row, per-thread partials of A x (M*T of them, or M*T*V lane sums)."""
+    A, x = P.inp("A", P.arr(M, N, P.F32)), P.inp("x", P.arr(N, P.F32))
+    e = P.join(P.mapWorkgroup(
+        lambda row: P.mapLocal(
+            lambda col: P.reduceSeq(lambda p, acc: P.add(acc, P.mul(P.fst(p), P.snd(p))), _zero(V), col),
+            columns(P.zip_(_vec(row, V), _vec(x, V)), T, thread_map)),
+        A))
+    return e, [A, x]
+
+
+def fold_rows(M: int, T: int):
+    """The GEMV second kernel: y_i = reduceSeq (+) 0 over row i's T partials."""
+    p = P.inp("p", P.arr(M * T, P.F32))
+    return P.mapGlobal(lambda r: P.reduceSeq(lambda v, acc: P.add(acc, v), 0.0, r), P.split(T, p)), [p]
+
+
+def dot_K1(n: int):
+    """The single-thread dot of Section 2.2 (one kernel, one thread)."""
+    x, y = P.inp("x", P.arr(n, P.F32)), P.inp("y", P.arr(n, P.F32))
+    return P.reduceSeq(lambda p, acc: P.add(acc, P.mul(P.fst(p), P.snd(p))), 0.0, P.zip_(x, y)), [x, y]

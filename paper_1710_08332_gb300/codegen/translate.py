@@ -1,0 +1,350 @@
+"""From functional phrases to an imperative loop nest (the paper's Stages I
+and II, Sections 4 and 5).
+
+Stage I is the pair of translations: the acceptor-passing translation
+``A(E, out)`` produces a command that writes the value of E through the
+acceptor ``out``, and the continuation-passing translation ``C(E, k)``
+produces a command that computes E and hands the resulting expression to the
+continuation k. Data-layout primitives (zip, split, join, transpose, fst,
+snd) never compute: C passes them on as views and A pushes them onto the
+acceptor (a split value is written through a "split acceptor", and so on).
+Stage II replaces the intermediate combinators by their definitions: mapI at
+a level becomes a parallel for at that level, and reduceI becomes a new
+private accumulator, its initialisation, a sequential for loop and the
+continuation applied to the accumulator.
+
+The result is a command tree of ``New`` (a temporary in an address space),
+``For`` (a loop at a level), ``Assign`` (acceptor := expression) and ``Seq``.
+Nested maps must run at strictly finer levels (workgroup > local > seq;
+global > seq), the legality rule the paper's conclusion asks for.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+from . import phrase as P
+
+# ---------------------------------------------------------------------------
+# index expressions
+# ---------------------------------------------------------------------------
+
+
+@dataclass(frozen=True)
+class IVar:
+    name: str
+
+
+@dataclass(frozen=True)
+class IConst:
+    v: int
+
+
+@dataclass(frozen=True)
+class IOp:
+    op: str  # "+", "*", "/", "%"
+    a: object
+    b: object
+
+
+def iadd(a, b):
+    if isinstance(a, IConst) and a.v == 0:
+        return b
+    if isinstance(b, IConst) and b.v == 0:
+        return a
+    if isinstance(a, IConst) and isinstance(b, IConst):
+        return IConst(a.v + b.v)
+    return IOp("+", a, b)
+
+
+def imul(a, n: int):
+    if n == 0:
+        return IConst(0)
+    if n == 1:
+        return a
+    if isinstance(a, IConst):
+        return IConst(a.v * n)
+    return IOp("*", a, IConst(n))
+
+
+def _multiple(a, n: int) -> bool:
+    """a is a multiple of n for every value of its variables (a sum of multiples)."""
+    if isinstance(a, IConst):
+        return a.v % n == 0
+    if isinstance(a, IOp):
+        if a.op == "+":
+            return _multiple(a.a, n) and _multiple(a.b, n)
+        if a.op == "*" and isinstance(a.b, IConst):
+            return a.b.v % n == 0 or _multiple(a.a, n)
+    return False
+
+
+def idiv(a, n: int):
+    if n == 1:
+        return a
+    if isinstance(a, IConst):
+        return IConst(a.v // n)
+    if isinstance(a, IOp) and a.op == "*" and isinstance(a.b, IConst) and a.b.v % n == 0:
+        return imul(a.a, a.b.v // n)
+    if isinstance(a, IOp) and a.op == "+" and _multiple(a.a, n) and _multiple(a.b, n):
+        return iadd(idiv(a.a, n), idiv(a.b, n))
+    return IOp("/", a, IConst(n))
+
+
+def imod(a, n: int):
+    if n == 1 or _multiple(a, n):
+        return IConst(0)
+    if isinstance(a, IConst):
+        return IConst(a.v % n)
+    return IOp("%", a, IConst(n))
+
+
+# ---------------------------------------------------------------------------
+# acceptors and commands
+# ---------------------------------------------------------------------------
+
+
+@dataclass(eq=False)
+class Temp:
+    """A temporary (Section 4's new): its type, address space and the
+    parallel loops it is hoisted out of (Section 6.4) -- filled in later."""
+    name: str
+    type: object
+    space: str
+    hoist: list = field(default_factory=list)  # [(loop variable, trip count)] outermost first
+
+
+class Acc:
+    pass
+
+
+@dataclass(eq=False)
+class AOut(Acc):
+    """The kernel's output array, or a temporary."""
+    name: str
+    type: object
+    temp: Temp | None = None
+
+
+@dataclass(eq=False)
+class AIdx(Acc):
+    acc: Acc
+    i: object
+
+
+@dataclass(eq=False)
+class ASplit(Acc):
+    """A(split n e, out) writes e through ASplit(n, out): e's element [q] goes
+    to out[q / n][q % n]."""
+    n: int
+    acc: Acc
+
+
+@dataclass(eq=False)
+class AJoin(Acc):
+    """A(join e, out) writes e (inner length m) through AJoin(m, out): e's
+    element [i][j] goes to out[i*m + j]."""
+    m: int
+    acc: Acc
+
+
+@dataclass(eq=False)
+class AAsScalar(Acc):
+    """A(asScalar e, out) writes e's vectors (width V) whole into the scalar array out."""
+    V: int
+    acc: Acc
+
+
+@dataclass(eq=False)
+class ATranspose(Acc):
+    """Acceptor for a transposed value: element [i][j] goes to acc[j][i]."""
+    acc: Acc
+
+
+class Comm:
+    pass
+
+
+@dataclass(eq=False)
+class Seq(Comm):
+    cs: list
+
+
+@dataclass(eq=False)
+class Assign(Comm):
+    acc: Acc
+    e: P.Phrase
+
+
+@dataclass(eq=False)
+class New(Comm):
+    temp: Temp
+    body: Comm
+
+
+@dataclass(eq=False)
+class For(Comm):
+    var: IVar
+    n: int
+    level: str
+    body: Comm
+
+
+class TranslationError(Exception):
+    pass
+
+
+# ---------------------------------------------------------------------------
+# Stage I + II
+# ---------------------------------------------------------------------------
+
+_RANK = {"global": 0, "workgroup": 0, "local": 1, "seq": 2}
+
+
+class Translator:
+    def __init__(self):
+        self.count = 0
+
+    def ivar(self, prefix="i"):
+        self.count += 1
+        return IVar(f"{prefix}{self.count}")
+
+    def temp(self, t, space):
+        self.count += 1
+        return Temp(f"t{self.count}", t, space)
+
+    # -- legality of nested levels ------------------------------------------
+
+    @staticmethod
+    def check_nesting(outer: list, level: str):
+        if not outer:
+            return
+        last = outer[-1]
+        if level == "seq":
+            return
+        if last in ("global", "local", "seq") or (last == "workgroup" and level != "local"):
+            raise TranslationError(f"illegal nesting: a {level} map inside a {last} map "
+                                   f"(a nested map must run at a strictly finer level)")
+
+    # -- A: acceptor-passing ------------------------------------------------
+
+    def A(self, e: P.Phrase, out: Acc, levels: list) -> Comm:
+        if isinstance(e, P.Map):
+            self.check_nesting(levels, e.level)
+
+            def body(x):
+                i = self.ivar()
+                inner = self.A(P.apply(e.f, P.Idx(x, i)), AIdx(out, i), levels + [e.level])
+                return For(i, e.e.type.n, e.level, inner)
+
+            return self.C(e.e, body, levels)
+        if isinstance(e, P.Reduce):
+            return self.C(e, lambda v: self.assign(out, v, levels), levels)
+        if isinstance(e, P.Split):
+            return self.A(e.e, ASplit(e.n, out), levels)
+        if isinstance(e, P.Join):
+            return self.A(e.e, AJoin(e.e.type.elem.n, out), levels)
+        if isinstance(e, P.Transpose):
+            return self.A(e.e, ATranspose(out), levels)
+        if isinstance(e, P.To):
+            return self.A(e.e, out, levels)
+        if isinstance(e, P.AsScalar) and e.computes():
+            return self.A(e.e, AAsScalar(e.e.type.elem.n, out), levels)
+        if P.is_scalar(e.type):
+            return self.C(e, lambda v: Assign(out, v), levels)
+        if isinstance(e.type, P.Arr) and not e.computes():
+            # a view of arrays written out element by element (mapSeq id)
+            return self.copy(e, out, levels)
+        if isinstance(e, (P.Zip, P.Proj)):
+            return self.C(e, lambda v: self.copy(v, out, levels), levels)
+        raise TranslationError(f"cannot write a {type(e).__name__} through an acceptor")
+
+    def assign(self, out, v, levels):
+        if P.is_scalar(v.type):
+            return Assign(out, v)
+        return self.copy(v, out, levels)
+
+    def copy(self, v: P.Phrase, out: Acc, levels: list) -> Comm:
+        if P.is_scalar(v.type):
+            return Assign(out, v)
+        if not isinstance(v.type, P.Arr):
+            raise TranslationError(f"cannot copy a value of type {v.type}")
+        i = self.ivar()
+        return For(i, v.type.n, "seq", self.copy(P.Idx(v, i), AIdx(out, i), levels + ["seq"]))
+
+    # -- C: continuation-passing --------------------------------------------
+
+    def C(self, e: P.Phrase, k, levels: list) -> Comm:
+        if not e.computes():
+            return k(e)
+        if isinstance(e, P.Reduce):
+            # reduceI: new accumulator := init; for i: acc := f(x[i], acc); k(acc)
+            def body(x):
+                t = self.temp(e.type, "private")
+                tv = P.Ident(t.name, t.type, temp="private")
+                acc = AOut(t.name, t.type, t)
+                i = self.ivar("r")
+                init = self.A(e.init, acc, levels)
+                step = self.A(P.apply(e.f, P.Idx(x, i), tv), acc, levels + ["seq"])
+                return New(t, Seq([init, For(i, e.e.type.n, "seq", step), k(tv)]))
+
+            return self.C(e.e, body, levels)
+        if isinstance(e, (P.Map, P.To)):
+            space = e.space if isinstance(e, P.To) else "global"
+            inner = e.e if isinstance(e, P.To) else e
+            if isinstance(inner, P.Map) and inner.level in ("global", "workgroup") and levels == []:
+                # the consumer would read elements other blocks wrote: that needs a kernel boundary
+                raise TranslationError("the result of a global or workgroup map is consumed in the same "
+                                       "kernel; split the program into two kernels")
+            t = self.temp(e.type, space)
+            tv = P.Ident(t.name, t.type, temp=space)
+            return New(t, Seq([self.A(inner, AOut(t.name, t.type, t), levels), k(tv)]))
+        if isinstance(e, P.Bin):
+            return self.C(e.a, lambda a: self.C(e.b, lambda b: k(P.Bin(e.op, a, b)), levels), levels)
+        if isinstance(e, P.Abs):
+            return self.C(e.a, lambda a: k(P.Abs(a)), levels)
+        if isinstance(e, P.Zip):
+            return self.C(e.a, lambda a: self.C(e.b, lambda b: k(P.Zip(a, b)), levels), levels)
+        if isinstance(e, P.Proj):
+            return self.C(e.e, lambda v: k(P.Proj(e.k, v)), levels)
+        if isinstance(e, P.Split):
+            return self.C(e.e, lambda v: k(P.Split(e.n, v)), levels)
+        if isinstance(e, P.Join):
+            return self.C(e.e, lambda v: k(P.Join(v)), levels)
+        if isinstance(e, P.Transpose):
+            return self.C(e.e, lambda v: k(P.Transpose(v)), levels)
+        if isinstance(e, P.Idx):
+            return self.C(e.e, lambda v: k(P.Idx(v, e.i)), levels)
+        if isinstance(e, P.AsVector):
+            return self.C(e.e, lambda v: k(P.AsVector(e.n, v)), levels)
+        if isinstance(e, P.AsScalar):
+            return self.C(e.e, lambda v: k(P.AsScalar(v)), levels)
+        raise TranslationError(f"cannot translate {type(e).__name__}")
+
+
+def translate(e: P.Phrase, out_name: str = "out") -> tuple[Comm, AOut]:
+    """The command writing the value of e to the output array ``out_name``."""
+    out = AOut(out_name, e.type)
+    return Translator().A(e, out, []), out
+
+
+# ---------------------------------------------------------------------------
+# hoisting (Section 6.4): temporaries in global memory move out of parallel
+# loops, each iteration getting its own slice
+# ---------------------------------------------------------------------------
+
+
+def hoist(c: Comm, loops=()) -> list:
+    """Record, for each global temporary, the parallel loops around it; return
+    every temporary found (in order)."""
+    found = []
+    if isinstance(c, Seq):
+        for x in c.cs:
+            found += hoist(x, loops)
+    elif isinstance(c, New):
+        if c.temp.space == "global":
+            c.temp.hoist = [(v, n) for (v, n, lvl) in loops if lvl != "seq"]
+        found.append(c.temp)
+        found += hoist(c.body, loops)
+    elif isinstance(c, For):
+        found += hoist(c.body, loops + ((c.var, c.n, c.level),))
+    return found

@@ -1,0 +1,267 @@
+"""The strategy-preserving code generator, checked on the host.
+
+Each program is a phrase over the paper's primitives; the generator's C
+backend compiles the loop nest it derives, and the result must be
+bit-identical to the oracle's evaluation of the same phrase written with the
+oracle's own primitives (c1). The CUDA source of every program must compile
+for sm_103a. Illegal level nestings and a kernel reading what other blocks
+of the same kernel wrote are rejected.
+"""
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import patterns as c1
+from paper_1710_08332_gb300 import codegen as G
+from paper_1710_08332_gb300.codegen import build as B
+from paper_1710_08332_gb300.codegen import emit as E
+from paper_1710_08332_gb300.codegen import programs as PR
+from paper_1710_08332_gb300.codegen import translate as T
+
+F = c1.F32
+
+
+def bits(a):
+    return np.asarray(a, np.float32).view(np.uint32)
+
+
+def uniform(n, seed):
+    return np.random.default_rng(seed).uniform(-1, 1, n).astype(np.float32)
+
+
+def cols(chunk, Tn, thread_map):
+    return c1.transpose(c1.split(Tn, chunk)) if thread_map == "interleaved" else c1.split(len(chunk) // Tn, chunk)
+
+
+def oracle_dot_partials(x, y, s, Tn, thread_map):
+    return c1.join(c1.mapWorkgroup(
+        lambda ch: c1.mapLocal(lambda col: c1.reduce_(lambda p, a: F.add(a, F.mul(p[0], p[1])), F.zero, col),
+                               cols(ch, Tn, thread_map)),
+        c1.split(s, c1.zip_(list(x), list(y)))))
+
+
+def oracle_fold(p):
+    return c1.reduce_(lambda v, a: F.add(a, v), F.zero, list(p))
+
+
+@pytest.mark.parametrize("thread_map", ["interleaved", "contig"])
+@pytest.mark.parametrize("n,s,Tn", [(4096, 512, 32), (6144, 2048, 64), (256, 256, 1)])
+def test_dot_two_kernels_match_oracle(n, s, Tn, thread_map):
+    x, y = uniform(n, 1), uniform(n, 2)
+    e, ins = PR.dot_partials(n, s, Tn, thread_map)
+    part = np.zeros(n // s * Tn, np.float32)
+    G.compile_c("dotp", e, ins).run(x, y, part)
+    want = oracle_dot_partials(x, y, s, Tn, thread_map)
+    assert np.array_equal(bits(part), bits(want))
+    e2, ins2 = PR.fold_all(part.size)
+    out = np.zeros(1, np.float32)
+    G.compile_c("fold", e2, ins2).run(part, out)
+    assert bits(out)[0] == bits([oracle_fold(want)])[0]
+
+
+def test_dot_K1_is_the_sequential_loop():
+    x, y = uniform(1000, 3), uniform(1000, 4)
+    e, ins = PR.dot_K1(1000)
+    out = np.zeros(1, np.float32)
+    G.compile_c("k1", e, ins).run(x, y, out)
+    acc = np.float32(0)
+    for a, b in zip(x, y):
+        acc = np.float32(acc + np.float32(a * b))
+    assert bits(out)[0] == bits([acc])[0]
+
+
+def test_asum_scal_gemv_match_oracle():
+    n, s, Tn = 8192, 1024, 64
+    x = uniform(n, 5)
+    x[::7] = -x[::7]
+    e, ins = PR.asum_partials(n, s, Tn, "contig")
+    part = np.zeros(n // s * Tn, np.float32)
+    G.compile_c("asump", e, ins).run(x, part)
+    want = c1.join(c1.mapWorkgroup(
+        lambda ch: c1.mapLocal(lambda col: c1.reduce_(lambda v, a: F.add(a, F.abs(v)), F.zero, col),
+                               cols(ch, Tn, "contig")), c1.split(s, list(x))))
+    assert np.array_equal(bits(part), bits(want))
+
+    e, ins = PR.scal(n, 1.5)
+    out = np.zeros(n, np.float32)
+    G.compile_c("scal", e, ins).run(x, out)
+    assert np.array_equal(bits(out), bits([F.mul(F.lit(1.5), v) for v in x]))
+
+    M, N, Tn = 37, 512, 32
+    A = uniform(M * N, 6)
+    xv = uniform(N, 7)
+    e, ins = PR.gemv_partials(M, N, Tn)
+    part = np.zeros(M * Tn, np.float32)
+    G.compile_c("gemvp", e, ins).run(A, xv, part)
+    rows = c1.split(N, list(A))
+    want = c1.join(c1.mapWorkgroup(
+        lambda row: c1.mapLocal(lambda col: c1.reduce_(lambda p, a: F.add(a, F.mul(p[0], p[1])), F.zero, col),
+                                cols(c1.zip_(row, list(xv)), Tn, "interleaved")), rows))
+    assert np.array_equal(bits(part), bits(want))
+    e, ins = PR.fold_rows(M, Tn)
+    y = np.zeros(M, np.float32)
+    G.compile_c("rows", e, ins).run(part, y)
+    assert np.array_equal(bits(y), bits([oracle_fold(r) for r in c1.split(Tn, want)]))
+
+
+@pytest.mark.parametrize("space", ["global", "private", "local"])
+def test_temporaries_in_each_address_space(space):
+    """A map's output consumed inside a workgroup loop becomes a temporary in
+    the annotated space; a global one is hoisted out of the parallel loop with
+    one slice per iteration (Section 6.4)."""
+    n, s = 2048, 256
+    x, y = uniform(n, 8), uniform(n, 9)
+    X, Y = G.inp("x", G.arr(n, G.F32)), G.inp("y", G.arr(n, G.F32))
+    wrap = {"global": lambda e: e, "private": G.to_private, "local": G.to_local}[space]
+    e = G.mapWorkgroup(
+        lambda ch: G.reduceSeq(lambda v, a: G.add(a, v), 0.0,
+                               wrap(G.mapSeq(lambda p: G.mul(G.fst(p), G.snd(p)), ch))),
+        G.split(s, G.zip_(X, Y)))
+    f = G.compile_c("tmp_" + space, e, [X, Y])
+    temps = f.temps_like()
+    assert len(temps) == (1 if space == "global" else 0)
+    if space == "global":
+        assert temps[0].size == n  # 8 workgroups x 256
+    out = np.zeros(n // s, np.float32)
+    f.run(x, y, out, *temps)
+    want = c1.map_(lambda ch: oracle_fold(c1.map_(lambda p: F.mul(p[0], p[1]), ch)),
+                   c1.split(s, c1.zip_(list(x), list(y))))
+    assert np.array_equal(bits(out), bits(want))
+
+
+def test_openmp_outer_loop_gives_the_same_bits():
+    n, s, Tn = 1 << 16, 4096, 128
+    x, y = uniform(n, 10), uniform(n, 11)
+    e, ins = PR.dot_partials(n, s, Tn)
+    a = np.zeros(n // s * Tn, np.float32)
+    b = np.zeros_like(a)
+    G.compile_c("dotp", e, ins).run(x, y, a)
+    G.compile_c("dotp", e, ins, openmp=True).run(x, y, b)
+    assert np.array_equal(bits(a), bits(b))
+
+
+def test_loop_nest_levels_follow_the_strategy():
+    e, ins = PR.dot_partials(4096, 512, 32)
+    comm, _ = T.translate(e)
+    levels = []
+
+    def walk(c):
+        if isinstance(c, T.For):
+            levels.append((c.level, c.n))
+            walk(c.body)
+        elif isinstance(c, T.Seq):
+            for x in c.cs:
+                walk(x)
+        elif isinstance(c, T.New):
+            assert c.temp.space == "private"  # reduceI's accumulator
+            walk(c.body)
+
+    walk(comm)
+    assert levels == [("workgroup", 8), ("local", 32), ("seq", 16)]
+
+
+def test_illegal_nestings_are_rejected():
+    x = G.inp("x", G.arr(1024, G.F32))
+    inner = lambda ch: G.mapWorkgroup(lambda v: G.mul(v, v), ch)
+    with pytest.raises(T.TranslationError, match="illegal nesting"):
+        T.translate(G.mapLocal(inner, G.split(32, x)))
+    with pytest.raises(T.TranslationError, match="illegal nesting"):
+        T.translate(G.mapGlobal(lambda ch: G.mapGlobal(lambda v: v, ch), G.split(32, x)))
+    with pytest.raises(T.TranslationError, match="illegal nesting"):
+        T.translate(G.mapWorkgroup(lambda ch: G.mapWorkgroup(lambda v: v, ch), G.split(32, x)))
+
+
+def test_cross_block_consumption_needs_a_kernel_boundary():
+    x = G.inp("x", G.arr(1024, G.F32))
+    e = G.reduceSeq(lambda v, a: G.add(a, v), 0.0,
+                    G.join(G.mapWorkgroup(lambda ch: G.mapLocal(lambda v: G.mul(v, v), ch), G.split(32, x))))
+    with pytest.raises(T.TranslationError, match="kernel"):
+        T.translate(e)
+
+
+def test_type_errors():
+    x = G.inp("x", G.arr(1000, G.F32))
+    with pytest.raises(TypeError):
+        G.split(3, x)
+    with pytest.raises(TypeError):
+        G.zip_(x, G.inp("y", G.arr(999, G.F32)))
+    with pytest.raises(TypeError):
+        G.join(x)
+
+
+@pytest.mark.skipif(not shutil.which("nvcc"), reason="nvcc not installed")
+def test_cuda_sources_compile_for_sm103a(tmp_path):
+    progs = {"dotp": PR.dot_partials(1 << 20, 8192, 256), "asump": PR.asum_partials(1 << 20, 8192, 256, "contig"),
+             "fold": PR.fold_all(4096), "scal": PR.scal(1 << 20, 1.5), "gemvp": PR.gemv_partials(512, 1024, 128),
+             "rows": PR.fold_rows(512, 128), "k1": PR.dot_K1(4096)}
+    for name, (e, ins) in progs.items():
+        src = B.cuda_source(E.generate(name, e, ins, "cuda"))
+        assert "__fadd_rn" in src or "__fmul_rn" in src
+        path = tmp_path / f"{name}.cu"
+        path.write_text(src)
+        r = subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-fmad=false", "-c",
+                            str(path), "-o", str(tmp_path / f"{name}.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+
+
+def vadd(a, b):
+    return tuple(F.add(p, q) for p, q in zip(a, b))
+
+
+def vmul(a, b):
+    return tuple(F.mul(p, q) for p, q in zip(a, b))
+
+
+def oracle_dot_partials_vec(x, y, s, Tn, thread_map, V=4):
+    zero = tuple(F.zero for _ in range(V))
+    return c1.asScalar(c1.join(c1.mapWorkgroup(
+        lambda ch: c1.mapLocal(lambda col: c1.reduce_(lambda p, a: vadd(a, vmul(p[0], p[1])), zero, col),
+                               cols(ch, Tn, thread_map)),
+        c1.split(s // V, c1.zip_(c1.asVector(V, list(x)), c1.asVector(V, list(y)))))))
+
+
+@pytest.mark.parametrize("thread_map", ["interleaved", "contig"])
+def test_vector_dot_scal_gemv_match_oracle(thread_map):
+    """asVector 4 streams, lane-wise folds, un-reduced lane partials (Section 6's float4 kernel)."""
+    n, s, Tn = 8192, 2048, 64
+    x, y = uniform(n, 12), uniform(n, 13)
+    e, ins = PR.dot_partials(n, s, Tn, thread_map, V=4)
+    part = np.zeros(n // s * Tn * 4, np.float32)
+    G.compile_c("dotv", e, ins).run(x, y, part)
+    assert np.array_equal(bits(part), bits(oracle_dot_partials_vec(x, y, s, Tn, thread_map)))
+
+    e, ins = PR.scal(n, 1.5, V=4)
+    out = np.zeros(n, np.float32)
+    G.compile_c("scalv", e, ins).run(x, out)
+    want = c1.asScalar(c1.map_(lambda v: vmul((F.lit(1.5),) * 4, v), c1.asVector(4, list(x))))
+    assert np.array_equal(bits(out), bits(want))
+
+    M, N, Tn = 24, 1024, 64
+    A, xv = uniform(M * N, 14), uniform(N, 15)
+    e, ins = PR.gemv_partials(M, N, Tn, thread_map, V=4)
+    part = np.zeros(M * Tn * 4, np.float32)
+    G.compile_c("gemvv", e, ins).run(A, xv, part)
+    zero = (F.zero,) * 4
+    want = c1.asScalar(c1.join(c1.mapWorkgroup(
+        lambda row: c1.mapLocal(lambda col: c1.reduce_(lambda p, a: vadd(a, vmul(p[0], p[1])), zero, col),
+                                cols(c1.zip_(c1.asVector(4, row), c1.asVector(4, list(xv))), Tn, thread_map)),
+        c1.split(N, list(A)))))
+    assert np.array_equal(bits(part), bits(want))
+
+
+def test_vector_views_must_keep_lanes_adjacent():
+    """asVector reads V adjacent numbers at an offset that is a multiple of V:
+    rows of an array qualify, columns (a transposed view) do not."""
+    A = G.inp("A", G.arr(8, 6, G.F32))  # rows of 6: row i starts at 6i
+    e = G.mapGlobal(lambda row: G.reduceSeq(lambda v, a: G.add(a, v), G.vlit(0.0, 2), G.asVector(2, row)), A)
+    src = E.generate("ok2", e, [A], "cuda")["source"]
+    assert "float2" in src
+    B = G.inp("B", G.arr(8, 8, G.F32))
+    e = G.mapGlobal(lambda col: G.reduceSeq(lambda v, a: G.add(a, v), G.vlit(0.0, 4), G.asVector(4, col)),
+                    G.transpose(B))
+    with pytest.raises(E.EmitError, match="adjacent"):
+        E.generate("bad4", e, [B], "cuda")
+    assert not E.divisible(T.iadd(T.imul(T.IVar("i"), 6), T.IConst(0)), 4)
+    assert E.divisible(T.iadd(T.imul(T.IVar("i"), 8), T.imul(T.IVar("j"), 4)), 4)

@@ -1,0 +1,144 @@
+"""Generated CUDA kernels on the GPU: bit-identical to the oracle's evaluation
+of the same phrase (c1), for every level mapping, thread mapping and address
+space the generator handles, and under launch shapes other than the default
+(the grid-stride loops make the result independent of them)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import patterns as c1
+from paper_1710_08332_gb300 import codegen as G
+from paper_1710_08332_gb300.codegen import programs as PR
+from tests.test_codegen_host import bits, cols, oracle_dot_partials, oracle_fold, uniform
+
+pytestmark = pytest.mark.gpu
+F = c1.F32
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run(kernel, *arrays, out_count, grid=None, block=None):
+    out = torch.full((out_count,), float("nan"), device="cuda")
+    kernel.run(*arrays, out, *kernel.temps_like(), grid=grid, block=block)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("thread_map", ["interleaved", "contig"])
+def test_dot_two_kernels(cuda_device, thread_map):
+    n, s, Tn = 1 << 16, 4096, 128
+    x, y = uniform(n, 21), uniform(n, 22)
+    e, ins = PR.dot_partials(n, s, Tn, thread_map)
+    k = G.compile_cuda("dotp", e, ins)
+    part = run(k, dev(x), dev(y), out_count=n // s * Tn)
+    want = oracle_dot_partials(x, y, s, Tn, thread_map)
+    assert np.array_equal(bits(part), bits(want))
+    # other launch shapes: fewer blocks than chunks, fewer threads than columns
+    for grid, block in ((3, 128), (16, 32), (64, 96)):
+        again = run(k, dev(x), dev(y), out_count=n // s * Tn, grid=grid, block=block)
+        assert np.array_equal(bits(again), bits(want))
+    e2, ins2 = PR.fold_all(part.size)
+    out = run(G.compile_cuda("fold", e2, ins2), dev(part), out_count=1)
+    assert bits(out)[0] == bits([oracle_fold(want)])[0]
+
+
+def test_asum_scal_gemv_k1(cuda_device):
+    n, s, Tn = 1 << 15, 2048, 64
+    x = uniform(n, 23)
+    e, ins = PR.asum_partials(n, s, Tn, "interleaved")
+    part = run(G.compile_cuda("asump", e, ins), dev(x), out_count=n // s * Tn)
+    want = c1.join(c1.mapWorkgroup(
+        lambda ch: c1.mapLocal(lambda col: c1.reduce_(lambda v, a: F.add(a, F.abs(v)), F.zero, col),
+                               cols(ch, Tn, "interleaved")), c1.split(s, list(x))))
+    assert np.array_equal(bits(part), bits(want))
+
+    e, ins = PR.scal(n, 1.5)
+    out = run(G.compile_cuda("scal", e, ins), dev(x), out_count=n)
+    assert np.array_equal(bits(out), bits(np.float32(1.5) * x))
+
+    M, N, Tn = 300, 1024, 128
+    A, xv = uniform(M * N, 24), uniform(N, 25)
+    e, ins = PR.gemv_partials(M, N, Tn, "contig")
+    part = run(G.compile_cuda("gemvp", e, ins), dev(A), dev(xv), out_count=M * Tn)
+    want = c1.join(c1.mapWorkgroup(
+        lambda row: c1.mapLocal(lambda col: c1.reduce_(lambda p, a: F.add(a, F.mul(p[0], p[1])), F.zero, col),
+                                cols(c1.zip_(row, list(xv)), Tn, "contig")), c1.split(N, list(A))))
+    assert np.array_equal(bits(part), bits(want))
+    e, ins = PR.fold_rows(M, Tn)
+    y = run(G.compile_cuda("rows", e, ins), dev(part), out_count=M)
+    assert np.array_equal(bits(y), bits([oracle_fold(r) for r in c1.split(Tn, want)]))
+
+    x1, y1 = uniform(3000, 26), uniform(3000, 27)
+    e, ins = PR.dot_K1(3000)
+    out = run(G.compile_cuda("k1", e, ins), dev(x1), dev(y1), out_count=1)
+    assert bits(out)[0] == bits([oracle_fold([F.mul(a, b) for a, b in zip(x1, y1)])])[0]
+
+
+@pytest.mark.parametrize("space", ["global", "private", "local"])
+def test_temporaries(cuda_device, space):
+    n, s = 1 << 14, 512
+    x, y = uniform(n, 28), uniform(n, 29)
+    X, Y = G.inp("x", G.arr(n, G.F32)), G.inp("y", G.arr(n, G.F32))
+    wrap = {"global": lambda e: e, "private": G.to_private, "local": G.to_local}[space]
+    level = G.mapLocal if space == "local" else G.mapSeq
+    e = G.mapWorkgroup(
+        lambda ch: G.reduceSeq(lambda v, a: G.add(a, v), 0.0, wrap(level(lambda p: G.mul(G.fst(p), G.snd(p)), ch))),
+        G.split(s, G.zip_(X, Y)))
+    k = G.compile_cuda("tmp_" + space, e, [X, Y])
+    want = c1.map_(lambda ch: oracle_fold(c1.map_(lambda p: F.mul(p[0], p[1]), ch)),
+                   c1.split(s, c1.zip_(list(x), list(y))))
+    for grid, block in ((None, 128), (5, 64)):
+        out = run(k, dev(x), dev(y), out_count=n // s, grid=grid, block=block)
+        assert np.array_equal(bits(out), bits(want))
+
+
+def test_backends_agree_at_size(cuda_device):
+    """n = 2^22: the CUDA kernel and the host C build of the same loop nest."""
+    n, s, Tn = 1 << 22, 16384, 256
+    x, y = uniform(n, 30), uniform(n, 31)
+    e, ins = PR.dot_partials(n, s, Tn)
+    part = run(G.compile_cuda("dotp", e, ins), dev(x), dev(y), out_count=n // s * Tn)
+    host = np.zeros(n // s * Tn, np.float32)
+    G.compile_c("dotp", e, ins, openmp=True).run(x, y, host)
+    assert np.array_equal(bits(part), bits(host))
+
+
+@pytest.mark.parametrize("thread_map", ["interleaved", "contig"])
+def test_vector_kernels(cuda_device, thread_map):
+    from tests.test_codegen_host import oracle_dot_partials_vec, vmul, vadd
+
+    n, s, Tn = 1 << 16, 4096, 128
+    x, y = uniform(n, 32), uniform(n, 33)
+    e, ins = PR.dot_partials(n, s, Tn, thread_map, V=4)
+    want = oracle_dot_partials_vec(x, y, s, Tn, thread_map)
+    for unroll in (1, 4, 16):  # unrolling reorders no step of a sequential loop
+        part = run(G.compile_cuda("dotv", e, ins, unroll=unroll), dev(x), dev(y), out_count=n // s * Tn * 4)
+        assert np.array_equal(bits(part), bits(want))
+    e2, ins2 = PR.fold_rows(part.size // 64, 64)
+    folded = run(G.compile_cuda("fold64", e2, ins2, unroll=16), dev(part), out_count=part.size // 64,
+                 grid=max(1, part.size // 64 // 256), block=256)
+    assert np.array_equal(bits(folded), bits([oracle_fold(r) for r in c1.split(64, list(want))]))
+
+    e, ins = PR.asum_partials(n, s, Tn, thread_map, V=4)
+    part = run(G.compile_cuda("asumv", e, ins), dev(x), out_count=n // s * Tn * 4)
+    zero = (F.zero,) * 4
+    want = c1.asScalar(c1.join(c1.mapWorkgroup(
+        lambda ch: c1.mapLocal(lambda col: c1.reduce_(lambda v, a: vadd(a, tuple(F.abs(q) for q in v)), zero, col),
+                               cols(ch, Tn, thread_map)), c1.split(s // 4, c1.asVector(4, list(x))))))
+    assert np.array_equal(bits(part), bits(want))
+
+    e, ins = PR.scal(n, 1.5, V=4)
+    out = run(G.compile_cuda("scalv", e, ins), dev(x), out_count=n, grid=37, block=128)
+    assert np.array_equal(bits(out), bits(np.float32(1.5) * x))
+
+    M, N, Tn = 200, 2048, 128
+    A, xv = uniform(M * N, 34), uniform(N, 35)
+    e, ins = PR.gemv_partials(M, N, Tn, thread_map, V=4)
+    part = run(G.compile_cuda("gemvv", e, ins), dev(A), dev(xv), out_count=M * Tn * 4)
+    want = c1.asScalar(c1.join(c1.mapWorkgroup(
+        lambda row: c1.mapLocal(lambda col: c1.reduce_(lambda p, a: vadd(a, vmul(p[0], p[1])), zero, col),
+                                cols(c1.zip_(c1.asVector(4, row), c1.asVector(4, list(xv))), Tn, thread_map)),
+        c1.split(N, list(A)))))
+    assert np.array_equal(bits(part), bits(want))
