@@ -288,6 +288,16 @@ def profile_case(args):
         def fn():
             b.forward(xs, ys, dot_out, As, gx, gy)
             b.backward(xs, ys, dot_g, dxs, dys, As, gx, gdy, dAs, dgx)
+    elif args.profile == "gen_dot":  # the generated dot partials kernel (asVector 4, split 2^15, 256 threads)
+        from paper_1710_08332_gb300 import codegen as G
+        from paper_1710_08332_gb300.codegen import programs as PR
+
+        x, y = W.bandwidth(dev, n=n)
+        k = G.compile_cuda("gen_dot_partials", *PR.dot_partials(n, 1 << 15, 256, V=4), unroll=4)
+        part = torch.empty(n // (1 << 15) * 256 * 4, device=dev)
+
+        def fn():
+            k.run(x, y, part)
     else:
         raise SystemExit(f"unknown profile case {args.profile}")
     for _ in range(1 + args.reps):
@@ -297,7 +307,7 @@ def profile_case(args):
     return 0
 
 
-PROFILE_CASES = {"dot", "asum", "scal", "dot_local", "asum_local", "gemm", "batched", "dot1m", "gemv"}
+PROFILE_CASES = {"dot", "asum", "scal", "dot_local", "asum_local", "gemm", "batched", "dot1m", "gemv", "gen_dot"}
 
 
 def bandwidth_workload(args, device, dist):
