@@ -462,6 +462,9 @@ def generate(name: str, expr: P.Phrase, inputs: list, backend: str = "cuda", unr
     """
     comm, out = T.translate(expr, "out")
     temps = T.hoist(comm)
+    from .check import check
+
+    check(comm)  # no two iterations of a parallel loop write one place
     em = Emitter(backend, inputs, out, temps, unroll)
     em.emit(comm, 1, ())
     params = []

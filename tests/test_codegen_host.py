@@ -265,3 +265,55 @@ def test_vector_views_must_keep_lanes_adjacent():
         E.generate("bad4", e, [B], "cuda")
     assert not E.divisible(T.iadd(T.imul(T.IVar("i"), 6), T.IConst(0)), 4)
     assert E.divisible(T.iadd(T.imul(T.IVar("i"), 8), T.imul(T.IVar("j"), 4)), 4)
+
+
+# --------------------------------------------------------------------------
+# race freedom of loop nests (the property the paper's type system gives)
+# --------------------------------------------------------------------------
+
+from paper_1710_08332_gb300.codegen import check as CK  # noqa: E402
+
+
+def _assign(acc):
+    return T.Assign(acc, G.lit(1.0))
+
+
+def test_checker_accepts_every_program():
+    progs = [PR.dot_partials(4096, 512, 32), PR.dot_partials(4096, 512, 32, "contig", V=4),
+             PR.asum_partials(4096, 512, 32), PR.scal(4096, 2.0, V=4), PR.gemv_partials(64, 512, 32),
+             PR.fold_rows(64, 32), PR.fold_all(64), PR.dot_K1(64)]
+    for e, _ in progs:
+        comm, _ = T.translate(e)
+        CK.check(comm)
+
+
+def test_checker_rejects_racy_loop_nests():
+    i, j = T.IVar("i"), T.IVar("j")
+    out1 = T.AOut("out", G.arr(32, G.F32))
+    # every local iteration writes out[0]
+    with pytest.raises(CK.RaceError):
+        CK.check(T.For(i, 32, "local", _assign(T.AIdx(out1, T.IConst(0)))))
+    # the workgroup index is ignored: workgroups overwrite each other
+    with pytest.raises(CK.RaceError):
+        CK.check(T.For(i, 4, "workgroup", T.For(j, 32, "local", _assign(T.AIdx(out1, j)))))
+    # out[i + j]: neighbouring iterations overlap
+    out2 = T.AOut("out", G.arr(64, G.F32))
+    with pytest.raises(CK.RaceError):
+        CK.check(T.For(i, 4, "global", T.For(j, 32, "seq", _assign(T.AIdx(out2, T.iadd(i, j))))))
+    # a private variable declared outside a thread-level loop is not per iteration
+    t = T.Temp("acc", G.F32, "private")
+    with pytest.raises(CK.RaceError):
+        CK.check(T.New(t, T.For(i, 32, "local", _assign(T.AOut("acc", G.F32, t)))))
+
+
+def test_checker_accepts_transposed_and_split_writes():
+    i, j = T.IVar("i"), T.IVar("j")
+    out = T.AOut("out", G.arr(32, 4, G.F32))
+    # out[j][i] = offset j*4 + i: a mixed-radix numbering, injective
+    CK.check(T.For(i, 4, "workgroup", T.For(j, 32, "local", _assign(T.AIdx(T.AIdx(T.ATranspose(out), i), j)))))
+    # a value split 8 written element q -> out[q / 8][q % 8] = q
+    flat = T.AOut("out", G.arr(16, 8, G.F32))
+    CK.check(T.For(i, 128, "global", _assign(T.AIdx(T.ASplit(8, flat), i))))
+    assert CK.linear_form(T.iadd(T.imul(T.idiv(i, 8), 8), T.imod(i, 8))) == ({"i": 1}, 0)
+    assert CK.injective({"a": 1, "b": 32}, {"a": 32, "b": 4})
+    assert not CK.injective({"a": 1, "b": 31}, {"a": 32, "b": 4})
