@@ -889,6 +889,15 @@ def codegen_workload(args, device, dist):
     per, step_ms, clk = timed_steps(args, device, dist, names, step)
     alone = standalone_us({k: calls[k] for k in ("gen_dot_partials", "library_dot", "gen_asum_partials",
                                                   "library_asum", "gen_scal", "gen_gemv_partials")}, bytes_)
+    # rewrite-based exploration: every derivation of hreduce (+) 0 (hmap (*) (zip x y)) over
+    # split 2^14..2^16, 128 / 256 threads, both thread maps, widths 1 and 4, timed whole
+    from paper_1710_08332_gb300.codegen import rewrite as RW
+
+    ranked = RW.explore("dot", [x, y], n, RW.derivations(n, threads=(128, 256)), reps=5)
+    explored = {"candidates": len(ranked),
+                "best": {"derivation": str(ranked[0][1]), "pipeline_us": round(ranked[0][0] * 1e3, 1)},
+                "worst": {"derivation": str(ranked[-1][1]), "pipeline_us": round(ranked[-1][0] * 1e3, 1)},
+                "library_dot_us": alone["library_dot"]["median_us"]}
     hbm = peaks()[0]
     kern = {k: {"avg_us": round(v * 1e3, 2)} for k, v in per.items()}
     for k, b in bytes_.items():
@@ -908,7 +917,7 @@ def codegen_workload(args, device, dist):
     world = dist.get_world_size() if dist else 1
     return _line(args, dist, round(world * 8 * n / (dot_ms / 1e3) / 1e9, 1), "GB/s", dot_ms, "f32", cfg, kern,
                  roof, clk, len(names) * args.steps,
-                 {"kernels_alone": alone,
+                 {"kernels_alone": alone, "explored_dot": explored,
                   "generated_dot_vs_library_dot": round(per["library_dot"] / dot_ms, 3)})
 
 

@@ -317,3 +317,60 @@ def test_checker_accepts_transposed_and_split_writes():
     assert CK.linear_form(T.iadd(T.imul(T.idiv(i, 8), 8), T.imod(i, 8))) == ({"i": 1}, 0)
     assert CK.injective({"a": 1, "b": 32}, {"a": 32, "b": 4})
     assert not CK.injective({"a": 1, "b": 31}, {"a": 32, "b": 4})
+
+
+# --------------------------------------------------------------------------
+# rewrite-based strategy exploration
+# --------------------------------------------------------------------------
+
+from paper_1710_08332_gb300.codegen import rewrite as RW  # noqa: E402
+
+
+def test_rewrite_rules_check_their_shapes():
+    with pytest.raises(RW.RuleError):
+        RW.rewrite("dot", RW.Derivation([RW.Rule("columns", (32, "interleaved"))]))
+    with pytest.raises(RW.RuleError):
+        RW.rewrite("dot", RW.Derivation([RW.Rule("split", (100,)), RW.Rule("vectorize", (8,))]))
+    e = RW.rewrite("asum", RW.Derivation([RW.Rule("split", (512,)), RW.Rule("columns", (32, "contig"))]))
+    assert e == RW.Reduce(RW.Each(RW.Reduce(RW.Each(RW.Reduce(RW.Map("abs", RW.HOLE)),
+                                                    RW.Columns(32, "contig", RW.HOLE))),
+                                  RW.Split(512, RW.Input("asum"))))
+    ds = RW.derivations(1 << 16, splits=(4096,), threads=(128,), maps=("interleaved",), widths=(1, 4))
+    assert [str(d) for d in ds] == ["split(4096) ; columns(128, interleaved) ; fuse ; lower",
+                                    "split(4096) ; columns(128, interleaved) ; vectorize(4) ; fuse ; lower"]
+
+
+@pytest.mark.parametrize("kind", ["dot", "asum"])
+@pytest.mark.parametrize("tm,V", [("interleaved", 1), ("contig", 4)])
+def test_derived_pipelines_match_oracle(kind, tm, V):
+    """Every kernel of a derivation, run on the host, equals the oracle's
+    evaluation of the same tree: per-thread folds (lanes with V), then the
+    folding stages in order."""
+    n, s, Tn = 1 << 14, 2048, 32
+    d = RW.Derivation([RW.Rule("split", (s,)), RW.Rule("columns", (Tn, tm))]
+                      + ([RW.Rule("vectorize", (V,))] if V > 1 else []) + [RW.Rule("fuse"), RW.Rule("lower")])
+    x, y = uniform(n, 40), uniform(n, 41)
+    cur = [x, y] if kind == "dot" else [x]
+    for name, ph, ins in RW.lower(kind, d, n):
+        f = G.compile_c("k_" + name, ph, ins)
+        count = next(c for (_, _, c, role) in f.params if role == "out")
+        out = np.zeros(count, np.float32)
+        f.run(*cur, out, *f.temps_like())
+        cur = [out]
+    # the oracle's tree: lane folds per thread column, then the stages of 64 / 256 / all
+    if kind == "dot":
+        items = c1.zip_(list(x), list(y)) if V == 1 else c1.zip_(c1.asVector(V, list(x)), c1.asVector(V, list(y)))
+        g = (lambda p: F.mul(p[0], p[1])) if V == 1 else (lambda p: vmul(p[0], p[1]))
+    else:
+        items = list(x) if V == 1 else c1.asVector(V, list(x))
+        g = F.abs if V == 1 else (lambda v: tuple(F.abs(q) for q in v))
+    add = F.add if V == 1 else vadd
+    zero = F.zero if V == 1 else (F.zero,) * V
+    parts = c1.join(c1.mapWorkgroup(
+        lambda ch: c1.mapLocal(lambda col: c1.reduce_(lambda v, a: add(a, g(v)), zero, col), cols(ch, Tn, tm)),
+        c1.split(s // V, items)))
+    vals = parts if V == 1 else c1.asScalar(parts)
+    while len(vals) > 1:
+        grp = 64 if len(vals) >= 64 * 256 else (256 if len(vals) > 256 else len(vals))
+        vals = [oracle_fold(r) for r in c1.split(grp, vals)]
+    assert bits(cur[0])[0] == bits(vals)[0]

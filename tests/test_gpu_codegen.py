@@ -142,3 +142,29 @@ def test_vector_kernels(cuda_device, thread_map):
                                 cols(c1.zip_(c1.asVector(4, row), c1.asVector(4, list(xv))), Tn, thread_map)),
         c1.split(N, list(A)))))
     assert np.array_equal(bits(part), bits(want))
+
+
+def test_exploration_ranks_derivations_and_each_is_exact_for_its_tree(cuda_device):
+    from oracle import naive64
+    from paper_1710_08332_gb300.codegen import rewrite as RW
+
+    n = 1 << 20
+    x, y = uniform(n, 42), uniform(n, 43)
+    dx, dy = dev(x), dev(y)
+    derivs = RW.derivations(n, splits=(1 << 14, 1 << 15), threads=(128, 256), maps=("interleaved", "contig"),
+                            widths=(1, 4))
+    ranked = RW.explore("dot", [dx, dy], n, derivs, reps=3)
+    assert len(ranked) == len(derivs) and ranked[0][0] <= ranked[-1][0]
+    exact, bound = naive64.dot_exact(x, y), 1e-5 * naive64.abs_dot_f64(x, y)
+    for _, d in ranked[:3] + ranked[-2:]:
+        got = RW.run_pipeline(RW.compile_pipeline("dot", d, n), [dx, dy])
+        torch.cuda.synchronize()
+        cur = [x, y]
+        for name, ph, ins in RW.lower("dot", d, n):  # the same tree on the host
+            f = G.compile_c("h_" + name, ph, ins)
+            count = next(c for (_, _, c, role) in f.params if role == "out")
+            out = np.zeros(count, np.float32)
+            f.run(*cur, out, *f.temps_like())
+            cur = [out]
+        assert bits(got.cpu().numpy())[0] == bits(cur[0])[0], str(d)
+        assert abs(float(cur[0][0]) - exact) <= bound
