@@ -280,6 +280,23 @@ __device__ __forceinline__ typename A::acc_t thread_fold(const typename E::in_t 
         r += H;
       }
     }
+    if constexpr (U >= 8) {
+      constexpr int Q = U / 4;
+      if (r + Q <= Rin) {  // a quarter batch left
+        in_t xv[Q][V], yv[Q][V];
+#pragma unroll
+        for (int u = 0; u < Q; ++u) {
+          load_vec<V, false>(x + base + (r + u) * step, xv[u]);
+          if constexpr (E::kTwo) load_vec<V, CACHE_Y>(y + base + (r + u) * step, yv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < Q; ++u)
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+            acc[v] = A::step(acc[v], E::elem(xv[u][v], E::kTwo ? yv[u][v] : xv[u][v]));
+        r += Q;
+      }
+    }
     for (; r < Rc; ++r) {
       const int64_t e0 = base + r * step;
       in_t xv[V], yv[V];

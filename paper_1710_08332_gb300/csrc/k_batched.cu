@@ -228,10 +228,15 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
     g.Npad = round_up(in.N, 4);
     g.part_base = h.dx_partials;
     const int64_t cg = (in.N + 3) / 4;  // column groups of 4
-    if (cg >= T) {                       // wide: tiles of T column groups, one row chunk per item
-      g.G = T;
-      g.cpi = 1;
-      g.tiles = (int32_t)((cg + T - 1) / T);
+    if (cg >= T) {
+      // wide: tiles of G column groups (G = T, T/2 or T/4, whichever leaves the fewest
+      // idle threads in the last tile), T / G row chunks side by side in one item
+      int64_t best = T;
+      for (int64_t G = T; G >= T / 4 && G >= 32; G /= 2)
+        if (((cg + G - 1) / G) * G < ((cg + best - 1) / best) * best) best = G;
+      g.G = (int32_t)best;
+      g.cpi = (int32_t)(T / best);
+      g.tiles = (int32_t)((cg + best - 1) / best);
     } else {                             // narrow: T / G row chunks side by side in one item
       g.G = (int32_t)next_pow2(cg);
       g.cpi = T / g.G;
