@@ -872,6 +872,14 @@ def codegen_workload(args, device, dist):
     M, N_ = A.shape
     kg = G.compile_cuda("gen_gemv_partials", *PR.gemv_partials(M, N_, 128))
     kr = G.compile_cuda("gen_gemv_rows", *PR.fold_rows(M, 128), unroll=16)
+    R = 32  # dx: row chunks of 32 (256 workgroups), then the fold over the chunks
+    kdx = G.compile_cuda("gen_gemv_dx_partials", *PR.gemv_bwd_dx_partials(M, N_, R), unroll=8)
+    kdf = G.compile_cuda("gen_gemv_dx_fold", *PR.gemv_bwd_dx_fold(M // R, N_), unroll=16)
+    kda = G.compile_cuda("gen_gemv_dA", *PR.gemv_bwd_dA(M, N_))
+    dyv = torch.rand(M, device=device)
+    dxpart = torch.empty(M // R * N_, device=device)
+    dxv = torch.empty(N_, device=device)
+    dAm = torch.empty(M * N_, device=device)
     part = torch.empty(m1, device=device)
     p2 = torch.empty(m1 // 64, device=device)
     p3 = torch.empty(m1 // 64 // 256, device=device)
@@ -889,6 +897,9 @@ def codegen_workload(args, device, dist):
         "gen_scal": lambda: ks.run(x, ys, grid=sms * 8, block=256),
         "gen_gemv_partials": lambda: kg.run(A, xv, gpart),
         "gen_gemv_rows": lambda: kr.run(gpart, yv, grid=M // 256, block=256),
+        "gen_gemv_dx_partials": lambda: kdx.run(A, dyv, dxpart),
+        "gen_gemv_dx_fold": lambda: kdf.run(dxpart, dxv, grid=N_ // 256, block=256),
+        "gen_gemv_dA": lambda: kda.run(dyv, xv, dAm),
     }
     st = dpia.ReduceStrategy(split=16384, threads=256, vec=4, second="tree", threads2=256)
     ws = dpia.workspace(dpia.dpia_dot_workspace_size(n, st), device)
@@ -896,7 +907,8 @@ def codegen_workload(args, device, dist):
     calls["library_dot"] = lambda: dpia.dpia_dot_f32(x, y, n, st, lib_out, ws)
     calls["library_asum"] = lambda: dpia.dpia_asum_f32(x, n, st, lib_out, ws)
     bytes_ = {"gen_dot_partials": 8 * n, "gen_asum_partials": 4 * n, "gen_scal": 8 * n,
-              "gen_gemv_partials": 4 * M * N_ + 4 * N_, "library_dot": 8 * n, "library_asum": 4 * n}
+              "gen_gemv_partials": 4 * M * N_ + 4 * N_, "gen_gemv_dx_partials": 4 * M * N_ + 4 * M,
+              "gen_gemv_dA": 4 * M * N_ + 4 * (M + N_), "library_dot": 8 * n, "library_asum": 4 * n}
     names = list(calls)
 
     def step(tl):
@@ -905,7 +917,8 @@ def codegen_workload(args, device, dist):
 
     per, step_ms, clk = timed_steps(args, device, dist, names, step)
     alone = standalone_us({k: calls[k] for k in ("gen_dot_partials", "library_dot", "gen_asum_partials",
-                                                  "library_asum", "gen_scal", "gen_gemv_partials")}, bytes_)
+                                                  "library_asum", "gen_scal", "gen_gemv_partials",
+                                                  "gen_gemv_dx_partials", "gen_gemv_dA")}, bytes_)
     # rewrite-based exploration: every derivation of hreduce (+) 0 (hmap (*) (zip x y)) over
     # split 2^14..2^16, 128 / 256 threads, both thread maps, widths 1 and 4, timed whole
     from paper_1710_08332_gb300.codegen import rewrite as RW

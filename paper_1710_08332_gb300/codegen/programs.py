@@ -7,6 +7,10 @@ is one or two kernels, the second folding the first one's partial results.
           result   = reduceSeq (+) 0 partials
     asum  the same with map abs
     scal  mapGlobal (lambda v. a * v) x
+    dA    mapWorkgroup (lambda d. mapLocal (lambda v. d * v) x) dy
+    dx    partials = mapWorkgroup (lambda (rows, dys). mapLocal (lambda col.
+                       reduceSeq (+) 0 (map (*) (zip col dys))) (transpose rows))
+                       (zip (split R A) (split R dy));  dx = mapGlobal fold (columns of partials)
     gemv  partials = join (mapWorkgroup (lambda row.
                        mapLocal (lambda col. reduceSeq (+) 0 (map (*) col))
                                 (columns (zip row x))) A)
@@ -101,3 +105,31 @@ def dot_K1(n: int):
     """The single-thread dot of Section 2.2 (one kernel, one thread)."""
     x, y = P.inp("x", P.arr(n, P.F32)), P.inp("y", P.arr(n, P.F32))
     return P.reduceSeq(lambda p, acc: P.add(acc, P.mul(P.fst(p), P.snd(p))), 0.0, P.zip_(x, y)), [x, y]
+
+
+def gemv_bwd_dA(M: int, N: int):
+    """dA = dy x^T: map (lambda d. map (lambda v. d * v) x) dy, a workgroup per row,
+    the row's columns over the workgroup's threads."""
+    dy, x = P.inp("dy", P.arr(M, P.F32)), P.inp("x", P.arr(N, P.F32))
+    return P.mapWorkgroup(lambda d: P.mapLocal(lambda v: P.mul(d, v), x), dy), [dy, x]
+
+
+def gemv_bwd_dx_partials(M: int, N: int, R: int):
+    """The first kernel of dx = A^T dy split over rows: for each chunk of R rows
+    (a workgroup) and each column (the workgroup's threads), the column's fold
+    over the chunk's rows in row order -- (M/R) x N partials."""
+    A, dy = P.inp("A", P.arr(M, N, P.F32)), P.inp("dy", P.arr(M, P.F32))
+    e = P.mapWorkgroup(
+        lambda c: P.mapLocal(
+            lambda col: P.reduceSeq(lambda q, acc: P.add(acc, P.mul(P.fst(q), P.snd(q))), 0.0,
+                                    P.zip_(col, P.snd(c))),
+            P.transpose(P.fst(c))),
+        P.zip_(P.split(R, A), P.split(R, dy)))
+    return e, [A, dy]
+
+
+def gemv_bwd_dx_fold(C: int, N: int):
+    """The second kernel: dx_j = the fold of column j's C chunk partials in chunk order."""
+    p = P.inp("p", P.arr(C * N, P.F32))
+    return P.mapGlobal(lambda col: P.reduceSeq(lambda v, acc: P.add(acc, v), 0.0, col),
+                       P.transpose(P.split(N, p))), [p]

@@ -374,3 +374,25 @@ def test_derived_pipelines_match_oracle(kind, tm, V):
         grp = 64 if len(vals) >= 64 * 256 else (256 if len(vals) > 256 else len(vals))
         vals = [oracle_fold(r) for r in c1.split(grp, vals)]
     assert bits(cur[0])[0] == bits(vals)[0]
+
+
+def test_gemv_backward_programs_match_the_library_trees():
+    """The generated dx (row chunks of R, then the chunk fold) computes the same
+    tree as the library's dx kernel: equal to the loop-nest oracle of that
+    kernel; dA = dy x^T exactly."""
+    from oracle import loopnest
+
+    M, N, R = 96, 72, 32
+    A = np.random.default_rng(50).standard_normal((M, N)).astype(np.float32)
+    dy, x = uniform(M, 51), uniform(N, 52)
+    e, ins = PR.gemv_bwd_dx_partials(M, N, R)
+    part = np.zeros(M // R * N, np.float32)
+    G.compile_c("dxp", e, ins).run(A.ravel().copy(), dy, part)
+    e, ins = PR.gemv_bwd_dx_fold(M // R, N)
+    dx = np.zeros(N, np.float32)
+    G.compile_c("dxf", e, ins).run(part, dx)
+    assert np.array_equal(bits(dx), bits(loopnest.gemv_bwd_dx_f32(A, dy, R)))
+    e, ins = PR.gemv_bwd_dA(M, N)
+    dA = np.zeros(M * N, np.float32)
+    G.compile_c("dA", e, ins).run(dy, x, dA)
+    assert np.array_equal(bits(dA.reshape(M, N)), bits(loopnest.gemv_bwd_dA_f32(x, dy)))

@@ -168,3 +168,19 @@ def test_exploration_ranks_derivations_and_each_is_exact_for_its_tree(cuda_devic
             cur = [out]
         assert bits(got.cpu().numpy())[0] == bits(cur[0])[0], str(d)
         assert abs(float(cur[0][0]) - exact) <= bound
+
+
+def test_generated_gemv_backward(cuda_device):
+    from oracle import loopnest
+
+    M, N, R = 512, 1000, 32
+    A = np.random.default_rng(53).standard_normal((M, N)).astype(np.float32)
+    dy, x = uniform(M, 54), uniform(N, 55)
+    e, ins = PR.gemv_bwd_dx_partials(M, N, R)
+    part = run(G.compile_cuda("dxp", e, ins, unroll=8), dev(A.ravel()), dev(dy), out_count=M // R * N)
+    e, ins = PR.gemv_bwd_dx_fold(M // R, N)
+    dx = run(G.compile_cuda("dxf", e, ins, unroll=8), dev(part), out_count=N, grid=4, block=256)
+    assert np.array_equal(bits(dx), bits(loopnest.gemv_bwd_dx_f32(A, dy, R)))
+    e, ins = PR.gemv_bwd_dA(M, N)
+    dA = run(G.compile_cuda("dA", e, ins), dev(dy), dev(x), out_count=M * N)
+    assert np.array_equal(bits(dA.reshape(M, N)), bits(loopnest.gemv_bwd_dA_f32(x, dy)))
