@@ -347,6 +347,8 @@ class Emitter:
                     self.lines.append(f"{pad}{ct} {t.name};")
             elif t.space == "local" and self.backend == "cuda":
                 ct = CTYPE[P.base_num(t.type).dtype]
+                if 4 * P.scalar_count(t.type) + sum(_shared_bytes(x) for x in self.shared) > 48 * 1024:
+                    raise EmitError(f"local temporaries of more than 48 KiB per block ({t.name}: {t.type})")
                 self.shared.append(f"  __shared__ {ct} {t.name}[{P.scalar_count(t.type)}];")
             elif t.space == "local":
                 ct = CTYPE[P.base_num(t.type).dtype]
@@ -424,6 +426,11 @@ class Emitter:
                 if inside_threads and not declared_inside:
                     raise EmitError(f"private value {name} is computed by one thread but read by "
                                     f"all threads of a thread-level map; place it in local memory")
+
+
+def _shared_bytes(decl: str) -> int:
+    """Bytes of a '__shared__ T name[count];' declaration (4-byte elements)."""
+    return 4 * int(decl.split("[")[1].split("]")[0])
 
 
 def _shares(c) -> bool:

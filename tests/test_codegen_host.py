@@ -396,3 +396,12 @@ def test_gemv_backward_programs_match_the_library_trees():
     dA = np.zeros(M * N, np.float32)
     G.compile_c("dA", e, ins).run(dy, x, dA)
     assert np.array_equal(bits(dA.reshape(M, N)), bits(loopnest.gemv_bwd_dA_f32(x, dy)))
+
+
+def test_local_temporaries_are_bounded():
+    X = G.inp("x", G.arr(1 << 16, G.F32))
+    e = G.mapWorkgroup(lambda ch: G.reduceSeq(lambda v, a: G.add(a, v), 0.0,
+                                              G.to_local(G.mapLocal(lambda v: G.mul(v, v), ch))),
+                       G.split(1 << 14, X))  # 64 KiB of shared memory per block
+    with pytest.raises(E.EmitError, match="48 KiB"):
+        E.generate("big_local", e, [X], "cuda")
