@@ -467,6 +467,13 @@ def generate(name: str, expr: P.Phrase, inputs: list, backend: str = "cuda", unr
 
     Returns {"source", "kernel", "params" (name, C type, count, role), "temps"}.
     """
+    import re
+
+    for p in inputs:
+        if not re.fullmatch(r"[A-Za-z_][A-Za-z_0-9]*", p.name) or re.fullmatch(r"[tir]\d+|out|dpia_\w*", p.name):
+            raise EmitError(f"input name {p.name!r}: a C identifier other than out, dpia_*, t<k>, i<k>, r<k>")
+    if len({p.name for p in inputs}) != len(inputs):
+        raise EmitError("two inputs share a name")
     comm, out = T.translate(expr, "out")
     temps = T.hoist(comm)
     from .check import check

@@ -405,3 +405,10 @@ def test_local_temporaries_are_bounded():
                        G.split(1 << 14, X))  # 64 KiB of shared memory per block
     with pytest.raises(E.EmitError, match="48 KiB"):
         E.generate("big_local", e, [X], "cuda")
+
+
+def test_input_names_must_not_clash_with_generated_names():
+    for bad in ("t3", "out", "i1", "2x", "dpia_lane4"):
+        X = G.inp(bad, G.arr(64, G.F32))
+        with pytest.raises(E.EmitError):
+            E.generate("k", G.mapGlobal(lambda v: G.mul(v, v), X), [X], "cuda")
