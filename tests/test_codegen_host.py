@@ -412,3 +412,28 @@ def test_input_names_must_not_clash_with_generated_names():
         X = G.inp(bad, G.arr(64, G.F32))
         with pytest.raises(E.EmitError):
             E.generate("k", G.mapGlobal(lambda v: G.mul(v, v), X), [X], "cuda")
+
+
+def test_random_dot_strategies_match_oracle():
+    """Thirty random derivations (split, threads, thread map, width) on random
+    lengths: every generated pipeline equals the oracle's evaluation of its tree."""
+    rng = np.random.default_rng(60)
+    done = 0
+    while done < 30:
+        V = int(rng.choice([1, 2, 4]))
+        Tn = int(rng.choice([1, 2, 8, 32, 64]))
+        R = int(rng.integers(1, 6))
+        s = Tn * V * R
+        C = int(rng.integers(1, 5))
+        n = s * C
+        tm = str(rng.choice(["interleaved", "contig"]))
+        x, y = uniform(n, 100 + done), uniform(n, 200 + done)
+        e, ins = PR.dot_partials(n, s, Tn, tm, V=V)
+        out = np.zeros(C * Tn * V, np.float32)
+        G.compile_c(f"rd{done}", e, ins).run(x, y, out)
+        if V == 1:
+            want = oracle_dot_partials(x, y, s, Tn, tm)
+        else:
+            want = oracle_dot_partials_vec(x, y, s, Tn, tm, V)
+        assert np.array_equal(bits(out), bits(want)), (n, s, Tn, tm, V)
+        done += 1
