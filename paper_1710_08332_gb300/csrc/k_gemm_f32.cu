@@ -3,8 +3,9 @@
 // each C_ij folded over k = 0..K-1 in order from +0, either with fmaf (the
 // contraction declared) or with a separately rounded multiply and add.
 //
-// The map over C is split into 128 x 128 tiles (a block each); inside a tile,
-// 256 threads own 8 x 8 elements each. k advances in slices of 16 staged in
+// The map over C is split into 128 x 128 tiles (a block each; with the
+// declared FMA, at most 128 registers so that two blocks share an SM); inside a
+// tile, 256 threads own 8 x 8 elements each. k advances in slices of 16 staged in
 // shared memory (double-buffered, the next slice prefetched through registers
 // while the current one is consumed). Every element's fold stays one
 // sequential chain in k, so the result is bit-identical to the oracle's loop.
@@ -12,6 +13,8 @@
 #include "kernels.h"
 
 namespace dpia {
+
+int resident_blocks(const void *kernel, int threads);
 
 namespace {
 
@@ -99,7 +102,7 @@ __device__ __forceinline__ void store_slices(float (*As)[BM], float (*Bs)[BN], c
 }
 
 template <bool TA, bool TB, bool FMA>
-__global__ void __launch_bounds__(NT) sgemm_fold_kernel(const GemmArgs g, int vec_ok) {
+__global__ void __launch_bounds__(NT, FMA ? 2 : 1) sgemm_fold_kernel(const GemmArgs g, int vec_ok) {
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN];
   const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
@@ -178,6 +181,145 @@ __global__ void __launch_bounds__(NT) sgemm_fold_kernel(const GemmArgs g, int ve
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tiles of 64 x 128 for the last rows of C: when the 128 x 128 tiles leave a
+// last wave less than half full, those rows are computed as half-height tiles
+// by a second launch, so the tail takes half a wave's time. Same fold, same
+// bits: 256 threads of 4 x 8 elements (rows ty*4 + i, columns as above).
+// ---------------------------------------------------------------------------
+
+constexpr int BMH = 64;
+
+template <bool TA>
+__device__ __forceinline__ void load_a_half(const GemmArgs &g, int64_t m0, int64_t k0, bool vec, float (&ra)[4]) {
+  const int tid = threadIdx.x;
+  if (vec) {
+    const float *p = !TA ? g.A + (m0 + tid / 4) * g.lda + k0 + (tid % 4) * 4   // row m, 4 k
+                         : g.A + (k0 + tid / 16) * g.lda + m0 + (tid % 16) * 4;  // k row, 4 m
+    const float4 u = __ldg(reinterpret_cast<const float4 *>(p));
+    ra[0] = u.x; ra[1] = u.y; ra[2] = u.z; ra[3] = u.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      ra[j] = !TA ? a_at<TA>(g, m0 + tid / 4, k0 + (tid % 4) * 4 + j) : a_at<TA>(g, m0 + (tid % 16) * 4 + j, k0 + tid / 16);
+  }
+}
+
+template <bool TA>
+__device__ __forceinline__ void store_a_half(float (*As)[BMH], const float (&ra)[4]) {
+  const int tid = threadIdx.x;
+  if (!TA) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) As[(tid % 4) * 4 + j][tid / 4] = ra[j];
+  } else {
+    *reinterpret_cast<float4 *>(&As[tid / 16][(tid % 16) * 4]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+  }
+}
+
+// B slices as in the full kernel (8 values per thread).
+template <bool TB>
+__device__ __forceinline__ void load_b(const GemmArgs &g, int64_t n0, int64_t k0, bool vec, float (&rb)[8]) {
+  const int tid = threadIdx.x;
+  if (vec) {
+    const float *p = !TB ? g.B + (k0 + tid / 16) * g.ldb + n0 + (tid % 16) * 8 : g.B + (n0 + tid / 2) * g.ldb + k0 + (tid % 2) * 8;
+    const float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p + 4));
+    rb[0] = u.x; rb[1] = u.y; rb[2] = u.z; rb[3] = u.w; rb[4] = v.x; rb[5] = v.y; rb[6] = v.z; rb[7] = v.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      rb[j] = !TB ? b_at<TB>(g, k0 + tid / 16, n0 + (tid % 16) * 8 + j) : b_at<TB>(g, k0 + (tid % 2) * 8 + j, n0 + tid / 2);
+  }
+}
+
+template <bool TB>
+__device__ __forceinline__ void store_b(float (*Bs)[BN], const float (&rb)[8]) {
+  const int tid = threadIdx.x;
+  if (!TB) {
+    *reinterpret_cast<float4 *>(&Bs[tid / 16][(tid % 16) * 8]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    *reinterpret_cast<float4 *>(&Bs[tid / 16][(tid % 16) * 8 + 4]) = make_float4(rb[4], rb[5], rb[6], rb[7]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) Bs[(tid % 2) * 8 + j][tid / 2] = rb[j];
+  }
+}
+
+template <bool TA, bool TB, bool FMA>
+__global__ void __launch_bounds__(NT) sgemm_fold_half_kernel(const GemmArgs g, int vec_ok) {
+  __shared__ __align__(16) float As[2][BK][BMH];
+  __shared__ __align__(16) float Bs[2][BK][BN];
+  const int64_t m0 = (int64_t)blockIdx.y * BMH, n0 = (int64_t)blockIdx.x * BN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const bool interior_mn = m0 + BMH <= g.M && n0 + BN <= g.N;
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+  const int64_t nk = ceil_div(g.K, BK);
+  float ra[4], rb[8];
+  {
+    const bool v0 = vec_ok && interior_mn && BK <= g.K;
+    load_a_half<TA>(g, m0, 0, v0, ra);
+    load_b<TB>(g, n0, 0, v0, rb);
+    store_a_half<TA>(As[0], ra);
+    store_b<TB>(Bs[0], rb);
+  }
+  __syncthreads();
+  for (int64_t kt = 0; kt < nk; ++kt) {
+    const int buf = kt & 1;
+    const int64_t k0 = kt * BK;
+    if (kt + 1 < nk) {
+      const int64_t k1 = k0 + BK;
+      const bool v1 = vec_ok && interior_mn && k1 + BK <= g.K;
+      load_a_half<TA>(g, m0, k1, v1, ra);
+      load_b<TB>(g, n0, k1, v1, rb);
+    }
+    const int kcount = g.K - k0 < BK ? (int)(g.K - k0) : BK;
+    for (int kk = 0; kk < kcount; ++kk) {  // exactly K terms in order
+      const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+      const float a[4] = {a0.x, a0.y, a0.z, a0.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = madd<FMA>(a[i], b[j], acc[i][j]);
+    }
+    if (kt + 1 < nk) {
+      store_a_half<TA>(As[buf ^ 1], ra);
+      store_b<TB>(Bs[buf ^ 1], rb);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t m = m0 + ty * 4 + i;
+    if (m >= g.M) continue;
+    float *crow = g.C + m * g.ldc;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t n = n0 + h * 64 + tx * 4;
+      if (vec_ok && n + 4 <= g.N) {
+        *reinterpret_cast<float4 *>(crow + n) =
+            make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (n + j < g.N) crow[n + j] = acc[i][4 * h + j];
+      }
+    }
+  }
+}
+
+template <bool FMA>
+const void *pick_half(int ta, int tb) {
+  if (!ta && !tb) return (const void *)sgemm_fold_half_kernel<false, false, FMA>;
+  if (!ta && tb) return (const void *)sgemm_fold_half_kernel<false, true, FMA>;
+  if (ta && !tb) return (const void *)sgemm_fold_half_kernel<true, false, FMA>;
+  return (const void *)sgemm_fold_half_kernel<true, true, FMA>;
+}
+
 template <bool FMA>
 const void *pick(int ta, int tb) {
   if (!ta && !tb) return (const void *)sgemm_fold_kernel<false, false, FMA>;
@@ -193,9 +335,25 @@ cudaError_t launch_gemm_f32(const float *A, const float *B, float *C, int64_t M,
                             int vec_ok, cudaStream_t stream) {
   GemmArgs g{A, B, C, M, N, K, lda, ldb, ldc};
   const void *k = fma ? pick<true>(transA, transB) : pick<false>(transA, transB);
-  dim3 grid((unsigned)ceil_div(N, BN), (unsigned)ceil_div(M, BM));
+  const int64_t tn = ceil_div(N, BN), tm = ceil_div(M, BM);
+  // a last wave of 128 x 128 tiles less than half full: its rows go to the
+  // half-height kernel, which finishes them in half a wave's time
+  const int64_t slots = (int64_t)sm_count() * resident_blocks(k, NT);
+  const int64_t total = tn * tm, rem = total % slots;
+  int64_t tail = 0;  // tile rows computed as half tiles
+  if (total > slots && rem > 0 && rem <= slots / 2) tail = ceil_div(rem, tn);
+  if (tail >= tm) tail = 0;
   void *args[] = {&g, &vec_ok};
-  return cudaLaunchKernel(k, grid, dim3(NT), args, 0, stream);
+  cudaError_t e = cudaLaunchKernel(k, dim3((unsigned)tn, (unsigned)(tm - tail)), dim3(NT), args, 0, stream);
+  if (e != cudaSuccess || tail == 0) return e;
+  const int64_t m_main = (tm - tail) * BM;
+  GemmArgs t = g;
+  t.A = transA ? A + m_main : A + m_main * lda;
+  t.C = C + m_main * ldc;
+  t.M = M - m_main;
+  const void *kh = fma ? pick_half<true>(transA, transB) : pick_half<false>(transA, transB);
+  void *targs[] = {&t, &vec_ok};
+  return cudaLaunchKernel(kh, dim3((unsigned)tn, (unsigned)ceil_div(t.M, BMH)), dim3(NT), targs, 0, stream);
 }
 
 }  // namespace dpia

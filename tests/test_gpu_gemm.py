@@ -150,3 +150,20 @@ def test_gemm_validation(cuda_device):
         dpia.dpia_gemm_f32(C, C, C, 64, 64, 64, 64, 64, 64, 0, 0)
     with pytest.raises(dpia.DPIAError, match="SHAPE"):
         dpia.dpia_gemm_f32(C, C, torch.zeros(4, device="cuda"), 64, 64, 64, 32, 64, 64, 0, 0)
+
+
+@pytest.mark.parametrize("tA,tB", [(0, 0), (1, 0), (0, 1)])
+def test_gemm_f32_tail_rows_as_half_tiles(cuda_device, tA, tB):
+    """2560 x 2048 tiles fill more than the SMs hold with a small last wave: the
+    last tile row runs as half-height tiles in a second launch; every element
+    is still the oracle's fold."""
+    M, N, K = 2560, 2048, 64
+    A = (torch.randn(K, M) if tA else torch.randn(M, K)).numpy()
+    B = (torch.randn(N, K) if tB else torch.randn(K, N)).numpy()
+    C = torch.full((M, N), float("nan"), device="cuda")
+    dpia.dpia_gemm_f32(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, M, N, K, A.shape[1], B.shape[1],
+                       N, tA, tB, "fma")
+    torch.cuda.synchronize()
+    rows = np.r_[0:8, 2300:2560]
+    want = loopnest.gemm_f32_sample(A, B, bool(tA), bool(tB), True, rows, np.arange(N))
+    assert_bits_equal(host(C)[rows], want, f"tail tA={tA} tB={tB}")
