@@ -928,6 +928,22 @@ def codegen_workload(args, device, dist):
                 "best": {"derivation": str(ranked[0][1]), "pipeline_us": round(ranked[0][0] * 1e3, 1)},
                 "worst": {"derivation": str(ranked[-1][1]), "pipeline_us": round(ranked[-1][0] * 1e3, 1)},
                 "library_dot_us": alone["library_dot"]["median_us"]}
+    # the same phrases on the host (the paper's multicore target): C with the
+    # outermost parallel loop on OpenMP threads, on 2^24 elements of the inputs
+    import numpy as np
+
+    nh = 1 << 24
+    hx, hy = x[:nh].cpu().numpy(), y[:nh].cpu().numpy()
+    hc = G.compile_c("host_dot_partials", *PR.dot_partials(nh, s, Tn, V=V), openmp=True)
+    hpart = np.zeros(nh // s * Tn * V, np.float32)
+    hc.run(hx, hy, hpart)
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < 3.0:
+        hc.run(hx, hy, hpart)
+        reps += 1
+    host_s = (time.perf_counter() - t0) / reps
+    host_line = {"kernel": "generated C, outermost parallel loop on OpenMP threads",
+                 "GB_s": round(8 * nh / host_s / 1e9, 2), "n": nh, "threads": os.cpu_count(), "reps": reps}
     hbm = peaks()[0]
     kern = {k: {"avg_us": round(v * 1e3, 2)} for k, v in per.items()}
     for k, b in bytes_.items():
@@ -947,7 +963,7 @@ def codegen_workload(args, device, dist):
     world = dist.get_world_size() if dist else 1
     return _line(args, dist, round(world * 8 * n / (dot_ms / 1e3) / 1e9, 1), "GB/s", dot_ms, "f32", cfg, kern,
                  roof, clk, len(names) * args.steps,
-                 {"kernels_alone": alone, "explored_dot": explored,
+                 {"kernels_alone": alone, "explored_dot": explored, "host_generated_dot_partials": host_line,
                   "generated_dot_vs_library_dot": round(per["library_dot"] / dot_ms, 3)})
 
 
