@@ -41,8 +41,11 @@ def _linear(idx, shape):
 
 def target(acc, path):
     """(place name, temp or None, offset index expression) written through acc."""
+    proj = None
     while True:
-        if isinstance(acc, T.AIdx):
+        if isinstance(acc, T.AProj):
+            proj = acc.k
+        elif isinstance(acc, T.AIdx):
             path = [acc.i] + path
         elif isinstance(acc, T.ASplit):
             path = [T.idiv(path[0], acc.n), T.imod(path[0], acc.n)] + path[1:]
@@ -56,6 +59,8 @@ def target(acc, path):
             t = acc.temp
             shape = _dims(acc.type)
             off = _linear(path, shape) if shape else T.IConst(0)
+            if proj is not None and t is None:  # arrays of pairs: two numbers per element
+                off = T.iadd(T.imul(off, 2), T.IConst(proj))
             if t is not None and t.space == "global" and t.hoist:
                 h = _linear([v for v, _ in t.hoist], [n for _, n in t.hoist])
                 off = T.iadd(T.imul(h, P.scalar_count(t.type)), off)

@@ -152,6 +152,10 @@ class Emitter:
             if len(path) < 2 or path[0][0] != "i" or path[1][0] != "p":
                 raise EmitError("a zipped pair must be indexed and projected")
             return self.access(e.b if path[1][1] else e.a, [path[0]] + path[2:])
+        if isinstance(e, P.Pair):
+            if not path or path[0][0] != "p":
+                raise EmitError("a pair must be projected")
+            return self.access(e.b if path[0][1] else e.a, path[1:])
         if isinstance(e, P.Split):
             if len(path) < 2 or path[0][0] != "i" or path[1][0] != "i":
                 raise EmitError("split read without two indices")
@@ -227,6 +231,10 @@ class Emitter:
                 raise EmitError(f"asVector of a {type(e).__name__}")
 
     def base_read(self, e: P.Ident, path: list) -> str:
+        if e.temp is not None and isinstance(e.type, P.PairT):
+            if len(path) != 1 or path[0][0] != "p":
+                raise EmitError("a pair temporary is read one component at a time")
+            return f"{e.name}_{path[0][1]}"
         idx = [s[1] for s in path]
         if any(s[0] != "i" for s in path):
             raise EmitError("projection of a non-pair")
@@ -272,7 +280,11 @@ class Emitter:
 
     # -- writes ---------------------------------------------------------------
 
-    def write(self, acc: T.Acc, path: list) -> str:
+    def write(self, acc: T.Acc, path: list, proj=None) -> str:
+        if isinstance(acc, T.AProj):
+            return self.write(acc.acc, path, acc.k)
+        if proj is not None:
+            return self.write_pair(acc, path, proj)
         if isinstance(acc, T.AIdx):
             return self.write(acc.acc, [acc.i] + path)
         if isinstance(acc, T.ASplit):
@@ -316,6 +328,29 @@ class Emitter:
             return f"{acc.name}[{render_index(linear(path, shape))}]"
         raise EmitError(f"unknown acceptor {type(acc).__name__}")
 
+    def write_pair(self, acc: T.Acc, path: list, k: int) -> str:
+        """Component k of the pair reached through acc by path."""
+        while not isinstance(acc, T.AOut):
+            if isinstance(acc, T.AIdx):
+                path = [acc.i] + path
+            elif isinstance(acc, T.ASplit):
+                path = [T.idiv(path[0], acc.n), T.imod(path[0], acc.n)] + path[1:]
+            elif isinstance(acc, T.AJoin):
+                path = [T.iadd(T.imul(path[0], acc.m), path[1])] + path[2:]
+            elif isinstance(acc, T.ATranspose):
+                path = [path[1], path[0]] + path[2:]
+            else:
+                raise EmitError(f"pair component through a {type(acc).__name__}")
+            acc = acc.acc
+        if acc.temp is not None:
+            if acc.temp.space != "private" or dims(acc.temp.type):
+                raise EmitError("pair temporaries are private scalars only")
+            return f"{acc.name}_{k}"
+        if not isinstance(P.base_elem(acc.type), P.PairT):
+            raise EmitError("pair component of a non-pair output")
+        off = linear(path, dims(acc.type)) if dims(acc.type) else T.IConst(0)
+        return f"{acc.name}[{render_index(T.iadd(T.imul(off, 2), T.IConst(k)))}]"
+
     # -- commands -------------------------------------------------------------
 
     def emit(self, c: T.Comm, ind: int, ctx: tuple):
@@ -336,6 +371,17 @@ class Emitter:
                 self.sync[-1] = True
             if isinstance(P.base_elem(t.type), P.VecT) and (dims(t.type) or t.space != "private"):
                 raise EmitError("vector temporaries are private scalars only")
+            if isinstance(t.type, P.PairT):
+                if t.space != "private":
+                    raise EmitError("pair temporaries are private scalars only")
+                par = sum(1 for l in ctx if l != "seq")
+                self.private_ctx[t.name] = (par, "local" in ctx or "global" in ctx)
+                self.lines.append(f"{pad}{ctype(t.type.a)} {t.name}_0;")
+                self.lines.append(f"{pad}{ctype(t.type.b)} {t.name}_1;")
+                self.emit(c.body, ind, ctx)
+                return
+            if isinstance(P.base_elem(t.type), P.PairT):
+                raise EmitError("arrays of pairs are outputs only")
             if t.space == "private":
                 ct = ctype(P.base_elem(t.type))
                 shape = dims(t.type)

@@ -82,6 +82,11 @@ def is_scalar(t) -> bool:
     return isinstance(t, (Num, VecT))
 
 
+def is_value(t) -> bool:
+    """A number, a vector, or a pair of them (e.g. a compensated sum's (s, c))."""
+    return is_scalar(t) or (isinstance(t, PairT) and is_scalar(t.a) and is_scalar(t.b))
+
+
 def arr(*dims_and_elem):
     """arr(n, m, F32) is the type n.m.f32."""
     *dims, elem = dims_and_elem
@@ -92,11 +97,13 @@ def arr(*dims_and_elem):
 
 
 def scalar_count(t) -> int:
-    """Numbers in a value of type t (arrays of numbers or vectors)."""
+    """Numbers in a value of type t (arrays of numbers, vectors or pairs of numbers)."""
     if isinstance(t, Num):
         return 1
     if isinstance(t, VecT):
         return t.n
+    if isinstance(t, PairT) and isinstance(t.a, Num) and t.a == t.b:
+        return 2
     if isinstance(t, Arr):
         return t.n * scalar_count(t.elem)
     raise TypeError(f"{t} is not an array of numbers")
@@ -107,6 +114,8 @@ def base_num(t) -> Num:
         t = t.elem
     if isinstance(t, VecT):
         return t.num
+    if isinstance(t, PairT) and isinstance(t.a, Num) and t.a == t.b:
+        return t.a
     if not isinstance(t, Num):
         raise TypeError(f"{t} is not an array of numbers")
     return t
@@ -235,8 +244,8 @@ class Reduce(Phrase):
     def __post_init__(self):
         if not isinstance(self.e.type, Arr):
             raise TypeError(f"reduce over a non-array {self.e.type}")
-        if not is_scalar(self.init.type):
-            raise TypeError("reduce accumulates numbers or vectors")
+        if not is_value(self.init.type):
+            raise TypeError("reduce accumulates numbers, vectors or pairs of them")
         ps = self.f.params
         if len(ps) != 2 or ps[0].type != self.e.type.elem or ps[1].type != self.init.type:
             raise TypeError("reduce function must take (element, accumulator)")
@@ -262,6 +271,22 @@ class Zip(Phrase):
         if not (isinstance(ta, Arr) and isinstance(tb, Arr) and ta.n == tb.n):
             raise TypeError(f"zip of {ta} and {tb}")
         self.type = Arr(ta.n, PairT(ta.elem, tb.elem))
+
+    def children(self):
+        return (self.a, self.b)
+
+
+@dataclass(eq=False)
+class Pair(Phrase):
+    """pair a b of two numbers (or vectors)."""
+    a: Phrase
+    b: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        if not (is_scalar(self.a.type) and is_scalar(self.b.type)):
+            raise TypeError(f"pair of {self.a.type} and {self.b.type}")
+        self.type = PairT(self.a.type, self.b.type)
 
     def children(self):
         return (self.a, self.b)
@@ -439,6 +464,10 @@ def snd(e):
     return Proj(1, e)
 
 
+def pair(a, b):
+    return Pair(a, b)
+
+
 def split(n, e):
     return Split(int(n), e)
 
@@ -524,6 +553,8 @@ def subst(p: Phrase, env: dict) -> Phrase:
         return Zip(subst(p.a, env), subst(p.b, env))
     if isinstance(p, Proj):
         return Proj(p.k, subst(p.e, env))
+    if isinstance(p, Pair):
+        return Pair(subst(p.a, env), subst(p.b, env))
     if isinstance(p, Split):
         return Split(p.n, subst(p.e, env))
     if isinstance(p, Join):

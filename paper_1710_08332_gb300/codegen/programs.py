@@ -133,3 +133,61 @@ def gemv_bwd_dx_fold(C: int, N: int):
     p = P.inp("p", P.arr(C * N, P.F32))
     return P.mapGlobal(lambda col: P.reduceSeq(lambda v, acc: P.add(acc, v), 0.0, col),
                        P.transpose(P.split(N, p))), [p]
+
+
+# ---------------------------------------------------------------------------
+# compensated (Kahan) folds: the accumulator is a pair (s, c)
+# ---------------------------------------------------------------------------
+
+
+def kahan_step(acc, e):
+    """One compensated step: y = e - c; t = s + y; c' = (t - s) - y; s' = t."""
+    s, c = P.fst(acc), P.snd(acc)
+    y = P.sub(e, c)
+    t = P.add(s, y)
+    return P.pair(t, P.sub(P.sub(t, s), y))
+
+
+def kahan_merge(acc, other_s, other_c):
+    """Merge another compensated partial (s2, c2): a step with e = s2 - c2."""
+    return kahan_step(acc, P.sub(other_s, other_c))
+
+
+def _zero_pair():
+    return P.pair(P.lit(0.0), P.lit(0.0))
+
+
+def dot_partials_kahan(n: int, s: int, T: int, thread_map: str = "interleaved"):
+    """Per-thread compensated sums of x . y: C*T pairs (s, c), stored as 2 numbers each."""
+    x, y = P.inp("x", P.arr(n, P.F32)), P.inp("y", P.arr(n, P.F32))
+    e = P.join(P.mapWorkgroup(
+        lambda chunk: P.mapLocal(
+            lambda col: P.reduceSeq(lambda p, acc: kahan_step(acc, P.mul(P.fst(p), P.snd(p))), _zero_pair(), col),
+            columns(chunk, T, thread_map)),
+        P.split(s, P.zip_(x, y))))
+    return e, [x, y]
+
+
+def _pair_items(p, m):
+    """The m pairs stored as 2m numbers, as an array of 2-element arrays."""
+    return P.split(2, p)
+
+
+def fold_pairs_rows(rows: int, g: int):
+    """rows groups of g stored pairs, each merged in order from (0, 0): rows pairs out."""
+    from .translate import IConst
+
+    p = P.inp("p", P.arr(2 * rows * g, P.F32))
+    return P.mapGlobal(
+        lambda grp: P.reduceSeq(lambda pr, acc: kahan_merge(acc, P.Idx(pr, IConst(0)), P.Idx(pr, IConst(1))),
+                                _zero_pair(), grp),
+        P.split(g, _pair_items(p, rows * g))), [p]
+
+
+def fold_pairs_all(m: int):
+    """The compensated sum of m stored pairs: s of their in-order merge."""
+    from .translate import IConst
+
+    p = P.inp("p", P.arr(2 * m, P.F32))
+    return P.fst(P.reduceSeq(lambda pr, acc: kahan_merge(acc, P.Idx(pr, IConst(0)), P.Idx(pr, IConst(1))),
+                             _zero_pair(), _pair_items(p, m))), [p]

@@ -148,6 +148,13 @@ class AJoin(Acc):
 
 
 @dataclass(eq=False)
+class AProj(Acc):
+    """Acceptor for one component (0 = fst, 1 = snd) of a pair acceptor."""
+    k: int
+    acc: Acc
+
+
+@dataclass(eq=False)
 class AAsScalar(Acc):
     """A(asScalar e, out) writes e's vectors (width V) whole into the scalar array out."""
     V: int
@@ -249,6 +256,11 @@ class Translator:
             return self.A(e.e, out, levels)
         if isinstance(e, P.AsScalar) and e.computes():
             return self.A(e.e, AAsScalar(e.e.type.elem.n, out), levels)
+        if isinstance(e, P.Pair):
+            return Seq([self.A(e.a, AProj(0, out), levels), self.A(e.b, AProj(1, out), levels)])
+        if isinstance(e.type, P.PairT) and P.is_value(e.type):
+            return self.C(e, lambda v: Seq([Assign(AProj(0, out), P.Proj(0, v)),
+                                            Assign(AProj(1, out), P.Proj(1, v))]), levels)
         if P.is_scalar(e.type):
             return self.C(e, lambda v: Assign(out, v), levels)
         if isinstance(e.type, P.Arr) and not e.computes():
@@ -261,6 +273,8 @@ class Translator:
     def assign(self, out, v, levels):
         if P.is_scalar(v.type):
             return Assign(out, v)
+        if isinstance(v.type, P.PairT):
+            return Seq([Assign(AProj(0, out), P.Proj(0, v)), Assign(AProj(1, out), P.Proj(1, v))])
         return self.copy(v, out, levels)
 
     def copy(self, v: P.Phrase, out: Acc, levels: list) -> Comm:
@@ -284,7 +298,17 @@ class Translator:
                 acc = AOut(t.name, t.type, t)
                 i = self.ivar("r")
                 init = self.A(e.init, acc, levels)
-                step = self.A(P.apply(e.f, P.Idx(x, i), tv), acc, levels + ["seq"])
+                if not isinstance(e.type, P.PairT):
+                    step = self.A(P.apply(e.f, P.Idx(x, i), tv), acc, levels + ["seq"])
+                else:
+                    # a pair is written component by component: the step goes to a
+                    # fresh pair first, so that its second component still reads
+                    # the old accumulator, then replaces the accumulator
+                    nt = self.temp(e.type, "private")
+                    nv = P.Ident(nt.name, nt.type, temp="private")
+                    step = New(nt, Seq([self.A(P.apply(e.f, P.Idx(x, i), tv), AOut(nt.name, nt.type, nt),
+                                               levels + ["seq"]),
+                                        self.assign(acc, nv, levels + ["seq"])]))
                 return New(t, Seq([init, For(i, e.e.type.n, "seq", step), k(tv)]))
 
             return self.C(e.e, body, levels)
@@ -306,6 +330,8 @@ class Translator:
             return self.C(e.a, lambda a: self.C(e.b, lambda b: k(P.Zip(a, b)), levels), levels)
         if isinstance(e, P.Proj):
             return self.C(e.e, lambda v: k(P.Proj(e.k, v)), levels)
+        if isinstance(e, P.Pair):
+            return self.C(e.a, lambda a: self.C(e.b, lambda b: k(P.Pair(a, b)), levels), levels)
         if isinstance(e, P.Split):
             return self.C(e.e, lambda v: k(P.Split(e.n, v)), levels)
         if isinstance(e, P.Join):

@@ -437,3 +437,31 @@ def test_random_dot_strategies_match_oracle():
             want = oracle_dot_partials_vec(x, y, s, Tn, tm, V)
         assert np.array_equal(bits(out), bits(want)), (n, s, Tn, tm, V)
         done += 1
+
+
+@pytest.mark.parametrize("tm", ["interleaved", "contig"])
+def test_compensated_pipeline_matches_oracle(tm):
+    """Kahan pairs as the fold's accumulator: per-thread compensated sums, then
+    group merges and the final merge, each equal to the oracle's kahan_step /
+    kahan_combine evaluation of the same tree."""
+    n, s, Tn, g = 1 << 13, 1024, 32, 16
+    x, y = uniform(n, 70), uniform(n, 71)
+    e, ins = PR.dot_partials_kahan(n, s, Tn, tm)
+    part = np.zeros(2 * n // s * Tn, np.float32)
+    G.compile_c("dk", e, ins).run(x, y, part)
+    want = c1.join(c1.mapWorkgroup(
+        lambda ch: c1.mapLocal(lambda col: c1.reduce_(lambda p, a: c1.kahan_step(F, a, F.mul(p[0], p[1])),
+                                                      (F.zero, F.zero), col), cols(ch, Tn, tm)),
+        c1.split(s, c1.zip_(list(x), list(y)))))
+    assert np.array_equal(bits(part), bits([v for pr in want for v in pr]))
+    m = len(want)
+    e, ins = PR.fold_pairs_rows(m // g, g)
+    grp = np.zeros(2 * (m // g), np.float32)
+    G.compile_c("kg", e, ins).run(part, grp)
+    merged = [c1.reduce_(lambda pr, a: c1.kahan_combine(F, a, pr), (F.zero, F.zero), r) for r in c1.split(g, want)]
+    assert np.array_equal(bits(grp), bits([v for pr in merged for v in pr]))
+    e, ins = PR.fold_pairs_all(len(merged))
+    out = np.zeros(1, np.float32)
+    G.compile_c("kf", e, ins).run(grp, out)
+    final = c1.reduce_(lambda pr, a: c1.kahan_combine(F, a, pr), (F.zero, F.zero), merged)
+    assert bits(out)[0] == bits([final[0]])[0]

@@ -184,3 +184,21 @@ def test_generated_gemv_backward(cuda_device):
     e, ins = PR.gemv_bwd_dA(M, N)
     dA = run(G.compile_cuda("dA", e, ins), dev(dy), dev(x), out_count=M * N)
     assert np.array_equal(bits(dA.reshape(M, N)), bits(loopnest.gemv_bwd_dA_f32(x, dy)))
+
+
+def test_generated_compensated_dot(cuda_device):
+    from tests.test_codegen_host import cols
+
+    n, s, Tn = 1 << 16, 4096, 128
+    x, y = uniform(n, 72), uniform(n, 73)
+    e, ins = PR.dot_partials_kahan(n, s, Tn)
+    part = run(G.compile_cuda("dk", e, ins, unroll=4), dev(x), dev(y), out_count=2 * n // s * Tn)
+    want = c1.join(c1.mapWorkgroup(
+        lambda ch: c1.mapLocal(lambda col: c1.reduce_(lambda p, a: c1.kahan_step(F, a, F.mul(p[0], p[1])),
+                                                      (F.zero, F.zero), col), cols(ch, Tn, "interleaved")),
+        c1.split(s, c1.zip_(list(x), list(y)))))
+    assert np.array_equal(bits(part), bits([v for pr in want for v in pr]))
+    e, ins = PR.fold_pairs_all(len(want))
+    out = run(G.compile_cuda("kf", e, ins), dev(part), out_count=1)
+    final = c1.reduce_(lambda pr, a: c1.kahan_combine(F, a, pr), (F.zero, F.zero), want)
+    assert bits(out)[0] == bits([final[0]])[0]
