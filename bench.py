@@ -845,7 +845,7 @@ def codegen_workload(args, device, dist):
     bandwidth inputs (n = 2^26) and the GEMV 8192^2 inputs, all reading their
     streams as asVector 4 (GEMV: scalar): the dot as four generated kernels
     (per-thread lane partials over 2048 chunks of 2^15 with 256 threads, then
-    three folding stages: 32768 sums of 64, 128 sums of 256, the last 128), the
+    the folding stages of the rewrite lowering's fold plan), the
     asum partials, scal, and the GEMV partials with the per-row fold; beside
     them the library's hand-written dot and asum on the same inputs."""
     import torch
@@ -863,9 +863,20 @@ def codegen_workload(args, device, dist):
     s, Tn, V = 1 << 15, 256, 4
     m1 = n // s * Tn * V  # lane partials of the first kernel
     k1 = G.compile_cuda("gen_dot_partials", *PR.dot_partials(n, s, Tn, V=V), unroll=4)
-    k2 = G.compile_cuda("gen_dot_fold64", *PR.fold_rows(m1 // 64, 64), unroll=16)
-    k3 = G.compile_cuda("gen_dot_fold256", *PR.fold_rows(m1 // 64 // 256, 256), unroll=16)
-    k4 = G.compile_cuda("gen_dot_fold", *PR.fold_all(m1 // 64 // 256), unroll=16)
+    from paper_1710_08332_gb300.codegen import rewrite as RW
+
+    folds, left = [], m1  # the folding stages of the 2M lane partials
+    for grp in RW.fold_plan(m1):
+        ph = PR.fold_all(left) if grp == left else PR.fold_rows(left // grp, grp)
+        folds.append((G.compile_cuda(f"gen_dot_fold_{left}_{grp}", *ph, unroll=16), left // grp))
+        left //= grp
+    fold_bufs = [torch.empty(max(cnt, 1), device=device) for _, cnt in folds]
+
+    def dot_folds():
+        src = part
+        for (k, cnt), dst in zip(folds, fold_bufs):
+            k.run(src, dst, grid=max(1, cnt // 256), block=min(256, cnt) if cnt > 1 else 1)
+            src = dst
     ka = G.compile_cuda("gen_asum_partials", *PR.asum_partials(n, s, Tn, V=V), unroll=4)
     ks = G.compile_cuda("gen_scal", *PR.scal(n, W.SCAL_A, V=V))
     A, xv, _ = W.gemv(device)
@@ -881,18 +892,13 @@ def codegen_workload(args, device, dist):
     dxv = torch.empty(N_, device=device)
     dAm = torch.empty(M * N_, device=device)
     part = torch.empty(m1, device=device)
-    p2 = torch.empty(m1 // 64, device=device)
-    p3 = torch.empty(m1 // 64 // 256, device=device)
-    out = torch.empty(1, device=device)
     ys = torch.empty_like(x)
     gpart = torch.empty(M * 128, device=device)
     yv = torch.empty(M, device=device)
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     calls = {
         "gen_dot_partials": lambda: k1.run(x, y, part),
-        "gen_dot_fold64": lambda: k2.run(part, p2, grid=p2.numel() // 256, block=256),
-        "gen_dot_fold256": lambda: k3.run(p2, p3, grid=1, block=p3.numel()),
-        "gen_dot_fold": lambda: k4.run(p3, out),
+        "gen_dot_folds": dot_folds,
         "gen_asum_partials": lambda: ka.run(x, part),
         "gen_scal": lambda: ks.run(x, ys, grid=sms * 8, block=256),
         "gen_gemv_partials": lambda: kg.run(A, xv, gpart),
@@ -948,14 +954,14 @@ def codegen_workload(args, device, dist):
     kern = {k: {"avg_us": round(v * 1e3, 2)} for k, v in per.items()}
     for k, b in bytes_.items():
         kern[k]["GB_s"] = round(b / per[k] / 1e6, 1)
-    dot_ms = sum(per[k] for k in ("gen_dot_partials", "gen_dot_fold64", "gen_dot_fold256", "gen_dot_fold"))
+    dot_ms = per["gen_dot_partials"] + per["gen_dot_folds"]
     achieved = 8 * n / per["gen_dot_partials"] / 1e6
     roof = {"bound": "hbm", "kernel": "gen_dot_partials (generated: mapWorkgroup / mapLocal / reduceSeq on "
                                       "asVector 4)",
             "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
             "traffic": None, "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": 8 * n,
             "frac_alone": round(alone["gen_dot_partials"]["GB_s"] / hbm, 4)}
-    cfg = {"workload": "generated kernels: dot n=2^26 (4 kernels), asum partials, scal (a=1.5), GEMV 8192^2 "
+    cfg = {"workload": "generated kernels: dot n=2^26 (partials + folding kernels), asum partials, scal (a=1.5), GEMV 8192^2 "
                        "partials + row folds, bandwidth inputs seed 1 / GEMV seed 2, asVector 4 (GEMV scalar), "
                        "sequential loops unrolled 4 (folds 16); beside them the "
                        "library's dot and asum (split 16384, tree)",

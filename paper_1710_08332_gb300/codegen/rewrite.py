@@ -203,17 +203,29 @@ def lower(kind: str, d: Derivation, n: int):
         P.split(s, xs)))
     kernels = [("partials", first, ins)]
     left = n // (s * V) * T * V
-    while left > 1:
-        grp = 64 if left >= 64 * 256 else (256 if left > 256 else left)
+    for grp in fold_plan(left):
         if grp == left:
             ph, i2 = PR.fold_all(left)
             kernels.append((f"fold{left}", ph, i2))
-            left = 1
         else:
             ph, i2 = PR.fold_rows(left // grp, grp)
             kernels.append((f"fold{grp}", ph, i2))
-            left //= grp
+        left //= grp
     return kernels
+
+
+def fold_plan(m: int) -> list:
+    """Group sizes of the folding kernels that reduce m partials to one: small
+    groups while many remain (many threads, each folding a few), larger ones
+    as they thin out, the last group folding what is left."""
+    plan = []
+    while m > 1:
+        g = 16 if m > 65536 else (32 if m > 64 else m)
+        if m % g:
+            g = m
+        plan.append(g)
+        m //= g
+    return plan
 
 
 def derivations(n: int, splits=(1 << 14, 1 << 15, 1 << 16), threads=(128, 256, 512),

@@ -370,10 +370,10 @@ def test_derived_pipelines_match_oracle(kind, tm, V):
         lambda ch: c1.mapLocal(lambda col: c1.reduce_(lambda v, a: add(a, g(v)), zero, col), cols(ch, Tn, tm)),
         c1.split(s // V, items)))
     vals = parts if V == 1 else c1.asScalar(parts)
-    while len(vals) > 1:
-        grp = 64 if len(vals) >= 64 * 256 else (256 if len(vals) > 256 else len(vals))
+    for grp in RW.fold_plan(len(vals)):  # the derivation's folding stages, in order
         vals = [oracle_fold(r) for r in c1.split(grp, vals)]
-    assert bits(cur[0])[0] == bits(vals)[0]
+    assert len(vals) == 1 and bits(cur[0])[0] == bits(vals)[0]
+    assert RW.fold_plan(1 << 19) == [16, 32, 32, 32] and RW.fold_plan(96) == [32, 3]
 
 
 def test_gemv_backward_programs_match_the_library_trees():
