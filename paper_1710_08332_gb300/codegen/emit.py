@@ -1,4 +1,4 @@
-"""Stage III (Section 5.3): the loop nest becomes CUDA C (or plain C).
+"""Stage III (Section 4.3): the loop nest becomes CUDA C (or plain C).
 
 Views are resolved into index arithmetic on the arrays they read: an access
 path (a list of index and projection steps, innermost last) is pushed through

@@ -1,5 +1,5 @@
 """Functional phrases: the data-parallel primitives of the paper's source
-language (Sections 2.1, 5 and 6.2), with their types.
+language (Sections 2.1, 3.3 and 6.2), with their types.
 
 A phrase is built from inputs (``Ident``), literals, arithmetic on numbers,
 ``map`` at a level of the GPU hierarchy (mapGlobal / mapWorkgroup / mapLocal /

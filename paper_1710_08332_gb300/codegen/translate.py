@@ -1,5 +1,5 @@
 """From functional phrases to an imperative loop nest (the paper's Stages I
-and II, Sections 4 and 5).
+and II, Sections 4.1 and 4.2).
 
 Stage I is the pair of translations: the acceptor-passing translation
 ``A(E, out)`` produces a command that writes the value of E through the
