@@ -241,7 +241,13 @@ enum { DPIA_CONTRACT_OFF = 0, DPIA_CONTRACT_FMA = 1 };
  * implemented tiles or exactly those values -- FP32: 128 x 128 x 16; BF16:
  * 256 x tile_n x 64 with tile_n in {128, 160, 192, 224, 256} (0 = the width
  * whose tiles fill the fewest waves of SMs). grid: CTAs of the persistent
- * BF16 kernel (0 = one per SM).
+ * BF16 kernel (0 = one per SM, or as many clusters as fit at once).
+ * cluster (BF16 only): CTAs per thread-block cluster, 1, 2 or 4, on
+ * consecutive 256-row tiles of the same tile column; each CTA copies 1/cluster
+ * of every B slice and the TMA multicasts it to all of them, so the cluster
+ * reads B from L2 once instead of cluster times. 0 = chosen per shape (2 when
+ * there are at least two tile rows). The value of C does not depend on it.
+ * The FP32 fold ignores grid and cluster.
  */
 typedef struct {
   int32_t contract;
@@ -249,6 +255,7 @@ typedef struct {
   int32_t tile_n;
   int32_t tile_k;
   int32_t grid;
+  int32_t cluster;
 } dpia_gemm_strategy;
 
 /*

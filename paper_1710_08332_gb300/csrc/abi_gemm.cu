@@ -13,7 +13,7 @@ cudaError_t launch_gemm_f32(const float *A, const float *B, float *C, int64_t M,
                             cudaStream_t stream);
 cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,
                              int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_n,
-                             int vec_ok, cudaStream_t stream);
+                             int cluster, int vec_ok, cudaStream_t stream);
 cudaError_t poll_device_status(unsigned *out);
 cudaError_t launch_bounded_wait_probe(uint64_t timeout_ns, cudaStream_t stream);
 int resident_blocks(const void *kernel, int threads);
@@ -151,6 +151,10 @@ dpia_status dpia_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64
     set_last_error("%s: grid=%d", fn, st->grid);
     return DPIA_ERR_STRATEGY;
   }
+  if (st->cluster != 0 && st->cluster != 1 && st->cluster != 2 && st->cluster != 4) {
+    set_last_error("%s: cluster=%d (0 = chosen per shape, or 1, 2, 4)", fn, st->cluster);
+    return DPIA_ERR_STRATEGY;
+  }
   int64_t ab = 0, bb = 0;
   dpia_status rc = check_gemm(fn, A, B, C, M, N, K, lda, ldb, ldc, transA, transB, 2, &ab, &bb);
   if (rc || M == 0 || N == 0) return rc;
@@ -166,7 +170,9 @@ dpia_status dpia_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64
   }
   const int vec_ok = aligned(C, 16) && ldc % 4 == 0;
   return cuda_status(
-      launch_gemm_bf16(A, B, C, M, N, K, lda, ldb, ldc, transA, transB, st->grid, st->tile_n, vec_ok, s), fn);
+      launch_gemm_bf16(A, B, C, M, N, K, lda, ldb, ldc, transA, transB, st->grid, st->tile_n, st->cluster, vec_ok,
+                       s),
+      fn);
 }
 
 dpia_status dpia_cast_f32_bf16(const float *x, uint16_t *y, int64_t n, dpia_stream_t stream) {

@@ -67,11 +67,21 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 struct Params {
   float *C;
   int64_t M, N, K, ldc;
-  int BN, tiles_n, num_tiles, k_blocks;
+  int BN, tiles_n, k_blocks;
+  int cm;             // CTAs per cluster, on consecutive tile rows sharing one tile column
+  int units;          // cluster work units: ceil(tile rows / cm) x tile columns
   int a_mn, b_mn, vec_ok;
   int a_3d;           // MN-major A loaded as one 3-D box {64 m, 64 k, 4 m-blocks}
-  uint32_t stage_tx;  // bytes the TMA loads of one stage deliver
+  uint32_t stage_tx;  // bytes one stage receives (all of A's and B's slices)
 };
+
+// Tile of work unit u for the CTA of cluster rank r: the cm CTAs of a cluster
+// take consecutive tile rows of the same tile column, so they read the same
+// B slices.
+__device__ __forceinline__ void unit_tile(const Params &p, int u, uint32_t r, int &tm, int &tn) {
+  tm = (u / p.tiles_n) * p.cm + (int)r;
+  tn = u % p.tiles_n;
+}
 
 // Bounded wait on a phase parity; false if it timed out or the CTA aborted.
 __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
@@ -104,6 +114,39 @@ __device__ __forceinline__ void tma_load_3d(const CUtensorMap *map, uint64_t *ba
       " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
+}
+
+// The same load delivered to the same shared-memory offset, and its bytes
+// counted on the mbarrier at the same offset, in every CTA of the cluster
+// whose bit is set in mask.
+__device__ __forceinline__ void tma_load_2d_mc(const CUtensorMap *map, uint64_t *bar, void *dst, int x, int y,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Every thread of every CTA of the cluster; release/acquire orders the
+// shared-memory writes (mbarrier initialisation) before the peers' accesses.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -151,6 +194,16 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                : "memory");
 }
 
+// One arrival, once the MMAs issued so far have completed, on the mbarrier at
+// this offset in every CTA of the cluster whose bit is set in mask.
+__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
@@ -181,7 +234,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], p.cm);  // released by the MMAs of every CTA of the cluster
     }
     mbar_init(tfull, 1);
     mbar_init(tempty, 32 * NUM_EPI_WARPS);
@@ -201,6 +254,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // the peers' mbarriers are initialised before any multicast copy or commit reaches them
+  if (p.cm > 1) cluster_sync();
+  const uint32_t rank = cluster_ctarank();  // 0 without clusters (a cluster of one)
+  const int cid = (int)cluster_id(), ncl = (int)cluster_count();
+  const uint16_t mask = (uint16_t)((1u << p.cm) - 1u);
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
@@ -208,8 +266,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int pending[STAGES] = {0, 0, 0};
     uint32_t pend_phase[STAGES] = {0, 0, 0};
     bool ok = true;
-    for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
-      const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
+    for (int u = cid; ok && u < p.units; u += ncl) {
+      int tm, tn;
+      unit_tile(p, u, rank, tm, tn);
       for (int kb = 0; kb < p.k_blocks; ++kb) {
         if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) {
           ok = false;
@@ -227,13 +286,35 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
           for (int j = 0; j < BM / 64; ++j) tma_load_2d(&tma_a, &full[stage], sa + j * MN_LBO, tm * BM + 64 * j, kb * BK);
         }
-        if (!p.b_mn) {
-          tma_load_2d(&tma_b, &full[stage], sb, kb * BK, tn * BN);
+        if (p.cm == 1) {
+          if (!p.b_mn) {
+            tma_load_2d(&tma_b, &full[stage], sb, kb * BK, tn * BN);
+          } else {
+            for (int j = 0; j * 64 < BN; ++j)
+              tma_load_2d(&tma_b, &full[stage], sb + j * MN_LBO, tn * BN + 64 * j, kb * BK);
+          }
+        } else if (!p.b_mn) {
+          // K-major B: this CTA copies rows [rank * BN/cm, +BN/cm) of the slice to every CTA
+          const int rows = BN / p.cm;
+          tma_load_2d_mc(&tma_b, &full[stage], sb + rank * rows * (BK * 2), kb * BK, tn * BN + (int)rank * rows, mask);
         } else {
-          for (int j = 0; j * 64 < BN; ++j) tma_load_2d(&tma_b, &full[stage], sb + j * MN_LBO, tn * BN + 64 * j, kb * BK);
+          // MN-major B: this CTA copies the 64-wide boxes j = rank, rank + cm, ... to every CTA
+          for (int j = (int)rank; j * 64 < BN; j += p.cm)
+            tma_load_2d_mc(&tma_b, &full[stage], sb + j * MN_LBO, tn * BN + 64 * j, kb * BK, mask);
         }
         pending[stage] = 1;
         pend_phase[stage] = phase;
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+    if (ok && p.cm > 1) {
+      // wait for every CTA of the cluster to release each stage's last use,
+      // so that no peer's commit reaches this CTA's barriers after it exits
+      for (int i = 0; ok && i < STAGES; ++i) {
+        ok = mbar_wait(&empty[stage], phase ^ 1, abort_flag);
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1;
@@ -255,7 +336,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     uint32_t stage = 0, phase = 0;
     bool ok = true;
     int iter = 0;
-    for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x, ++iter) {
+    for (int u = cid; ok && u < p.units; u += ncl, ++iter) {
       if (!mbar_wait(tempty, (iter & 1) ^ 1, abort_flag)) {
         ok = false;
         break;
@@ -276,7 +357,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           for (int h = 0; h < 2; ++h)  // rows 128*h .. 128*h+127 of the tile
             umma(tmem_base + h * 256, operand_desc(a0, p.a_mn, h, k), db, idesc, (kb | k) != 0);
         }
-        umma_commit(&empty[stage]);
+        if (p.cm == 1)
+          umma_commit(&empty[stage]);
+        else
+          umma_commit_mc(&empty[stage], mask);  // every CTA's producer refills this stage
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1;
@@ -294,8 +378,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int q = warp & 3;         // TMEM lane quarter this warp may access
     const int h = (warp - 2) >> 2;  // accumulator (row half of the tile)
     int iter = 0;
-    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++iter) {
-      const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
+    for (int u = cid; u < p.units; u += ncl, ++iter) {
+      int tm, tn;
+      unit_tile(p, u, rank, tm, tn);
       if (!mbar_wait(tfull, iter & 1, abort_flag)) break;
       fence_after();
       const int64_t row = (int64_t)tm * BM + 128 * h + 32 * q + lane;
@@ -329,6 +414,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   fence_before();
   __syncthreads();
+  // no CTA leaves while a peer may still copy into its shared memory
+  if (p.cm > 1) cluster_sync();
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
@@ -391,17 +478,14 @@ bool make_map_mn3d(CUtensorMap *map, const void *base, int64_t K, int64_t M, int
 
 int resident_blocks(const void *kernel, int threads);
 
-// op(A) is M x K: A stored M x K (transA = 0, K-major) or K x M (transA = 1,
-// MN-major). op(B) is K x N: B stored K x N (transB = 0, MN-major) or N x K
-// (transB = 1, K-major).
-// Tile width: the BN in {256, 224, ..., 128} whose tiles fill the fewest
-// waves of CTAs, weighted by the tile's cost (proportional to BN).
-int pick_bn(int64_t M, int64_t N, int ctas) {
+// Tile width: the BN in {256, 224, ..., 128} whose cluster work units fill the
+// fewest waves of clusters, weighted by the tile's cost (proportional to BN).
+int pick_bn(int64_t M, int64_t N, int clusters, int cm) {
   int best = 256;
   int64_t best_cost = -1;
   for (int bn = 256; bn >= 128; bn -= 32) {
-    const int64_t tiles = ceil_div(M, BM) * ceil_div(N, bn);
-    const int64_t waves = ceil_div(tiles, ctas);
+    const int64_t units = ceil_div(ceil_div(M, BM), cm) * ceil_div(N, bn);
+    const int64_t waves = ceil_div(units, clusters);
     const int64_t cost = waves * bn;
     if (best_cost < 0 || cost < best_cost) {
       best_cost = cost;
@@ -411,12 +495,48 @@ int pick_bn(int64_t M, int64_t N, int ctas) {
   return best;
 }
 
+// Clusters of cm CTAs that fit on the GPU at once (0 if none), per device.
+int max_clusters(int cm) {
+  static int cached[64][3] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  const int slot = cm == 1 ? 0 : cm == 2 ? 1 : 2;
+  if (cached[dev][slot] == 0) {
+    int n = 0;
+    if (cm == 1) {
+      n = sm_count();
+    } else {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cm * 64);
+      cfg.blockDim = dim3(NUM_THREADS);
+      cfg.dynamicSmemBytes = SMEM_BYTES;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = cm;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (cudaOccupancyMaxActiveClusters(&n, reinterpret_cast<const void *>(gemm_bf16_tcgen05_kernel), &cfg) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+      }
+    }
+    cached[dev][slot] = n > 0 ? n : -1;
+  }
+  return cached[dev][slot] > 0 ? cached[dev][slot] : 0;
+}
+
 // op(A) is M x K: A stored M x K (transA = 0, K-major) or K x M (transA = 1,
 // MN-major). op(B) is K x N: B stored K x N (transB = 0, MN-major) or N x K
-// (transB = 1, K-major). tile_n = 0 picks BN per shape.
+// (transB = 1, K-major). tile_n = 0 picks BN per shape; cluster = 0 picks the
+// CTAs per cluster (1, 2 or 4) that share each B slice through TMA multicast;
+// grid > 0 gives the CTAs of the persistent grid (rounded down to whole
+// clusters, at least one cluster).
 cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,
                              int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_n,
-                             int vec_ok, cudaStream_t stream) {
+                             int cluster, int vec_ok, cudaStream_t stream) {
   static bool attr_set = false;
   const void *kfn = reinterpret_cast<const void *>(gemm_bf16_tcgen05_kernel);
   if (!attr_set) {
@@ -424,13 +544,20 @@ cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int ctas = grid > 0 ? grid : sm_count();
-  const int BN = tile_n > 0 ? tile_n : pick_bn(M, N, ctas);
+  const int64_t tiles_m = ceil_div(M, BM);
+  int cm = cluster;
+  if (cm == 0) cm = tiles_m >= 2 && max_clusters(2) > 0 ? 2 : 1;
+  if (cm != 1 && cm != 2 && cm != 4) return cudaErrorInvalidValue;
+  const int fit = max_clusters(cm);
+  if (fit == 0) return cudaErrorInvalidConfiguration;
+  const int clusters = grid > 0 ? (grid / cm > 0 ? grid / cm : 1) : fit;
+  const int BN = tile_n > 0 ? tile_n : pick_bn(M, N, clusters, cm);
   alignas(64) CUtensorMap ma, mb;
   const int a_3d = transA && M % 64 == 0;
   bool ok = transA ? (a_3d ? make_map_mn3d(&ma, A, K, M, lda) : make_map(&ma, A, K, M, lda, 64, BK))
                    : make_map(&ma, A, M, K, lda, BK, BM);
-  ok = ok && (transB ? make_map(&mb, B, N, K, ldb, BK, BN) : make_map(&mb, B, K, N, ldb, 64, BK));
+  // a K-major B slice is copied in cm parts of BN / cm rows, one per CTA of the cluster
+  ok = ok && (transB ? make_map(&mb, B, N, K, ldb, BK, BN / cm) : make_map(&mb, B, K, N, ldb, 64, BK));
   if (!ok) return cudaErrorInvalidValue;
   Params p;
   p.C = C;
@@ -440,17 +567,31 @@ cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int
   p.ldc = ldc;
   p.BN = BN;
   p.tiles_n = (int)ceil_div(N, BN);
-  p.num_tiles = (int)(ceil_div(M, BM) * p.tiles_n);
   p.k_blocks = (int)ceil_div(K, BK);
+  p.cm = cm;
+  p.units = (int)(ceil_div(tiles_m, cm) * p.tiles_n);
   p.a_mn = transA ? 1 : 0;
   p.b_mn = transB ? 0 : 1;
   p.vec_ok = vec_ok;
   p.a_3d = a_3d;
   const uint32_t b_tx = p.b_mn ? (uint32_t)ceil_div(BN, 64) * (64u * BK * 2u) : (uint32_t)BN * BK * 2u;
   p.stage_tx = (uint32_t)A_BYTES + b_tx;
-  int g = ctas < p.num_tiles ? ctas : p.num_tiles;
+  const int g = (clusters < p.units ? clusters : p.units) * cm;
   void *args[] = {&ma, &mb, &p};
-  return cudaLaunchKernel(kfn, dim3(g), dim3(NUM_THREADS), args, SMEM_BYTES, stream);
+  if (cm == 1) return cudaLaunchKernel(kfn, dim3(g), dim3(NUM_THREADS), args, SMEM_BYTES, stream);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(g);
+  cfg.blockDim = dim3(NUM_THREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cm;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, kfn, args);
 }
 
 unsigned *device_status_word() {

@@ -159,3 +159,27 @@ def test_selftest_bounded_wait_range():
     assert L.dpia_selftest_bounded_wait(0, None) == N.ERR_SHAPE
     assert L.dpia_selftest_bounded_wait(2000001, None) == N.ERR_SHAPE
     assert "timeout_us" in dpia.dpia_last_error_message()
+
+
+def test_gemm_strategy_validation():
+    """The BF16 GEMM's tiles are 256 x tile_n x 64 and its clusters 1, 2 or 4
+    CTAs (0 = chosen); anything else is refused before any CUDA call."""
+    L = N.lib()
+    p = ctypes.c_void_p
+
+    def call(**kw):
+        st = N.GemmStrategyC(1, kw.get("tile_m", 0), kw.get("tile_n", 0), kw.get("tile_k", 0), kw.get("grid", 0),
+                             kw.get("cluster", 0))
+        return L.dpia_gemm_bf16(p(0x10000), p(0x20000), p(0x30000), 512, 512, 512, 512, 512, 512, 0, 0,
+                                ctypes.byref(st), None)
+
+    assert ctypes.sizeof(N.GemmStrategyC) == 6 * 4
+    for c in (3, 5, 8, -1):
+        assert call(cluster=c) == N.ERR_STRATEGY
+        assert "cluster" in dpia.dpia_last_error_message()
+    assert call(grid=-1) == N.ERR_STRATEGY
+    assert call(tile_n=96) == N.ERR_UNSUPPORTED
+    assert call(tile_n=240) == N.ERR_UNSUPPORTED
+    assert call(tile_m=128) == N.ERR_UNSUPPORTED
+    assert L.dpia_gemm_bf16(p(0x10000), p(0x20000), p(0x30000), 512, 512, 512, 512, 512, 512, 0, 0, None,
+                            None) == N.ERR_NULL

@@ -122,6 +122,53 @@ def test_gemm_bf16_tolerance(cuda_device, tA, tB, M, N, K, tile_n):
     assert dpia.dpia_poll_device_status() == 0
 
 
+@pytest.mark.parametrize("cluster", [1, 2, 4])
+@pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("M,N,K,tile_n", [(768, 448, 192, 224), (520, 300, 136, 0), (1024, 256, 64, 128),
+                                          (256, 520, 320, 160)])
+def test_gemm_bf16_clusters(cuda_device, tA, tB, M, N, K, tile_n, cluster):
+    """CTAs of a cluster share each B slice through TMA multicast: the same
+    products with 1, 2 or 4 CTAs per cluster, including tile-row counts that
+    leave a cluster's last CTA past M (3 tile rows with clusters of 2 or 4,
+    1 tile row with any cluster) and a small persistent grid (several work
+    units per cluster)."""
+    g = torch.Generator().manual_seed(11 * M + 5 * N + K + tA + 2 * tB)
+    opA = torch.randn(M, K, generator=g).numpy()
+    opB = torch.randn(K, N, generator=g).numpy()
+    A, B = _store(opA, tA), _store(opB, tB)
+    lda = (A.shape[1] + 7) // 8 * 8
+    ldb = (B.shape[1] + 7) // 8 * 8
+    Ad = torch.zeros(A.shape[0], lda, device="cuda")
+    Ad[:, :A.shape[1]] = torch.from_numpy(A)
+    Bd = torch.zeros(B.shape[0], ldb, device="cuda")
+    Bd[:, :B.shape[1]] = torch.from_numpy(B)
+    Ab, Bb = dpia.to_bf16(Ad), dpia.to_bf16(Bd)
+    for grid in (0, 2 * cluster):
+        C = torch.full((M, N), float("nan"), device="cuda")
+        dpia.dpia_gemm_bf16(Ab, Bb, C, M, N, K, lda, ldb, N, tA, tB, grid=grid, tile_n=tile_n, cluster=cluster)
+        torch.cuda.synchronize()
+        _bf16_check(host(C).astype(np.float64), opA, opB,
+                    f"bf16 cluster={cluster} grid={grid} tA={tA} tB={tB} {M}x{N}x{K}")
+        assert dpia.dpia_poll_device_status() == 0
+
+
+def test_gemm_bf16_cluster_results_agree(cuda_device, gemm_inputs):
+    """Multicast changes where B's bytes come from, not the products: at
+    4096^3 the three cluster sizes, with the same tile width, give
+    bit-identical C (the same MMAs in the same k order for every C_ij)."""
+    A, B, _ = gemm_inputs
+    n = W.GEMM_MNK
+    Ab, Bb = dpia.to_bf16(A), dpia.to_bf16(B)
+    out = []
+    for cluster in (1, 2, 4):
+        C = torch.empty(n, n, device="cuda")
+        dpia.dpia_gemm_bf16(Ab, Bb, C, n, n, n, n, n, n, 0, 0, tile_n=224, cluster=cluster)
+        out.append(C)
+    torch.cuda.synchronize()
+    assert dpia.dpia_poll_device_status() == 0
+    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
+
+
 def test_gemm_bf16_4096(cuda_device, gemm_inputs):
     """The GEMM workload (4096^3): forward and both backward products."""
     A, B, dC = gemm_inputs
