@@ -697,10 +697,10 @@ def gemm_workload(args, device, dist):
                             "bound": "alu", "peak_TFLOP_s": round(fma_peak, 1),
                             "peak_source": f"{sms} SMs x 128 FP32 FMA lanes x 2 flops x {sm_mhz:.0f} MHz (median "
                                            "clock under load)", "frac": round(fl / f32 / 1e9 / fma_peak, 4)}
-    # each launch alone (L2 flushed before it) with 1, 2 and 4 CTAs per cluster sharing B by TMA multicast
+    # each launch alone (L2 flushed before it) on one CTA per tile (cta_group::1) and on CTA pairs (cta_group::2)
     flush = L2Flush(device)
     by_cluster = {}
-    for cl in (1, 2, 4):
+    for cl in (1, 2):
         calls = {"bf16_fwd": lambda cl=cl: dpia.dpia_gemm_bf16(Ab, Bb, C, n, n, n, n, n, n, 0, 0, cluster=cl),
                  "bf16_bwd_dA": lambda cl=cl: dpia.dpia_gemm_bf16(dCb, Bb, gA, n, n, n, n, n, n, 0, 1, cluster=cl),
                  "bf16_bwd_dB": lambda cl=cl: dpia.dpia_gemm_bf16(Ab, dCb, gB, n, n, n, n, n, n, 1, 0, cluster=cl)}
@@ -1224,8 +1224,8 @@ def main(argv=None):
                     help="run a small case of one kernel --reps times (for ncu captures); no JSON line")
     ap.add_argument("--n", type=int, default=1 << 25, help="elements (or rows x cols) of the --profile case")
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2, 4],
-                    help="CTAs per cluster of the BF16 GEMM in the gemm --profile case (0 = chosen)")
+    ap.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2],
+                    help="CTAs per 256-row tile of the BF16 GEMM in the gemm --profile case (0 = chosen)")
     args = ap.parse_args(argv)
     if args.profile:
         return profile_case(args)

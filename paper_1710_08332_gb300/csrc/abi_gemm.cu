@@ -151,8 +151,8 @@ dpia_status dpia_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64
     set_last_error("%s: grid=%d", fn, st->grid);
     return DPIA_ERR_STRATEGY;
   }
-  if (st->cluster != 0 && st->cluster != 1 && st->cluster != 2 && st->cluster != 4) {
-    set_last_error("%s: cluster=%d (0 = chosen per shape, or 1, 2, 4)", fn, st->cluster);
+  if (st->cluster != 0 && st->cluster != 1 && st->cluster != 2) {
+    set_last_error("%s: cluster=%d (0 = chosen per shape, 1 = one CTA per tile, 2 = a CTA pair)", fn, st->cluster);
     return DPIA_ERR_STRATEGY;
   }
   int64_t ab = 0, bb = 0;

@@ -67,21 +67,11 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 struct Params {
   float *C;
   int64_t M, N, K, ldc;
-  int BN, tiles_n, k_blocks;
-  int cm;             // CTAs per cluster, on consecutive tile rows sharing one tile column
-  int units;          // cluster work units: ceil(tile rows / cm) x tile columns
+  int BN, tiles_n, num_tiles, k_blocks;
   int a_mn, b_mn, vec_ok;
   int a_3d;           // MN-major A loaded as one 3-D box {64 m, 64 k, 4 m-blocks}
-  uint32_t stage_tx;  // bytes one stage receives (all of A's and B's slices)
+  uint32_t stage_tx;  // bytes the TMA loads of one stage deliver
 };
-
-// Tile of work unit u for the CTA of cluster rank r: the cm CTAs of a cluster
-// take consecutive tile rows of the same tile column, so they read the same
-// B slices.
-__device__ __forceinline__ void unit_tile(const Params &p, int u, uint32_t r, int &tm, int &tn) {
-  tm = (u / p.tiles_n) * p.cm + (int)r;
-  tn = u % p.tiles_n;
-}
 
 // Bounded wait on a phase parity; false if it timed out or the CTA aborted.
 __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
@@ -114,39 +104,6 @@ __device__ __forceinline__ void tma_load_3d(const CUtensorMap *map, uint64_t *ba
       " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
-}
-
-// The same load delivered to the same shared-memory offset, and its bytes
-// counted on the mbarrier at the same offset, in every CTA of the cluster
-// whose bit is set in mask.
-__device__ __forceinline__ void tma_load_2d_mc(const CUtensorMap *map, uint64_t *bar, void *dst, int x, int y,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_id() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_count() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-  return r;
-}
-// Every thread of every CTA of the cluster; release/acquire orders the
-// shared-memory writes (mbarrier initialisation) before the peers' accesses.
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -194,16 +151,6 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                : "memory");
 }
 
-// One arrival, once the MMAs issued so far have completed, on the mbarrier at
-// this offset in every CTA of the cluster whose bit is set in mask.
-__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
@@ -234,7 +181,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], p.cm);  // released by the MMAs of every CTA of the cluster
+      mbar_init(&empty[s], 1);
     }
     mbar_init(tfull, 1);
     mbar_init(tempty, 32 * NUM_EPI_WARPS);
@@ -254,11 +201,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  // the peers' mbarriers are initialised before any multicast copy or commit reaches them
-  if (p.cm > 1) cluster_sync();
-  const uint32_t rank = cluster_ctarank();  // 0 without clusters (a cluster of one)
-  const int cid = (int)cluster_id(), ncl = (int)cluster_count();
-  const uint16_t mask = (uint16_t)((1u << p.cm) - 1u);
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
@@ -266,9 +208,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int pending[STAGES] = {0, 0, 0};
     uint32_t pend_phase[STAGES] = {0, 0, 0};
     bool ok = true;
-    for (int u = cid; ok && u < p.units; u += ncl) {
-      int tm, tn;
-      unit_tile(p, u, rank, tm, tn);
+    for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
+      const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
       for (int kb = 0; kb < p.k_blocks; ++kb) {
         if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) {
           ok = false;
@@ -286,35 +227,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
           for (int j = 0; j < BM / 64; ++j) tma_load_2d(&tma_a, &full[stage], sa + j * MN_LBO, tm * BM + 64 * j, kb * BK);
         }
-        if (p.cm == 1) {
-          if (!p.b_mn) {
-            tma_load_2d(&tma_b, &full[stage], sb, kb * BK, tn * BN);
-          } else {
-            for (int j = 0; j * 64 < BN; ++j)
-              tma_load_2d(&tma_b, &full[stage], sb + j * MN_LBO, tn * BN + 64 * j, kb * BK);
-          }
-        } else if (!p.b_mn) {
-          // K-major B: this CTA copies rows [rank * BN/cm, +BN/cm) of the slice to every CTA
-          const int rows = BN / p.cm;
-          tma_load_2d_mc(&tma_b, &full[stage], sb + rank * rows * (BK * 2), kb * BK, tn * BN + (int)rank * rows, mask);
+        if (!p.b_mn) {
+          tma_load_2d(&tma_b, &full[stage], sb, kb * BK, tn * BN);
         } else {
-          // MN-major B: this CTA copies the 64-wide boxes j = rank, rank + cm, ... to every CTA
-          for (int j = (int)rank; j * 64 < BN; j += p.cm)
-            tma_load_2d_mc(&tma_b, &full[stage], sb + j * MN_LBO, tn * BN + 64 * j, kb * BK, mask);
+          for (int j = 0; j * 64 < BN; ++j) tma_load_2d(&tma_b, &full[stage], sb + j * MN_LBO, tn * BN + 64 * j, kb * BK);
         }
         pending[stage] = 1;
         pend_phase[stage] = phase;
-        if (++stage == STAGES) {
-          stage = 0;
-          phase ^= 1;
-        }
-      }
-    }
-    if (ok && p.cm > 1) {
-      // wait for every CTA of the cluster to release each stage's last use,
-      // so that no peer's commit reaches this CTA's barriers after it exits
-      for (int i = 0; ok && i < STAGES; ++i) {
-        ok = mbar_wait(&empty[stage], phase ^ 1, abort_flag);
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1;
@@ -336,7 +255,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     uint32_t stage = 0, phase = 0;
     bool ok = true;
     int iter = 0;
-    for (int u = cid; ok && u < p.units; u += ncl, ++iter) {
+    for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x, ++iter) {
       if (!mbar_wait(tempty, (iter & 1) ^ 1, abort_flag)) {
         ok = false;
         break;
@@ -357,10 +276,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           for (int h = 0; h < 2; ++h)  // rows 128*h .. 128*h+127 of the tile
             umma(tmem_base + h * 256, operand_desc(a0, p.a_mn, h, k), db, idesc, (kb | k) != 0);
         }
-        if (p.cm == 1)
-          umma_commit(&empty[stage]);
-        else
-          umma_commit_mc(&empty[stage], mask);  // every CTA's producer refills this stage
+        umma_commit(&empty[stage]);
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1;
@@ -378,9 +294,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int q = warp & 3;         // TMEM lane quarter this warp may access
     const int h = (warp - 2) >> 2;  // accumulator (row half of the tile)
     int iter = 0;
-    for (int u = cid; u < p.units; u += ncl, ++iter) {
-      int tm, tn;
-      unit_tile(p, u, rank, tm, tn);
+    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++iter) {
+      const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
       if (!mbar_wait(tfull, iter & 1, abort_flag)) break;
       fence_after();
       const int64_t row = (int64_t)tm * BM + 128 * h + 32 * q + lane;
@@ -414,8 +329,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   fence_before();
   __syncthreads();
-  // no CTA leaves while a peer may still copy into its shared memory
-  if (p.cm > 1) cluster_sync();
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
@@ -423,11 +336,308 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- CTA pairs
+// The same product with the tile's two 128-row halves on two SMs (a cluster
+// of two CTAs, tcgen05 cta_group::2): each CTA stages its own 128 rows of the
+// A slice and its half of the B slice's columns; one M=256 MMA issued by the
+// even CTA reads both CTAs' shared memory and writes rows 0..127 of the
+// accumulator to its own tensor memory and rows 128..255 to its peer's. Each
+// SM then reads every operand byte from its shared memory once per k step
+// (the one-SM tile reads its B slice twice, once per 128-row half), and each
+// SM's accumulator is 128 x BN, so two of them fit in tensor memory and the
+// epilogue of one tile overlaps the MMAs of the next.
+//   warp 0    -- TMA producer (both CTAs): its A rows and B columns of a
+//                k-slice into a 6-stage ring of 32 KiB stages; the copies of
+//                both CTAs complete on the even CTA's full barrier;
+//   warp 1    -- allocates 512 TMEM columns in both CTAs (collectively); in
+//                the even CTA one thread issues the MMAs (M=256, N=BN, K=16)
+//                and commits stage releases and finished accumulators to the
+//                barriers of both CTAs;
+//   warps 2-5 -- epilogue (both CTAs): its 128 rows of the accumulator, then
+//                a release arrival on the even CTA's tempty barrier.
+constexpr int P_STAGES = 6;
+constexpr int P_A_BYTES = 128 * BK * 2;               // 16 KiB: this CTA's 128 rows
+constexpr int P_B_BYTES = 128 * BK * 2;               // 16 KiB: this CTA's half of the widest B slice
+constexpr int P_STAGE_BYTES = P_A_BYTES + P_B_BYTES;  // 32 KiB
+constexpr int P_EPI_WARPS = 4;
+constexpr int P_THREADS = 64 + 32 * P_EPI_WARPS;
+constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + 1024 + 256;
+
+struct PairParams {
+  float *C;
+  int64_t M, N, K, ldc;
+  int BN, tiles_n, k_blocks, units;  // units: 256 x BN tiles
+  int a_mn, b_mn, vec_ok;
+  int a_3d;           // MN-major A loaded as one 3-D box {64 m, 64 k, 2 m-blocks}
+  uint32_t stage_tx;  // bytes both CTAs' copies of one stage deliver to the even CTA's barrier
+};
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// All threads of both CTAs; release/acquire orders shared-memory writes (the
+// mbarrier initialisation) before the peer's accesses.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address in the cluster window of the variable at this CTA-relative shared
+// address in the CTA of the given rank.
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t smem_addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Copies into this CTA's shared memory whose bytes complete on an mbarrier of
+// either CTA of the pair (bar: its address in the cluster window).
+__device__ __forceinline__ void tma2_load_2d(const CUtensorMap *map, uint32_t bar, void *dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma2_load_3d(const CUtensorMap *map, uint32_t bar, void *dst, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void umma2(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// One arrival on the mbarrier at this offset in both CTAs once the MMAs
+// issued so far have completed.
+__device__ __forceinline__ void umma2_commit_both(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+__device__ __forceinline__ void umma2_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__global__ void __launch_bounds__(P_THREADS, 1)
+    gemm_bf16_pair_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b,
+                          const PairParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + P_STAGES * P_STAGE_BYTES);  // used in the even CTA
+  uint64_t *empty = full + P_STAGES;
+  uint64_t *tfull = empty + P_STAGES;  // [2]: accumulator ready
+  uint64_t *tempty = tfull + 2;        // [2]: accumulator drained by both CTAs (used in the even CTA)
+  uint64_t *drain = tempty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();  // 0: issues the MMAs; 1: its peer
+  const int BN = p.BN, HN = BN / 2;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES; ++s) {
+      mbar_init(&full[s], 1);   // the even CTA's expect_tx arrival, plus both CTAs' bytes
+      mbar_init(&empty[s], 1);  // the MMA commit
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 2 * P_EPI_WARPS);  // one arrival per epilogue warp of both CTAs
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tma_a)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tma_b)) : "memory");
+  }
+  if (warp == 1) {  // one warp of each CTA of the pair allocates, collectively
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  cluster_sync();  // both CTAs' barriers are initialised before any copy or commit reaches them
+  const uint32_t tmem_base = *tmem_slot;
+  const int cid = (int)cluster_id(), ncl = (int)cluster_count();
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer (both CTAs)
+    const uint32_t full0 = map_to_rank(smem_u32(full), 0);
+    uint32_t stage = 0, phase = 0;
+    int pending[P_STAGES] = {};
+    uint32_t pend_phase[P_STAGES] = {};
+    bool ok = true;
+    for (int u = cid; ok && u < p.units; u += ncl) {
+      const int tm = u / p.tiles_n, tn = u % p.tiles_n;
+      const int row0 = tm * BM + (int)rank * 128;  // this CTA's rows of op(A)
+      const int col0 = tn * BN + (int)rank * HN;   // this CTA's columns of op(B)
+      for (int kb = 0; kb < p.k_blocks; ++kb) {
+        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        pending[stage] = 0;
+        if (rank == 0) mbar_expect_tx(&full[stage], p.stage_tx);
+        const uint32_t fb = full0 + stage * 8u;
+        uint8_t *sa = smem + stage * P_STAGE_BYTES;
+        uint8_t *sb = sa + P_A_BYTES;
+        if (!p.a_mn) {
+          tma2_load_2d(&tma_a, fb, sa, kb * BK, row0);
+        } else if (p.a_3d) {
+          tma2_load_3d(&tma_a, fb, sa, 0, kb * BK, row0 / 64);
+        } else {
+          for (int j = 0; j < 2; ++j) tma2_load_2d(&tma_a, fb, sa + j * MN_LBO, row0 + 64 * j, kb * BK);
+        }
+        if (!p.b_mn) {
+          tma2_load_2d(&tma_b, fb, sb, kb * BK, col0);
+        } else {
+          for (int j = 0; j * 64 < HN; ++j) tma2_load_2d(&tma_b, fb, sb + j * MN_LBO, col0 + 64 * j, kb * BK);
+        }
+        pending[stage] = 1;
+        pend_phase[stage] = phase;
+        if (++stage == P_STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+    // each stage's last use released: no commit reaches this CTA's barriers after it exits
+    for (int i = 0; ok && i < P_STAGES; ++i) {
+      ok = mbar_wait(&empty[stage], phase ^ 1, abort_flag);
+      if (++stage == P_STAGES) {
+        stage = 0;
+        phase ^= 1;
+      }
+    }
+    if (!ok && rank == 0) {
+      // drain copies still in flight (both CTAs' bytes complete on these barriers)
+      for (int s = 0; s < P_STAGES; ++s) {
+        if (!pending[s]) continue;
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(&full[s], pend_phase[s]) && globaltimer() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ------------------------------------------------------------ MMA issuer (even CTA)
+    const uint32_t idesc = idesc_bf16(256, BN, p.a_mn, p.b_mn);
+    uint32_t stage = 0, phase = 0;
+    bool ok = true;
+    int iter = 0;
+    for (int u = cid; ok && u < p.units; u += ncl, ++iter) {
+      const int acc = iter & 1;
+      const uint32_t use = (uint32_t)iter >> 1;
+      if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, abort_flag)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+      const uint32_t d = tmem_base + (uint32_t)acc * 256;
+      for (int kb = 0; kb < p.k_blocks; ++kb) {
+        if (!mbar_wait(&full[stage], phase, abort_flag)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t a0 = smem_u32(smem + stage * P_STAGE_BYTES);
+        const uint32_t b0 = a0 + P_A_BYTES;
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k)
+          umma2(d, operand_desc(a0, p.a_mn, 0, k), operand_desc(b0, p.b_mn, 0, k), idesc, (kb | k) != 0);
+        umma2_commit_both(&empty[stage]);
+        if (++stage == P_STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (ok) umma2_commit_both(&tfull[acc]);
+    }
+    umma2_commit(drain);
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue (both CTAs)
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const uint32_t tempty0 = map_to_rank(smem_u32(tempty), 0);
+    int iter = 0;
+    for (int u = cid; u < p.units; u += ncl, ++iter) {
+      const int acc = iter & 1;
+      const uint32_t use = (uint32_t)iter >> 1;
+      const int tm = u / p.tiles_n, tn = u % p.tiles_n;
+      if (!mbar_wait(&tfull[acc], use & 1, abort_flag)) break;
+      fence_after();
+      const int64_t row = (int64_t)tm * BM + 128 * rank + 32 * q + lane;
+      float *crow = p.C + row * p.ldc;
+      const uint32_t tbase = tmem_base + (uint32_t)acc * 256 + ((uint32_t)(32 * q) << 16);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        tmem_ld32(tbase + c, r);
+        if (c + 32 >= BN) {  // accumulator read out: the MMAs may refill it
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(tempty0 + (uint32_t)acc * 8u);
+        }
+        if (row < p.M) {
+          const int64_t col0 = (int64_t)tn * BN + c;
+          if (p.vec_ok && col0 + 32 <= p.N) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4 *>(crow + col0 + j) =
+                  make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                              __uint_as_float(r[j + 3]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (col0 + j < p.N) crow[col0 + j] = __uint_as_float(r[j]);
+          }
+        }
+      }
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  cluster_sync();  // no CTA frees its tensor memory or leaves while its peer's MMAs or copies may reach it
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // 3-D view of a row-major K x M bf16 matrix (M contiguous) as {64 m, K, M/64
-// blocks}: a box {64, 64, 4} lands in shared memory as four [64 k][64 m]
-// blocks, the MN-major layout the descriptors read, in one copy. Needs M a
-// multiple of 64 (the view never reads past a row).
-bool make_map_mn3d(CUtensorMap *map, const void *base, int64_t K, int64_t M, int64_t ld);
+// blocks}: a box {64, 64, blocks} lands in shared memory as that many
+// [64 k][64 m] blocks, the MN-major layout the descriptors read, in one copy.
+// Needs M a multiple of 64 (the view never reads past a row).
+bool make_map_mn3d(CUtensorMap *map, const void *base, int64_t K, int64_t M, int64_t ld, int blocks);
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -461,12 +671,12 @@ bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, in
   return r == CUDA_SUCCESS;
 }
 
-bool make_map_mn3d(CUtensorMap *map, const void *base, int64_t K, int64_t M, int64_t ld) {
+bool make_map_mn3d(CUtensorMap *map, const void *base, int64_t K, int64_t M, int64_t ld, int blocks) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {64, (cuuint64_t)K, (cuuint64_t)(M / 64)};
   cuuint64_t strides[2] = {(cuuint64_t)ld * 2, 128};
-  cuuint32_t box[3] = {64, (cuuint32_t)BK, (cuuint32_t)(BM / 64)};
+  cuuint32_t box[3] = {64, (cuuint32_t)BK, (cuuint32_t)blocks};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -478,14 +688,15 @@ bool make_map_mn3d(CUtensorMap *map, const void *base, int64_t K, int64_t M, int
 
 int resident_blocks(const void *kernel, int threads);
 
-// Tile width: the BN in {256, 224, ..., 128} whose cluster work units fill the
-// fewest waves of clusters, weighted by the tile's cost (proportional to BN).
-int pick_bn(int64_t M, int64_t N, int clusters, int cm) {
+// Tile width: the BN in {256, 224, ..., 128} whose 256-row tiles fill the
+// fewest waves of the slots that run at once (CTAs, or CTA pairs), weighted
+// by the tile's cost (proportional to BN).
+int pick_bn(int64_t M, int64_t N, int slots) {
   int best = 256;
   int64_t best_cost = -1;
   for (int bn = 256; bn >= 128; bn -= 32) {
-    const int64_t units = ceil_div(ceil_div(M, BM), cm) * ceil_div(N, bn);
-    const int64_t waves = ceil_div(units, clusters);
+    const int64_t tiles = ceil_div(M, BM) * ceil_div(N, bn);
+    const int64_t waves = ceil_div(tiles, slots);
     const int64_t cost = waves * bn;
     if (best_cost < 0 || cost < best_cost) {
       best_cost = cost;
@@ -495,69 +706,117 @@ int pick_bn(int64_t M, int64_t N, int clusters, int cm) {
   return best;
 }
 
-// Clusters of cm CTAs that fit on the GPU at once (0 if none), per device.
-int max_clusters(int cm) {
-  static int cached[64][3] = {};
+// CTA pairs of the pair kernel that fit on the GPU at once (0 if none), per device.
+int pair_slots() {
+  static int cached[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-  const int slot = cm == 1 ? 0 : cm == 2 ? 1 : 2;
-  if (cached[dev][slot] == 0) {
+  if (cached[dev] == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * 64);
+    cfg.blockDim = dim3(P_THREADS);
+    cfg.dynamicSmemBytes = P_SMEM_BYTES;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     int n = 0;
-    if (cm == 1) {
-      n = sm_count();
-    } else {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(cm * 64);
-      cfg.blockDim = dim3(NUM_THREADS);
-      cfg.dynamicSmemBytes = SMEM_BYTES;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = cm;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      if (cudaOccupancyMaxActiveClusters(&n, reinterpret_cast<const void *>(gemm_bf16_tcgen05_kernel), &cfg) !=
-          cudaSuccess) {
-        cudaGetLastError();
-        n = 0;
-      }
+    if (cudaOccupancyMaxActiveClusters(&n, reinterpret_cast<const void *>(gemm_bf16_pair_kernel), &cfg) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
     }
-    cached[dev][slot] = n > 0 ? n : -1;
+    cached[dev] = n > 0 ? n : -1;
   }
-  return cached[dev][slot] > 0 ? cached[dev][slot] : 0;
+  return cached[dev] > 0 ? cached[dev] : 0;
+}
+
+cudaError_t set_smem_attrs() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(gemm_bf16_tcgen05_kernel),
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(reinterpret_cast<const void *>(gemm_bf16_pair_kernel),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+// The pair kernel: 256 x BN tiles, each on a cluster of two CTAs.
+cudaError_t launch_pair(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,
+                        int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_n,
+                        int vec_ok, int fit, cudaStream_t stream) {
+  const int clusters = grid > 0 ? (grid / 2 > 0 ? grid / 2 : 1) : fit;
+  const int BN = tile_n > 0 ? tile_n : pick_bn(M, N, clusters);
+  const int HN = BN / 2;
+  alignas(64) CUtensorMap ma, mb;
+  const int a_3d = transA && M % 64 == 0;
+  bool ok = transA ? (a_3d ? make_map_mn3d(&ma, A, K, M, lda, 2) : make_map(&ma, A, K, M, lda, 64, BK))
+                   : make_map(&ma, A, M, K, lda, BK, 128);
+  ok = ok && (transB ? make_map(&mb, B, N, K, ldb, BK, HN) : make_map(&mb, B, K, N, ldb, 64, BK));
+  if (!ok) return cudaErrorInvalidValue;
+  PairParams p;
+  p.C = C;
+  p.M = M;
+  p.N = N;
+  p.K = K;
+  p.ldc = ldc;
+  p.BN = BN;
+  p.tiles_n = (int)ceil_div(N, BN);
+  p.k_blocks = (int)ceil_div(K, BK);
+  p.units = (int)(ceil_div(M, BM) * p.tiles_n);
+  p.a_mn = transA ? 1 : 0;
+  p.b_mn = transB ? 0 : 1;
+  p.vec_ok = vec_ok;
+  p.a_3d = a_3d;
+  const uint32_t b_half = p.b_mn ? (uint32_t)ceil_div(HN, 64) * (64u * BK * 2u) : (uint32_t)HN * BK * 2u;
+  p.stage_tx = 2u * ((uint32_t)P_A_BYTES + b_half);
+  const int g = 2 * (clusters < p.units ? clusters : p.units);
+  void *args[] = {&ma, &mb, &p};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(g);
+  cfg.blockDim = dim3(P_THREADS);
+  cfg.dynamicSmemBytes = P_SMEM_BYTES;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(gemm_bf16_pair_kernel), args);
 }
 
 // op(A) is M x K: A stored M x K (transA = 0, K-major) or K x M (transA = 1,
 // MN-major). op(B) is K x N: B stored K x N (transB = 0, MN-major) or N x K
-// (transB = 1, K-major). tile_n = 0 picks BN per shape; cluster = 0 picks the
-// CTAs per cluster (1, 2 or 4) that share each B slice through TMA multicast;
-// grid > 0 gives the CTAs of the persistent grid (rounded down to whole
-// clusters, at least one cluster).
+// (transB = 1, K-major). tile_n = 0 picks BN per shape. cluster: 1 = one CTA
+// per 256-row tile (cta_group::1), 2 = a CTA pair per tile (cta_group::2),
+// 0 = the pair when the tile has rows for both CTAs (M > 128) and pairs fit.
+// grid > 0: CTAs of the persistent grid (a pair kernel takes whole pairs).
 cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,
                              int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_n,
                              int cluster, int vec_ok, cudaStream_t stream) {
-  static bool attr_set = false;
-  const void *kfn = reinterpret_cast<const void *>(gemm_bf16_tcgen05_kernel);
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
+  cudaError_t e = set_smem_attrs();
+  if (e != cudaSuccess) return e;
+  if (cluster != 1) {
+    const int fit = pair_slots();
+    if (cluster == 2 && fit == 0) return cudaErrorInvalidConfiguration;
+    if (fit > 0 && (cluster == 2 || M > 128))
+      return launch_pair(A, B, C, M, N, K, lda, ldb, ldc, transA, transB, grid, tile_n, vec_ok, fit, stream);
   }
-  const int64_t tiles_m = ceil_div(M, BM);
-  int cm = cluster;
-  if (cm == 0) cm = tiles_m >= 2 && max_clusters(2) > 0 ? 2 : 1;
-  if (cm != 1 && cm != 2 && cm != 4) return cudaErrorInvalidValue;
-  const int fit = max_clusters(cm);
-  if (fit == 0) return cudaErrorInvalidConfiguration;
-  const int clusters = grid > 0 ? (grid / cm > 0 ? grid / cm : 1) : fit;
-  const int BN = tile_n > 0 ? tile_n : pick_bn(M, N, clusters, cm);
+  const void *kfn = reinterpret_cast<const void *>(gemm_bf16_tcgen05_kernel);
+  const int ctas = grid > 0 ? grid : sm_count();
+  const int BN = tile_n > 0 ? tile_n : pick_bn(M, N, ctas);
   alignas(64) CUtensorMap ma, mb;
   const int a_3d = transA && M % 64 == 0;
-  bool ok = transA ? (a_3d ? make_map_mn3d(&ma, A, K, M, lda) : make_map(&ma, A, K, M, lda, 64, BK))
+  bool ok = transA ? (a_3d ? make_map_mn3d(&ma, A, K, M, lda, BM / 64) : make_map(&ma, A, K, M, lda, 64, BK))
                    : make_map(&ma, A, M, K, lda, BK, BM);
-  // a K-major B slice is copied in cm parts of BN / cm rows, one per CTA of the cluster
-  ok = ok && (transB ? make_map(&mb, B, N, K, ldb, BK, BN / cm) : make_map(&mb, B, K, N, ldb, 64, BK));
+  ok = ok && (transB ? make_map(&mb, B, N, K, ldb, BK, BN) : make_map(&mb, B, K, N, ldb, 64, BK));
   if (!ok) return cudaErrorInvalidValue;
   Params p;
   p.C = C;
@@ -567,31 +826,17 @@ cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int
   p.ldc = ldc;
   p.BN = BN;
   p.tiles_n = (int)ceil_div(N, BN);
+  p.num_tiles = (int)(ceil_div(M, BM) * p.tiles_n);
   p.k_blocks = (int)ceil_div(K, BK);
-  p.cm = cm;
-  p.units = (int)(ceil_div(tiles_m, cm) * p.tiles_n);
   p.a_mn = transA ? 1 : 0;
   p.b_mn = transB ? 0 : 1;
   p.vec_ok = vec_ok;
   p.a_3d = a_3d;
   const uint32_t b_tx = p.b_mn ? (uint32_t)ceil_div(BN, 64) * (64u * BK * 2u) : (uint32_t)BN * BK * 2u;
   p.stage_tx = (uint32_t)A_BYTES + b_tx;
-  const int g = (clusters < p.units ? clusters : p.units) * cm;
+  int g = ctas < p.num_tiles ? ctas : p.num_tiles;
   void *args[] = {&ma, &mb, &p};
-  if (cm == 1) return cudaLaunchKernel(kfn, dim3(g), dim3(NUM_THREADS), args, SMEM_BYTES, stream);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(g);
-  cfg.blockDim = dim3(NUM_THREADS);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
-  cfg.stream = stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cm;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, kfn, args);
+  return cudaLaunchKernel(kfn, dim3(g), dim3(NUM_THREADS), args, SMEM_BYTES, stream);
 }
 
 unsigned *device_status_word() {

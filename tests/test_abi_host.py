@@ -162,8 +162,9 @@ def test_selftest_bounded_wait_range():
 
 
 def test_gemm_strategy_validation():
-    """The BF16 GEMM's tiles are 256 x tile_n x 64 and its clusters 1, 2 or 4
-    CTAs (0 = chosen); anything else is refused before any CUDA call."""
+    """The BF16 GEMM's tiles are 256 x tile_n x 64, computed by one CTA or a
+    CTA pair (cluster 1 or 2; 0 = chosen); anything else is refused before any
+    CUDA call."""
     L = N.lib()
     p = ctypes.c_void_p
 
@@ -174,7 +175,7 @@ def test_gemm_strategy_validation():
                                 ctypes.byref(st), None)
 
     assert ctypes.sizeof(N.GemmStrategyC) == 6 * 4
-    for c in (3, 5, 8, -1):
+    for c in (3, 4, 8, -1):
         assert call(cluster=c) == N.ERR_STRATEGY
         assert "cluster" in dpia.dpia_last_error_message()
     assert call(grid=-1) == N.ERR_STRATEGY
