@@ -267,7 +267,7 @@ def profile_case(args):
         C = torch.empty(m, m, device=dev)
 
         def fn():
-            dpia.dpia_gemm_bf16(Ab, Bb, C, m, m, m, m, m, m, 0, 0, cluster=args.cluster)
+            dpia.dpia_gemm_bf16(Ab, Bb, C, m, m, m, m, m, m, 0, 0, cluster=args.cluster, tile_m=args.tile_m)
             dpia.dpia_gemm_f32(A, B, C, m, m, m, m, m, m, 0, 0, "fma")
     elif args.profile == "batched":  # the first 512 dots and 16 GEMVs of the batched workload
         import math
@@ -697,18 +697,26 @@ def gemm_workload(args, device, dist):
                             "bound": "alu", "peak_TFLOP_s": round(fma_peak, 1),
                             "peak_source": f"{sms} SMs x 128 FP32 FMA lanes x 2 flops x {sm_mhz:.0f} MHz (median "
                                            "clock under load)", "frac": round(fl / f32 / 1e9 / fma_peak, 4)}
-    # each launch alone (L2 flushed before it) on one CTA per tile (cta_group::1) and on CTA pairs (cta_group::2)
+    # each launch alone (L2 flushed before it): one CTA per 256-row tile (cta_group::1), CTA pairs
+    # (cta_group::2) on 256-row and 512-row tiles, and cuBLAS (torch.matmul, bf16 out) on the same shape
     flush = L2Flush(device)
     by_cluster = {}
-    for cl in (1, 2):
-        calls = {"bf16_fwd": lambda cl=cl: dpia.dpia_gemm_bf16(Ab, Bb, C, n, n, n, n, n, n, 0, 0, cluster=cl),
-                 "bf16_bwd_dA": lambda cl=cl: dpia.dpia_gemm_bf16(dCb, Bb, gA, n, n, n, n, n, n, 0, 1, cluster=cl),
-                 "bf16_bwd_dB": lambda cl=cl: dpia.dpia_gemm_bf16(Ab, dCb, gB, n, n, n, n, n, n, 1, 0, cluster=cl)}
+    Cb = torch.empty(n, n, device=device, dtype=torch.bfloat16)
+    for label, cl, tm in (("1", 1, 0), ("2", 2, 256), ("2x512", 2, 512)):
+        calls = {"bf16_fwd": lambda cl=cl, tm=tm: dpia.dpia_gemm_bf16(Ab, Bb, C, n, n, n, n, n, n, 0, 0,
+                                                                      cluster=cl, tile_m=tm),
+                 "bf16_bwd_dA": lambda cl=cl, tm=tm: dpia.dpia_gemm_bf16(dCb, Bb, gA, n, n, n, n, n, n, 0, 1,
+                                                                         cluster=cl, tile_m=tm),
+                 "bf16_bwd_dB": lambda cl=cl, tm=tm: dpia.dpia_gemm_bf16(Ab, dCb, gB, n, n, n, n, n, n, 1, 0,
+                                                                         cluster=cl, tile_m=tm)}
         alone = standalone_us(calls, {}, flush=flush, reps=10)
-        by_cluster[str(cl)] = {k: {"median_us": v["median_us"], "TFLOP_s": round(fl / v["median_us"] / 1e6, 1),
+        by_cluster[label] = {k: {"median_us": v["median_us"], "TFLOP_s": round(fl / v["median_us"] / 1e6, 1),
                                    "frac": round(fl / v["median_us"] / 1e6 / bf16_peak, 4)}
                                for k, v in alone.items()}
     kern["alone_by_cluster"] = by_cluster
+    cub = standalone_us({"bf16_fwd": lambda: torch.matmul(Ab, Bb, out=Cb)}, {}, flush=flush, reps=10)["bf16_fwd"]
+    kern["cublas_same_shape"] = {"what": "torch.matmul(A, B) in bf16 (bf16 output), each launch alone, L2 flushed",
+                                 "median_us": cub["median_us"], "TFLOP_s": round(fl / cub["median_us"] / 1e6, 1)}
     dominant = max(per, key=per.get)  # the launch with the largest time share
     achieved = fl / per[dominant] / 1e9
     world = dist.get_world_size() if dist else 1
@@ -1225,7 +1233,9 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=1 << 25, help="elements (or rows x cols) of the --profile case")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2],
-                    help="CTAs per 256-row tile of the BF16 GEMM in the gemm --profile case (0 = chosen)")
+                    help="CTAs per tile of the BF16 GEMM in the gemm --profile case (0 = one)")
+    ap.add_argument("--tile-m", type=int, default=0, choices=[0, 256, 512],
+                    help="rows per tile of the BF16 GEMM in the gemm --profile case (512: CTA pairs only)")
     args = ap.parse_args(argv)
     if args.profile:
         return profile_case(args)

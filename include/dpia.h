@@ -239,15 +239,16 @@ enum { DPIA_CONTRACT_OFF = 0, DPIA_CONTRACT_FMA = 1 };
  * contraction declared explicitly -- the paper's num is abstract, so the
  * rounding of a step is part of the strategy). tile_m/n/k: 0 for the
  * implemented tiles or exactly those values -- FP32: 128 x 128 x 16; BF16:
- * 256 x tile_n x 64 with tile_n in {128, 160, 192, 224, 256} (0 = the width
- * whose tiles fill the fewest waves). grid: CTAs of the persistent BF16
- * kernel (0 = one per SM, or as many CTA pairs as fit at once).
- * cluster (BF16 only): CTAs per 256-row tile. 1: one CTA (one SM) computes
- * the tile with two M=128 MMAs (tcgen05 cta_group::1). 2: a cluster of two
- * CTAs on two SMs, each staging 128 rows of A and half of B's columns, with
- * one M=256 MMA across the pair (cta_group::2). 0 = the pair when M > 128.
- * The value of C does not depend on it. The FP32 fold ignores grid and
- * cluster.
+ * tile_m x tile_n x 64 with tile_m 256 (512 on CTA pairs) and tile_n in
+ * {128, 160, 192, 224, 256} (0 = the width whose tiles fill the fewest
+ * waves). grid: CTAs of the persistent BF16 kernel (0 = one per SM, or as
+ * many CTA pairs as fit at once).
+ * cluster (BF16 only): 1 (or 0): one CTA (one SM) per 256-row tile, two M=128
+ * MMAs per k step (tcgen05 cta_group::1). 2: a cluster of two CTAs on two
+ * SMs per tile, each staging 128 rows of every 256-row block of A and half
+ * of B's columns, one M=256 MMA per block across the pair (cta_group::2);
+ * tile_m 512 gives each SM two blocks that share its half of B. The value of
+ * C does not depend on it. The FP32 fold ignores grid and cluster.
  */
 typedef struct {
   int32_t contract;

@@ -12,8 +12,8 @@ cudaError_t launch_gemm_f32(const float *A, const float *B, float *C, int64_t M,
                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int fma, int vec_ok,
                             cudaStream_t stream);
 cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,
-                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_n,
-                             int cluster, int vec_ok, cudaStream_t stream);
+                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_m,
+                             int tile_n, int cluster, int vec_ok, cudaStream_t stream);
 cudaError_t poll_device_status(unsigned *out);
 cudaError_t launch_bounded_wait_probe(uint64_t timeout_ns, cudaStream_t stream);
 int resident_blocks(const void *kernel, int threads);
@@ -142,9 +142,11 @@ dpia_status dpia_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64
     set_last_error("%s: strategy is NULL", fn);
     return DPIA_ERR_NULL;
   }
-  if ((st->tile_m && st->tile_m != 256) || (st->tile_k && st->tile_k != 64) ||
+  if ((st->tile_m && st->tile_m != 256 && !(st->tile_m == 512 && st->cluster == 2)) ||
+      (st->tile_k && st->tile_k != 64) ||
       (st->tile_n && (st->tile_n < 128 || st->tile_n > 256 || st->tile_n % 32 != 0))) {
-    set_last_error("%s: tiles are 256 x tile_n x 64 with tile_n in {128, 160, ..., 256} (0 = chosen per shape)", fn);
+    set_last_error("%s: tiles are tile_m x tile_n x 64 with tile_m 256 (512 on a CTA pair, cluster = 2) and "
+                   "tile_n in {128, 160, ..., 256} (0 = chosen per shape)", fn);
     return DPIA_ERR_UNSUPPORTED;
   }
   if (st->grid < 0) {
@@ -170,8 +172,8 @@ dpia_status dpia_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64
   }
   const int vec_ok = aligned(C, 16) && ldc % 4 == 0;
   return cuda_status(
-      launch_gemm_bf16(A, B, C, M, N, K, lda, ldb, ldc, transA, transB, st->grid, st->tile_n, st->cluster, vec_ok,
-                       s),
+      launch_gemm_bf16(A, B, C, M, N, K, lda, ldb, ldc, transA, transB, st->grid, st->tile_m, st->tile_n,
+                       st->cluster, vec_ok, s),
       fn);
 }
 

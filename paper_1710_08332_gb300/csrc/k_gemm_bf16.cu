@@ -337,36 +337,43 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 }
 
 // ---------------------------------------------------------------- CTA pairs
-// The same product with the tile's two 128-row halves on two SMs (a cluster
-// of two CTAs, tcgen05 cta_group::2): each CTA stages its own 128 rows of the
-// A slice and its half of the B slice's columns; one M=256 MMA issued by the
-// even CTA reads both CTAs' shared memory and writes rows 0..127 of the
-// accumulator to its own tensor memory and rows 128..255 to its peer's. Each
-// SM then reads every operand byte from its shared memory once per k step
-// (the one-SM tile reads its B slice twice, once per 128-row half), and each
-// SM's accumulator is 128 x BN, so two of them fit in tensor memory and the
-// epilogue of one tile overlaps the MMAs of the next.
-//   warp 0    -- TMA producer (both CTAs): its A rows and B columns of a
-//                k-slice into a 6-stage ring of 32 KiB stages; the copies of
-//                both CTAs complete on the even CTA's full barrier;
-//   warp 1    -- allocates 512 TMEM columns in both CTAs (collectively); in
-//                the even CTA one thread issues the MMAs (M=256, N=BN, K=16)
-//                and commits stage releases and finished accumulators to the
-//                barriers of both CTAs;
-//   warps 2-5 -- epilogue (both CTAs): its 128 rows of the accumulator, then
-//                a release arrival on the even CTA's tempty barrier.
-constexpr int P_STAGES = 6;
-constexpr int P_A_BYTES = 128 * BK * 2;               // 16 KiB: this CTA's 128 rows
-constexpr int P_B_BYTES = 128 * BK * 2;               // 16 KiB: this CTA's half of the widest B slice
-constexpr int P_STAGE_BYTES = P_A_BYTES + P_B_BYTES;  // 32 KiB
-constexpr int P_EPI_WARPS = 4;
-constexpr int P_THREADS = 64 + 32 * P_EPI_WARPS;
-constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + 1024 + 256;
+// The same product with each 256-row block of the tile on two SMs (a cluster
+// of two CTAs, tcgen05 cta_group::2): each CTA stages 128 rows of the block's
+// A slice and half of the B slice's columns; one M=256 MMA issued by the even
+// CTA reads both CTAs' shared memory and writes rows 0..127 of the block's
+// accumulator to its own tensor memory and rows 128..255 to its peer's. A
+// tile has MH such blocks (256 * MH rows) that share the B slice:
+//   MH = 1: each SM's accumulator is 128 x BN, so two fit in tensor memory
+//           and the epilogue of one tile overlaps the MMAs of the next; six
+//           32 KiB stages;
+//   MH = 2: each SM holds two 128 x BN accumulators (one tile, as in the
+//           one-SM kernel) but stages only half of each B slice: 23% fewer
+//           operand bytes per flop than the one-SM tile; four 48 KiB stages.
+//   warp 0 -- TMA producer (both CTAs): its A rows and B columns of a
+//             k-slice; the copies of both CTAs complete on the even CTA's
+//             full barrier;
+//   warp 1 -- allocates 512 TMEM columns in both CTAs (collectively); in the
+//             even CTA one thread issues the MMAs (M=256, N=BN, K=16) and
+//             commits stage releases and finished accumulators to the
+//             barriers of both CTAs;
+//   warps 2.. -- epilogue (both CTAs, 4 * MH warps): its rows of the
+//             accumulators, then a release arrival on the even CTA's tempty.
+template <int MH>
+struct Pair {
+  static constexpr int A_BYTES = MH * 128 * BK * 2;  // this CTA's 128 rows of each 256-row block
+  static constexpr int B_BYTES = 128 * BK * 2;       // this CTA's half of the widest B slice
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGES = MH == 1 ? 6 : 4;
+  static constexpr int SLOTS = MH == 1 ? 2 : 1;  // accumulator sets in tensor memory
+  static constexpr int EPI_WARPS = 4 * MH;
+  static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+};
 
 struct PairParams {
   float *C;
   int64_t M, N, K, ldc;
-  int BN, tiles_n, k_blocks, units;  // units: 256 x BN tiles
+  int BN, tiles_n, k_blocks, units;  // units: (256 * MH) x BN tiles
   int a_mn, b_mn, vec_ok;
   int a_3d;           // MN-major A loaded as one 3-D box {64 m, 64 k, 2 m-blocks}
   uint32_t stage_tx;  // bytes both CTAs' copies of one stage deliver to the even CTA's barrier
@@ -442,15 +449,18 @@ __device__ __forceinline__ void umma2_commit(uint64_t *bar) {
                : "memory");
 }
 
-__global__ void __launch_bounds__(P_THREADS, 1)
+template <int MH>
+__global__ void __launch_bounds__(Pair<MH>::THREADS, 1)
     gemm_bf16_pair_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b,
                           const PairParams p) {
+  using PC = Pair<MH>;
+  constexpr int STAGES_ = PC::STAGES, SLOTS = PC::SLOTS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + P_STAGES * P_STAGE_BYTES);  // used in the even CTA
-  uint64_t *empty = full + P_STAGES;
-  uint64_t *tfull = empty + P_STAGES;  // [2]: accumulator ready
-  uint64_t *tempty = tfull + 2;        // [2]: accumulator drained by both CTAs (used in the even CTA)
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES_ * PC::STAGE_BYTES);  // used in the even CTA
+  uint64_t *empty = full + STAGES_;
+  uint64_t *tfull = empty + STAGES_;  // [SLOTS]: accumulators ready
+  uint64_t *tempty = tfull + 2;       // [SLOTS]: accumulators drained by both CTAs (used in the even CTA)
   uint64_t *drain = tempty + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -459,13 +469,13 @@ __global__ void __launch_bounds__(P_THREADS, 1)
   const uint32_t rank = cluster_ctarank();  // 0: issues the MMAs; 1: its peer
   const int BN = p.BN, HN = BN / 2;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < P_STAGES; ++s) {
+    for (int s = 0; s < STAGES_; ++s) {
       mbar_init(&full[s], 1);   // the even CTA's expect_tx arrival, plus both CTAs' bytes
       mbar_init(&empty[s], 1);  // the MMA commit
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < SLOTS; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 2 * P_EPI_WARPS);  // one arrival per epilogue warp of both CTAs
+      mbar_init(&tempty[b], 2 * PC::EPI_WARPS);  // one arrival per epilogue warp of both CTAs
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -485,18 +495,18 @@ __global__ void __launch_bounds__(P_THREADS, 1)
   cluster_sync();  // both CTAs' barriers are initialised before any copy or commit reaches them
   const uint32_t tmem_base = *tmem_slot;
   const int cid = (int)cluster_id(), ncl = (int)cluster_count();
+  constexpr int TILE_M = 256 * MH;
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer (both CTAs)
     const uint32_t full0 = map_to_rank(smem_u32(full), 0);
     uint32_t stage = 0, phase = 0;
-    int pending[P_STAGES] = {};
-    uint32_t pend_phase[P_STAGES] = {};
+    int pending[STAGES_] = {};
+    uint32_t pend_phase[STAGES_] = {};
     bool ok = true;
     for (int u = cid; ok && u < p.units; u += ncl) {
       const int tm = u / p.tiles_n, tn = u % p.tiles_n;
-      const int row0 = tm * BM + (int)rank * 128;  // this CTA's rows of op(A)
-      const int col0 = tn * BN + (int)rank * HN;   // this CTA's columns of op(B)
+      const int col0 = tn * BN + (int)rank * HN;  // this CTA's columns of op(B)
       for (int kb = 0; kb < p.k_blocks; ++kb) {
         if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) {
           ok = false;
@@ -505,14 +515,19 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         pending[stage] = 0;
         if (rank == 0) mbar_expect_tx(&full[stage], p.stage_tx);
         const uint32_t fb = full0 + stage * 8u;
-        uint8_t *sa = smem + stage * P_STAGE_BYTES;
-        uint8_t *sb = sa + P_A_BYTES;
-        if (!p.a_mn) {
-          tma2_load_2d(&tma_a, fb, sa, kb * BK, row0);
-        } else if (p.a_3d) {
-          tma2_load_3d(&tma_a, fb, sa, 0, kb * BK, row0 / 64);
-        } else {
-          for (int j = 0; j < 2; ++j) tma2_load_2d(&tma_a, fb, sa + j * MN_LBO, row0 + 64 * j, kb * BK);
+        uint8_t *sa = smem + stage * PC::STAGE_BYTES;
+        uint8_t *sb = sa + PC::A_BYTES;
+#pragma unroll
+        for (int h = 0; h < MH; ++h) {
+          const int row0 = tm * TILE_M + h * 256 + (int)rank * 128;  // this CTA's rows of op(A) in block h
+          uint8_t *sah = sa + h * (128 * BK * 2);
+          if (!p.a_mn) {
+            tma2_load_2d(&tma_a, fb, sah, kb * BK, row0);
+          } else if (p.a_3d) {
+            tma2_load_3d(&tma_a, fb, sah, 0, kb * BK, row0 / 64);
+          } else {
+            for (int j = 0; j < 2; ++j) tma2_load_2d(&tma_a, fb, sah + j * MN_LBO, row0 + 64 * j, kb * BK);
+          }
         }
         if (!p.b_mn) {
           tma2_load_2d(&tma_b, fb, sb, kb * BK, col0);
@@ -521,23 +536,23 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         }
         pending[stage] = 1;
         pend_phase[stage] = phase;
-        if (++stage == P_STAGES) {
+        if (++stage == STAGES_) {
           stage = 0;
           phase ^= 1;
         }
       }
     }
     // each stage's last use released: no commit reaches this CTA's barriers after it exits
-    for (int i = 0; ok && i < P_STAGES; ++i) {
+    for (int i = 0; ok && i < STAGES_; ++i) {
       ok = mbar_wait(&empty[stage], phase ^ 1, abort_flag);
-      if (++stage == P_STAGES) {
+      if (++stage == STAGES_) {
         stage = 0;
         phase ^= 1;
       }
     }
     if (!ok && rank == 0) {
       // drain copies still in flight (both CTAs' bytes complete on these barriers)
-      for (int s = 0; s < P_STAGES; ++s) {
+      for (int s = 0; s < STAGES_; ++s) {
         if (!pending[s]) continue;
         const uint64_t t0 = globaltimer();
         while (!mbar_try_wait(&full[s], pend_phase[s]) && globaltimer() - t0 < kTimeoutNs) {
@@ -551,32 +566,36 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     bool ok = true;
     int iter = 0;
     for (int u = cid; ok && u < p.units; u += ncl, ++iter) {
-      const int acc = iter & 1;
-      const uint32_t use = (uint32_t)iter >> 1;
-      if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, abort_flag)) {
+      const int sl = iter % SLOTS;
+      const uint32_t use = (uint32_t)(iter / SLOTS);
+      if (!mbar_wait(&tempty[sl], (use & 1) ^ 1, abort_flag)) {
         ok = false;
         break;
       }
       fence_after();
-      const uint32_t d = tmem_base + (uint32_t)acc * 256;
       for (int kb = 0; kb < p.k_blocks; ++kb) {
         if (!mbar_wait(&full[stage], phase, abort_flag)) {
           ok = false;
           break;
         }
         fence_after();
-        const uint32_t a0 = smem_u32(smem + stage * P_STAGE_BYTES);
-        const uint32_t b0 = a0 + P_A_BYTES;
+        const uint32_t a0 = smem_u32(smem + stage * PC::STAGE_BYTES);
+        const uint32_t b0 = a0 + PC::A_BYTES;
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k)
-          umma2(d, operand_desc(a0, p.a_mn, 0, k), operand_desc(b0, p.b_mn, 0, k), idesc, (kb | k) != 0);
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint64_t db = operand_desc(b0, p.b_mn, 0, k);
+#pragma unroll
+          for (int h = 0; h < MH; ++h)  // accumulator of block h: columns (sl + h) * 256 ..
+            umma2(tmem_base + (uint32_t)(sl + h) * 256, operand_desc(a0 + h * (128 * BK * 2), p.a_mn, 0, k), db,
+                  idesc, (kb | k) != 0);
+        }
         umma2_commit_both(&empty[stage]);
-        if (++stage == P_STAGES) {
+        if (++stage == STAGES_) {
           stage = 0;
           phase ^= 1;
         }
       }
-      if (ok) umma2_commit_both(&tfull[acc]);
+      if (ok) umma2_commit_both(&tfull[sl]);
     }
     umma2_commit(drain);
     const uint64_t t0 = globaltimer();
@@ -584,18 +603,19 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     }
   } else if (warp >= 2) {
     // ------------------------------------------------------------ epilogue (both CTAs)
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int q = warp & 3;         // TMEM lane quarter this warp may access
+    const int h = (warp - 2) >> 2;  // 256-row block of the tile
     const uint32_t tempty0 = map_to_rank(smem_u32(tempty), 0);
     int iter = 0;
     for (int u = cid; u < p.units; u += ncl, ++iter) {
-      const int acc = iter & 1;
-      const uint32_t use = (uint32_t)iter >> 1;
+      const int sl = iter % SLOTS;
+      const uint32_t use = (uint32_t)(iter / SLOTS);
       const int tm = u / p.tiles_n, tn = u % p.tiles_n;
-      if (!mbar_wait(&tfull[acc], use & 1, abort_flag)) break;
+      if (!mbar_wait(&tfull[sl], use & 1, abort_flag)) break;
       fence_after();
-      const int64_t row = (int64_t)tm * BM + 128 * rank + 32 * q + lane;
+      const int64_t row = (int64_t)tm * TILE_M + 256 * h + 128 * rank + 32 * q + lane;
       float *crow = p.C + row * p.ldc;
-      const uint32_t tbase = tmem_base + (uint32_t)acc * 256 + ((uint32_t)(32 * q) << 16);
+      const uint32_t tbase = tmem_base + (uint32_t)(sl + h) * 256 + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
       for (int c = 0; c < BN; c += 32) {
         uint32_t r[32];
@@ -603,7 +623,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         if (c + 32 >= BN) {  // accumulator read out: the MMAs may refill it
           fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive_cluster(tempty0 + (uint32_t)acc * 8u);
+          if (lane == 0) mbar_arrive_cluster(tempty0 + (uint32_t)sl * 8u);
         }
         if (row < p.M) {
           const int64_t col0 = (int64_t)tn * BN + c;
@@ -688,14 +708,14 @@ bool make_map_mn3d(CUtensorMap *map, const void *base, int64_t K, int64_t M, int
 
 int resident_blocks(const void *kernel, int threads);
 
-// Tile width: the BN in {256, 224, ..., 128} whose 256-row tiles fill the
-// fewest waves of the slots that run at once (CTAs, or CTA pairs), weighted
-// by the tile's cost (proportional to BN).
-int pick_bn(int64_t M, int64_t N, int slots) {
+// Tile width: the BN in {256, 224, ..., 128} whose tiles (tile_m rows) fill
+// the fewest waves of the slots that run at once (CTAs, or CTA pairs),
+// weighted by the tile's cost (proportional to BN).
+int pick_bn(int64_t M, int64_t N, int slots, int tile_m) {
   int best = 256;
   int64_t best_cost = -1;
   for (int bn = 256; bn >= 128; bn -= 32) {
-    const int64_t tiles = ceil_div(M, BM) * ceil_div(N, bn);
+    const int64_t tiles = ceil_div(M, tile_m) * ceil_div(N, bn);
     const int64_t waves = ceil_div(tiles, slots);
     const int64_t cost = waves * bn;
     if (best_cost < 0 || cost < best_cost) {
@@ -706,25 +726,33 @@ int pick_bn(int64_t M, int64_t N, int slots) {
   return best;
 }
 
+template <int MH>
+cudaLaunchConfig_t pair_config(cudaLaunchAttribute *attr, int grid, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(Pair<MH>::THREADS);
+  cfg.dynamicSmemBytes = Pair<MH>::SMEM_BYTES;
+  cfg.stream = stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
 // CTA pairs of the pair kernel that fit on the GPU at once (0 if none), per device.
+template <int MH>
 int pair_slots() {
   static int cached[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   if (cached[dev] == 0) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * 64);
-    cfg.blockDim = dim3(P_THREADS);
-    cfg.dynamicSmemBytes = P_SMEM_BYTES;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    const cudaLaunchConfig_t cfg = pair_config<MH>(attr, 2 * 64, nullptr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, reinterpret_cast<const void *>(gemm_bf16_pair_kernel), &cfg) !=
+    if (cudaOccupancyMaxActiveClusters(&n, reinterpret_cast<const void *>(gemm_bf16_pair_kernel<MH>), &cfg) !=
         cudaSuccess) {
       cudaGetLastError();
       n = 0;
@@ -740,18 +768,22 @@ cudaError_t set_smem_attrs() {
   cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(gemm_bf16_tcgen05_kernel),
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(reinterpret_cast<const void *>(gemm_bf16_pair_kernel),
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+    e = cudaFuncSetAttribute(reinterpret_cast<const void *>(gemm_bf16_pair_kernel<1>),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, Pair<1>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(reinterpret_cast<const void *>(gemm_bf16_pair_kernel<2>),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, Pair<2>::SMEM_BYTES);
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-// The pair kernel: 256 x BN tiles, each on a cluster of two CTAs.
+// The pair kernel: (256 * MH) x BN tiles, each on a cluster of two CTAs.
+template <int MH>
 cudaError_t launch_pair(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,
                         int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_n,
                         int vec_ok, int fit, cudaStream_t stream) {
   const int clusters = grid > 0 ? (grid / 2 > 0 ? grid / 2 : 1) : fit;
-  const int BN = tile_n > 0 ? tile_n : pick_bn(M, N, clusters);
+  const int BN = tile_n > 0 ? tile_n : pick_bn(M, N, clusters, 256 * MH);
   const int HN = BN / 2;
   alignas(64) CUtensorMap ma, mb;
   const int a_3d = transA && M % 64 == 0;
@@ -768,50 +800,41 @@ cudaError_t launch_pair(const uint16_t *A, const uint16_t *B, float *C, int64_t 
   p.BN = BN;
   p.tiles_n = (int)ceil_div(N, BN);
   p.k_blocks = (int)ceil_div(K, BK);
-  p.units = (int)(ceil_div(M, BM) * p.tiles_n);
+  p.units = (int)(ceil_div(M, 256 * MH) * p.tiles_n);
   p.a_mn = transA ? 1 : 0;
   p.b_mn = transB ? 0 : 1;
   p.vec_ok = vec_ok;
   p.a_3d = a_3d;
   const uint32_t b_half = p.b_mn ? (uint32_t)ceil_div(HN, 64) * (64u * BK * 2u) : (uint32_t)HN * BK * 2u;
-  p.stage_tx = 2u * ((uint32_t)P_A_BYTES + b_half);
+  p.stage_tx = 2u * ((uint32_t)Pair<MH>::A_BYTES + b_half);
   const int g = 2 * (clusters < p.units ? clusters : p.units);
   void *args[] = {&ma, &mb, &p};
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(g);
-  cfg.blockDim = dim3(P_THREADS);
-  cfg.dynamicSmemBytes = P_SMEM_BYTES;
-  cfg.stream = stream;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(gemm_bf16_pair_kernel), args);
+  const cudaLaunchConfig_t cfg = pair_config<MH>(attr, g, stream);
+  return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(gemm_bf16_pair_kernel<MH>), args);
 }
 
 // op(A) is M x K: A stored M x K (transA = 0, K-major) or K x M (transA = 1,
 // MN-major). op(B) is K x N: B stored K x N (transB = 0, MN-major) or N x K
 // (transB = 1, K-major). tile_n = 0 picks BN per shape. cluster: 1 = one CTA
-// per 256-row tile (cta_group::1), 2 = a CTA pair per tile (cta_group::2),
-// 0 = the pair when the tile has rows for both CTAs (M > 128) and pairs fit.
-// grid > 0: CTAs of the persistent grid (a pair kernel takes whole pairs).
+// per 256-row tile (cta_group::1), 2 = a CTA pair per tile of tile_m = 256
+// or 512 rows (cta_group::2), 0 = one CTA per tile. grid > 0: CTAs of the
+// persistent grid (a pair kernel takes whole pairs).
 cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,
-                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_n,
-                             int cluster, int vec_ok, cudaStream_t stream) {
+                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_m,
+                             int tile_n, int cluster, int vec_ok, cudaStream_t stream) {
   cudaError_t e = set_smem_attrs();
   if (e != cudaSuccess) return e;
-  if (cluster != 1) {
-    const int fit = pair_slots();
-    if (cluster == 2 && fit == 0) return cudaErrorInvalidConfiguration;
-    if (fit > 0 && (cluster == 2 || M > 128))
-      return launch_pair(A, B, C, M, N, K, lda, ldb, ldc, transA, transB, grid, tile_n, vec_ok, fit, stream);
+  if (cluster == 2) {
+    const int fit = tile_m == 512 ? pair_slots<2>() : pair_slots<1>();
+    if (fit == 0) return cudaErrorInvalidConfiguration;
+    return tile_m == 512
+               ? launch_pair<2>(A, B, C, M, N, K, lda, ldb, ldc, transA, transB, grid, tile_n, vec_ok, fit, stream)
+               : launch_pair<1>(A, B, C, M, N, K, lda, ldb, ldc, transA, transB, grid, tile_n, vec_ok, fit, stream);
   }
   const void *kfn = reinterpret_cast<const void *>(gemm_bf16_tcgen05_kernel);
   const int ctas = grid > 0 ? grid : sm_count();
-  const int BN = tile_n > 0 ? tile_n : pick_bn(M, N, ctas);
+  const int BN = tile_n > 0 ? tile_n : pick_bn(M, N, ctas, BM);
   alignas(64) CUtensorMap ma, mb;
   const int a_3d = transA && M % 64 == 0;
   bool ok = transA ? (a_3d ? make_map_mn3d(&ma, A, K, M, lda, BM / 64) : make_map(&ma, A, K, M, lda, 64, BK))

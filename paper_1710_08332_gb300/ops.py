@@ -105,8 +105,9 @@ def dpia_gemv_bwd_f32(A, M, N_, lda, x, dy, dx, dA, ldda, row_split, ws, stream=
                                       _stream(stream)), "dpia_gemv_bwd_f32")
 
 
-def _gst(contract="fma", grid=0, tile_n=0, cluster=0):
-    return ctypes.byref(N.GemmStrategyC(1 if contract == "fma" else 0, 0, int(tile_n), 0, int(grid), int(cluster)))
+def _gst(contract="fma", grid=0, tile_n=0, cluster=0, tile_m=0):
+    return ctypes.byref(N.GemmStrategyC(1 if contract == "fma" else 0, int(tile_m), int(tile_n), 0, int(grid),
+                                        int(cluster)))
 
 
 def dpia_gemm_f32(A, B, C, M, N_, K, lda, ldb, ldc, transA=0, transB=0, contract="fma", stream=None):
@@ -117,11 +118,11 @@ def dpia_gemm_f32(A, B, C, M, N_, K, lda, ldb, ldc, transA=0, transB=0, contract
 
 
 def dpia_gemm_bf16(A, B, C, M, N_, K, lda, ldb, ldc, transA=0, transB=0, grid=0, tile_n=0, cluster=0,
-                   stream=None):
+                   tile_m=0, stream=None):
     """A, B: torch.bfloat16 (or int16/uint16 bit patterns) device tensors; C float32."""
     _need_cuda(A, B, C)
     N.check(N.lib().dpia_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), int(M), int(N_), int(K), int(lda), int(ldb),
-                                   int(ldc), int(transA), int(transB), _gst("fma", grid, tile_n, cluster),
+                                   int(ldc), int(transA), int(transB), _gst("fma", grid, tile_n, cluster, tile_m),
                                    _stream(stream)), "dpia_gemm_bf16")
 
 

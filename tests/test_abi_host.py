@@ -162,9 +162,9 @@ def test_selftest_bounded_wait_range():
 
 
 def test_gemm_strategy_validation():
-    """The BF16 GEMM's tiles are 256 x tile_n x 64, computed by one CTA or a
-    CTA pair (cluster 1 or 2; 0 = chosen); anything else is refused before any
-    CUDA call."""
+    """The BF16 GEMM's tiles are 256 (or, on CTA pairs, 512) x tile_n x 64,
+    computed by one CTA or a CTA pair (cluster 1 or 2; 0 = one CTA); anything
+    else is refused before any CUDA call."""
     L = N.lib()
     p = ctypes.c_void_p
 
@@ -182,5 +182,7 @@ def test_gemm_strategy_validation():
     assert call(tile_n=96) == N.ERR_UNSUPPORTED
     assert call(tile_n=240) == N.ERR_UNSUPPORTED
     assert call(tile_m=128) == N.ERR_UNSUPPORTED
+    assert call(tile_m=512, cluster=1) == N.ERR_UNSUPPORTED  # 512-row tiles only on CTA pairs
+    assert call(tile_m=512) == N.ERR_UNSUPPORTED
     assert L.dpia_gemm_bf16(p(0x10000), p(0x20000), p(0x30000), 512, 512, 512, 512, 512, 512, 0, 0, None,
                             None) == N.ERR_NULL

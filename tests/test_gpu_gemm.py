@@ -122,16 +122,18 @@ def test_gemm_bf16_tolerance(cuda_device, tA, tB, M, N, K, tile_n):
     assert dpia.dpia_poll_device_status() == 0
 
 
-@pytest.mark.parametrize("cluster", [1, 2])
+@pytest.mark.parametrize("cluster,tile_m", [(1, 0), (2, 256), (2, 512)])
 @pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0), (1, 1)])
 @pytest.mark.parametrize("M,N,K,tile_n", [(768, 448, 192, 224), (520, 300, 136, 0), (1024, 256, 64, 128),
-                                          (100, 520, 320, 160), (384, 200, 72, 256)])
-def test_gemm_bf16_cta_pairs(cuda_device, tA, tB, M, N, K, tile_n, cluster):
+                                          (100, 520, 320, 160), (384, 200, 72, 256), (1280, 96, 128, 128)])
+def test_gemm_bf16_cta_pairs(cuda_device, tA, tB, M, N, K, tile_n, cluster, tile_m):
     """One CTA per 256-row tile (cluster 1) or a CTA pair (cluster 2: each CTA
-    stages 128 rows of A and half of B's columns, one M=256 MMA across both):
-    ragged M, N and K, a tile whose second half lies past M (M = 100, 384),
-    odd halves of B (tile_n 160: 80 columns per CTA), and a small persistent
-    grid (several tiles per pair, both accumulators of each CTA in turn)."""
+    stages 128 rows of every 256-row block of A and half of B's columns, one
+    M=256 MMA per block across both; tile_m 512 = two blocks per tile):
+    ragged M, N and K, tiles whose later blocks lie past M (M = 100, 384, 520,
+    768 with 512-row tiles), odd halves of B (tile_n 160: 80 columns per CTA),
+    N below one tile, and a small persistent grid (several tiles per pair, both
+    accumulator sets of each CTA in turn)."""
     g = torch.Generator().manual_seed(11 * M + 5 * N + K + tA + 2 * tB)
     opA = torch.randn(M, K, generator=g).numpy()
     opB = torch.randn(K, N, generator=g).numpy()
@@ -145,26 +147,28 @@ def test_gemm_bf16_cta_pairs(cuda_device, tA, tB, M, N, K, tile_n, cluster):
     Ab, Bb = dpia.to_bf16(Ad), dpia.to_bf16(Bd)
     for grid in (0, 2):
         C = torch.full((M, N), float("nan"), device="cuda")
-        dpia.dpia_gemm_bf16(Ab, Bb, C, M, N, K, lda, ldb, N, tA, tB, grid=grid, tile_n=tile_n, cluster=cluster)
+        dpia.dpia_gemm_bf16(Ab, Bb, C, M, N, K, lda, ldb, N, tA, tB, grid=grid, tile_m=tile_m, tile_n=tile_n,
+                            cluster=cluster)
         torch.cuda.synchronize()
         _bf16_check(host(C).astype(np.float64), opA, opB,
-                    f"bf16 cluster={cluster} grid={grid} tA={tA} tB={tB} {M}x{N}x{K}")
+                    f"bf16 cluster={cluster} tile_m={tile_m} grid={grid} tA={tA} tB={tB} {M}x{N}x{K}")
         assert dpia.dpia_poll_device_status() == 0
 
 
 @pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0)])
 def test_gemm_bf16_pair_matches_single(cuda_device, gemm_inputs, tA, tB):
     """At 4096^3 (the three layouts of the forward and backward products) the
-    CTA pair and the single CTA compute every C_ij from the same bf16 products
-    over the same k-slices; both stay within the f32 accumulation bound of the
-    FP64 product (checked on sampled rows) and agree to a few f32 ulps."""
+    single CTA and the CTA pair (256- and 512-row tiles) compute every C_ij
+    from the same bf16 products over the same k-slices; each stays within the
+    f32 accumulation bound of the FP64 product (checked on sampled rows) and
+    they agree to a few f32 ulps."""
     A, B, _ = gemm_inputs
     n = W.GEMM_MNK
     Ab, Bb = dpia.to_bf16(A), dpia.to_bf16(B)
     out = []
-    for cluster in (1, 2):
+    for cluster, tile_m in ((1, 0), (2, 256), (2, 512)):
         C = torch.empty(n, n, device="cuda")
-        dpia.dpia_gemm_bf16(Ab, Bb, C, n, n, n, n, n, n, tA, tB, tile_n=224, cluster=cluster)
+        dpia.dpia_gemm_bf16(Ab, Bb, C, n, n, n, n, n, n, tA, tB, tile_m=tile_m, tile_n=224, cluster=cluster)
         out.append(C)
     torch.cuda.synchronize()
     assert dpia.dpia_poll_device_status() == 0
@@ -174,9 +178,10 @@ def test_gemm_bf16_pair_matches_single(cuda_device, gemm_inputs, tA, tB):
     rows = np.arange(0, n, 211)[:20]
     for C in out:
         _bf16_check(host(C)[rows].astype(np.float64), opA[rows], opB, f"4096^3 tA={tA} tB={tB}")
-    d = (out[0] - out[1]).abs().max().item()
     scale = out[0].abs().max().item()
-    assert d <= 1e-5 * scale, (d, scale)
+    for C in out[1:]:
+        d = (out[0] - C).abs().max().item()
+        assert d <= 1e-5 * scale, (d, scale)
 
 
 def test_gemm_bf16_4096(cuda_device, gemm_inputs):
