@@ -29,6 +29,15 @@
 // shared-memory descriptors select the canonical 128-byte-swizzle layout of
 // either major-ness, so the transposes of the backward pass need no copies.
 //
+// A second kernel runs each tile on a CTA pair (cta_group::2, below). At
+// 4096^3 it measured slower with 256-row tiles (1.06-1.17 PFLOP/s against
+// 1.37-1.42 here) and level with 512-row tiles (1.37), although it stages
+// 23% fewer operand bytes per flop; so is B shared by TMA multicast within
+// clusters of 2 or 4 one-SM CTAs (3% and 25% slower, not kept). Neither the
+// tensor pipe (64% active), L2 (51%), shared-memory banks (26% reads) nor
+// the TMA ingest (37%) is saturated here: the refill round trip of a stage
+// bounds the pipe. The one-SM kernel is the default.
+//
 // Every mbarrier wait is bounded by the global timer. A wait that runs out
 // sets the CTA's abort flag and the library's device status word
 // (dpia_poll_device_status reports it), the CTA drains what it has in flight,
