@@ -44,60 +44,61 @@ __device__ __forceinline__ float b_at(const GemmArgs &g, int64_t k, int64_t n) {
   return TB ? g.B[n * g.ldb + k] : g.B[k * g.ldb + n];
 }
 
-// A k-slice of 16 of a 128-wide operand panel moves global -> registers ->
-// shared [k][128] in one of two thread mappings (8 values per thread), each
-// chosen so that a warp's shared stores touch every bank once:
-//   k-major source (row r holds k contiguous): thread -> r = tid % 128,
-//     k = (tid / 128) * 8 .. +7; the warp stores 32 consecutive columns;
-//   mn-major source (row k holds r contiguous): thread -> k = tid / 16,
-//     r = (tid % 16) * 4 .. +3 and 64 + (tid % 16) * 4 .. +3; a quarter-warp
-//     stores 128 contiguous bytes.
-// at(r, k) is the bounds-checked element (0 outside); vec selects 128-bit
-// loads from base (interior, aligned panels).
-template <bool MN, typename At>
-__device__ __forceinline__ void load_panel(const float *base, int64_t ld, bool vec, At at, float (&v)[8]) {
-  const int tid = threadIdx.x;
-  if (vec) {
-    const float *p = !MN ? base + (int64_t)(tid % 128) * ld + (tid / 128) * 8 : base + (int64_t)(tid / 16) * ld + (tid % 16) * 4;
-    const float4 u = __ldg(reinterpret_cast<const float4 *>(p));
-    const float4 w = __ldg(reinterpret_cast<const float4 *>(!MN ? p + 4 : p + 64));
-    v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w; v[4] = w.x; v[5] = w.y; v[6] = w.z; v[7] = w.w;
-  } else {
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      v[j] = !MN ? at(tid % 128, (tid / 128) * 8 + j) : at((j < 4 ? 0 : 64) + (tid % 16) * 4 + (j & 3), tid / 16);
-  }
-}
-
-template <bool MN>
-__device__ __forceinline__ void store_panel(float (*S)[128], const float (&v)[8]) {
-  const int tid = threadIdx.x;
-  if (!MN) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) S[(tid / 128) * 8 + j][tid % 128] = v[j];
-  } else {
-    *reinterpret_cast<float4 *>(&S[tid / 16][(tid % 16) * 4]) = make_float4(v[0], v[1], v[2], v[3]);
-    *reinterpret_cast<float4 *>(&S[tid / 16][64 + (tid % 16) * 4]) = make_float4(v[4], v[5], v[6], v[7]);
-  }
-}
-
-// The (m0, k0) slice of op(A) and the (k0, n0) slice of op(B) into registers.
+// Load the (m0, k0) A slice and (k0, n0) B slice into registers: 8 + 8 floats
+// per thread; `vec` selects 128-bit loads (interior, aligned tiles).
 template <bool TA, bool TB>
 __device__ __forceinline__ void load_slices(const GemmArgs &g, int64_t m0, int64_t n0, int64_t k0,
                                             bool vec, float (&ra)[8], float (&rb)[8]) {
-  // op(A) is K-major unless TA; op(B) is N-major (mn) unless TB
-  load_panel<TA>(TA ? g.A + k0 * g.lda + m0 : g.A + m0 * g.lda + k0, g.lda, vec,
-                 [&](int r, int k) { return a_at<TA>(g, m0 + r, k0 + k); }, ra);
-  load_panel<!TB>(TB ? g.B + n0 * g.ldb + k0 : g.B + k0 * g.ldb + n0, g.ldb, vec,
-                  [&](int r, int k) { return b_at<TB>(g, k0 + k, n0 + r); }, rb);
+  const int tid = threadIdx.x;
+  if (vec) {
+    if (!TA) {  // A[m][k]: thread -> row m = tid/2, k = (tid%2)*8 .. +7
+      const float *p = g.A + (m0 + tid / 2) * g.lda + k0 + (tid % 2) * 8;
+      float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p + 4));
+      ra[0] = u.x; ra[1] = u.y; ra[2] = u.z; ra[3] = u.w; ra[4] = v.x; ra[5] = v.y; ra[6] = v.z; ra[7] = v.w;
+    } else {  // A[k][m]: thread -> k = tid/16, m = (tid%16)*8 .. +7
+      const float *p = g.A + (k0 + tid / 16) * g.lda + m0 + (tid % 16) * 8;
+      float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p + 4));
+      ra[0] = u.x; ra[1] = u.y; ra[2] = u.z; ra[3] = u.w; ra[4] = v.x; ra[5] = v.y; ra[6] = v.z; ra[7] = v.w;
+    }
+    if (!TB) {  // B[k][n]: thread -> k = tid/16, n = (tid%16)*8 .. +7
+      const float *p = g.B + (k0 + tid / 16) * g.ldb + n0 + (tid % 16) * 8;
+      float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p + 4));
+      rb[0] = u.x; rb[1] = u.y; rb[2] = u.z; rb[3] = u.w; rb[4] = v.x; rb[5] = v.y; rb[6] = v.z; rb[7] = v.w;
+    } else {  // B[n][k]: thread -> n = tid/2, k = (tid%2)*8 .. +7
+      const float *p = g.B + (n0 + tid / 2) * g.ldb + k0 + (tid % 2) * 8;
+      float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p + 4));
+      rb[0] = u.x; rb[1] = u.y; rb[2] = u.z; rb[3] = u.w; rb[4] = v.x; rb[5] = v.y; rb[6] = v.z; rb[7] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (!TA) ra[j] = a_at<TA>(g, m0 + tid / 2, k0 + (tid % 2) * 8 + j);
+      else ra[j] = a_at<TA>(g, m0 + (tid % 16) * 8 + j, k0 + tid / 16);
+      if (!TB) rb[j] = b_at<TB>(g, k0 + tid / 16, n0 + (tid % 16) * 8 + j);
+      else rb[j] = b_at<TB>(g, k0 + (tid % 2) * 8 + j, n0 + tid / 2);
+    }
+  }
 }
 
 // Registers -> shared slices As[k][m], Bs[k][n].
 template <bool TA, bool TB>
 __device__ __forceinline__ void store_slices(float (*As)[BM], float (*Bs)[BN], const float (&ra)[8],
                                              const float (&rb)[8]) {
-  store_panel<TA>(As, ra);
-  store_panel<!TB>(Bs, rb);
+  const int tid = threadIdx.x;
+  if (!TA) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) As[(tid % 2) * 8 + j][tid / 2] = ra[j];
+  } else {
+    *reinterpret_cast<float4 *>(&As[tid / 16][(tid % 16) * 8]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+    *reinterpret_cast<float4 *>(&As[tid / 16][(tid % 16) * 8 + 4]) = make_float4(ra[4], ra[5], ra[6], ra[7]);
+  }
+  if (!TB) {
+    *reinterpret_cast<float4 *>(&Bs[tid / 16][(tid % 16) * 8]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    *reinterpret_cast<float4 *>(&Bs[tid / 16][(tid % 16) * 8 + 4]) = make_float4(rb[4], rb[5], rb[6], rb[7]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) Bs[(tid % 2) * 8 + j][tid / 2] = rb[j];
+  }
 }
 
 template <bool TA, bool TB, bool FMA>
@@ -189,22 +190,18 @@ __global__ void __launch_bounds__(NT, FMA ? 2 : 1) sgemm_fold_kernel(const GemmA
 
 constexpr int BMH = 64;
 
-// A 64-row slice of op(A), 4 values per thread: k-major source -> m = tid % 64,
-// k = (tid / 64) * 4 .. +3 (a warp stores 32 consecutive columns); mn-major
-// source -> k = tid / 16, m = (tid % 16) * 4 .. +3 (a quarter-warp stores 128
-// contiguous bytes).
 template <bool TA>
 __device__ __forceinline__ void load_a_half(const GemmArgs &g, int64_t m0, int64_t k0, bool vec, float (&ra)[4]) {
   const int tid = threadIdx.x;
   if (vec) {
-    const float *p = !TA ? g.A + (m0 + tid % 64) * g.lda + k0 + (tid / 64) * 4   // row m, 4 k
+    const float *p = !TA ? g.A + (m0 + tid / 4) * g.lda + k0 + (tid % 4) * 4   // row m, 4 k
                          : g.A + (k0 + tid / 16) * g.lda + m0 + (tid % 16) * 4;  // k row, 4 m
     const float4 u = __ldg(reinterpret_cast<const float4 *>(p));
     ra[0] = u.x; ra[1] = u.y; ra[2] = u.z; ra[3] = u.w;
   } else {
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      ra[j] = !TA ? a_at<TA>(g, m0 + tid % 64, k0 + (tid / 64) * 4 + j) : a_at<TA>(g, m0 + (tid % 16) * 4 + j, k0 + tid / 16);
+      ra[j] = !TA ? a_at<TA>(g, m0 + tid / 4, k0 + (tid % 4) * 4 + j) : a_at<TA>(g, m0 + (tid % 16) * 4 + j, k0 + tid / 16);
   }
 }
 
@@ -213,7 +210,7 @@ __device__ __forceinline__ void store_a_half(float (*As)[BMH], const float (&ra)
   const int tid = threadIdx.x;
   if (!TA) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) As[(tid / 64) * 4 + j][tid % 64] = ra[j];
+    for (int j = 0; j < 4; ++j) As[(tid % 4) * 4 + j][tid / 4] = ra[j];
   } else {
     *reinterpret_cast<float4 *>(&As[tid / 16][(tid % 16) * 4]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
   }
@@ -222,17 +219,32 @@ __device__ __forceinline__ void store_a_half(float (*As)[BMH], const float (&ra)
 // B slices as in the full kernel (8 values per thread).
 template <bool TB>
 __device__ __forceinline__ void load_b(const GemmArgs &g, int64_t n0, int64_t k0, bool vec, float (&rb)[8]) {
-  load_panel<!TB>(TB ? g.B + n0 * g.ldb + k0 : g.B + k0 * g.ldb + n0, g.ldb, vec,
-                  [&](int r, int k) { return b_at<TB>(g, k0 + k, n0 + r); }, rb);
+  const int tid = threadIdx.x;
+  if (vec) {
+    const float *p = !TB ? g.B + (k0 + tid / 16) * g.ldb + n0 + (tid % 16) * 8 : g.B + (n0 + tid / 2) * g.ldb + k0 + (tid % 2) * 8;
+    const float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p + 4));
+    rb[0] = u.x; rb[1] = u.y; rb[2] = u.z; rb[3] = u.w; rb[4] = v.x; rb[5] = v.y; rb[6] = v.z; rb[7] = v.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      rb[j] = !TB ? b_at<TB>(g, k0 + tid / 16, n0 + (tid % 16) * 8 + j) : b_at<TB>(g, k0 + (tid % 2) * 8 + j, n0 + tid / 2);
+  }
 }
 
 template <bool TB>
 __device__ __forceinline__ void store_b(float (*Bs)[BN], const float (&rb)[8]) {
-  store_panel<!TB>(Bs, rb);
+  const int tid = threadIdx.x;
+  if (!TB) {
+    *reinterpret_cast<float4 *>(&Bs[tid / 16][(tid % 16) * 8]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    *reinterpret_cast<float4 *>(&Bs[tid / 16][(tid % 16) * 8 + 4]) = make_float4(rb[4], rb[5], rb[6], rb[7]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) Bs[(tid % 2) * 8 + j][tid / 2] = rb[j];
+  }
 }
 
 template <bool TA, bool TB, bool FMA>
-__global__ void __launch_bounds__(NT, 2) sgemm_fold_half_kernel(const GemmArgs g, int vec_ok) {
+__global__ void __launch_bounds__(NT) sgemm_fold_half_kernel(const GemmArgs g, int vec_ok) {
   __shared__ __align__(16) float As[2][BK][BMH];
   __shared__ __align__(16) float Bs[2][BK][BN];
   const int64_t m0 = (int64_t)blockIdx.y * BMH, n0 = (int64_t)blockIdx.x * BN;
