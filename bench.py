@@ -717,6 +717,15 @@ def gemm_workload(args, device, dist):
     cub = standalone_us({"bf16_fwd": lambda: torch.matmul(Ab, Bb, out=Cb)}, {}, flush=flush, reps=10)["bf16_fwd"]
     kern["cublas_same_shape"] = {"what": "torch.matmul(A, B) in bf16 (bf16 output), each launch alone, L2 flushed",
                                  "median_us": cub["median_us"], "TFLOP_s": round(fl / cub["median_us"] / 1e6, 1)}
+    prec = torch.get_float32_matmul_precision()
+    torch.set_float32_matmul_precision("highest")  # FP32 on the CUDA cores, no TF32
+    try:
+        cuf = standalone_us({"f32": lambda: torch.matmul(A, B, out=Cf)}, {}, flush=flush, reps=5)["f32"]
+    finally:
+        torch.set_float32_matmul_precision(prec)
+    kern["f32_fold_fwd"]["cublas_same_shape"] = {
+        "what": "torch.matmul(A, B) in FP32 with TF32 off (no fixed fold order), each launch alone, L2 flushed",
+        "median_us": cuf["median_us"], "TFLOP_s": round(fl / cuf["median_us"] / 1e6, 2)}
     dominant = max(per, key=per.get)  # the launch with the largest time share
     achieved = fl / per[dominant] / 1e9
     world = dist.get_world_size() if dist else 1
