@@ -71,7 +71,8 @@ constexpr uint32_t LAYOUT_SW128 = 2;
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int NUM_THREADS = 64 + 32 * NUM_EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int EPI_BUF_BYTES = 32 * 32 * 4;  // a warp's 32 x 32 f32 staging block
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + NUM_EPI_WARPS * EPI_BUF_BYTES + 1024 + 256;
 
 struct Params {
   float *C;
@@ -172,12 +173,44 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Stores one 32 x 32 block of an accumulator into C: lane i holds the 32
+// values of row row0 + i, columns col0 .. col0 + 31. A block whose 32 columns
+// lie in C (rows 16-byte aligned) passes through the warp's 4 KiB shared
+// buffer, its 128-bit chunks XOR-swizzled by row so that neither the writes
+// (lane = row) nor the reads (8 lanes = one row) conflict on banks; each
+// global store instruction then writes four whole 128-byte row segments
+// instead of 32 pieces of 32 rows. Other blocks are stored element by element.
+__device__ __forceinline__ void store_block(float *buf, const uint32_t (&r)[32], float *C, int64_t ldc, int64_t M,
+                                            int64_t N, int64_t row0, int64_t col0, int vec_ok, int lane) {
+  if (vec_ok && col0 + 32 <= N) {  // the same for the whole warp
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      *reinterpret_cast<float4 *>(buf + lane * 32 + ((j ^ (lane & 7)) << 2)) =
+          make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]), __uint_as_float(r[4 * j + 2]),
+                      __uint_as_float(r[4 * j + 3]));
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int rr = 4 * i + (lane >> 3), c = lane & 7;
+      const float4 v = *reinterpret_cast<const float4 *>(buf + rr * 32 + ((c ^ (rr & 7)) << 2));
+      if (row0 + rr < M) *reinterpret_cast<float4 *>(C + (row0 + rr) * ldc + col0 + 4 * c) = v;
+    }
+    __syncwarp();  // the buffer is free for the next block
+  } else if (row0 + lane < M) {
+    float *crow = C + (row0 + lane) * ldc;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (col0 + j < N) crow[col0 + j] = __uint_as_float(r[j]);
+  }
+}
+
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     gemm_bf16_tcgen05_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b,
                              const Params p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+  float *epi_buf = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES);  // [NUM_EPI_WARPS][32 * 32]
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES + NUM_EPI_WARPS * EPI_BUF_BYTES);
   uint64_t *empty = full + STAGES;
   uint64_t *tfull = empty + STAGES;
   uint64_t *tempty = tfull + 1;
@@ -307,9 +340,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
       if (!mbar_wait(tfull, iter & 1, abort_flag)) break;
       fence_after();
-      const int64_t row = (int64_t)tm * BM + 128 * h + 32 * q + lane;
-      float *crow = p.C + row * p.ldc;
+      const int64_t row0 = (int64_t)tm * BM + 128 * h + 32 * q;  // this warp's 32 rows
       const uint32_t tbase = tmem_base + h * 256 + ((uint32_t)(32 * q) << 16);
+      float *buf = epi_buf + (warp - 2) * (32 * 32);
 #pragma unroll 1
       for (int c = 0; c < BN; c += 32) {
         uint32_t r[32];
@@ -318,20 +351,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           fence_before();
           mbar_arrive(tempty);
         }
-        if (row < p.M) {
-          const int64_t col0 = (int64_t)tn * BN + c;
-          if (p.vec_ok && col0 + 32 <= p.N) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              *reinterpret_cast<float4 *>(crow + col0 + j) =
-                  make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                              __uint_as_float(r[j + 3]));
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (col0 + j < p.N) crow[col0 + j] = __uint_as_float(r[j]);
-          }
-        }
+        store_block(buf, r, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c, p.vec_ok, lane);
       }
     }
   }
@@ -376,7 +396,7 @@ struct Pair {
   static constexpr int SLOTS = MH == 1 ? 2 : 1;  // accumulator sets in tensor memory
   static constexpr int EPI_WARPS = 4 * MH;
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_WARPS * EPI_BUF_BYTES + 1024 + 256;
 };
 
 struct PairParams {
@@ -466,7 +486,9 @@ __global__ void __launch_bounds__(Pair<MH>::THREADS, 1)
   constexpr int STAGES_ = PC::STAGES, SLOTS = PC::SLOTS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES_ * PC::STAGE_BYTES);  // used in the even CTA
+  float *epi_buf = reinterpret_cast<float *>(smem + STAGES_ * PC::STAGE_BYTES);  // [EPI_WARPS][32 * 32]
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES_ * PC::STAGE_BYTES +
+                                                PC::EPI_WARPS * EPI_BUF_BYTES);  // used in the even CTA
   uint64_t *empty = full + STAGES_;
   uint64_t *tfull = empty + STAGES_;  // [SLOTS]: accumulators ready
   uint64_t *tempty = tfull + 2;       // [SLOTS]: accumulators drained by both CTAs (used in the even CTA)
@@ -622,9 +644,9 @@ __global__ void __launch_bounds__(Pair<MH>::THREADS, 1)
       const int tm = u / p.tiles_n, tn = u % p.tiles_n;
       if (!mbar_wait(&tfull[sl], use & 1, abort_flag)) break;
       fence_after();
-      const int64_t row = (int64_t)tm * TILE_M + 256 * h + 128 * rank + 32 * q + lane;
-      float *crow = p.C + row * p.ldc;
+      const int64_t row0 = (int64_t)tm * TILE_M + 256 * h + 128 * rank + 32 * q;  // this warp's 32 rows
       const uint32_t tbase = tmem_base + (uint32_t)(sl + h) * 256 + ((uint32_t)(32 * q) << 16);
+      float *buf = epi_buf + (warp - 2) * (32 * 32);
 #pragma unroll 1
       for (int c = 0; c < BN; c += 32) {
         uint32_t r[32];
@@ -634,20 +656,7 @@ __global__ void __launch_bounds__(Pair<MH>::THREADS, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive_cluster(tempty0 + (uint32_t)sl * 8u);
         }
-        if (row < p.M) {
-          const int64_t col0 = (int64_t)tn * BN + c;
-          if (p.vec_ok && col0 + 32 <= p.N) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              *reinterpret_cast<float4 *>(crow + col0 + j) =
-                  make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                              __uint_as_float(r[j + 3]));
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (col0 + j < p.N) crow[col0 + j] = __uint_as_float(r[j]);
-          }
-        }
+        store_block(buf, r, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c, p.vec_ok, lane);
       }
     }
   }
