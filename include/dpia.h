@@ -243,12 +243,13 @@ enum { DPIA_CONTRACT_OFF = 0, DPIA_CONTRACT_FMA = 1 };
  * {128, 160, 192, 224, 256} (0 = the width whose tiles fill the fewest
  * waves). grid: CTAs of the persistent BF16 kernel (0 = one per SM, or as
  * many CTA pairs as fit at once).
- * cluster (BF16 only): 1 (or 0): one CTA (one SM) per 256-row tile, two M=128
- * MMAs per k step (tcgen05 cta_group::1). 2: a cluster of two CTAs on two
- * SMs per tile, each staging 128 rows of every 256-row block of A and half
- * of B's columns, one M=256 MMA per block across the pair (cta_group::2);
- * tile_m 512 gives each SM two blocks that share its half of B. The value of
- * C does not depend on it. The FP32 fold ignores grid and cluster.
+ * cluster (BF16 only): 1: one CTA (one SM) per 256-row tile, two M=128 MMAs
+ * per k step (tcgen05 cta_group::1). 2: a cluster of two CTAs on two SMs per
+ * tile, each staging 128 rows of every 256-row block of A and half of B's
+ * columns, one M=256 MMA per block across the pair (cta_group::2); tile_m 512
+ * gives each SM two blocks that share its half of B. 0: a pair with 512-row
+ * tiles when M >= 512, else one CTA. The value of C does not depend on it.
+ * The FP32 fold ignores grid and cluster.
  */
 typedef struct {
   int32_t contract;

@@ -161,7 +161,9 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 32 lanes x 32 columns of 32-bit values from tensor memory (lane = row);
+// the registers are valid after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
       "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -170,8 +172,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Stores one 32 x 32 block of an accumulator into C: lane i holds the 32
 // values of row row0 + i, columns col0 .. col0 + 31. A block whose 32 columns
@@ -344,14 +346,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const uint32_t tbase = tmem_base + h * 256 + ((uint32_t)(32 * q) << 16);
       float *buf = epi_buf + (warp - 2) * (32 * 32);
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
-        uint32_t r[32];
-        tmem_ld32(tbase + c, r);
-        if (c + 32 >= BN) {
+      for (int c = 0; c < BN; c += 64) {  // two 32-column blocks per round trip to tensor memory
+        uint32_t r0[32], r1[32];
+        const bool two = c + 32 < BN;  // the same for the whole warp
+        tmem_ld32_async(tbase + c, r0);
+        if (two) tmem_ld32_async(tbase + c + 32, r1);
+        tmem_wait_ld();
+        if (c + 64 >= BN) {
           fence_before();
           mbar_arrive(tempty);
         }
-        store_block(buf, r, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c, p.vec_ok, lane);
+        store_block(buf, r0, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c, p.vec_ok, lane);
+        if (two) store_block(buf, r1, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c + 32, p.vec_ok, lane);
       }
     }
   }
@@ -648,15 +654,19 @@ __global__ void __launch_bounds__(Pair<MH>::THREADS, 1)
       const uint32_t tbase = tmem_base + (uint32_t)(sl + h) * 256 + ((uint32_t)(32 * q) << 16);
       float *buf = epi_buf + (warp - 2) * (32 * 32);
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
-        uint32_t r[32];
-        tmem_ld32(tbase + c, r);
-        if (c + 32 >= BN) {  // accumulator read out: the MMAs may refill it
+      for (int c = 0; c < BN; c += 64) {  // two 32-column blocks per round trip to tensor memory
+        uint32_t r0[32], r1[32];
+        const bool two = c + 32 < BN;  // the same for the whole warp
+        tmem_ld32_async(tbase + c, r0);
+        if (two) tmem_ld32_async(tbase + c + 32, r1);
+        tmem_wait_ld();
+        if (c + 64 >= BN) {  // accumulator read out: the MMAs may refill it
           fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive_cluster(tempty0 + (uint32_t)sl * 8u);
         }
-        store_block(buf, r, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c, p.vec_ok, lane);
+        store_block(buf, r0, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c, p.vec_ok, lane);
+        if (two) store_block(buf, r1, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c + 32, p.vec_ok, lane);
       }
     }
   }
@@ -836,13 +846,18 @@ cudaError_t launch_pair(const uint16_t *A, const uint16_t *B, float *C, int64_t 
 // MN-major). op(B) is K x N: B stored K x N (transB = 0, MN-major) or N x K
 // (transB = 1, K-major). tile_n = 0 picks BN per shape. cluster: 1 = one CTA
 // per 256-row tile (cta_group::1), 2 = a CTA pair per tile of tile_m = 256
-// or 512 rows (cta_group::2), 0 = one CTA per tile. grid > 0: CTAs of the
-// persistent grid (a pair kernel takes whole pairs).
+// or 512 rows (cta_group::2), 0 = a CTA pair per 512-row tile when M >= 512,
+// else one CTA per tile. grid > 0: CTAs of the persistent grid (a pair
+// kernel takes whole pairs).
 cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,
                              int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_m,
                              int tile_n, int cluster, int vec_ok, cudaStream_t stream) {
   cudaError_t e = set_smem_attrs();
   if (e != cudaSuccess) return e;
+  if (cluster == 0 && M >= 512 && pair_slots<2>() > 0) {  // the default for tiles that fill 512 rows
+    cluster = 2;
+    tile_m = 512;
+  }
   if (cluster == 2) {
     const int fit = tile_m == 512 ? pair_slots<2>() : pair_slots<1>();
     if (fit == 0) return cudaErrorInvalidConfiguration;
