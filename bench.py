@@ -732,9 +732,10 @@ def gemm_workload(args, device, dist):
     total = 3 * fl
     layouts = {"bf16_fwd": "C = A B, B MN-major", "bf16_bwd_dA": "dA = dC B^T, both K-major",
                "bf16_bwd_dB": "dB = A^T dC, both MN-major"}
-    roof = {"bound": "tensor", "kernel": f"gemm_bf16_tcgen05_kernel ({dominant}: {layouts[dominant]})",
+    roof = {"bound": "tensor",
+            "kernel": f"gemm_bf16_pair_kernel<2>, 512-row tiles on CTA pairs ({dominant}: {layouts[dominant]})",
             "achieved": round(achieved, 1), "peak": bf16_peak, "unit": "TFLOP/s", "frac": round(achieved / bf16_peak, 4),
-            "traffic": profile_traffic("gemm_bf16_tcgen05_4096.md", GEMM_SOURCES),
+            "traffic": profile_traffic("gemm_bf16_4096.md", GEMM_SOURCES),
             "traffic_note": "DRAM bytes of one forward launch of the same kernel (ncu)",
             "peak_source": f"{src} bf16_tflops (cuBLAS burst)",
             "frac_per_launch": {k: round(fl / v / 1e9 / bf16_peak, 4) for k, v in per.items()}}

@@ -29,14 +29,15 @@
 // shared-memory descriptors select the canonical 128-byte-swizzle layout of
 // either major-ness, so the transposes of the backward pass need no copies.
 //
-// A second kernel runs each tile on a CTA pair (cta_group::2, below). At
-// 4096^3 it measured slower with 256-row tiles (1.06-1.17 PFLOP/s against
-// 1.37-1.42 here) and level with 512-row tiles (1.37), although it stages
-// 23% fewer operand bytes per flop; so is B shared by TMA multicast within
-// clusters of 2 or 4 one-SM CTAs (3% and 25% slower, not kept). Neither the
-// tensor pipe (64% active), L2 (51%), shared-memory banks (26% reads) nor
-// the TMA ingest (37%) is saturated here: the refill round trip of a stage
-// bounds the pipe. The one-SM kernel is the default.
+// A second kernel runs each tile on a CTA pair (cta_group::2, below); with
+// 512-row tiles it stages 23% fewer operand bytes per flop and is the
+// default when M >= 512. The epilogue of both kernels stages each warp's
+// 32 x 32 block in shared memory so that C is written in whole 128-byte row
+// segments; writing C is the part of a tile the MMAs cannot overlap (both
+// accumulators fill tensor memory). Measured at 4096^3: 512-row pairs
+// 1.58-1.60 PFLOP/s, one SM per tile 1.49-1.56, 256-row pairs 1.18-1.28; B
+// shared by TMA multicast within clusters of one-SM CTAs measured slower
+// and was not kept.
 //
 // Every mbarrier wait is bounded by the global timer. A wait that runs out
 // sets the CTA's abort flag and the library's device status word
