@@ -726,6 +726,21 @@ def gemm_workload(args, device, dist):
     kern["f32_fold_fwd"]["cublas_same_shape"] = {
         "what": "torch.matmul(A, B) in FP32 with TF32 off (no fixed fold order), each launch alone, L2 flushed",
         "median_us": cuf["median_us"], "TFLOP_s": round(fl / cuf["median_us"] / 1e6, 2)}
+    if args.gemm_ksweep:
+        # the forward over K at M = N = 4096: the slope is the mainloop's rate, the intercept the
+        # per-launch cost (writing C, filling the pipeline, the launch itself)
+        sweep = {}
+        for K in (512, 1024, 2048, 4096, 8192):
+            Ak = torch.randn(n, K, device=device, generator=torch.Generator(device=device).manual_seed(4))
+            Bk = torch.randn(K, n, device=device, generator=torch.Generator(device=device).manual_seed(5))
+            Akb, Bkb = dpia.to_bf16(Ak), dpia.to_bf16(Bk)
+            del Ak, Bk
+            calls = {"one_sm": lambda: dpia.dpia_gemm_bf16(Akb, Bkb, C, n, n, K, K, n, n, 0, 0, cluster=1),
+                     "pair_512": lambda: dpia.dpia_gemm_bf16(Akb, Bkb, C, n, n, K, K, n, n, 0, 0, cluster=2,
+                                                             tile_m=512),
+                     "cublas_bf16_out": lambda: torch.matmul(Akb, Bkb, out=Cb)}
+            sweep[str(K)] = {k: v["median_us"] for k, v in standalone_us(calls, {}, flush=flush, reps=15).items()}
+        kern["k_sweep_us"] = sweep
     dominant = max(per, key=per.get)  # the launch with the largest time share
     achieved = fl / per[dominant] / 1e9
     world = dist.get_world_size() if dist else 1
@@ -1244,6 +1259,8 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2],
                     help="CTAs per tile of the BF16 GEMM in the gemm --profile case (0 = one)")
+    ap.add_argument("--gemm-ksweep", action="store_true",
+                    help="gemm workload: also time the forward at K = 512..8192 (M = N = 4096)")
     ap.add_argument("--tile-m", type=int, default=0, choices=[0, 256, 512],
                     help="rows per tile of the BF16 GEMM in the gemm --profile case (512: CTA pairs only)")
     args = ap.parse_args(argv)
