@@ -79,7 +79,8 @@ struct Params {
   float *C;
   int64_t M, N, K, ldc;
   int BN, tiles_n, num_tiles, k_blocks;
-  int a_mn, b_mn, vec_ok;
+  int a_mn, b_mn;
+  int vec_ok;         // C has a tensor map: the epilogue stores through the TMA engine
   int a_3d;           // MN-major A loaded as one 3-D box {64 m, 64 k, 4 m-blocks}
   uint32_t stage_tx;  // bytes the TMA loads of one stage deliver
 };
@@ -176,29 +177,47 @@ __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Bulk tensor store of a shared-memory box to global memory (the TMA engine
+// writes it while the warp goes on; elements outside the tensor are skipped).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the committed stores have read their shared-memory source
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// the committed stores have completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Stores one 32 x 32 block of an accumulator into C: lane i holds the 32
-// values of row row0 + i, columns col0 .. col0 + 31. A block whose 32 columns
-// lie in C (rows 16-byte aligned) passes through the warp's 4 KiB shared
-// buffer, its 128-bit chunks XOR-swizzled by row so that neither the writes
-// (lane = row) nor the reads (8 lanes = one row) conflict on banks; each
-// global store instruction then writes four whole 128-byte row segments
-// instead of 32 pieces of 32 rows. Other blocks are stored element by element.
-__device__ __forceinline__ void store_block(float *buf, const uint32_t (&r)[32], float *C, int64_t ldc, int64_t M,
-                                            int64_t N, int64_t row0, int64_t col0, int vec_ok, int lane) {
-  if (vec_ok && col0 + 32 <= N) {  // the same for the whole warp
+// values of row row0 + i, columns col0 .. col0 + 31. With a tensor map of C
+// (C 16-byte aligned, rows a multiple of 16 bytes apart) the block goes into
+// the warp's 4 KiB of shared memory in the 128-byte swizzle (16-byte chunk j
+// of row i at chunk j ^ (i % 8): conflict-free for the writing lanes) and one
+// lane hands it to the TMA engine, which writes whole rows and skips what
+// lies outside C; the warp does not wait for the writes. Otherwise the block
+// is stored element by element.
+__device__ __forceinline__ void store_block(float *buf, const uint32_t (&r)[32], const CUtensorMap *tma_c, float *C,
+                                            int64_t ldc, int64_t M, int64_t N, int64_t row0, int64_t col0,
+                                            int tma_ok, int lane) {
+  if (tma_ok) {
+    if (row0 < M && col0 < N) {  // the same for the whole warp
+      if (lane == 0) bulk_wait_read();  // the warp's previous block has left the buffer
+      __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      *reinterpret_cast<float4 *>(buf + lane * 32 + ((j ^ (lane & 7)) << 2)) =
-          make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]), __uint_as_float(r[4 * j + 2]),
-                      __uint_as_float(r[4 * j + 3]));
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int rr = 4 * i + (lane >> 3), c = lane & 7;
-      const float4 v = *reinterpret_cast<const float4 *>(buf + rr * 32 + ((c ^ (rr & 7)) << 2));
-      if (row0 + rr < M) *reinterpret_cast<float4 *>(C + (row0 + rr) * ldc + col0 + 4 * c) = v;
+      for (int j = 0; j < 8; ++j)
+        *reinterpret_cast<float4 *>(buf + lane * 32 + ((j ^ (lane & 7)) << 2)) =
+            make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]), __uint_as_float(r[4 * j + 2]),
+                        __uint_as_float(r[4 * j + 3]));
+      fence_proxy_async_smem();  // the generic-proxy writes, before the TMA engine reads them
+      __syncwarp();
+      if (lane == 0) {
+        tma_store_2d(tma_c, buf, (int)col0, (int)row0);
+        bulk_commit();
+      }
     }
-    __syncwarp();  // the buffer is free for the next block
   } else if (row0 + lane < M) {
     float *crow = C + (row0 + lane) * ldc;
 #pragma unroll
@@ -209,7 +228,7 @@ __device__ __forceinline__ void store_block(float *buf, const uint32_t (&r)[32],
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     gemm_bf16_tcgen05_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b,
-                             const Params p) {
+                             const __grid_constant__ CUtensorMap tma_c, const Params p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float *epi_buf = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES);  // [NUM_EPI_WARPS][32 * 32]
@@ -357,10 +376,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           fence_before();
           mbar_arrive(tempty);
         }
-        store_block(buf, r0, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c, p.vec_ok, lane);
-        if (two) store_block(buf, r1, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c + 32, p.vec_ok, lane);
+        store_block(buf, r0, &tma_c, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c, p.vec_ok, lane);
+        if (two) store_block(buf, r1, &tma_c, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c + 32, p.vec_ok, lane);
       }
     }
+    if (lane == 0) bulk_wait_all();  // the stores of C have completed (and left shared memory)
   }
 
   fence_before();
@@ -410,7 +430,8 @@ struct PairParams {
   float *C;
   int64_t M, N, K, ldc;
   int BN, tiles_n, k_blocks, units;  // units: (256 * MH) x BN tiles
-  int a_mn, b_mn, vec_ok;
+  int a_mn, b_mn;
+  int vec_ok;         // C has a tensor map: the epilogue stores through the TMA engine
   int a_3d;           // MN-major A loaded as one 3-D box {64 m, 64 k, 2 m-blocks}
   uint32_t stage_tx;  // bytes both CTAs' copies of one stage deliver to the even CTA's barrier
 };
@@ -488,7 +509,7 @@ __device__ __forceinline__ void umma2_commit(uint64_t *bar) {
 template <int MH>
 __global__ void __launch_bounds__(Pair<MH>::THREADS, 1)
     gemm_bf16_pair_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b,
-                          const PairParams p) {
+                          const __grid_constant__ CUtensorMap tma_c, const PairParams p) {
   using PC = Pair<MH>;
   constexpr int STAGES_ = PC::STAGES, SLOTS = PC::SLOTS;
   extern __shared__ uint8_t smem_raw[];
@@ -666,10 +687,11 @@ __global__ void __launch_bounds__(Pair<MH>::THREADS, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive_cluster(tempty0 + (uint32_t)sl * 8u);
         }
-        store_block(buf, r0, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c, p.vec_ok, lane);
-        if (two) store_block(buf, r1, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c + 32, p.vec_ok, lane);
+        store_block(buf, r0, &tma_c, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c, p.vec_ok, lane);
+        if (two) store_block(buf, r1, &tma_c, p.C, p.ldc, p.M, p.N, row0, (int64_t)tn * BN + c + 32, p.vec_ok, lane);
       }
     }
+    if (lane == 0) bulk_wait_all();  // the stores of C have completed (and left shared memory)
   }
 
   fence_before();
@@ -716,6 +738,21 @@ bool make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, in
                   CU_TENSOR_MAP_INTERLEAVE_NONE,
                   box_inner * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// f32 tensor map of C (rows x cols, leading dimension ld elements) for the
+// epilogue's stores: 32 x 32 boxes of 128-byte rows, 128-byte swizzle.
+bool make_map_c(CUtensorMap *map, float *base, int64_t rows, int64_t cols, int64_t ld) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -832,12 +869,13 @@ cudaError_t launch_pair(const uint16_t *A, const uint16_t *B, float *C, int64_t 
   p.units = (int)(ceil_div(M, 256 * MH) * p.tiles_n);
   p.a_mn = transA ? 1 : 0;
   p.b_mn = transB ? 0 : 1;
-  p.vec_ok = vec_ok;
+  alignas(64) CUtensorMap mc;
+  p.vec_ok = vec_ok && make_map_c(&mc, C, M, N, ldc);  // else C is stored element by element
   p.a_3d = a_3d;
   const uint32_t b_half = p.b_mn ? (uint32_t)ceil_div(HN, 64) * (64u * BK * 2u) : (uint32_t)HN * BK * 2u;
   p.stage_tx = 2u * ((uint32_t)Pair<MH>::A_BYTES + b_half);
   const int g = 2 * (clusters < p.units ? clusters : p.units);
-  void *args[] = {&ma, &mb, &p};
+  void *args[] = {&ma, &mb, &mc, &p};
   cudaLaunchAttribute attr[1];
   const cudaLaunchConfig_t cfg = pair_config<MH>(attr, g, stream);
   return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(gemm_bf16_pair_kernel<MH>), args);
@@ -887,12 +925,13 @@ cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int
   p.k_blocks = (int)ceil_div(K, BK);
   p.a_mn = transA ? 1 : 0;
   p.b_mn = transB ? 0 : 1;
-  p.vec_ok = vec_ok;
+  alignas(64) CUtensorMap mc;
+  p.vec_ok = vec_ok && make_map_c(&mc, C, M, N, ldc);  // else C is stored element by element
   p.a_3d = a_3d;
   const uint32_t b_tx = p.b_mn ? (uint32_t)ceil_div(BN, 64) * (64u * BK * 2u) : (uint32_t)BN * BK * 2u;
   p.stage_tx = (uint32_t)A_BYTES + b_tx;
   int g = ctas < p.num_tiles ? ctas : p.num_tiles;
-  void *args[] = {&ma, &mb, &p};
+  void *args[] = {&ma, &mb, &mc, &p};
   return cudaLaunchKernel(kfn, dim3(g), dim3(NUM_THREADS), args, SMEM_BYTES, stream);
 }
 

@@ -125,15 +125,17 @@ def test_gemm_bf16_tolerance(cuda_device, tA, tB, M, N, K, tile_n):
 @pytest.mark.parametrize("cluster,tile_m", [(1, 0), (2, 256), (2, 512)])
 @pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0), (1, 1)])
 @pytest.mark.parametrize("M,N,K,tile_n", [(768, 448, 192, 224), (520, 300, 136, 0), (1024, 256, 64, 128),
-                                          (100, 520, 320, 160), (384, 200, 72, 256), (1280, 96, 128, 128)])
+                                          (100, 520, 320, 160), (384, 200, 72, 256), (1280, 96, 128, 128),
+                                          (600, 301, 64, 0)])
 def test_gemm_bf16_cta_pairs(cuda_device, tA, tB, M, N, K, tile_n, cluster, tile_m):
     """One CTA per 256-row tile (cluster 1) or a CTA pair (cluster 2: each CTA
     stages 128 rows of every 256-row block of A and half of B's columns, one
     M=256 MMA per block across both; tile_m 512 = two blocks per tile):
     ragged M, N and K, tiles whose later blocks lie past M (M = 100, 384, 520,
     768 with 512-row tiles), odd halves of B (tile_n 160: 80 columns per CTA),
-    N below one tile, and a small persistent grid (several tiles per pair, both
-    accumulator sets of each CTA in turn)."""
+    N below one tile, C rows not a multiple of 16 bytes apart (N = 301: no
+    tensor map of C, stored element by element), and a small persistent grid
+    (several tiles per pair, both accumulator sets of each CTA in turn)."""
     g = torch.Generator().manual_seed(11 * M + 5 * N + K + tA + 2 * tB)
     opA = torch.randn(M, K, generator=g).numpy()
     opB = torch.randn(K, N, generator=g).numpy()
