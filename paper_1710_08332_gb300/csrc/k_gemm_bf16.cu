@@ -32,9 +32,9 @@
 // A second kernel runs each tile on a CTA pair (cta_group::2, below); with
 // 512-row tiles it stages 23% fewer operand bytes per flop and is the
 // default when M >= 512. The epilogue of both kernels stages each warp's
-// 32 x 32 block in shared memory so that C is written in whole 128-byte row
-// segments; writing C is the part of a tile the MMAs cannot overlap (both
-// accumulators fill tensor memory). Measured at 4096^3: 512-row pairs
+// 32 x 32 block in shared memory and hands it to the TMA engine, which writes
+// whole 128-byte rows of C; writing C is the part of a tile the MMAs cannot
+// overlap (both accumulators fill tensor memory). Measured at 4096^3: 512-row pairs
 // 1.58-1.60 PFLOP/s, one SM per tile 1.49-1.56, 256-row pairs 1.18-1.28; B
 // shared by TMA multicast within clusters of one-SM CTAs measured slower
 // and was not kept.
