@@ -115,6 +115,9 @@ int64_t next_pow2(int64_t v) {
   return p;
 }
 
+// Rows of a dA item (the backward kernel stages their dy values in shared memory).
+constexpr int kDaRows = 32;
+
 // Validate and plan; returns DPIA_OK and fills b.
 dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, const dpia_gemv_instance *gemvs,
                        const dpia_batch_options *opt, Built &b) {
@@ -147,7 +150,7 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
   h.n_gemvs = ng;
   h.schedule = opt->schedule;
   h.rows_per_item = T / 32 * 4;  // a warp per row, four rows per warp
-  h.da_rows_per_item = 32;
+  h.da_rows_per_item = kDaRows;
   h.bwd_elems_per_item = 4 * (int64_t)T * 8;
   std::vector<std::pair<int64_t, Item>> fwd, bwd;  // (cost, item)
   for (int32_t i = 0; i < nd; ++i) {
@@ -445,6 +448,8 @@ __global__ void __launch_bounds__(256, 3) batch_fwd_kernel(const FwdArgs a) {
 __global__ void __launch_bounds__(256, 4) batch_bwd_kernel(const BwdArgs a) {
   __shared__ int last;
   __shared__ int64_t range[2];
+  __shared__ float dys[2][kDaRows];  // the dy values of the block's dA items, by item parity
+  int n_da = 0;
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(a.plan);
   const DotDesc *__restrict__ dots = reinterpret_cast<const DotDesc *>(a.plan + h->dots_off);
   const GemvDesc *__restrict__ gemvs = reinterpret_cast<const GemvDesc *>(a.plan + h->gemvs_off);
@@ -487,14 +492,20 @@ __global__ void __launch_bounds__(256, 4) batch_bwd_kernel(const BwdArgs a) {
       const int64_t cg = (g.N + 3) / 4;
       const int64_t Gc = cg < T ? (int64_t)next_pow2_dev(cg) : T;  // threads per row
       const int64_t rows_par = T / Gc;
-      // eight rows at a time: their dy values are loaded together, then each
-      // x group is loaded once and stored scaled into the eight rows
+      // the item's dy values in one coalesced load; a block reaches its next dA
+      // item (the other buffer's next use) only after every warp passed this
+      // barrier, so one barrier per item suffices
+      float *dyb = dys[n_da++ & 1];
+      if (t < r1 - w.a) dyb[t] = __ldg(a.gdy + g.y_off + w.a + t);
+      __syncthreads();
+      // eight rows at a time: each x group is loaded once and stored scaled
+      // into the eight rows
       for (int64_t rb = w.a + t / Gc; rb < r1; rb += 8 * rows_par) {
         float dv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int64_t r = rb + u * rows_par;
-          dv[u] = r < r1 ? __ldg(a.gdy + g.y_off + r) : 0.0f;
+          dv[u] = r < r1 ? dyb[r - w.a] : 0.0f;
         }
         float *row0 = a.dAs + g.a_off + rb * g.lda;
         const int64_t rstep = rows_par * g.lda;
