@@ -352,58 +352,6 @@ __device__ __forceinline__ void block_item_range(const int64_t *end, int64_t n, 
 }
 
 constexpr int kSeqStage = 1024;
-constexpr int kXs = 4096;  // GEMV columns whose x a forward item stages in shared memory
-
-// One chunk of a GEMV row folded exactly as thread_fold folds it (each of the V
-// lanes sums its items in order r = 0..Rc-1, items past n are the identity
-// (0, 0), then the lanes are folded in order), with x read from shared memory:
-// only the row's loads hold registers, so sixteen vectors per lane are in
-// flight where thread_fold keeps eight of the row and eight of x.
-__device__ __forceinline__ float row_fold_xs(const float *__restrict__ row, const float *xs, int64_t n,
-                                             int64_t base, int64_t Rc, int64_t step) {
-  constexpr int U = 16;
-  float acc[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) acc[v] = 0.0f;
-  const int64_t room = n - V - base;  // vector r lies below n  <=>  r * step <= room
-  int64_t Rin = room < 0 ? 0 : room / step + 1;
-  if (Rin > Rc) Rin = Rc;
-  int64_t r = 0;
-  for (; r + U <= Rin; r += U) {
-    float av[U][V];
-#pragma unroll
-    for (int u = 0; u < U; ++u) load_vec<V, false>(row + base + (r + u) * step, av[u]);
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const float4 xv = *reinterpret_cast<const float4 *>(xs + base + (r + u) * step);
-      acc[0] = __fadd_rn(acc[0], __fmul_rn(av[u][0], xv.x));
-      acc[1] = __fadd_rn(acc[1], __fmul_rn(av[u][1], xv.y));
-      acc[2] = __fadd_rn(acc[2], __fmul_rn(av[u][2], xv.z));
-      acc[3] = __fadd_rn(acc[3], __fmul_rn(av[u][3], xv.w));
-    }
-  }
-  for (; r < Rin; ++r) {
-    float av[V];
-    load_vec<V, false>(row + base + r * step, av);
-    const float4 xv = *reinterpret_cast<const float4 *>(xs + base + r * step);
-    acc[0] = __fadd_rn(acc[0], __fmul_rn(av[0], xv.x));
-    acc[1] = __fadd_rn(acc[1], __fmul_rn(av[1], xv.y));
-    acc[2] = __fadd_rn(acc[2], __fmul_rn(av[2], xv.z));
-    acc[3] = __fadd_rn(acc[3], __fmul_rn(av[3], xv.w));
-  }
-  for (; r < Rc; ++r) {  // the vector straddling n, then identity items
-    const int64_t e0 = base + r * step;
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const bool in = e0 + v < n;
-      acc[v] = __fadd_rn(acc[v], __fmul_rn(in ? row[e0 + v] : 0.0f, in ? xs[e0 + v] : 0.0f));
-    }
-  }
-  float t = 0.0f;
-#pragma unroll
-  for (int v = 0; v < V; ++v) t = __fadd_rn(t, acc[v]);
-  return t;
-}
 
 // The forward kernel runs at 3 blocks of 256 per SM (85 registers): its GEMV
 // rows keep 32 items per lane in flight, which measured faster than 4 blocks
@@ -412,7 +360,6 @@ __device__ __forceinline__ float row_fold_xs(const float *__restrict__ row, cons
 __global__ void __launch_bounds__(256, 3) batch_fwd_kernel(const FwdArgs a) {
   __shared__ float sm[32];
   __shared__ float stage[kSeqStage];
-  __shared__ __align__(16) float xs[kXs];  // x of the block's current GEMV item, when it fits
   __shared__ int last;
   __shared__ int64_t range[2];
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(a.plan);
@@ -482,24 +429,13 @@ __global__ void __launch_bounds__(256, 3) batch_fwd_kernel(const FwdArgs a) {
       const int64_t warps = blockDim.x >> 5;
       const int64_t r_end = w.a + h->rows_per_item < g.M ? w.a + h->rows_per_item : g.M;
       const float *x = a.gx + g.x_off;
-      const bool staged = g.N <= kXs;  // the same for the whole block
-      if (staged) {  // x once per item, shared by its rows
-        __syncthreads();  // the block's previous item is done with xs
-        for (int64_t i = t; i < g.N; i += blockDim.x) xs[i] = __ldg(x + i);
-        __syncthreads();
-      }
       for (int64_t r = w.a + warp; r < r_end; r += warps) {
         const float *row = a.As + g.a_off + r * g.lda;
         float acc = 0.0f;
         for (int64_t c = 0; c < g.Crow; ++c) {
-          const int64_t base = c * g.s + lane * g.tstride;
-          float v;
-          if (staged) {
-            v = row_fold_xs(row, xs, g.N, base, g.Rc, g.step);
-          } else {
-            const bool full = (c + 1) * g.s <= g.N;
-            v = thread_fold<DotF32, SumF32, V, true, 1, true>(row, x, g.N, base, g.Rc, g.step, full);
-          }
+          const bool full = (c + 1) * g.s <= g.N;
+          float v = thread_fold<DotF32, SumF32, V, true, 1, true>(row, x, g.N, c * g.s + lane * g.tstride, g.Rc,
+                                                                  g.step, full);
           v = warp_tree<SumF32>(v, 32);
           if (lane == 0) acc = __fadd_rn(acc, v);
         }
