@@ -157,6 +157,30 @@ def test_gemm_bf16_cta_pairs(cuda_device, tA, tB, M, N, K, tile_n, cluster, tile
         assert dpia.dpia_poll_device_status() == 0
 
 
+@pytest.mark.parametrize("cluster,tile_m", [(1, 0), (2, 256), (2, 512)])
+@pytest.mark.parametrize("offset", [4, 1])
+def test_gemm_bf16_strided_c_untouched_outside(cuda_device, cluster, tile_m, offset):
+    """C as a column window of a wider matrix (ldc > N): with a 16-byte aligned
+    window (offset 4) C is written through its tensor map, whose bounds clip
+    the ragged tiles; with offset 1 element by element. Either way exactly the
+    M x N window changes: the columns beside it keep their NaNs."""
+    M, N, K = 700, 300, 200
+    g = torch.Generator().manual_seed(99 + offset + cluster)
+    opA = torch.randn(M, K, generator=g).numpy()
+    opB = torch.randn(K, N, generator=g).numpy()
+    Ab = dpia.to_bf16(torch.from_numpy(opA).cuda())
+    Bb = dpia.to_bf16(torch.from_numpy(opB).cuda())
+    ldc = N + 20
+    big = torch.full((M, ldc), float("nan"), device="cuda")
+    C = big[:, offset:offset + N]
+    dpia.dpia_gemm_bf16(Ab, Bb, C, M, N, K, K, N, ldc, 0, 0, tile_m=tile_m, cluster=cluster)
+    torch.cuda.synchronize()
+    assert dpia.dpia_poll_device_status() == 0
+    _bf16_check(host(C).astype(np.float64), opA, opB, f"strided C offset={offset} cluster={cluster}")
+    hb = host(big)
+    assert np.isnan(hb[:, :offset]).all() and np.isnan(hb[:, offset + N:]).all()
+
+
 @pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0)])
 def test_gemm_bf16_pair_matches_single(cuda_device, gemm_inputs, tA, tB):
     """At 4096^3 (the three layouts of the forward and backward products) the
