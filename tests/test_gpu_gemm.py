@@ -164,7 +164,7 @@ def test_gemm_bf16_strided_c_untouched_outside(cuda_device, cluster, tile_m, off
     window (offset 4) C is written through its tensor map, whose bounds clip
     the ragged tiles; with offset 1 element by element. Either way exactly the
     M x N window changes: the columns beside it keep their NaNs."""
-    M, N, K = 700, 300, 200
+    M, N, K = 700, 296, 200  # K and N multiples of 8: A's and B's rows 16-byte aligned, as TMA needs
     g = torch.Generator().manual_seed(99 + offset + cluster)
     opA = torch.randn(M, K, generator=g).numpy()
     opB = torch.randn(K, N, generator=g).numpy()
