@@ -184,117 +184,107 @@ __global__ void __launch_bounds__(NT, FMA ? 2 : 1) sgemm_fold_kernel(const GemmA
 // ---------------------------------------------------------------------------
 // Tiles of 64 x 128 for the last rows of C: when the 128 x 128 tiles leave a
 // last wave less than half full, those rows are computed as half-height tiles
-// by a second launch, so the tail takes half a wave's time. Same fold, same
-// bits: 256 threads of 4 x 8 elements (rows ty*4 + i, columns as above).
+// by a second launch. Same fold, same bits, same 8 x 8 elements per thread as
+// the full tile (rows ty*4 + i and 32 + ty*4 + i, columns as above), on 128
+// threads, so that four blocks share an SM.
 // ---------------------------------------------------------------------------
 
-constexpr int BMH = 64;
+constexpr int BMH = 64, NTH = 128;
 
-template <bool TA>
-__device__ __forceinline__ void load_a_half(const GemmArgs &g, int64_t m0, int64_t k0, bool vec, float (&ra)[4]) {
+// The (m0, k0) slice of op(A) (64 x 16) and the (k0, n0) slice of op(B)
+// (16 x 128) into registers, 8 and 16 values per thread.
+template <bool TA, bool TB>
+__device__ __forceinline__ void load_half_slices(const GemmArgs &g, int64_t m0, int64_t n0, int64_t k0, bool vec,
+                                                 float (&ra)[8], float (&rb)[16]) {
   const int tid = threadIdx.x;
   if (vec) {
-    const float *p = !TA ? g.A + (m0 + tid / 4) * g.lda + k0 + (tid % 4) * 4   // row m, 4 k
-                         : g.A + (k0 + tid / 16) * g.lda + m0 + (tid % 16) * 4;  // k row, 4 m
-    const float4 u = __ldg(reinterpret_cast<const float4 *>(p));
-    ra[0] = u.x; ra[1] = u.y; ra[2] = u.z; ra[3] = u.w;
-  } else {
+    // A[m][k]: m = tid/2, k = (tid%2)*8 .. +7;  A[k][m]: k = tid/8, m = (tid%8)*8 .. +7
+    const float *pa = !TA ? g.A + (m0 + tid / 2) * g.lda + k0 + (tid % 2) * 8
+                          : g.A + (k0 + tid / 8) * g.lda + m0 + (tid % 8) * 8;
+    const float4 u = __ldg(reinterpret_cast<const float4 *>(pa)), v = __ldg(reinterpret_cast<const float4 *>(pa + 4));
+    ra[0] = u.x; ra[1] = u.y; ra[2] = u.z; ra[3] = u.w; ra[4] = v.x; ra[5] = v.y; ra[6] = v.z; ra[7] = v.w;
+    // B[k][n]: k = tid/8, n = (tid%8)*16 .. +15;  B[n][k]: n = tid, k = 0 .. 15
+    const float *pb = !TB ? g.B + (k0 + tid / 8) * g.ldb + n0 + (tid % 8) * 16 : g.B + (n0 + tid) * g.ldb + k0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      ra[j] = !TA ? a_at<TA>(g, m0 + tid / 4, k0 + (tid % 4) * 4 + j) : a_at<TA>(g, m0 + (tid % 16) * 4 + j, k0 + tid / 16);
-  }
-}
-
-template <bool TA>
-__device__ __forceinline__ void store_a_half(float (*As)[BMH], const float (&ra)[4]) {
-  const int tid = threadIdx.x;
-  if (!TA) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) As[(tid % 4) * 4 + j][tid / 4] = ra[j];
-  } else {
-    *reinterpret_cast<float4 *>(&As[tid / 16][(tid % 16) * 4]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
-  }
-}
-
-// B slices as in the full kernel (8 values per thread).
-template <bool TB>
-__device__ __forceinline__ void load_b(const GemmArgs &g, int64_t n0, int64_t k0, bool vec, float (&rb)[8]) {
-  const int tid = threadIdx.x;
-  if (vec) {
-    const float *p = !TB ? g.B + (k0 + tid / 16) * g.ldb + n0 + (tid % 16) * 8 : g.B + (n0 + tid / 2) * g.ldb + k0 + (tid % 2) * 8;
-    const float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p + 4));
-    rb[0] = u.x; rb[1] = u.y; rb[2] = u.z; rb[3] = u.w; rb[4] = v.x; rb[5] = v.y; rb[6] = v.z; rb[7] = v.w;
+    for (int q = 0; q < 4; ++q) {
+      const float4 w = __ldg(reinterpret_cast<const float4 *>(pb + 4 * q));
+      rb[4 * q] = w.x; rb[4 * q + 1] = w.y; rb[4 * q + 2] = w.z; rb[4 * q + 3] = w.w;
+    }
   } else {
 #pragma unroll
     for (int j = 0; j < 8; ++j)
-      rb[j] = !TB ? b_at<TB>(g, k0 + tid / 16, n0 + (tid % 16) * 8 + j) : b_at<TB>(g, k0 + (tid % 2) * 8 + j, n0 + tid / 2);
+      ra[j] = !TA ? a_at<TA>(g, m0 + tid / 2, k0 + (tid % 2) * 8 + j) : a_at<TA>(g, m0 + (tid % 8) * 8 + j, k0 + tid / 8);
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      rb[j] = !TB ? b_at<TB>(g, k0 + tid / 8, n0 + (tid % 8) * 16 + j) : b_at<TB>(g, k0 + j, n0 + tid);
   }
 }
 
-template <bool TB>
-__device__ __forceinline__ void store_b(float (*Bs)[BN], const float (&rb)[8]) {
+template <bool TA, bool TB>
+__device__ __forceinline__ void store_half_slices(float (*As)[BMH], float (*Bs)[BN], const float (&ra)[8],
+                                                  const float (&rb)[16]) {
   const int tid = threadIdx.x;
+  if (!TA) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) As[(tid % 2) * 8 + j][tid / 2] = ra[j];
+  } else {
+    *reinterpret_cast<float4 *>(&As[tid / 8][(tid % 8) * 8]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+    *reinterpret_cast<float4 *>(&As[tid / 8][(tid % 8) * 8 + 4]) = make_float4(ra[4], ra[5], ra[6], ra[7]);
+  }
   if (!TB) {
-    *reinterpret_cast<float4 *>(&Bs[tid / 16][(tid % 16) * 8]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
-    *reinterpret_cast<float4 *>(&Bs[tid / 16][(tid % 16) * 8 + 4]) = make_float4(rb[4], rb[5], rb[6], rb[7]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      *reinterpret_cast<float4 *>(&Bs[tid / 8][(tid % 8) * 16 + 4 * q]) =
+          make_float4(rb[4 * q], rb[4 * q + 1], rb[4 * q + 2], rb[4 * q + 3]);
   } else {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) Bs[(tid % 2) * 8 + j][tid / 2] = rb[j];
+    for (int j = 0; j < 16; ++j) Bs[j][tid] = rb[j];
   }
 }
 
 template <bool TA, bool TB, bool FMA>
-__global__ void __launch_bounds__(NT) sgemm_fold_half_kernel(const GemmArgs g, int vec_ok) {
+__global__ void __launch_bounds__(NTH, 4) sgemm_fold_half_kernel(const GemmArgs g, int vec_ok) {
   __shared__ __align__(16) float As[2][BK][BMH];
   __shared__ __align__(16) float Bs[2][BK][BN];
   const int64_t m0 = (int64_t)blockIdx.y * BMH, n0 = (int64_t)blockIdx.x * BN;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // ty in 0..7
   const bool interior_mn = m0 + BMH <= g.M && n0 + BN <= g.N;
-  float acc[4][8];
+  float acc[8][8];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
   const int64_t nk = ceil_div(g.K, BK);
-  float ra[4], rb[8];
-  {
-    const bool v0 = vec_ok && interior_mn && BK <= g.K;
-    load_a_half<TA>(g, m0, 0, v0, ra);
-    load_b<TB>(g, n0, 0, v0, rb);
-    store_a_half<TA>(As[0], ra);
-    store_b<TB>(Bs[0], rb);
-  }
+  float ra[8], rb[16];
+  load_half_slices<TA, TB>(g, m0, n0, 0, vec_ok && interior_mn && BK <= g.K, ra, rb);
+  store_half_slices<TA, TB>(As[0], Bs[0], ra, rb);
   __syncthreads();
   for (int64_t kt = 0; kt < nk; ++kt) {
     const int buf = kt & 1;
     const int64_t k0 = kt * BK;
     if (kt + 1 < nk) {
       const int64_t k1 = k0 + BK;
-      const bool v1 = vec_ok && interior_mn && k1 + BK <= g.K;
-      load_a_half<TA>(g, m0, k1, v1, ra);
-      load_b<TB>(g, n0, k1, v1, rb);
+      load_half_slices<TA, TB>(g, m0, n0, k1, vec_ok && interior_mn && k1 + BK <= g.K, ra, rb);
     }
     const int kcount = g.K - k0 < BK ? (int)(g.K - k0) : BK;
     for (int kk = 0; kk < kcount; ++kk) {  // exactly K terms in order
       const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][32 + ty * 4]);
       const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
       const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
-      const float a[4] = {a0.x, a0.y, a0.z, a0.w};
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = madd<FMA>(a[i], b[j], acc[i][j]);
     }
-    if (kt + 1 < nk) {
-      store_a_half<TA>(As[buf ^ 1], ra);
-      store_b<TB>(Bs[buf ^ 1], rb);
-    }
+    if (kt + 1 < nk) store_half_slices<TA, TB>(As[buf ^ 1], Bs[buf ^ 1], ra, rb);
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t m = m0 + ty * 4 + i;
+  for (int i = 0; i < 8; ++i) {
+    const int64_t m = m0 + (i < 4 ? ty * 4 + i : 32 + ty * 4 + (i - 4));
     if (m >= g.M) continue;
     float *crow = g.C + m * g.ldc;
 #pragma unroll
@@ -353,7 +343,7 @@ cudaError_t launch_gemm_f32(const float *A, const float *B, float *C, int64_t M,
   t.M = M - m_main;
   const void *kh = fma ? pick_half<true>(transA, transB) : pick_half<false>(transA, transB);
   void *targs[] = {&t, &vec_ok};
-  return cudaLaunchKernel(kh, dim3((unsigned)tn, (unsigned)ceil_div(t.M, BMH)), dim3(NT), targs, 0, stream);
+  return cudaLaunchKernel(kh, dim3((unsigned)tn, (unsigned)ceil_div(t.M, BMH)), dim3(NTH), targs, 0, stream);
 }
 
 }  // namespace dpia
