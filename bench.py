@@ -947,9 +947,9 @@ def codegen_workload(args, device, dist):
         "gen_asum_partials": lambda: ka.run(x, part),
         "gen_scal": lambda: ks.run(x, ys, grid=sms * 8, block=256),
         "gen_gemv_partials": lambda: kg.run(A, xv, gpart),
-        "gen_gemv_rows": lambda: kr.run(gpart, yv, grid=M // 256, block=256),
+        "gen_gemv_rows": lambda: kr.run(gpart, yv, grid=M // 64, block=64),  # a thread per row over 128 SMs
         "gen_gemv_dx_partials": lambda: kdx.run(A, dyv, dxpart),
-        "gen_gemv_dx_fold": lambda: kdf.run(dxpart, dxv, grid=N_ // 256, block=256),
+        "gen_gemv_dx_fold": lambda: kdf.run(dxpart, dxv, grid=N_ // 64, block=64),  # a thread per column
         "gen_gemv_dA": lambda: kda.run(dyv, xv, dAm),
     }
     st = dpia.ReduceStrategy(split=16384, threads=256, vec=4, second="tree", threads2=256)
