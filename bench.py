@@ -927,10 +927,10 @@ def codegen_workload(args, device, dist):
     A, xv, _ = W.gemv(device)
     M, N_ = A.shape
     kg = G.compile_cuda("gen_gemv_partials", *PR.gemv_partials(M, N_, 128))
-    kr = G.compile_cuda("gen_gemv_rows", *PR.fold_rows(M, 128), unroll=16)
+    kr = G.compile_cuda("gen_gemv_rows", *PR.fold_rows(M, 128), unroll=64)
     R = 32  # dx: row chunks of 32 (256 workgroups), then the fold over the chunks
     kdx = G.compile_cuda("gen_gemv_dx_partials", *PR.gemv_bwd_dx_partials(M, N_, R), unroll=8)
-    kdf = G.compile_cuda("gen_gemv_dx_fold", *PR.gemv_bwd_dx_fold(M // R, N_), unroll=16)
+    kdf = G.compile_cuda("gen_gemv_dx_fold", *PR.gemv_bwd_dx_fold(M // R, N_), unroll=64)
     kda = G.compile_cuda("gen_gemv_dA", *PR.gemv_bwd_dA(M, N_))
     dyv = torch.rand(M, device=device)
     dxpart = torch.empty(M // R * N_, device=device)
