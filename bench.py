@@ -902,7 +902,7 @@ def codegen_workload(args, device, dist):
 
     n = W.BW_N
     x, y = W.bandwidth(device)
-    # streams read as asVector 4; sequential loops unrolled 4 (the folds 16) so
+    # streams read as asVector 4; sequential loops unrolled 4 (the folds 64) so
     # that loads issue ahead of the dependent steps (a sweep of split, threads,
     # width and unroll factor chose these)
     s, Tn, V = 1 << 15, 256, 4
@@ -913,14 +913,14 @@ def codegen_workload(args, device, dist):
     folds, left = [], m1  # the folding stages of the 2M lane partials
     for grp in RW.fold_plan(m1):
         ph = PR.fold_all(left) if grp == left else PR.fold_rows(left // grp, grp)
-        folds.append((G.compile_cuda(f"gen_dot_fold_{left}_{grp}", *ph, unroll=16), left // grp))
+        folds.append((G.compile_cuda(f"gen_dot_fold_{left}_{grp}", *ph, unroll=64), left // grp))
         left //= grp
     fold_bufs = [torch.empty(max(cnt, 1), device=device) for _, cnt in folds]
 
     def dot_folds():
         src = part
         for (k, cnt), dst in zip(folds, fold_bufs):
-            k.run(src, dst, grid=max(1, cnt // 256), block=min(256, cnt) if cnt > 1 else 1)
+            k.run(src, dst, grid=max(1, cnt // 64), block=min(64, cnt) if cnt > 1 else 1)
             src = dst
     ka = G.compile_cuda("gen_asum_partials", *PR.asum_partials(n, s, Tn, V=V), unroll=4)
     ks = G.compile_cuda("gen_scal", *PR.scal(n, W.SCAL_A, V=V))

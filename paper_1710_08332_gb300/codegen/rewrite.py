@@ -215,14 +215,13 @@ def lower(kind: str, d: Derivation, n: int):
 
 
 def fold_plan(m: int) -> list:
-    """Group sizes of the folding kernels that reduce m partials to one: small
-    groups while many remain (many threads, each folding a few), larger ones
-    as they thin out, the last group folding what is left."""
+    """Group sizes of the folding kernels that reduce m partials to one: groups
+    of up to 128 (a thread folds a group with its loads in a few batches), so
+    that 2^21 partials take three kernels (2^21 -> 16384 -> 128 -> 1); a group
+    size divides what is left, and the last group folds what remains."""
     plan = []
     while m > 1:
-        g = 16 if m > 65536 else (32 if m > 64 else m)
-        if m % g:
-            g = m
+        g = m if m <= 128 else next((d for d in (128, 64, 32, 16, 8, 4, 2) if m % d == 0), m)
         plan.append(g)
         m //= g
     return plan
@@ -255,11 +254,11 @@ def compile_pipeline(kind: str, d: Derivation, n: int):
     out = []
     for name, ph, ins in lower(kind, d, n):
         tag = f"{kind}_{name}_" + "_".join(str(a) for r in d.rules for a in r.args)
-        k = compile_cuda(("x" + tag).replace("-", "_"), ph, ins, unroll=4 if name == "partials" else 16)
+        k = compile_cuda(("x" + tag).replace("-", "_"), ph, ins, unroll=4 if name == "partials" else 64)
         grid, block = k.default_launch()
-        if name.startswith("fold") and name != "partials":
+        if name.startswith("fold") and name != "partials":  # a thread per group, blocks of 64 over many SMs
             rows = ph.type.n if isinstance(ph.type, P.Arr) else 1
-            block = min(256, rows) if rows > 1 else 1
+            block = min(64, rows) if rows > 1 else 1
             grid = max(1, rows // block) if rows > 1 else 1
         out.append((k, grid, block))
     return out

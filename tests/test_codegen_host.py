@@ -373,7 +373,8 @@ def test_derived_pipelines_match_oracle(kind, tm, V):
     for grp in RW.fold_plan(len(vals)):  # the derivation's folding stages, in order
         vals = [oracle_fold(r) for r in c1.split(grp, vals)]
     assert len(vals) == 1 and bits(cur[0])[0] == bits(vals)[0]
-    assert RW.fold_plan(1 << 19) == [16, 32, 32, 32] and RW.fold_plan(96) == [32, 3]
+    assert RW.fold_plan(1 << 19) == [128, 128, 32] and RW.fold_plan(96) == [96]
+    assert RW.fold_plan(1 << 21) == [128, 128, 128] and RW.fold_plan(3 * 257) == [3 * 257]
 
 
 def test_gemv_backward_programs_match_the_library_trees():
