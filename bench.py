@@ -912,7 +912,7 @@ def codegen_workload(args, device, dist):
 
     folds, left = [], m1  # the folding stages of the 2M lane partials
     for grp in RW.fold_plan(m1):
-        ph = PR.fold_all(left) if grp == left else PR.fold_rows(left // grp, grp)
+        ph = PR.fold_all(left) if grp == left else PR.fold_cols(left // grp, grp)
         folds.append((G.compile_cuda(f"gen_dot_fold_{left}_{grp}", *ph, unroll=64), left // grp))
         left //= grp
     fold_bufs = [torch.empty(max(cnt, 1), device=device) for _, cnt in folds]

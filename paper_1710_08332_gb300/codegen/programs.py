@@ -101,6 +101,15 @@ def fold_rows(M: int, T: int):
     return P.mapGlobal(lambda r: P.reduceSeq(lambda v, acc: P.add(acc, v), 0.0, r), P.split(T, p)), [p]
 
 
+def fold_cols(rows: int, g: int):
+    """A folding kernel over strided groups: rows outputs, output j the fold of
+    p[j], p[rows + j], .., p[(g - 1) rows + j] in that order (the transpose of
+    split rows: consecutive threads read consecutive partials)."""
+    p = P.inp("p", P.arr(rows * g, P.F32))
+    return P.mapGlobal(lambda col: P.reduceSeq(lambda v, acc: P.add(acc, v), 0.0, col),
+                       P.transpose(P.split(rows, p))), [p]
+
+
 def dot_K1(n: int):
     """The single-thread dot of Section 2.2 (one kernel, one thread)."""
     x, y = P.inp("x", P.arr(n, P.F32)), P.inp("y", P.arr(n, P.F32))

@@ -208,7 +208,7 @@ def lower(kind: str, d: Derivation, n: int):
             ph, i2 = PR.fold_all(left)
             kernels.append((f"fold{left}", ph, i2))
         else:
-            ph, i2 = PR.fold_rows(left // grp, grp)
+            ph, i2 = PR.fold_cols(left // grp, grp)
             kernels.append((f"fold{grp}", ph, i2))
         left //= grp
     return kernels
@@ -218,7 +218,9 @@ def fold_plan(m: int) -> list:
     """Group sizes of the folding kernels that reduce m partials to one: groups
     of up to 128 (a thread folds a group with its loads in a few batches), so
     that 2^21 partials take three kernels (2^21 -> 16384 -> 128 -> 1); a group
-    size divides what is left, and the last group folds what remains."""
+    size divides what is left, and the last group folds what remains. A
+    stage's groups are strided (fold_cols): output j folds partials j,
+    j + rows, .. so that the threads' loads are coalesced."""
     plan = []
     while m > 1:
         g = m if m <= 128 else next((d for d in (128, 64, 32, 16, 8, 4, 2) if m % d == 0), m)

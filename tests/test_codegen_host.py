@@ -357,7 +357,7 @@ def test_derived_pipelines_match_oracle(kind, tm, V):
         out = np.zeros(count, np.float32)
         f.run(*cur, out, *f.temps_like())
         cur = [out]
-    # the oracle's tree: lane folds per thread column, then the stages of 64 / 256 / all
+    # the oracle's tree: lane folds per thread column, then the fold plan's strided stages
     if kind == "dot":
         items = c1.zip_(list(x), list(y)) if V == 1 else c1.zip_(c1.asVector(V, list(x)), c1.asVector(V, list(y)))
         g = (lambda p: F.mul(p[0], p[1])) if V == 1 else (lambda p: vmul(p[0], p[1]))
@@ -371,7 +371,8 @@ def test_derived_pipelines_match_oracle(kind, tm, V):
         c1.split(s // V, items)))
     vals = parts if V == 1 else c1.asScalar(parts)
     for grp in RW.fold_plan(len(vals)):  # the derivation's folding stages, in order
-        vals = [oracle_fold(r) for r in c1.split(grp, vals)]
+        rows = len(vals) // grp  # output j folds vals[j], vals[rows + j], ... (strided groups)
+        vals = [oracle_fold(vals[j::rows]) for j in range(rows)]
     assert len(vals) == 1 and bits(cur[0])[0] == bits(vals)[0]
     assert RW.fold_plan(1 << 19) == [128, 128, 32] and RW.fold_plan(96) == [96]
     assert RW.fold_plan(1 << 21) == [128, 128, 128] and RW.fold_plan(3 * 257) == [3 * 257]
