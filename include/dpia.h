@@ -248,8 +248,9 @@ enum { DPIA_CONTRACT_OFF = 0, DPIA_CONTRACT_FMA = 1 };
  * tile, each staging 128 rows of every 256-row block of A and half of B's
  * columns, one M=256 MMA per block across the pair (cta_group::2); tile_m 512
  * gives each SM two blocks that share its half of B. 0: a pair with 512-row
- * tiles when M >= 512, else one CTA. The value of C does not depend on it.
- * The FP32 fold ignores grid and cluster.
+ * tiles when M >= 512 and pairs fit on the device, else one CTA. cluster = 2
+ * where no CTA pair fits returns DPIA_ERR_CUDA. The value of C does not
+ * depend on it. The FP32 fold ignores grid and cluster.
  */
 typedef struct {
   int32_t contract;
