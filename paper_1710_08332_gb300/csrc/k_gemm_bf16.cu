@@ -16,9 +16,8 @@
 //                 same B slice, and commits each stage back to the producer
 //                 and each finished tile to the epilogue;
 //   warps 2..9 -- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 of
-//                 accumulator (w-2)/4 with tcgen05.ld, then f32 stores.
-//                 (Sixteen epilogue warps, two per lane quarter and
-//                 accumulator, measured no faster at 4096^3.)
+//                 accumulator (w-2)/4 with tcgen05.ld and stores them as f32
+//                 (below).
 // Two M=128 products per B slice halve the operand bytes per flop against a
 // 128-row tile. BN (<= 256, a multiple of 32) is chosen per shape so that the
 // tiles fill whole waves of SMs. The producer keeps prefetching the next tile
@@ -34,10 +33,10 @@
 // default when M >= 512. The epilogue of both kernels stages each warp's
 // 32 x 32 block in shared memory and hands it to the TMA engine, which writes
 // whole 128-byte rows of C; writing C is the part of a tile the MMAs cannot
-// overlap (both accumulators fill tensor memory). Measured at 4096^3: 512-row pairs
-// 1.58-1.60 PFLOP/s, one SM per tile 1.49-1.56, 256-row pairs 1.18-1.28; B
-// shared by TMA multicast within clusters of one-SM CTAs measured slower
-// and was not kept.
+// overlap (both accumulators fill tensor memory). Measured at 4096^3, each
+// launch alone: 512-row pairs 1.60 PFLOP/s, one SM per tile 1.53-1.60,
+// 256-row pairs 1.20-1.29; B shared by TMA multicast within clusters of
+// one-SM CTAs measured slower and was not kept.
 //
 // Every mbarrier wait is bounded by the global timer. A wait that runs out
 // sets the CTA's abort flag and the library's device status word
@@ -771,8 +770,6 @@ bool make_map_mn3d(CUtensorMap *map, const void *base, int64_t K, int64_t M, int
 }
 
 }  // namespace
-
-int resident_blocks(const void *kernel, int threads);
 
 // Tile width: the BN in {256, 224, ..., 128} whose tiles (tile_m rows) fill
 // the fewest waves of the slots that run at once (CTAs, or CTA pairs),
