@@ -467,3 +467,23 @@ def test_compensated_pipeline_matches_oracle(tm):
     G.compile_c("kf", e, ins).run(grp, out)
     final = c1.reduce_(lambda pr, a: c1.kahan_combine(F, a, pr), (F.zero, F.zero), merged)
     assert bits(out)[0] == bits([final[0]])[0]
+
+
+@pytest.mark.parametrize("rows,g", [(1, 7), (5, 128), (64, 3), (300, 32)])
+def test_fold_cols_folds_strided_groups_in_order(rows, g):
+    """fold_cols(rows, g): output j is the sequential f32 fold of p[j],
+    p[rows + j], ..., p[(g - 1) rows + j] from +0 -- the transpose of split
+    rows -- and its threads' reads are p[i], p[i + 1], ... for consecutive j."""
+    p = np.random.default_rng(rows * 1000 + g).standard_normal(rows * g).astype(np.float32)
+    out = np.zeros(rows, np.float32)
+    e, ins = PR.fold_cols(rows, g)
+    G.compile_c("fcols", e, ins).run(p, out)
+    want = np.zeros(rows, np.float32)
+    for j in range(rows):
+        acc = np.float32(0.0)
+        for k in range(g):
+            acc = np.float32(acc + p[k * rows + j])
+        want[j] = acc
+    assert out.tobytes() == want.tobytes()
+    src = B.cuda_source(E.generate("fcols", e, ins, backend="cuda"))
+    assert "blockIdx" in src and "__global__" in src
