@@ -140,6 +140,58 @@ def tune_reduce(op: str, x, y=None, candidates=None, reps: int = 10, use_cache: 
     return best, timings
 
 
+def gemm_bf16_candidates(M: int):
+    """(cluster, tile_m, tile_n) choices of the BF16 GEMM: one CTA per 256-row
+    tile or a CTA pair per 256- or 512-row tile, each with the width picked
+    per shape (tile_n 0) or a fixed width."""
+    widths = (0, 128, 192, 224, 256)
+    cands = [(1, 0, w) for w in widths] + [(2, 256, w) for w in widths]
+    if M > 256:
+        cands += [(2, 512, w) for w in widths]
+    return cands
+
+
+def tune_gemm_bf16(M: int, N: int, K: int, transA: int = 0, transB: int = 0, candidates=None,
+                   reps: int = 5, use_cache: bool = True, device="cuda"):
+    """Fastest (cluster, tile_m, tile_n) of dpia_gemm_bf16 for this shape and
+    operand layout, timed on random bf16 operands (L2 warm; the choice only
+    moves work between SMs, never the value of C).
+
+    Returns ((cluster, tile_m, tile_n), {label: ms}); pass the first as the
+    keyword arguments cluster=, tile_m=, tile_n= of ops.dpia_gemm_bf16.
+    """
+    dev = torch.device(device)
+    key = f"gemm_bf16/{M}x{N}x{K}/t{transA}{transB}/{torch.cuda.get_device_name(dev)}"
+    if use_cache:
+        with _lock:
+            hit = _load().get(key)
+        if hit:
+            return tuple(hit["choice"]), hit.get("timings", {})
+    g = torch.Generator(device=dev).manual_seed(0)
+    pad8 = lambda v: (v + 7) // 8 * 8  # TMA wants rows 16 bytes apart
+    ra, ca = (K, M) if transA else (M, K)
+    rb, cb = (N, K) if transB else (K, N)
+    A = torch.randn(ra, pad8(ca), generator=g, device=dev).to(torch.bfloat16)
+    B = torch.randn(rb, pad8(cb), generator=g, device=dev).to(torch.bfloat16)
+    C = torch.empty(M, N, device=dev)
+    lda, ldb = A.shape[1], B.shape[1]
+    timings = {}
+    best, best_ms = None, float("inf")
+    for cl, tm, tn in candidates or gemm_bf16_candidates(M):
+        fn = lambda: ops.dpia_gemm_bf16(A, B, C, M, N, K, lda, ldb, N, transA, transB, tile_n=tn, cluster=cl,
+                                        tile_m=tm)
+        ms = time_call(fn, reps=reps)
+        timings[f"cluster{cl}:m{tm or 256}:n{tn or 'auto'}"] = ms
+        if ms < best_ms:
+            best, best_ms = (cl, tm, tn), ms
+    if use_cache:
+        with _lock:
+            d = _load()
+            d[key] = {"choice": list(best), "timings": timings}
+            _save(d)
+    return best, timings
+
+
 def _label(st: ReduceStrategy) -> str:
     return (f"{st.map_level}:s{st.split}:T{st.threads}:V{st.vec}:{st.second}"
             f"{st.threads2 if st.second == 'tree' else ''}{':local' if st.stage == 'local' else ''}")
