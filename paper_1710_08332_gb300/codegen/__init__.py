@@ -12,5 +12,6 @@ from .phrase import (F32, I32, I64, Arr, Num, PairT, VecT, abs_, add, arr, asSca
                      lit, mapGlobal, mapLocal, mapSeq, mapWorkgroup, mul, reduceSeq, snd, split, sub, to_global,
                      to_local, to_private, transpose, vlit, zip_)
 from .translate import TranslationError
+from .typecheck import TypeCheckError
 
 __all__ = [n for n in dir() if not n.startswith("_")]

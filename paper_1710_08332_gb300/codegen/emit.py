@@ -523,8 +523,10 @@ def generate(name: str, expr: P.Phrase, inputs: list, backend: str = "cuda", unr
     comm, out = T.translate(expr, "out")
     temps = T.hoist(comm)
     from .check import check
+    from .typecheck import typecheck
 
-    check(comm)  # no two iterations of a parallel loop write one place
+    typecheck(comm, out)  # phrase types, passive parallel bodies, legal nesting (race-free by construction)
+    check(comm)  # and, on the index arithmetic: no two iterations of a parallel loop write one place
     em = Emitter(backend, inputs, out, temps, unroll)
     em.emit(comm, 1, ())
     params = []

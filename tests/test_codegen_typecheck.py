@@ -1,0 +1,171 @@
+"""The type checker of translated phrases (no GPU): every program the
+generator emits is well typed, and planted mistakes -- a type mismatch, a
+parallel loop writing outside its own element acceptor, reading what it
+writes, an illegal nesting -- are rejected. The write-race checker, which
+works on the index arithmetic instead of the types, rejects the same races."""
+import pytest
+
+from paper_1710_08332_gb300.codegen import check as CK
+from paper_1710_08332_gb300.codegen import phrase as P
+from paper_1710_08332_gb300.codegen import programs as PR
+from paper_1710_08332_gb300.codegen import rewrite as RW
+from paper_1710_08332_gb300.codegen import translate as T
+from paper_1710_08332_gb300.codegen import typecheck as TC
+
+PROGRAMS = {
+    "dot_partials": lambda: PR.dot_partials(1 << 12, 1 << 10, 64),
+    "dot_partials_contig": lambda: PR.dot_partials(1 << 12, 1 << 10, 64, thread_map="contig"),
+    "dot_partials_V4": lambda: PR.dot_partials(1 << 12, 1 << 10, 64, V=4),
+    "asum_partials_V4": lambda: PR.asum_partials(1 << 12, 1 << 10, 64, V=4),
+    "fold_all": lambda: PR.fold_all(256),
+    "fold_rows": lambda: PR.fold_rows(64, 32),
+    "fold_cols": lambda: PR.fold_cols(64, 32),
+    "scal": lambda: PR.scal(1024, 1.5),
+    "scal_V4": lambda: PR.scal(1024, 1.5, V=4),
+    "gemv_partials": lambda: PR.gemv_partials(64, 256, 32),
+    "gemv_partials_V4": lambda: PR.gemv_partials(64, 256, 16, V=4),
+    "dot_K1": lambda: PR.dot_K1(512),
+    "gemv_bwd_dA": lambda: PR.gemv_bwd_dA(64, 128),
+    "gemv_bwd_dx_partials": lambda: PR.gemv_bwd_dx_partials(64, 128, 16),
+    "gemv_bwd_dx_fold": lambda: PR.gemv_bwd_dx_fold(4, 128),
+    "dot_partials_kahan": lambda: PR.dot_partials_kahan(1 << 12, 1 << 10, 64),
+    "fold_pairs_rows": lambda: PR.fold_pairs_rows(16, 8),
+    "fold_pairs_all": lambda: PR.fold_pairs_all(16),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PROGRAMS))
+def test_every_program_is_well_typed(name):
+    e, _ = PROGRAMS[name]()
+    c, out = T.translate(e)
+    TC.typecheck(c, out)
+
+
+def test_temporaries_and_explored_pipelines_are_well_typed():
+    n = 1 << 14
+    x = P.inp("x", P.arr(n, P.F32))
+    for space, wrap in (("local", P.to_local), ("private", P.to_private), ("global", P.to_global)):
+        e = P.join(P.mapWorkgroup(lambda ch: P.mapLocal(
+            lambda col: P.reduceSeq(lambda v, a: P.add(a, v), 0.0, col),
+            P.split(8, wrap(P.mapLocal(lambda v: P.mul(v, v), ch)))), P.split(1024, x)))
+        c, out = T.translate(e)
+        TC.typecheck(c, out)
+    for d in RW.derivations(n, splits=(1 << 12,), threads=(64,), widths=(1, 4)):
+        for _, ph, _ in RW.lower("dot", d, n):
+            c, out = T.translate(ph)
+            TC.typecheck(c, out)
+
+
+F = P.F32
+
+
+def _out(t, name="out"):
+    return T.AOut(name, t)
+
+
+def _lit():
+    return P.Lit(1.0)
+
+
+def test_assignment_of_the_wrong_type():
+    with pytest.raises(TC.TypeCheckError, match="types differ"):
+        TC.typecheck(T.Assign(_out(P.Arr(4, F)), _lit()))
+    with pytest.raises(TC.TypeCheckError, match="types differ"):
+        TC.typecheck(T.Assign(_out(F), P.Lit(1.0, P.I32)))
+
+
+def test_views_have_their_types():
+    o = _out(P.Arr(2, P.Arr(4, F)))
+    assert TC.acc_type(T.ASplit(4, o)) == P.Arr(8, F)
+    assert TC.acc_type(T.AJoin(4, _out(P.Arr(8, F)))) == P.Arr(2, P.Arr(4, F))
+    assert TC.acc_type(T.ATranspose(o)) == P.Arr(4, P.Arr(2, F))
+    assert TC.acc_type(T.AAsScalar(4, _out(P.Arr(8, F)))) == P.Arr(2, P.VecT(4, F))
+    assert TC.acc_type(T.AProj(1, _out(P.PairT(F, P.I32)))) == P.I32
+    with pytest.raises(TC.TypeCheckError, match="split acceptor"):
+        TC.acc_type(T.ASplit(3, o))
+    with pytest.raises(TC.TypeCheckError, match="join acceptor"):
+        TC.acc_type(T.AJoin(3, _out(P.Arr(8, F))))
+    with pytest.raises(TC.TypeCheckError, match="element acceptor"):
+        TC.acc_type(T.AIdx(_out(F), T.IConst(0)))
+
+
+def test_a_parallel_loop_writes_only_its_own_element():
+    i, j = T.IVar("i1"), T.IVar("i2")
+    # each iteration writes element i of out, through a split view: well typed
+    ok = T.For(i, 8, "global", T.Assign(T.AIdx(T.ASplit(4, _out(P.Arr(2, P.Arr(4, F)))), i), _lit()))
+    TC.typecheck(ok)
+    CK.check(ok)
+    # every iteration writes the same scalar
+    shared = T.For(i, 8, "global", T.Assign(_out(F, "s"), _lit()))
+    with pytest.raises(TC.TypeCheckError, match="outside its own element acceptor"):
+        TC.typecheck(shared)
+    with pytest.raises(CK.RaceError):
+        CK.check(shared)
+    # every iteration writes element j of a sequential loop inside it
+    wrong = T.For(i, 8, "global", T.For(j, 4, "seq", T.Assign(T.AIdx(_out(P.Arr(4, F)), j), _lit())))
+    with pytest.raises(TC.TypeCheckError, match="outside its own element acceptor"):
+        TC.typecheck(wrong)
+    with pytest.raises(CK.RaceError):
+        CK.check(wrong)
+    # a workgroup loop's local loop writes inside the workgroup's element: both own it
+    nested = T.For(i, 4, "workgroup", T.For(j, 8, "local", T.Assign(
+        T.AIdx(T.AIdx(_out(P.Arr(4, P.Arr(8, F))), i), j), _lit())))
+    TC.typecheck(nested)
+    # the local loop forgets its index: every thread of a workgroup writes one element
+    lost = T.For(i, 4, "workgroup", T.For(j, 8, "local", T.Assign(T.AIdx(_out(P.Arr(4, F)), i), _lit())))
+    with pytest.raises(TC.TypeCheckError, match="local loop over i2"):
+        TC.typecheck(lost)
+    with pytest.raises(CK.RaceError):
+        CK.check(lost)
+
+
+def test_iteration_temporaries_are_private_to_the_iteration():
+    i, r = T.IVar("i1"), T.IVar("r2")
+    t = T.Temp("t3", F, "private")
+    acc = T.AOut(t.name, F, t)
+    tv = P.Ident(t.name, F, temp="private")
+    body = T.New(t, T.Seq([T.Assign(acc, _lit()),
+                           T.For(r, 4, "seq", T.Assign(acc, P.Bin("+", tv, _lit()))),
+                           T.Assign(T.AIdx(_out(P.Arr(8, F)), i), tv)]))
+    TC.typecheck(T.For(i, 8, "global", body))
+    # the same accumulator declared outside the parallel loop is shared by its iterations
+    hoisted = T.New(t, T.For(i, 8, "global", T.Seq([
+        T.Assign(acc, _lit()), T.Assign(T.AIdx(_out(P.Arr(8, F)), i), tv)])))
+    with pytest.raises(TC.TypeCheckError):
+        TC.typecheck(hoisted)
+
+
+def test_a_parallel_loop_may_not_read_what_it_writes():
+    i = T.IVar("i1")
+    t = T.Temp("t2", P.Arr(8, F), "global")
+    tv = P.Ident(t.name, t.type, temp="global")
+    # iteration i writes t[i] and reads t[(i + 1) % 8]: the acceptor and the expression of t interfere
+    c = T.New(t, T.For(i, 8, "global", T.Assign(T.AIdx(T.AOut(t.name, t.type, t), i),
+                                                P.Idx(tv, T.IOp("%", T.IOp("+", i, T.IConst(1)), T.IConst(8))))))
+    with pytest.raises(TC.TypeCheckError, match="interference"):
+        TC.typecheck(c)
+    CK.check(c)  # the write pattern alone is disjoint: only the types see the conflict
+    # writing t in one parallel loop and reading it in the next is fine
+    j = T.IVar("i3")
+    ok = T.New(t, T.Seq([T.For(i, 8, "global", T.Assign(T.AIdx(T.AOut(t.name, t.type, t), i), _lit())),
+                         T.For(j, 8, "global", T.Assign(T.AIdx(_out(P.Arr(8, F)), j), P.Idx(tv, j)))]))
+    TC.typecheck(ok)
+
+
+@pytest.mark.parametrize("outer,inner", [("local", "workgroup"), ("workgroup", "workgroup"),
+                                         ("global", "local"), ("seq", "global"), ("seq", "local"),
+                                         ("local", "local")])
+def test_illegal_nestings(outer, inner):
+    i, j = T.IVar("i1"), T.IVar("i2")
+    out = _out(P.Arr(4, P.Arr(4, F)))
+    c = T.For(i, 4, outer, T.For(j, 4, inner, T.Assign(T.AIdx(T.AIdx(out, i), j), _lit())))
+    with pytest.raises(TC.TypeCheckError, match="strictly finer"):
+        TC.typecheck(c)
+
+
+@pytest.mark.parametrize("outer,inner", [("workgroup", "local"), ("workgroup", "seq"), ("local", "seq"),
+                                         ("global", "seq"), ("seq", "seq")])
+def test_legal_nestings(outer, inner):
+    i, j = T.IVar("i1"), T.IVar("i2")
+    out = _out(P.Arr(4, P.Arr(4, F)))
+    TC.typecheck(T.For(i, 4, outer, T.For(j, 4, inner, T.Assign(T.AIdx(T.AIdx(out, i), j), _lit()))))
