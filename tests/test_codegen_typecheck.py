@@ -169,3 +169,47 @@ def test_legal_nestings(outer, inner):
     i, j = T.IVar("i1"), T.IVar("i2")
     out = _out(P.Arr(4, P.Arr(4, F)))
     TC.typecheck(T.For(i, 4, outer, T.For(j, 4, inner, T.Assign(T.AIdx(T.AIdx(out, i), j), _lit()))))
+
+
+def _parallel_writes(c, par=(), out=None):
+    """(assignment, element acceptor) pairs whose element index is the variable
+    of an enclosing parallel loop."""
+    out = [] if out is None else out
+    if isinstance(c, T.Seq):
+        for x in c.cs:
+            _parallel_writes(x, par, out)
+    elif isinstance(c, T.New):
+        _parallel_writes(c.body, par, out)
+    elif isinstance(c, T.For):
+        _parallel_writes(c.body, par + ((c.var.name,) if c.level != "seq" else ()), out)
+    elif isinstance(c, T.Assign):
+        a = c.acc
+        while not isinstance(a, T.AOut):
+            if isinstance(a, T.AIdx) and isinstance(a.i, T.IVar) and a.i.name in par:
+                out.append((c, a))
+            a = a.acc
+    return out
+
+
+@pytest.mark.parametrize("name", sorted(PROGRAMS))
+def test_every_planted_shared_write_is_rejected(name):
+    """Mutation test: each element acceptor a parallel loop writes through,
+    in turn indexed by a constant instead of the loop's variable (so that all
+    iterations write one element), makes the program ill typed -- and racy
+    for the index-arithmetic checker too."""
+    e, _ = PROGRAMS[name]()
+    c, out = T.translate(e)
+    sites = _parallel_writes(c)
+    assert sites or name in ("fold_all", "fold_pairs_all", "dot_K1")
+    for _, a in sites:
+        keep = a.i
+        a.i = T.IConst(0)
+        try:
+            with pytest.raises(TC.TypeCheckError):
+                TC.typecheck(c, out)
+            with pytest.raises(CK.RaceError):
+                CK.check(c)
+        finally:
+            a.i = keep
+    TC.typecheck(c, out)
+    CK.check(c)
