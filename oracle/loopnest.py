@@ -2,7 +2,12 @@
 
 The shared object is built with the system C compiler at ``-O2
 -ffp-contract=off`` (no ``-ffast-math``, no ``-march``), so each float + and *
-is rounded separately on both x86-64 and AArch64 hosts.
+is rounded separately on both x86-64 and AArch64 hosts, and with ``-fopenmp``:
+the independent units of a strategy (chunks, rows, columns, GEMM entries, map
+elements) may run on several host threads, while every fold across units runs
+on one thread in the strategy's order, so results do not depend on the thread
+count. ``set_threads`` chooses it; the loader starts with every core this
+process may run on (``os.sched_getaffinity``).
 """
 from __future__ import annotations
 
@@ -17,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "loopnest.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle_loopnest.so")
-CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11", "-fopenmp"]
 
 _lock = threading.Lock()
 _lib = None
@@ -42,7 +47,21 @@ def lib():
         if _lib is None:
             _lib = ctypes.CDLL(build())
             _declare(_lib)
+            _lib.oracle_set_threads(len(os.sched_getaffinity(0)))
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Use ``n`` host threads for the per-unit loops; returns the previous count."""
+    L = lib()
+    old = L.oracle_threads()
+    if L.oracle_set_threads(int(n)) != 0:
+        raise ValueError(f"set_threads: bad thread count {n}")
+    return old
+
+
+def threads() -> int:
+    return lib().oracle_threads()
 
 
 _f = ctypes.POINTER(ctypes.c_float)
@@ -67,6 +86,14 @@ def _declare(L):
     L.oracle_gemv_bwd_dA_f32.restype = None
     L.oracle_gemm_f32_sample.argtypes = [_f, _f, _L, _L, _L, _L, _L, _I, _I, _I,
                                          _i64p, _L, _i64p, _L, _f]
+    L.oracle_lane_partials_f32.argtypes = [_I, _f, _f, _L, _L, _I, _I, _I, _I, _f]
+    L.oracle_lane_partials_f32.restype = ctypes.c_int
+    L.oracle_set_threads.argtypes = [_I]
+    L.oracle_set_threads.restype = ctypes.c_int
+    L.oracle_threads.argtypes = []
+    L.oracle_threads.restype = ctypes.c_int
+    L.oracle_max_threads.argtypes = []
+    L.oracle_max_threads.restype = ctypes.c_int
     for name in ("oracle_dot_f32", "oracle_asum_f32", "oracle_dot_f32_partials",
                  "oracle_dot_i32", "oracle_gemv_f32", "oracle_gemv_bwd_dx_f32",
                  "oracle_gemm_f32_sample"):
@@ -115,6 +142,20 @@ def dot_f32_partials(x, y, st) -> np.ndarray:
     s, T, V, inter, _, _, _, pad = _st_args(st)
     _check(lib().oracle_dot_f32_partials(_fp(x), _fp(y), x.size, s, T, V, inter, pad, _fp(out)),
            "dot_f32_partials")
+    return out
+
+
+def lane_partials_f32(kind, x, y, st) -> np.ndarray:
+    """The un-reduced first level of Section 6's kernel: for chunk c, thread t
+    and lane v (at index (c*T + t)*V + v) the fold of that lane's items from +0
+    (kind "dot": x*y; "asum": |x|). st.pad pads a ragged last chunk."""
+    x = _c32(x)
+    y = _c32(y) if y is not None else None
+    C = -(-x.size // st.s)
+    out = np.zeros(C * st.T * st.V, np.float32)
+    s, T, V, inter, _, _, _, pad = _st_args(st)
+    _check(lib().oracle_lane_partials_f32({"dot": 0, "asum": 1}[kind], _fp(x), _fp(y), x.size, s, T, V, inter,
+                                          pad, _fp(out)), "lane_partials_f32")
     return out
 
 

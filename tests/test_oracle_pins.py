@@ -513,3 +513,79 @@ def test_gradient_adjoints_match_finite_differences():
     gA, gB = grads.gemm_adjoint(A, B, dC)
     assert np.allclose(gA, grads.central_fd(grads.gemm_fwd, [A, B], 0, dC), atol=1e-6)
     assert np.allclose(gB, grads.central_fd(grads.gemm_fwd, [A, B], 1, dC), atol=1e-6)
+
+
+@pytest.mark.parametrize("st", [P.Strategy(s=256, T=32, V=4), P.Strategy(s=512, T=64, V=2, thread_map="contig"),
+                                P.Strategy(s=1024, T=128, V=4, second="tree", T2=64, pad=True),
+                                P.Strategy(s=256, T=32, V=4, compensated=True, pad=True),
+                                P.Strategy(s=512, T=64, V=1, second="tree", T2=32, compensated=True)],
+                         ids=["plain", "contig", "tree-pad", "kahan-pad", "kahan-tree"])
+def test_loopnest_threads_do_not_change_bits(st):
+    """c2 with its units (chunks, rows, columns, GEMM entries) on several host
+    threads equals c2 on one thread bit for bit: every fold across units still
+    runs on one thread in the strategy's order."""
+    rng = np.random.default_rng(21)
+    n = 64 * st.s - (37 if st.pad else 0)
+    x = rng.uniform(-1, 1, n).astype(np.float32)
+    y = rng.uniform(-1, 1, n).astype(np.float32)
+    xi = rng.integers(-100, 101, n).astype(np.int32)
+    A = rng.standard_normal((40, 300)).astype(np.float32)
+    B = rng.standard_normal((300, 50)).astype(np.float32)
+    xv = rng.uniform(-1, 1, 300).astype(np.float32)
+    dy = rng.uniform(-1, 1, 40).astype(np.float32)
+    gst = P.Strategy(s=64, T=8, V=4, pad=True, compensated=st.compensated)
+
+    def run():
+        return [loopnest.dot_f32(x, y, st).tobytes(), loopnest.asum_f32(x, st).tobytes(),
+                loopnest.dot_f32_partials(x, y, P.Strategy(s=st.s, T=st.T, V=st.V, thread_map=st.thread_map,
+                                                          pad=st.pad)).tobytes(),
+                loopnest.dot_i32(xi, xi, st), loopnest.gemv_f32(A, xv, gst).tobytes(),
+                loopnest.gemv_bwd_dx_f32(A, dy, 7).tobytes(), loopnest.gemv_bwd_dA_f32(xv, dy).tobytes(),
+                loopnest.gemm_f32(A, B).tobytes(), loopnest.scal_f32(1.5, x).tobytes(),
+                b"".join(a.tobytes() for a in loopnest.dot_bwd_f32(x, y, 0.75))]
+
+    old = loopnest.set_threads(1)
+    try:
+        one = run()
+        loopnest.set_threads(8)
+        many = run()
+    finally:
+        loopnest.set_threads(old)
+    assert one == many
+
+
+@pytest.mark.parametrize("kind", ["dot", "asum"])
+@pytest.mark.parametrize("tm,V", [("interleaved", 1), ("interleaved", 4), ("contig", 2), ("contig", 4)])
+def test_lane_partials_equal_pattern_evaluator(kind, tm, V):
+    """c2's un-reduced lane partials (Section 6's kernel stores them) equal c1's
+    join (mapWorkgroup (mapLocal (reduce lanewise))) over asVector V, and
+    folding each thread's lanes in lane order and reducing the threads by the
+    block tree gives c2's chunk partials."""
+    rng = np.random.default_rng(77)
+    n, s, T = 4096, 512, 16
+    x = rng.uniform(-1, 1, n).astype(np.float32)
+    y = rng.uniform(-1, 1, n).astype(np.float32)
+    st = P.Strategy(s=s, T=T, V=V, thread_map=tm)
+    got = loopnest.lane_partials_f32(kind, x, y if kind == "dot" else None, st)
+    F = P.F32
+    zero = (F.zero,) * V
+    if kind == "dot":
+        items = P.zip_(P.asVector(V, list(x)), P.asVector(V, list(y)))
+        g = lambda p: tuple(F.mul(a, b) for a, b in zip(p[0], p[1]))
+    else:
+        items = P.asVector(V, list(x))
+        g = lambda v: tuple(F.abs(a) for a in v)
+    cols = (lambda ch: P.transpose(P.split(T, ch))) if tm == "interleaved" else (lambda ch: P.split(len(ch) // T, ch))
+    want = P.asScalar(P.join(P.mapWorkgroup(
+        lambda ch: P.mapLocal(lambda col: P.reduce_(lambda v, a: tuple(F.add(p, q) for p, q in zip(a, g(v))),
+                                                     zero, col), cols(ch)),
+        P.split(s // V, items))))
+    assert np.asarray(want, np.float32).tobytes() == got.tobytes()
+    if kind == "dot":
+        lanes = got.reshape(n // s, T, V)
+        chunk = []
+        for c in range(n // s):
+            th = [P.reduce_(lambda v, a: F.add(a, v), F.zero, list(lanes[c, t])) for t in range(T)]
+            chunk.append(P.halving_tree(P.join([[P.halving_tree(g_, F.add)] for g_ in P.split(min(32, T), th)]),
+                                        F.add))
+        assert np.asarray(chunk, np.float32).tobytes() == loopnest.dot_f32_partials(x, y, st).tobytes()
