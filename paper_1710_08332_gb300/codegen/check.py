@@ -13,6 +13,8 @@ write the same place. Offsets are linear forms in the loop variables
 (quotient and remainder by the same divisor are recombined first); a form is
 injective on its box when its coefficients, in increasing order, each exceed
 the largest value the smaller terms can add up to (a mixed-radix numbering).
+Every write, parallel or not, must also stay inside its place: the largest
+offset over all loop variables is below the number of elements written into.
 """
 from __future__ import annotations
 
@@ -142,8 +144,25 @@ def injective(form: dict, ranges: dict) -> bool:
     return True
 
 
+def place_size(acc) -> int:
+    """Numbers in the place an acceptor writes into (an output, or a temporary
+    with one slice per iteration of the parallel loops it is hoisted out of)."""
+    while not isinstance(acc, T.AOut):
+        acc = acc.acc
+    if not isinstance(acc.type, (P.Arr, P.PairT)) and not P.is_scalar(acc.type):
+        raise RaceError(f"cannot size {acc.name} of type {acc.type}")
+    n = P.scalar_count(acc.type) if not isinstance(acc.type, P.VecT) else 1
+    if isinstance(P.base_elem(acc.type), P.VecT):
+        n = max(1, n // P.base_elem(acc.type).n)  # vector outputs are addressed by vector
+    if acc.temp is not None and acc.temp.space == "global":
+        for _, k in acc.temp.hoist:
+            n *= k
+    return n
+
+
 def check(comm) -> None:
-    """Raise RaceError if two iterations of a parallel loop may write one place."""
+    """Raise RaceError if two iterations of a parallel loop may write one place,
+    or if a write may fall outside the place it writes into."""
     _walk(comm, [], {})
 
 
@@ -158,7 +177,14 @@ def _walk(c, loops, declared):
     elif isinstance(c, T.For):
         _walk(c.body, loops + [c], declared)
     elif isinstance(c, T.Assign):
+        from .typecheck import index_max
+
         name, temp, off = target(c.acc, [])
+        top = index_max(off, {L.var.name: L.n for L in loops})
+        size = place_size(c.acc)
+        if top is None or top >= size:
+            raise RaceError(f"a write to {name} may fall outside its {size} elements "
+                            f"(offset {'unbounded' if top is None else f'up to {top}'})")
         for k, L in enumerate(loops):
             if L.level == "seq":
                 continue

@@ -13,7 +13,9 @@ parallel loop over i receives the i-th element acceptor of its output and may
 write only through it (or through temporaries it declares itself); every
 other identifier it uses must be passive, i.e. only read. Because every view
 re-indexes injectively, the i-th elements of an acceptor are disjoint for
-distinct i, so a program that checks is race-free by construction. Further:
+distinct i, so a program that checks is race-free by construction. Every
+index, written or read, is bounded by the length of the array it indexes
+(a loop's trip count may not exceed it). Further:
 the body may not read a temporary that the same parallel loop writes (the
 acceptor of a variable and its expression would interfere), and parallel
 loops nest at strictly finer levels (workgroup > local; global and local
@@ -71,6 +73,57 @@ def acc_type(a: T.Acc):
             raise TypeCheckError(f"asScalar acceptor of width {a.V} over acc[{t}]")
         return P.Arr(t.n // a.V, P.VecT(a.V, t.elem))
     raise TypeCheckError(f"unknown acceptor {type(a).__name__}")
+
+
+def index_max(i, trips: dict):
+    """The largest value the index expression takes while every loop variable v
+    runs over 0..trips[v]-1, or None if it cannot be bounded (an unknown
+    variable, a negative constant or an unsupported operation)."""
+    if isinstance(i, T.IConst):
+        return i.v if i.v >= 0 else None
+    if isinstance(i, T.IVar):
+        n = trips.get(i.name)
+        return None if n is None else max(n - 1, 0)
+    if isinstance(i, T.IOp):
+        a = index_max(i.a, trips)
+        if i.op == "%" and isinstance(i.b, T.IConst) and i.b.v > 0:
+            return min(a, i.b.v - 1) if a is not None else i.b.v - 1
+        b = index_max(i.b, trips)
+        if a is None or b is None:
+            return None
+        if i.op == "+":
+            return a + b
+        if i.op == "*":
+            return a * b
+        if i.op == "/" and isinstance(i.b, T.IConst) and i.b.v > 0:
+            return a // i.b.v
+    return None
+
+
+def _check_bound(i, n: int, trips: dict, what: str):
+    m = index_max(i, trips)
+    if m is None:
+        raise TypeCheckError(f"{what}: cannot bound the index by the loops around it")
+    if m >= n:
+        raise TypeCheckError(f"{what}: the index reaches {m}, past the {n} elements of the array "
+                             f"(a loop runs longer than the array it indexes)")
+
+
+def _acc_bounds(a: T.Acc, trips: dict):
+    """Every element acceptor on the way to the root indexes within its array."""
+    while not isinstance(a, T.AOut):
+        if isinstance(a, T.AIdx):
+            t = acc_type(a.acc)
+            _check_bound(a.i, t.n, trips, f"write through element acceptor of acc[{t}]")
+        a = a.acc
+
+
+def _exp_bounds(e: P.Phrase, trips: dict):
+    """Every element read (Idx) indexes within its array."""
+    if isinstance(e, P.Idx):
+        _check_bound(e.i, e.e.type.n, trips, f"read of an element of exp[{e.e.type}]")
+    for child in e.children():
+        _exp_bounds(child, trips)
 
 
 def _root(a: T.Acc) -> T.AOut:
@@ -133,16 +186,16 @@ class _Frame:
         self.written = set()  # temporaries declared outside and written inside
 
 
-def _check(c: T.Comm, frames: list, levels: list):
+def _check(c: T.Comm, frames: list, levels: list, trips: dict, out: T.AOut | None):
     if isinstance(c, T.Seq):
         for x in c.cs:
-            _check(x, frames, levels)
+            _check(x, frames, levels, trips, out)
     elif isinstance(c, T.New):
         if c.temp.space not in P.SPACES:
             raise TypeCheckError(f"temporary {c.temp.name} in unknown address space {c.temp.space}")
         for f in frames:  # declared inside every enclosing parallel loop: each iteration's own
             f.local.add(c.temp.name)
-        _check(c.body, frames, levels)
+        _check(c.body, frames, levels, trips, out)
     elif isinstance(c, T.For):
         if not isinstance(c.n, int) or c.n < 0:
             raise TypeCheckError(f"loop over {c.var.name} with trip count {c.n!r}")
@@ -153,9 +206,10 @@ def _check(c: T.Comm, frames: list, levels: list):
             if last in ("global", "local", "seq") or (last == "workgroup" and c.level != "local"):
                 raise TypeCheckError(f"a {c.level} loop inside a {last} loop (parallel loops nest at "
                                      f"strictly finer levels, never inside a sequential loop)")
+        inner = {**trips, c.var.name: c.n}
         if c.level in PARALLEL:
             f = _Frame(c.var, c.level)
-            _check(c.body, frames + [f], levels + [c.level])
+            _check(c.body, frames + [f], levels + [c.level], inner, out)
             read = set()
             _reads(c.body, read)
             clash = sorted(read & f.written)
@@ -164,14 +218,19 @@ def _check(c: T.Comm, frames: list, levels: list):
                                      f"{'ies' if len(clash) > 1 else 'y'} {', '.join(clash)} that its "
                                      f"iterations write (interference)")
         else:
-            _check(c.body, frames, levels + [c.level])
+            _check(c.body, frames, levels + [c.level], inner, out)
     elif isinstance(c, T.Assign):
         if not isinstance(c.e, P.Phrase):
             raise TypeCheckError("assignment of something that is not an expression")
         d = acc_type(c.acc)
         if d != c.e.type:
             raise TypeCheckError(f"acc[{d}] := exp[{c.e.type}]: the types differ")
+        _acc_bounds(c.acc, trips)
+        _exp_bounds(c.e, trips)
         root = _root(c.acc)
+        if out is not None and root.temp is None and root.name != out.name:
+            raise TypeCheckError(f"the command writes {root.name}, which is neither its output {out.name} "
+                                 f"nor a temporary")
         for f in frames:  # every enclosing parallel loop must own the write
             if root.name in f.local or _owned_by(c.acc, f.var):
                 continue
@@ -188,8 +247,12 @@ def typecheck(c: T.Comm, out: T.AOut | None = None) -> None:
     """Raise TypeCheckError unless the command is well typed: every assignment
     writes an expression of its acceptor's data type, every parallel loop
     writes only through its own element acceptor or its own temporaries and
-    reads none of the temporaries it writes, and loops nest legally. ``out``
-    is the kernel's output acceptor, checked against the command's writes."""
+    reads none of the temporaries it writes, loops nest legally, and every
+    element index, written or read, stays below the length of the array it
+    indexes for all values of the loop variables around it (the paper's parfor
+    over n hands each of its n iterations one of the n elements). ``out`` is
+    the kernel's output acceptor: every write that is not to a temporary must
+    go to it."""
     if out is not None and not isinstance(out, T.AOut):
         raise TypeCheckError("the output must be an output acceptor")
-    _check(c, [], [])
+    _check(c, [], [], {}, out)

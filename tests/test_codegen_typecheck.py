@@ -213,3 +213,36 @@ def test_every_planted_shared_write_is_rejected(name):
             a.i = keep
     TC.typecheck(c, out)
     CK.check(c)
+
+
+def test_loop_longer_than_the_array_it_indexes_is_rejected():
+    """A parfor over n hands its iterations the n elements of its acceptor: a
+    loop of 64 iterations writing element i of a 4-element output (or reading
+    element i of a 4-element input) is out of bounds, and both checkers say so."""
+    i = T.IVar("i")
+    out = T.AOut("out", P.arr(4, P.F32))
+    bad = T.For(i, 64, "global", T.Assign(T.AIdx(out, i), P.lit(1.0)))
+    with pytest.raises(TC.TypeCheckError, match="past the 4 elements"):
+        TC.typecheck(bad, out)
+    with pytest.raises(CK.RaceError, match="outside"):
+        CK.check(bad)
+    with pytest.raises(TC.TypeCheckError, match="past the 4 elements"):
+        TC.typecheck(T.For(i, 8, "seq", T.Assign(T.AIdx(out, T.IConst(5)), P.lit(1.0))), out)
+    x = P.inp("x", P.arr(4, P.F32))
+    big = T.AOut("out", P.arr(64, P.F32))
+    with pytest.raises(TC.TypeCheckError, match="read of an element"):
+        TC.typecheck(T.For(i, 64, "global", T.Assign(T.AIdx(big, i), P.Idx(x, i))), big)
+    # the same loops within bounds pass
+    ok = T.For(i, 4, "global", T.Assign(T.AIdx(out, i), P.Idx(x, i)))
+    TC.typecheck(ok, out)
+    CK.check(ok)
+
+
+def test_write_to_something_other_than_the_output_is_rejected():
+    i = T.IVar("i")
+    out = T.AOut("out", P.arr(4, P.F32))
+    stray = T.AOut("stray", P.arr(4, P.F32))
+    c = T.For(i, 4, "global", T.Assign(T.AIdx(stray, i), P.lit(1.0)))
+    with pytest.raises(TC.TypeCheckError, match="neither its output"):
+        TC.typecheck(c, out)
+    TC.typecheck(c, stray)
