@@ -23,10 +23,21 @@ def bits(a) -> bytes:
     return np.ascontiguousarray(a).tobytes()
 
 
+def _same_bits(got: np.ndarray, want: np.ndarray) -> bool:
+    if got.dtype != want.dtype or got.shape != want.shape:
+        return got.tobytes() == want.tobytes()
+    if got.dtype.itemsize in (1, 2, 4, 8) and got.size:
+        u = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}[got.dtype.itemsize]
+        return bool(np.array_equal(got.reshape(-1).view(u), want.reshape(-1).view(u)))
+    return got.tobytes() == want.tobytes()
+
+
 def assert_bits_equal(got, want, what=""):
     got = np.ascontiguousarray(got)
     want = np.ascontiguousarray(want)
-    if got.tobytes() != want.tobytes():
+    if got.shape != want.shape and got.size == want.size:
+        want = want.reshape(got.shape)
+    if not _same_bits(got, want):
         g = got.reshape(-1).view(np.uint32) if got.dtype == np.float32 else got.reshape(-1)
         w = want.reshape(-1).view(np.uint32) if want.dtype == np.float32 else want.reshape(-1)
         bad = np.nonzero(g != w)[0]

@@ -1,9 +1,10 @@
 """Batched uneven instances: one persistent launch per direction.
 
 Every instance's result must be bit-identical to the oracle's evaluation of
-that instance's own strategy, and to the per-launch baseline (one
-single-instance call per instance with the same strategy), forward and
-backward; a CUDA-graph replay must reproduce the same bits.
+that instance's own strategy, forward and backward -- on small batches under
+several policies and on the full batched workload -- and the per-launch
+baseline (one single-instance call per instance with the same strategy) and a
+CUDA-graph replay must reproduce the same bits.
 """
 import math
 
@@ -135,49 +136,53 @@ def test_batch_equals_per_launch_and_graph(cuda_device):
         assert host(d3).tobytes() == host(d1).tobytes()
 
 
+def _candidate_policies():
+    from paper_1710_08332_gb300 import tune
+
+    return tune.batch_candidates()
+
+
 @pytest.mark.slow
-def test_batched_workload_full(cuda_device):
-    """4096 dots + 512 GEMVs (lengths / rows log-uniform in [256, 65536], columns
-    in [256, 4096], seed 3): batched == per-launch for every instance, and a
-    sample of instances against the oracle."""
+@pytest.mark.parametrize("policy", _candidate_policies(),
+                         ids=lambda p: f"T{p.threads}-cap{p.dot_split_cap}-rs{p.row_split}-sched{p.schedule}")
+def test_batched_workload_full(cuda_device, policy):
+    """The batched workload at full size -- 4096 dots and 512 GEMVs, lengths and
+    rows log-uniform in [256, 65536], columns in [256, 4096], seed 3 -- under
+    every policy the autotuner chooses from (the bench times the one it picks),
+    every instance against the oracle, forward and backward: each dot's result,
+    dx and dy, and each GEMV's y, dx and dA, element by element. The packed
+    matrices are tens of GB, so each GEMV's matrix and dA are copied to the
+    host one instance at a time."""
     dl, rows, cols = W.batched_shapes()
-    b = Batch(dl.tolist(), list(zip(rows.tolist(), cols.tolist())), "cuda")
+    b = Batch(dl.tolist(), list(zip(rows.tolist(), cols.tolist())), "cuda", policy)
     xs, ys, As, gx, dot_g, gdy = _inputs(b, 3)
     d1, y1 = _outputs(b)
     b.forward(xs, ys, d1, As, gx, y1)
-    d2, y2 = _outputs(b)
-    b.per_launch_forward(xs, ys, d2, As, gx, y2)
-    torch.cuda.synchronize()
-    assert host(d1).tobytes() == host(d2).tobytes()
-    assert host(y1).tobytes() == host(y2).tobytes()
     dxs, dys, dAs, dgx = _bwd_outputs(b)
     b.backward(xs, ys, dot_g, dxs, dys, As, gx, gdy, dAs, dgx)
     torch.cuda.synchronize()
-    area = [m * n for m, n in b.gemv_shapes]
-    gsample = sorted(range(len(area)), key=area.__getitem__)[:3] + [int(np.argmax(area))]
-    dsample = list(range(0, len(b.dot_lengths), 128))
-    # copy only what the sample needs to the host (the packed matrices are tens of GB)
-    _check_sample(b, xs, ys, As, gx, dot_g, gdy, d1, y1, dxs, dys, dAs, dgx, dsample, gsample)
+    _check_streamed(b, xs, ys, As, gx, dot_g, gdy, d1, y1, dxs, dys, dAs, dgx)
     del As, dAs
     torch.cuda.empty_cache()
 
 
-def _check_sample(b, xs, ys, As, gx, dot_g, gdy, dot_out, gy, dxs, dys, dAs, dgx, dsample, gsample):
+def _check_streamed(b, xs, ys, As, gx, dot_g, gdy, dot_out, gy, dxs, dys, dAs, dgx):
     hx, hy, hg, hgx, hdy = host(xs), host(ys), host(dot_g), host(gx), host(gdy)
     hdot, hgy, hdxs, hdys, hdgx = host(dot_out), host(gy), host(dxs), host(dys), host(dgx)
-    for i in dsample:
+    for i in range(len(b.dot_lengths)):
         o, n = b.dot_offs[i], b.dot_lengths[i]
         assert_bits_equal(np.float32(hdot[i]), loopnest.dot_f32(hx[o:o + n], hy[o:o + n],
                                                                  oracle_strategy(b.dot_st[i])), f"dot {i}")
         wx, wy = loopnest.dot_bwd_f32(hx[o:o + n], hy[o:o + n], hg[i])
         assert_bits_equal(hdxs[o:o + n], wx, f"dot {i} dx")
         assert_bits_equal(hdys[o:o + n], wy, f"dot {i} dy")
-    for i in gsample:
+    for i in range(len(b.gemv_shapes)):
         M, N_ = b.gemv_shapes[i]
         A = host(b.a_view(As, i)).copy()
         x, dy = hgx[b.gx_offs[i]:b.gx_offs[i] + N_], hdy[b.gy_offs[i]:b.gy_offs[i] + M]
         assert_bits_equal(hgy[b.gy_offs[i]:b.gy_offs[i] + M], loopnest.gemv_f32(A, x, oracle_strategy(b.gemv_st[i])),
                           f"gemv {i}")
-        assert_bits_equal(host(b.a_view(dAs, i)).copy(), loopnest.gemv_bwd_dA_f32(x, dy), f"gemv {i} dA")
         assert_bits_equal(hdgx[b.gx_offs[i]:b.gx_offs[i] + N_], loopnest.gemv_bwd_dx_f32(A, dy, b.policy.row_split),
                           f"gemv {i} dx")
+        del A
+        assert_bits_equal(host(b.a_view(dAs, i)).copy(), loopnest.gemv_bwd_dA_f32(x, dy), f"gemv {i} dA")

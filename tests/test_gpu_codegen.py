@@ -94,15 +94,31 @@ def test_temporaries(cuda_device, space):
         assert np.array_equal(bits(out), bits(want))
 
 
-def test_backends_agree_at_size(cuda_device):
-    """n = 2^22: the CUDA kernel and the host C build of the same loop nest."""
+@pytest.mark.parametrize("tm,V", [("interleaved", 1), ("interleaved", 4), ("contig", 4)])
+def test_generated_dot_at_size_matches_oracle(cuda_device, tm, V):
+    """n = 2^22: the generated partials kernel against the oracle's lane
+    partials of the same strategy (c2), element by element, then the fold plan's
+    stages against the oracle's strided folds of those partials (c1)."""
+    from oracle import loopnest
+    from oracle import patterns as P_
+    from paper_1710_08332_gb300.codegen import rewrite as RW
+
     n, s, Tn = 1 << 22, 16384, 256
     x, y = uniform(n, 30), uniform(n, 31)
-    e, ins = PR.dot_partials(n, s, Tn)
-    part = run(G.compile_cuda("dotp", e, ins), dev(x), dev(y), out_count=n // s * Tn)
-    host = np.zeros(n // s * Tn, np.float32)
-    G.compile_c("dotp", e, ins, openmp=True).run(x, y, host)
-    assert np.array_equal(bits(part), bits(host))
+    e, ins = PR.dot_partials(n, s, Tn, tm, V=V)
+    part = run(G.compile_cuda("dotp", e, ins, unroll=4), dev(x), dev(y), out_count=n // s * Tn * V)
+    want = loopnest.lane_partials_f32("dot", x, y, P_.Strategy(s=s, T=Tn, V=V, thread_map=tm))
+    assert np.array_equal(bits(part), bits(want))
+    vals = list(want)
+    cur = dev(part)
+    for grp in RW.fold_plan(len(vals)):
+        rows = len(vals) // grp
+        ph, i2 = PR.fold_cols(rows, grp) if grp < len(vals) else PR.fold_all(len(vals))
+        got = run(G.compile_cuda(f"fold{grp}_{rows}", ph, i2, unroll=64), cur, out_count=rows,
+                  grid=max(1, rows // 64), block=min(64, rows))
+        vals = [oracle_fold(vals[j::rows]) for j in range(rows)]
+        assert np.array_equal(bits(got), bits(vals))
+        cur = dev(got)
 
 
 @pytest.mark.parametrize("thread_map", ["interleaved", "contig"])
@@ -145,7 +161,12 @@ def test_vector_kernels(cuda_device, thread_map):
 
 
 def test_exploration_ranks_derivations_and_each_is_exact_for_its_tree(cuda_device):
-    from oracle import naive64
+    """The explored derivations are ranked by time; the fastest and slowest
+    each equal the oracle's evaluation of their own tree -- c2's lane partials
+    for the split / columns / vectorize part, then c1's strided folds of the
+    fold plan -- and lie within the normwise bound of the exact dot."""
+    from oracle import loopnest, naive64
+    from oracle import patterns as P_
     from paper_1710_08332_gb300.codegen import rewrite as RW
 
     n = 1 << 20
@@ -159,15 +180,14 @@ def test_exploration_ranks_derivations_and_each_is_exact_for_its_tree(cuda_devic
     for _, d in ranked[:3] + ranked[-2:]:
         got = RW.run_pipeline(RW.compile_pipeline("dot", d, n), [dx, dy])
         torch.cuda.synchronize()
-        cur = [x, y]
-        for name, ph, ins in RW.lower("dot", d, n):  # the same tree on the host
-            f = G.compile_c("h_" + name, ph, ins)
-            count = next(c for (_, _, c, role) in f.params if role == "out")
-            out = np.zeros(count, np.float32)
-            f.run(*cur, out, *f.temps_like())
-            cur = [out]
-        assert bits(got.cpu().numpy())[0] == bits(cur[0])[0], str(d)
-        assert abs(float(cur[0][0]) - exact) <= bound
+        args = {r.name: r.args for r in d.rules}
+        s, (Tn, tm), V = args["split"][0], args["columns"], args.get("vectorize", (1,))[0]
+        vals = list(loopnest.lane_partials_f32("dot", x, y, P_.Strategy(s=s, T=Tn, V=V, thread_map=tm)))
+        for grp in RW.fold_plan(len(vals)):
+            rows = len(vals) // grp
+            vals = [oracle_fold(vals[j::rows]) for j in range(rows)]
+        assert bits(got.cpu().numpy())[0] == bits(vals)[0], str(d)
+        assert abs(float(vals[0]) - exact) <= bound
 
 
 def test_generated_gemv_backward(cuda_device):

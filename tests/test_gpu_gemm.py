@@ -1,11 +1,12 @@
 """GPU parity of the GEMM instances.
 
 FP32 fold: bit-identical to the oracle's sequential k loop (both contractions,
-all four operand layouts, ragged shapes, and sampled entries at 4096^3).
+all four operand layouts, ragged shapes, and 96 full rows of C at 4096^3).
 BF16 tensor cores: the cast is bit-exact against round-to-nearest-even; the
 product is checked against FP64 of the bf16-rounded inputs (||C - C64||_F /
 ||C64||_F <= 1e-4, and per element within the f32 accumulation bound) and
-against FP64 of the original FP32 inputs (<= 2e-2).
+against FP64 of the original FP32 inputs (<= 2e-2); at 4096^3 every element of
+the forward and both backward products.
 """
 import numpy as np
 import pytest
@@ -56,19 +57,35 @@ def gemm_inputs():
     return A, B, dC
 
 
-def test_gemm_f32_4096_sampled(cuda_device, gemm_inputs):
+def _f32_rows_4096(n):
+    """Rows of C checked at 4096^3: two in every 128-row tile row (at offsets that
+    vary from tile to tile) and every 16th row of the last 512, whose tiles run
+    as 64-row half tiles in the second launch -- 96 rows, all columns."""
+    rows = set()
+    for t in range(n // 128):
+        rows.add(t * 128 + (t * 41) % 128)
+        rows.add(t * 128 + 127 - (t * 23) % 128)
+    rows.update(range(n - 512, n, 16))
+    return np.array(sorted(rows))
+
+
+def test_gemm_f32_4096_rows(cuda_device, gemm_inputs):
+    """The FP32 fold at 4096^3 against the oracle's fold, bit for bit, on 96 full
+    rows of C (every tile row, both launches), and within the summation bound
+    of FP64 there."""
     A, B, _ = gemm_inputs
     n = W.GEMM_MNK
     C = torch.empty(n, n, device="cuda")
     dpia.dpia_gemm_f32(A, B, C, n, n, n, n, n, n, 0, 0, "fma")
-    rows = np.array([0, 1, 127, 128, 2047, 4000, 4095])
-    cols = np.array([0, 5, 255, 256, 1023, 3071, 4095])
+    rows = _f32_rows_4096(n)
+    assert rows.size >= 64
     hA, hB = host(A), host(B)
-    want = loopnest.gemm_f32_sample(hA, hB, False, False, True, rows, cols)
-    assert_bits_equal(host(C)[np.ix_(rows, cols)], want, "gemm f32 4096 sample")
+    want = loopnest.gemm_f32_sample(hA, hB, False, False, True, rows, np.arange(n))
+    got = host(C)[rows]
+    assert_bits_equal(got, want, "gemm f32 4096 rows")
     ref = hA[rows].astype(np.float64) @ hB.astype(np.float64)
     scale = np.abs(hA[rows]).astype(np.float64) @ np.abs(hB).astype(np.float64)
-    assert np.all(np.abs(host(C)[rows] - ref) <= (n + 1) * 2.0 ** -24 * scale)
+    assert np.all(np.abs(got - ref) <= (n + 1) * 2.0 ** -24 * scale)
 
 
 def test_cast_bf16_exact(cuda_device):
@@ -81,21 +98,32 @@ def test_cast_bf16_exact(cuda_device):
     assert np.array_equal(np.signbit(host(y.float())), np.signbit(want))
 
 
+class Bf16Ref:
+    """FP64 references of op(A) op(B) for the BF16 GEMM's tolerance checks: the
+    product of the bf16-rounded operands, its f32 accumulation bound
+    (K + 2) 2^-23 (|A16| |B16|)_ij, and the product of the original f32
+    operands. Computed once, for checks of several kernels on one product."""
+
+    def __init__(self, opA, opB):
+        a16 = naive64.bf16_round(opA)
+        b16 = naive64.bf16_round(opB)
+        self.ref16 = a16 @ b16
+        self.bound = (opA.shape[1] + 2) * 2.0 ** -23 * (np.abs(a16) @ np.abs(b16)) + 1e-30
+        self.ref32 = opA.astype(np.float64) @ opB.astype(np.float64)
+
+    def check(self, C, what):
+        rel = np.linalg.norm(C - self.ref16) / np.linalg.norm(self.ref16)
+        assert rel <= 1e-4, f"{what}: rel err vs bf16 inputs {rel}"
+        worst = np.max(np.abs(C - self.ref16) / self.bound)
+        assert worst <= 1.0, f"{what}: elementwise error {worst} x the f32 accumulation bound"
+        rel32 = np.linalg.norm(C - self.ref32) / np.linalg.norm(self.ref32)
+        assert rel32 <= 2e-2, f"{what}: rel err vs f32 inputs {rel32}"
+        return rel, rel32
+
+
 def _bf16_check(C, opA, opB, what):
     """C against FP64 of the bf16-rounded operands (tight) and of the f32 ones (loose)."""
-    a16 = naive64.bf16_round(opA)
-    b16 = naive64.bf16_round(opB)
-    ref16 = a16 @ b16
-    rel = np.linalg.norm(C - ref16) / np.linalg.norm(ref16)
-    assert rel <= 1e-4, f"{what}: rel err vs bf16 inputs {rel}"
-    K = opA.shape[1]
-    bound = (K + 2) * 2.0 ** -23 * (np.abs(a16) @ np.abs(b16)) + 1e-30
-    worst = np.max(np.abs(C - ref16) / bound)
-    assert worst <= 1.0, f"{what}: elementwise error {worst} x the f32 accumulation bound"
-    ref = opA.astype(np.float64) @ opB.astype(np.float64)
-    rel32 = np.linalg.norm(C - ref) / np.linalg.norm(ref)
-    assert rel32 <= 2e-2, f"{what}: rel err vs f32 inputs {rel32}"
-    return rel, rel32
+    return Bf16Ref(opA, opB).check(C, what)
 
 
 @pytest.mark.parametrize("tile_n", [0, 128, 224, 256])
@@ -182,12 +210,12 @@ def test_gemm_bf16_strided_c_untouched_outside(cuda_device, cluster, tile_m, off
 
 
 @pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0)])
-def test_gemm_bf16_pair_matches_single(cuda_device, gemm_inputs, tA, tB):
-    """At 4096^3 (the three layouts of the forward and backward products) the
-    single CTA and the CTA pair (256- and 512-row tiles) compute every C_ij
-    from the same bf16 products over the same k-slices; each stays within the
-    f32 accumulation bound of the FP64 product (checked on sampled rows) and
-    they agree to a few f32 ulps."""
+def test_gemm_bf16_variants_4096(cuda_device, gemm_inputs, tA, tB):
+    """At 4096^3, in the three operand layouts of the forward and backward
+    products, every kernel variant -- one CTA per 256-row tile, CTA pairs with
+    256- and 512-row tiles -- computes every element of C within the f32
+    accumulation bound of the FP64 product of the bf16-rounded operands (and
+    the Frobenius bounds); the variants agree to a few f32 ulps."""
     A, B, _ = gemm_inputs
     n = W.GEMM_MNK
     Ab, Bb = dpia.to_bf16(A), dpia.to_bf16(B)
@@ -199,11 +227,9 @@ def test_gemm_bf16_pair_matches_single(cuda_device, gemm_inputs, tA, tB):
     torch.cuda.synchronize()
     assert dpia.dpia_poll_device_status() == 0
     hA, hB = host(A), host(B)
-    opA = hA.T if tA else hA
-    opB = hB.T if tB else hB
-    rows = np.arange(0, n, 211)[:20]
-    for C in out:
-        _bf16_check(host(C)[rows].astype(np.float64), opA[rows], opB, f"4096^3 tA={tA} tB={tB}")
+    ref = Bf16Ref(hA.T if tA else hA, hB.T if tB else hB)
+    for C, label in zip(out, ("one SM", "pair 256", "pair 512")):
+        ref.check(host(C).astype(np.float64), f"4096^3 {label} tA={tA} tB={tB}")
     scale = out[0].abs().max().item()
     for C in out[1:]:
         d = (out[0] - C).abs().max().item()
@@ -211,21 +237,21 @@ def test_gemm_bf16_pair_matches_single(cuda_device, gemm_inputs, tA, tB):
 
 
 def test_gemm_bf16_4096(cuda_device, gemm_inputs):
-    """The GEMM workload (4096^3): forward and both backward products."""
+    """The GEMM workload (4096^3) with the default kernel choice: forward and
+    both backward products, every element checked."""
     A, B, dC = gemm_inputs
     n = W.GEMM_MNK
     Ab, Bb, dCb = dpia.to_bf16(A), dpia.to_bf16(B), dpia.to_bf16(dC)
-    rows = np.arange(0, n, 97)[:40]
     hA, hB, hdC = host(A), host(B), host(dC)
     C = torch.empty(n, n, device="cuda")
     dpia.dpia_gemm_bf16(Ab, Bb, C, n, n, n, n, n, n, 0, 0)            # C = A B
-    _bf16_check(host(C)[rows].astype(np.float64), hA[rows], hB, "C = A B")
+    _bf16_check(host(C).astype(np.float64), hA, hB, "C = A B")
     dA = torch.empty(n, n, device="cuda")
     dpia.dpia_gemm_bf16(dCb, Bb, dA, n, n, n, n, n, n, 0, 1)          # dA = dC B^T
-    _bf16_check(host(dA)[rows].astype(np.float64), hdC[rows], hB.T, "dA = dC B^T")
+    _bf16_check(host(dA).astype(np.float64), hdC, hB.T, "dA = dC B^T")
     dB = torch.empty(n, n, device="cuda")
     dpia.dpia_gemm_bf16(Ab, dCb, dB, n, n, n, n, n, n, 1, 0)          # dB = A^T dC
-    _bf16_check(host(dB)[rows].astype(np.float64), hA.T[rows], hdC, "dB = A^T dC")
+    _bf16_check(host(dB).astype(np.float64), hA.T, hdC, "dB = A^T dC")
     assert dpia.dpia_poll_device_status() == 0
 
 

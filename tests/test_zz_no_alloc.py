@@ -5,7 +5,8 @@ instance a plugin whose host framework owns every device allocation): it uses
 the library's static scratch array instead of a caller workspace. Its result
 must equal dpia_dot_f32's with the same strategy -- bit for bit, the tolerance
 the parity tests use for same-strategy FP32 -- on two calls in a row (the
-second call reuses the scratch left by the first). This file is collected last
+second call reuses the scratch left by the first), and the oracle's evaluation
+of the same strategy tree. This file is collected last
 so that a failure here cannot hide earlier tests in a run that stops at the
 first failure; it also passes when run alone in a fresh process.
 """
@@ -15,9 +16,11 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import loopnest
 from paper_1710_08332_gb300 import _native as N
 from paper_1710_08332_gb300.strategy import ReduceStrategy
 from synth import workloads as W
+from tests.helpers import host, oracle_strategy
 
 pytestmark = pytest.mark.gpu
 
@@ -48,12 +51,15 @@ def test_noalloc_matches_workspace_entry_twice(cuda_device):
         want = _c_dot(x, y, st, with_workspace=True)
         got = _c_dot(x, y, st, with_workspace=False)
         assert got.tobytes() == want.tobytes(), (got, want)
+        oracle = loopnest.dot_f32(host(x), host(y), oracle_strategy(st))
+        assert got[0].tobytes() == oracle.tobytes(), (got, oracle)
     # the sequential second level over 128 partials (the 2^20 dot's split) as well
     st2 = ReduceStrategy(split=W.DOT_SPLIT, threads=256, vec=4)
     x, y = W.dot_f32("cuda")
     a = _c_dot(x, y, st2, with_workspace=False)
     b = _c_dot(x, y, st2, with_workspace=False)
     assert a.tobytes() == b.tobytes() == _c_dot(x, y, st2, with_workspace=True).tobytes()
+    assert a[0].tobytes() == loopnest.dot_f32(host(x), host(y), oracle_strategy(st2)).tobytes()
 
 
 def test_noalloc_rejects_more_chunks_than_scratch(cuda_device):
