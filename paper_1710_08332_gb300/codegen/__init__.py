@@ -1,6 +1,7 @@
 """A strategy-preserving code generator: functional phrases over the paper's
-primitives (map at a level of the hierarchy, reduceSeq, zip, split, join,
-transpose, address-space annotations) are translated to an imperative loop
+primitives (map at a level of the hierarchy -- work-group, warp, lane,
+local, sequential --, reduceSeq, zip, split, join, transpose, address-space
+annotations, lane trees and the last work-group's second level) are translated to an imperative loop
 nest (acceptor- and continuation-passing translations, then the mapI /
 reduceI expansion) and emitted as CUDA C for sm_103a or as C for the host.
 The emitted code evaluates exactly the tree the phrase denotes, so its
@@ -9,8 +10,8 @@ results are bit-identical to any other evaluation of the same phrase.
 from .build import CFunction, CudaKernel, compile_c, compile_cuda
 from .emit import EmitError, generate
 from .phrase import (F32, I32, I64, Arr, Num, PairT, VecT, abs_, add, arr, asScalar, asVector, fst, inp, join,
-                     lit, mapGlobal, mapLocal, mapSeq, mapWorkgroup, mul, reduceSeq, snd, split, sub, to_global,
-                     to_local, to_private, transpose, vlit, zip_)
+                     lanes, lit, mapGlobal, mapLane, mapLocal, mapSeq, mapWarp, mapWorkgroup, mul, reduceSeq,
+                     reduceTree, secondLevel, snd, split, sub, to_global, to_local, to_private, transpose, vlit, zip_)
 from .translate import TranslationError
 from .typecheck import TypeCheckError
 

@@ -1,7 +1,7 @@
 """Compile generated kernels and call them.
 
 CUDA: the kernel plus an ``extern "C"`` launcher are compiled by nvcc for
-sm_103a into a shared object (cached by source hash under _build/gen) and
+sm_103a into a shared object (cached by source hash under codegen/_build) and
 called through ctypes with device pointers. C: the loop nest is compiled by
 the system C compiler (no contraction of * and +) and called with host
 arrays; the outermost parallel loop may run on OpenMP threads, since a
@@ -20,7 +20,7 @@ from . import emit as E
 from . import phrase as P
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-CACHE = os.path.join(os.path.dirname(HERE), "_build", "gen")
+CACHE = os.path.join(HERE, "_build")
 _lock = threading.Lock()
 NP_DTYPE = {"float": "float32", "int": "int32", "long long": "int64"}
 
@@ -32,11 +32,21 @@ def _nvcc():
     raise RuntimeError("nvcc not found: generated CUDA kernels need the CUDA toolkit")
 
 
+_locks = {}
+
+
+def _lock_for(key: str) -> threading.Lock:
+    with _lock:
+        return _locks.setdefault(key, threading.Lock())
+
+
 def _build(src: str, suffix: str, cmd_for) -> str:
+    """Compile src once into the cache (one lock per source, so that different
+    kernels may compile on several threads at once)."""
     h = hashlib.sha256(src.encode()).hexdigest()[:20]
     d = os.path.join(CACHE, h)
     lib = os.path.join(d, "lib.so")
-    with _lock:
+    with _lock_for(h):
         if not os.path.exists(lib):
             os.makedirs(d, exist_ok=True)
             path = os.path.join(d, "src" + suffix)
@@ -86,18 +96,27 @@ class CudaKernel:
     def params(self):
         return self.gen["params"]
 
+    @property
+    def uses_warps(self) -> bool:
+        """The kernel has warp or lane loops (shuffles need all 32 lanes of a warp)."""
+        return any(lvl in ("warp", "lane") for lvl, _ in _parallel_loops(self.gen["comm"]))
+
     def default_launch(self, sms: int = 152):
         """(grid, block) from the loop nest: the workgroup loop's trip count (or
         the global loop's) and the local loop's trip count, within limits."""
-        wg = gl = loc = None
+        wg = gl = loc = warp = None
         for lvl, n in _parallel_loops(self.gen["comm"]):
             if lvl == "workgroup" and wg is None:
                 wg = n
             elif lvl == "local" and loc is None:
                 loc = n
+            elif lvl == "warp" and warp is None:
+                warp = n
             elif lvl == "global" and gl is None:
                 gl = n
-        block = min(loc, 1024) if loc else 256
+        block = min(loc, 1024) if loc else (min(32 * warp, 1024) if warp else 256)
+        if self.uses_warps:
+            block = max(32, block // 32 * 32)
         if wg is not None:
             grid = max(1, min(wg, 65535 * 32))
         elif gl is not None:
@@ -121,6 +140,8 @@ class CudaKernel:
         grid, block = grid or g0, block or b0
         if not (1 <= block <= 1024 and grid >= 1):
             raise ValueError("grid >= 1 and 1 <= block <= 1024")
+        if self.uses_warps and block % 32:
+            raise ValueError("a kernel with warp or lane loops needs whole warps: block a multiple of 32")
         s = stream or torch.cuda.current_stream()
         rc = self.fn(*[ctypes.c_void_p(a.data_ptr()) for a in arrays], int(grid), int(block),
                      ctypes.c_void_p(s.cuda_stream))
@@ -175,13 +196,10 @@ class CFunction:
 
 
 def _omp_outer(src: str) -> str:
-    """Run the first loop of the function body on OpenMP threads."""
-    lines = src.split("\n")
-    for k, ln in enumerate(lines):
-        if ln.startswith("  for ("):
-            lines.insert(k, "  #pragma omp parallel for schedule(static)")
-            break
-    return "\n".join(lines)
+    """Run the outermost parallel loops (work-group or global maps, marked by
+    the emitter) on OpenMP threads; sequential loops, such as a fold at the top
+    of a program or the second level after the work-group loop, stay on one."""
+    return src.replace(E.OMP_MARK, "#pragma omp parallel for schedule(static)")
 
 
 def _parallel_loops(c, out=None):
@@ -196,6 +214,11 @@ def _parallel_loops(c, out=None):
         for x in c.cs:
             _parallel_loops(x, out)
     elif isinstance(c, T.New):
+        _parallel_loops(c.body, out)
+    elif isinstance(c, T.TreeReduce):
+        out.append(("lane", c.buf.type.n))
+        _parallel_loops(c.fill, out)
+    elif isinstance(c, T.LastBlock):
         _parallel_loops(c.body, out)
     return out
 

@@ -176,6 +176,15 @@ def _walk(c, loops, declared):
         _walk(c.body, loops, d)
     elif isinstance(c, T.For):
         _walk(c.body, loops + [c], declared)
+    elif isinstance(c, T.TreeReduce):
+        # the buffer and the result are the enclosing iteration's own; the fill's
+        # lane loop writes element l of the buffer (the halving steps then write
+        # buf[l] for l < h from buf[l + h], never a place another step reads)
+        d = dict(declared)
+        d[c.buf.name] = d[c.res.name] = len(loops)
+        _walk(c.fill, loops, d)
+    elif isinstance(c, T.LastBlock):
+        _walk(c.body, [], declared)  # one block, after every block's loop
     elif isinstance(c, T.Assign):
         from .typecheck import index_max
 

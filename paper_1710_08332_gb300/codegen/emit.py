@@ -9,10 +9,20 @@ through acceptors are resolved the same way. Loops map to the hierarchy:
     global     for (i = blockIdx.x*blockDim.x + threadIdx.x; i < n; i += gridDim.x*blockDim.x)
     workgroup  for (i = blockIdx.x; i < n; i += gridDim.x)
     local      for (i = threadIdx.x; i < n; i += blockDim.x)
+    warp       for (i = threadIdx.x / 32; i < n; i += blockDim.x / 32)
+    lane       for (i = threadIdx.x % 32; i < n; i += 32)
     seq        for (i = 0; i < n; ++i)
 
 A statement outside every parallel loop runs in one thread (thread 0 of block
-0, or thread 0 of the workgroup when it sits in a workgroup loop only). Where
+0, thread 0 of the workgroup when it sits in a workgroup loop only, lane 0
+when it sits in a warp loop). A lane tree keeps element l in lane l's
+register and combines with warp shuffles (``__shfl_down_sync`` by L/2, L/4,
+.., 1: lane l adds lane l + h's value, the halving tree); the C backend keeps
+the elements in an array and runs the same halving loops. The second level
+runs in the last block: every block fences its writes and takes a ticket
+(atomicAdd on a counter); the block that draws the last one fences again,
+reads the parts through L2 (``__ldcg``), computes the second level and puts
+the counter back to zero -- no block ever waits for another. Where
 a temporary in local or global memory is in scope, block barriers separate a
 local loop from the statements before and after it and end every iteration of
 a loop that contains a local loop, so no thread reads what another has not
@@ -58,6 +68,9 @@ __device__ __forceinline__ float dpia_lane2(float2 v, long long l) { return l ==
 __device__ __forceinline__ float4 dpia_vabs4(float4 a) { return make_float4(fabsf(a.x), fabsf(a.y), fabsf(a.z), fabsf(a.w)); }
 __device__ __forceinline__ float2 dpia_vabs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 """
+
+THREADED = ("local", "warp", "lane")  # levels whose loops spread over the threads of a block
+OMP_MARK = "/* dpia: outermost parallel loop */"
 
 C_PRELUDE = """#include <math.h>
 typedef struct { float x, y, z, w; } float4;
@@ -125,6 +138,8 @@ def linear(idx: list, shape: list):
 
 
 class Emitter:
+    in_last = False  # emitting the last block's second level: parts are read through L2
+
     def __init__(self, backend: str, inputs: list, out: T.AOut, temps: list, unroll: int = 1):
         if backend not in ("cuda", "c"):
             raise EmitError(f"unknown backend {backend}")
@@ -187,6 +202,17 @@ class Emitter:
             if isinstance(lane, T.IConst):
                 return f"({v}).{LANES[lane.v]}"
             return f"dpia_lane{V}({v}, {render_index(lane)})"
+        if isinstance(e, P.Lanes):
+            V = e.e.type.n
+            if len(path) != 1 or path[0][0] != "i":
+                raise EmitError("lanes read must select one lane")
+            v = self.access(e.e, [])
+            lane = path[0][1]
+            if isinstance(lane, T.IConst):
+                return f"({v}).{LANES[lane.v]}"
+            return f"dpia_lane{V}({v}, {render_index(lane)})"
+        if isinstance(e, Shuffle):
+            return f"__shfl_down_sync(0xffffffffu, {self.access(e.e, path)}, {e.offset})"
         if isinstance(e, P.Lit):
             return self.literal(e)
         if isinstance(e, P.Bin):
@@ -245,10 +271,15 @@ class Emitter:
                 return e.name if isinstance(e.type, P.Num) else f"{e.name}[0]"
             return f"{e.name}[{render_index(linear(idx, dims(e.type)))}]"
         t = self.temps[e.name]
-        return self.temp_ref(t, idx)
+        ref = self.temp_ref(t, idx)
+        if self.in_last and t.space == "global" and self.backend == "cuda":
+            return f"__ldcg(&{ref})"  # written by other blocks: read through L2, not a stale L1 line
+        return ref
 
     def temp_ref(self, t: T.Temp, idx: list) -> str:
         shape = dims(t.type)
+        if t.lanes and self.backend == "cuda":
+            return t.name  # element l of a lane tree's buffer is lane l's register
         if t.space == "private":
             if not shape:
                 return t.name
@@ -357,13 +388,14 @@ class Emitter:
         """ctx: the levels of the enclosing loops."""
         pad = "  " * ind
         if isinstance(c, T.Seq):
+            uniform = _block_uniform(ctx)  # every thread of the block runs this code: a barrier may go here
             for k, x in enumerate(c.cs):
-                local = self.backend == "cuda" and self.sync[-1] and _has_level(x, "local")
+                local = self.backend == "cuda" and self.sync[-1] and uniform and _threaded(x)
                 if local and k > 0:  # what the block's threads read was written by others
-                    self.lines.append(f"{pad}__syncthreads();")
+                    self.barrier(pad)
                 self.emit(x, ind, ctx)
                 if local and k + 1 < len(c.cs):  # and the other way round
-                    self.lines.append(f"{pad}__syncthreads();")
+                    self.barrier(pad)
             return
         if isinstance(c, T.New):
             t = c.temp
@@ -375,7 +407,7 @@ class Emitter:
                 if t.space != "private":
                     raise EmitError("pair temporaries are private scalars only")
                 par = sum(1 for l in ctx if l != "seq")
-                self.private_ctx[t.name] = (par, "local" in ctx or "global" in ctx)
+                self.private_ctx[t.name] = (par, _per_thread(ctx))
                 self.lines.append(f"{pad}{ctype(t.type.a)} {t.name}_0;")
                 self.lines.append(f"{pad}{ctype(t.type.b)} {t.name}_1;")
                 self.emit(c.body, ind, ctx)
@@ -386,7 +418,7 @@ class Emitter:
                 ct = ctype(P.base_elem(t.type))
                 shape = dims(t.type)
                 par = sum(1 for l in ctx if l != "seq")
-                self.private_ctx[t.name] = (par, "local" in ctx or "global" in ctx)
+                self.private_ctx[t.name] = (par, _per_thread(ctx))
                 if shape:
                     self.lines.append(f"{pad}{ct} {t.name}[{P.scalar_count(t.type)}];")
                 else:
@@ -408,6 +440,10 @@ class Emitter:
             return
         if isinstance(c, T.For):
             v, n = c.var.name, c.n
+            if self.backend == "c" and c.level in ("workgroup", "global") and not ctx:
+                # the outermost parallel loop: its iterations write disjoint places, so
+                # the host build may run them on threads (each declares its own temporaries)
+                self.lines.append(f"{pad}{OMP_MARK}")
             if self.backend == "c" or c.level == "seq":
                 if c.level == "seq" and not self.has_parallel(c.body) and self.guard(ctx):
                     # a sequential loop outside the thread-level loops runs in one thread
@@ -426,6 +462,10 @@ class Emitter:
                 self.lines.append(f"{pad}for (long long {v} = blockIdx.x; {v} < {n}; {v} += gridDim.x) {{")
             elif c.level == "local":
                 self.lines.append(f"{pad}for (long long {v} = threadIdx.x; {v} < {n}; {v} += blockDim.x) {{")
+            elif c.level == "warp":
+                self.lines.append(f"{pad}for (long long {v} = threadIdx.x >> 5; {v} < {n}; {v} += blockDim.x >> 5) {{")
+            elif c.level == "lane":
+                self.lines.append(f"{pad}for (long long {v} = threadIdx.x & 31; {v} < {n}; {v} += 32) {{")
             elif c.level == "global":
                 self.lines.append(f"{pad}for (long long {v} = (long long)blockIdx.x * blockDim.x + threadIdx.x; "
                                   f"{v} < {n}; {v} += (long long)gridDim.x * blockDim.x) {{")
@@ -434,18 +474,89 @@ class Emitter:
             self.emit(c.body, ind + 1, ctx + (c.level,))
             self.sync.pop()
             if (self.backend == "cuda" and shared and c.level in ("workgroup", "seq")
-                    and _has_level(c.body, "local")):
+                    and _block_uniform(ctx) and _threaded(c.body)):
                 # the next iteration's thread-level loops overwrite what this one's threads still read
-                self.lines.append(f"{pad}  __syncthreads();")
+                self.barrier(pad + "  ")
             self.lines.append(f"{pad}}}")
             return
+        if isinstance(c, T.TreeReduce):
+            self.emit_tree(c, ind, ctx)
+            return
+        if isinstance(c, T.LastBlock):
+            self.emit_last_block(c, ind, ctx)
+            return
         raise EmitError(f"unknown command {type(c).__name__}")
+
+    def barrier(self, pad: str):
+        """A block barrier, unless the line before is one already."""
+        if not (self.lines and self.lines[-1].strip() == "__syncthreads();"):
+            self.lines.append(f"{pad}__syncthreads();")
+
+    def emit_tree(self, c: T.TreeReduce, ind: int, ctx: tuple):
+        pad = "  " * ind
+        L = c.buf.type.n
+        et = c.buf.type.elem
+        bufv = P.Ident(c.buf.name, c.buf.type, temp="private")
+        ct = ctype(et)
+        zero = self.literal(P.Lit(0.0, et))
+        self.private_ctx[c.buf.name] = (sum(1 for l in ctx if l != "seq"), _per_thread(ctx))
+        if self.backend == "cuda":
+            if "warp" not in ctx or "lane" in ctx:
+                raise EmitError("a lane tree runs directly inside a warp loop")
+            # lane l keeps element l; lanes past L hold zeros, which never reach lane 0
+            self.lines.append(f"{pad}{ct} {c.buf.name} = {zero};")
+            self.emit(c.fill, ind, ctx)
+            reg = P.Ident(c.buf.name, et, temp="private")
+            h = L // 2
+            while h >= 1:  # every lane of the warp takes part in each shuffle
+                step = P.apply(c.f, reg, Shuffle(reg, h))
+                self.lines.append(f"{pad}{c.buf.name} = {self.access(step, [])};")
+                h //= 2
+            self.lines.append(f"{pad}{c.res.name} = {c.buf.name};  // the tree's value, in lane 0")
+            return
+        self.lines.append(f"{pad}{ct} {c.buf.name}[{L}];")
+        self.emit(c.fill, ind, ctx)
+        h = L // 2
+        while h >= 1:
+            j = T.IVar("dpia_l")
+            step = P.apply(c.f, P.Idx(bufv, j), P.Idx(bufv, T.iadd(j, T.IConst(h))))
+            self.lines.append(f"{pad}for (long long dpia_l = 0; dpia_l < {h}; ++dpia_l) "
+                              f"{c.buf.name}[dpia_l] = {self.access(step, [])};")
+            h //= 2
+        self.lines.append(f"{pad}{c.res.name} = {c.buf.name}[0];")
+
+    def emit_last_block(self, c: T.LastBlock, ind: int, ctx: tuple):
+        pad = "  " * ind
+        if ctx:
+            raise EmitError("the second level runs outside every loop")
+        inner = ("workgroup",)
+        if self.backend == "c":
+            self.emit(c.body, ind, inner)
+            return
+        tk = c.ticket.name
+        self.shared.append("  __shared__ int dpia_last;")
+        self.lines.append(f"{pad}__threadfence();  // this block's parts are visible before its ticket")
+        self.barrier(pad)
+        self.lines += [
+                       f"{pad}if (threadIdx.x == 0) dpia_last = atomicAdd({tk}, 1) == (int)gridDim.x - 1;",
+                       f"{pad}__syncthreads();",
+                       f"{pad}if (dpia_last) {{",
+                       f"{pad}  __threadfence();"]
+        self.in_last = True
+        self.sync.append(True)
+        self.emit(c.body, ind + 1, inner)
+        self.sync.pop()
+        self.in_last = False
+        self.lines += [f"{pad}  if (threadIdx.x == 0) {tk}[0] = 0;  // the counter is zero for the next launch",
+                       f"{pad}}}"]
 
     def guard(self, ctx) -> str:
         if self.backend == "c" or "guarded" in ctx:
             return ""
-        if "local" in ctx or "global" in ctx:
+        if "local" in ctx or "global" in ctx or "lane" in ctx:
             return ""
+        if "warp" in ctx:
+            return "if ((threadIdx.x & 31) == 0) "
         if "workgroup" in ctx:
             return "if (threadIdx.x == 0) "
         return "if (blockIdx.x == 0 && threadIdx.x == 0) "
@@ -458,6 +569,8 @@ class Emitter:
             return any(Emitter.has_parallel(x) for x in c.cs)
         if isinstance(c, T.New):
             return Emitter.has_parallel(c.body)
+        if isinstance(c, (T.TreeReduce, T.LastBlock)):
+            return True
         return False
 
     def check_private_reads(self, e, ctx):
@@ -465,7 +578,7 @@ class Emitter:
         a single thread computes it may not be read inside a thread-level loop."""
         if self.backend != "cuda":
             return
-        inside_threads = "local" in ctx or "global" in ctx
+        inside_threads = _per_thread(ctx)
         for name in _idents(e):
             if name in self.private_ctx:
                 _, declared_inside = self.private_ctx[name]
@@ -475,8 +588,30 @@ class Emitter:
 
 
 def _shared_bytes(decl: str) -> int:
-    """Bytes of a '__shared__ T name[count];' declaration (4-byte elements)."""
-    return 4 * int(decl.split("[")[1].split("]")[0])
+    """Bytes of a '__shared__ T name[count];' (or scalar 'T name;') declaration, 4-byte elements."""
+    return 4 * int(decl.split("[")[1].split("]")[0]) if "[" in decl else 4
+
+
+class Shuffle(P.Phrase):
+    """The value of e in the lane ``offset`` lanes above this one (emitted by
+    the lane tree only)."""
+
+    def __init__(self, e, offset: int):
+        self.e, self.offset, self.type = e, offset, e.type
+
+    def children(self):
+        return (self.e,)
+
+
+def _block_uniform(ctx) -> bool:
+    """Every thread of the block runs code in ctx (no thread-level loop or guard
+    around it), so a block barrier there is reached by all of them."""
+    return not (set(ctx) & {"local", "global", "warp", "lane", "guarded"})
+
+
+def _per_thread(ctx) -> bool:
+    """Code in ctx runs once per thread (inside a local, global or lane loop)."""
+    return "local" in ctx or "global" in ctx or "lane" in ctx
 
 
 def _shares(c) -> bool:
@@ -487,6 +622,8 @@ def _shares(c) -> bool:
         return _shares(c.body)
     if isinstance(c, T.Seq):
         return any(_shares(x) for x in c.cs)
+    if isinstance(c, T.TreeReduce):
+        return _shares(c.fill)
     return False
 
 
@@ -497,7 +634,17 @@ def _has_level(c, level) -> bool:
         return any(_has_level(x, level) for x in c.cs)
     if isinstance(c, T.New):
         return _has_level(c.body, level)
+    if isinstance(c, T.TreeReduce):
+        return c.level == level or _has_level(c.fill, level)
+    if isinstance(c, T.LastBlock):
+        return _has_level(c.body, level)
     return False
+
+
+def _threaded(c) -> bool:
+    """c runs loops spread over the block's threads (its reads and writes of
+    shared temporaries need barriers around them)."""
+    return any(_has_level(c, lvl) for lvl in THREADED)
 
 
 def _idents(e):
@@ -516,8 +663,9 @@ def generate(name: str, expr: P.Phrase, inputs: list, backend: str = "cuda", unr
     import re
 
     for p in inputs:
-        if not re.fullmatch(r"[A-Za-z_][A-Za-z_0-9]*", p.name) or re.fullmatch(r"[tir]\d+|out|dpia_\w*", p.name):
-            raise EmitError(f"input name {p.name!r}: a C identifier other than out, dpia_*, t<k>, i<k>, r<k>")
+        if not re.fullmatch(r"[A-Za-z_][A-Za-z_0-9]*", p.name) or re.fullmatch(r"[tirl]\d+|out|dpia_\w*", p.name):
+            raise EmitError(f"input name {p.name!r}: a C identifier other than out, dpia_*, t<k>, i<k>, r<k>, "
+                            f"l<k>")
     if len({p.name for p in inputs}) != len(inputs):
         raise EmitError("two inputs share a name")
     comm, out = T.translate(expr, "out")

@@ -3,20 +3,32 @@ language (Sections 2.1, 3.3 and 6.2), with their types.
 
 A phrase is built from inputs (``Ident``), literals, arithmetic on numbers,
 ``map`` at a level of the GPU hierarchy (mapGlobal / mapWorkgroup / mapLocal /
-mapSeq), the sequential ``reduce`` (reduceSeq), and the data-layout
-primitives ``zip``, ``fst``, ``snd``, ``split``, ``join``, ``transpose``,
-``asVector`` and ``asScalar`` (vectors num<V> of Section 6.2, + - * lane-wise);
-``to_private`` / ``to_local`` / ``to_global`` choose the address space of a
-map's output when it becomes a temporary (Section 6.2, address spaces).
-Types are checked as the phrase is built: a number type, an array ``n.d`` or
-a pair.
+mapSeq, and between work-group and work-item the warp: mapWarp over a block's
+warps, mapLane over a warp's 32 lanes), the sequential ``reduce``
+(reduceSeq), and the data-layout primitives ``zip``, ``fst``, ``snd``,
+``split``, ``join``, ``transpose``, ``asVector`` and ``asScalar`` (vectors
+num<V> of Section 6.2, + - * lane-wise) and ``lanes`` (a vector's V numbers
+as an array); ``to_private`` / ``to_local`` / ``to_global`` choose the
+address space of a map's output when it becomes a temporary (Section 6.2,
+address spaces). Types are checked as the phrase is built: a number type, an
+array ``n.d`` or a pair.
+
+Two constructs go beyond the paper's primitives, each with a plain meaning:
+``reduceTree lane f xs`` reduces L <= 32 numbers (L a power of two) by the
+halving tree -- element l becomes f(x_l, x_{l + L/2}), repeated until one
+remains -- one number per lane of a warp (on the GPU, warp shuffles); and
+``secondLevel parts f`` is f applied to the array ``parts`` that a work-group
+map produces: the work-groups write their parts, and f runs in one work-group
+once all of them have (the join and second-level reduce of Section 2.1 in
+the same kernel, by the last work-group to finish).
 """
 from __future__ import annotations
 
 import itertools
 from dataclasses import dataclass, field
 
-LEVELS = ("global", "workgroup", "local", "seq")
+LEVELS = ("global", "workgroup", "warp", "lane", "local", "seq")
+WARP = 32  # lanes of a warp
 SPACES = ("global", "local", "private")
 
 # ---------------------------------------------------------------------------
@@ -418,6 +430,72 @@ class Idx(Phrase):
         return (self.e,)
 
 
+@dataclass(eq=False)
+class Lanes(Phrase):
+    """lanes: num<V> -> V.num, the vector's numbers as an array (a view)."""
+    e: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        if not isinstance(self.e.type, VecT):
+            raise TypeError(f"lanes of a non-vector {self.e.type}")
+        self.type = Arr(self.e.type.n, self.e.type.num)
+
+    def children(self):
+        return (self.e,)
+
+
+@dataclass(eq=False)
+class ReduceTree(Phrase):
+    """reduceTree lane f xs: the halving tree over L = len xs numbers, L a power
+    of two no larger than a warp: while L > 1, x_l := f(x_l, x_{l + L/2}) for
+    l < L/2, L := L/2; the result is x_0."""
+    level: str
+    f: Lam
+    e: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        t = self.e.type
+        if self.level != "lane":
+            raise TypeError(f"reduceTree at level {self.level}: trees run over the lanes of a warp")
+        if not (isinstance(t, Arr) and isinstance(t.elem, Num) and t.n >= 1 and t.n & (t.n - 1) == 0
+                and t.n <= WARP):
+            raise TypeError(f"reduceTree over {t}: a power-of-two array of at most {WARP} numbers")
+        ps = self.f.params
+        if len(ps) != 2 or ps[0].type != t.elem or ps[1].type != t.elem or self.f.body.type != t.elem:
+            raise TypeError("reduceTree's function combines two elements into one")
+        self.type = t.elem
+
+    def children(self):
+        return (self.e, self.f.body)
+
+    def computes(self):
+        return True
+
+
+@dataclass(eq=False)
+class SecondLevel(Phrase):
+    """secondLevel parts f: f applied to the array of per-work-group parts, in
+    one work-group after every work-group has written its part."""
+    parts: Phrase
+    f: Lam
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        if not isinstance(self.parts.type, Arr) or not isinstance(base_elem(self.parts.type), Num):
+            raise TypeError(f"second level over {self.parts.type}: an array of numbers")
+        if len(self.f.params) != 1 or self.f.params[0].type != self.parts.type:
+            raise TypeError("the second level's function takes the array of parts")
+        self.type = self.f.body.type
+
+    def children(self):
+        return (self.parts, self.f.body)
+
+    def computes(self):
+        return True
+
+
 # ---------------------------------------------------------------------------
 # constructors in the paper's notation
 # ---------------------------------------------------------------------------
@@ -443,6 +521,31 @@ def mapLocal(f, e):
 
 def mapSeq(f, e):
     return map_at("seq", f, e)
+
+
+def mapWarp(f, e):
+    """map over the warps of a work-group (one element per warp)."""
+    return map_at("warp", f, e)
+
+
+def mapLane(f, e):
+    """map over the 32 lanes of a warp (one element per lane)."""
+    return map_at("lane", f, e)
+
+
+def lanes(e):
+    return Lanes(e)
+
+
+def reduceTree(f, e, level="lane"):
+    """f is a Python function (a, b) -> combined element."""
+    t = e.type.elem if isinstance(e.type, Arr) else None
+    return ReduceTree(level, lam([t, t], f), e)
+
+
+def secondLevel(parts, fn):
+    """fn is a Python function of the array of parts."""
+    return SecondLevel(parts, lam([parts.type], fn))
 
 
 def reduceSeq(f, init, e):
@@ -569,6 +672,12 @@ def subst(p: Phrase, env: dict) -> Phrase:
         return AsScalar(subst(p.e, env))
     if isinstance(p, Idx):
         return Idx(subst(p.e, env), p.i)
+    if isinstance(p, Lanes):
+        return Lanes(subst(p.e, env))
+    if isinstance(p, ReduceTree):
+        return ReduceTree(p.level, Lam(p.f.params, subst(p.f.body, env)), subst(p.e, env))
+    if isinstance(p, SecondLevel):
+        return SecondLevel(subst(p.parts, env), Lam(p.f.params, subst(p.f.body, env)))
     raise TypeError(f"cannot substitute into {type(p).__name__}")
 
 

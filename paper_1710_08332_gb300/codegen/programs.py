@@ -200,3 +200,116 @@ def fold_pairs_all(m: int):
     p = P.inp("p", P.arr(2 * m, P.F32))
     return P.fst(P.reduceSeq(lambda pr, acc: kahan_merge(acc, P.Idx(pr, IConst(0)), P.Idx(pr, IConst(1))),
                              _zero_pair(), _pair_items(p, m))), [p]
+
+
+# ---------------------------------------------------------------------------
+# the whole strategy in one kernel: per-thread folds, the in-block tree (lane
+# trees within warps, then over the warp sums), and the second level in the
+# last work-group
+# ---------------------------------------------------------------------------
+
+
+def _plus(a, b):
+    return P.add(a, b)
+
+
+def block_tree(parts):
+    """The block's tree over its T thread results (T a power of two, 1..1024):
+    a lane tree over each group of min(32, T) consecutive results, then a lane
+    tree over the group sums -- a one-element array (the work-group's result).
+    Each stage's input is a local temporary: other threads wrote it."""
+    T = parts.type.n
+    L = min(P.WARP, T)
+    sums = P.mapWarp(lambda g: P.reduceTree(_plus, g), P.split(L, P.to_local(parts)))
+    W = T // L
+    if W == 1:
+        return sums
+    return P.mapWarp(lambda g: P.reduceTree(_plus, g), P.split(W, P.to_local(sums)))
+
+
+def thread_results(chunk, T: int, thread_map: str, V: int, step, zero_lane=0.0):
+    """mapLocal over the chunk's T columns: each thread folds its column from
+    +0 with ``step`` (lane-wise on num<V>), then folds its V lanes in lane order
+    from +0."""
+    def column(col):
+        acc = P.reduceSeq(step, _zero(V), col)
+        if V == 1:
+            return acc
+        return P.reduceSeq(lambda v, a: P.add(a, v), P.lit(zero_lane), P.lanes(acc))
+    return P.mapLocal(column, columns(chunk, T, thread_map))
+
+
+def second_level(parts, second: str, T2: int):
+    """The fold of the C chunk results: in chunk order from +0 by one thread
+    (seq), or T2 threads each folding results r*T2 + t from +0, then the block
+    tree (tree; C must be a multiple of T2)."""
+    C = parts.type.n
+    if second == "seq":
+        return P.reduceSeq(lambda v, a: P.add(a, v), 0.0, parts)
+    if C % T2:
+        raise ValueError(f"a tree second level over {C} results needs a thread count dividing it, not {T2}")
+    cols = P.mapLocal(lambda col: P.reduceSeq(lambda v, a: P.add(a, v), 0.0, col), P.transpose(P.split(T2, parts)))
+    return block_tree(cols)
+
+
+def _reduce_R(items, n_items: int, s: int, T: int, thread_map: str, V: int, second: str, T2: int, step):
+    if s % (T * V) or n_items % s:
+        raise ValueError(f"split {s} over {T} threads x {V} lanes does not divide {n_items} items")
+    chunks = P.split(s // V, items)
+    parts = P.join(P.mapWorkgroup(lambda ch: block_tree(thread_results(ch, T, thread_map, V, step)), chunks))
+    return P.secondLevel(parts, lambda p: second_level(p, second, T2))
+
+
+def dot_R(n: int, s: int, T: int, V: int = 4, thread_map: str = "interleaved", second: str = "tree",
+          T2: int = 256):
+    """x . y in one kernel with the canonical strategy (split s, T threads per
+    chunk, V lanes, the thread map, the second level): the same tree as the
+    library's dot and the oracle's loop nest."""
+    x, y = P.inp("x", P.arr(n, P.F32)), P.inp("y", P.arr(n, P.F32))
+    step = lambda p, acc: P.add(acc, P.mul(P.fst(p), P.snd(p)))
+    return _reduce_R(P.zip_(_vec(x, V), _vec(y, V)), n, s, T, thread_map, V, second, T2, step), [x, y]
+
+
+def asum_R(n: int, s: int, T: int, V: int = 4, thread_map: str = "interleaved", second: str = "tree",
+           T2: int = 256):
+    """sum |x_i| in one kernel with the canonical strategy."""
+    x = P.inp("x", P.arr(n, P.F32))
+    step = lambda v, acc: P.add(acc, P.abs_(v))
+    return _reduce_R(_vec(x, V), n, s, T, thread_map, V, second, T2, step), [x]
+
+
+def gemv_R(M: int, N: int, T: int, V: int = 4, thread_map: str = "interleaved"):
+    """y = A x with a work-group per row (one chunk per row: split N): each row's
+    T thread folds and the block tree, in one kernel -- the library's GEMV with
+    rows at block level and split = N."""
+    if N % (T * V):
+        raise ValueError(f"a row of {N} does not split over {T} threads x {V} lanes")
+    A, x = P.inp("A", P.arr(M, N, P.F32)), P.inp("x", P.arr(N, P.F32))
+    step = lambda p, acc: P.add(acc, P.mul(P.fst(p), P.snd(p)))
+    e = P.join(P.mapWorkgroup(
+        lambda row: block_tree(thread_results(P.zip_(_vec(row, V), _vec(x, V)), T, thread_map, V, step)), A))
+    return e, [A, x]
+
+
+def gemv_R_warp(M: int, N: int, rows_per_block: int, V: int = 4):
+    """y = A x with rows at warp level: a work-group takes rows_per_block rows,
+    a warp per row; lane l folds the row's items l, l + 32, .. (interleaved, on
+    num<V>), folds its lanes, and the lane tree reduces the 32 results -- the
+    library's GEMV with rows at warp level and split = N."""
+    if N % (P.WARP * V) or M % rows_per_block:
+        raise ValueError("rows of N items over 32 lanes x V, and M rows over blocks of rows_per_block")
+    A, x = P.inp("A", P.arr(M, N, P.F32)), P.inp("x", P.arr(N, P.F32))
+    step = lambda p, acc: P.add(acc, P.mul(P.fst(p), P.snd(p)))
+
+    def lane_result(col):
+        acc = P.reduceSeq(step, _zero(V), col)
+        return acc if V == 1 else P.reduceSeq(lambda v, a: P.add(a, v), 0.0, P.lanes(acc))
+
+    e = P.join(P.mapWorkgroup(
+        lambda rows: P.mapWarp(
+            lambda row: P.reduceTree(_plus, P.mapLane(lane_result,
+                                                      columns(P.zip_(_vec(row, V), _vec(x, V)), P.WARP,
+                                                              "interleaved"))),
+            rows),
+        P.split(rows_per_block, A)))
+    return e, [A, x]

@@ -1,30 +1,44 @@
 """Rewrite-based exploration of strategies (the search Section 2.1 points to).
 
-A reduction starts as a strategy-free expression over a small grammar
+A computation starts as a strategy-free expression over a small grammar
 
     E ::= Reduce E | Map f E | Each B E | Split s E | Columns T m E | Vec V E | Input xs
+        | Tree E | Last k T2 E | Rows l B E
     B ::= E with a Hole for the element
 
-starting from ``Reduce (Map f (Input xs))`` (dot: f = (*) over zip x y; asum:
-f = abs). Rules rewrite the tree; each holds in real arithmetic for the
-associative + with identity 0:
+from ``Reduce (Map f (Input xs))`` (dot: f = (*) over zip x y; asum: f = abs;
+asum_scal: f = abs over the map (a *) of x, the sum of |a x_i|) or, for GEMV,
+``Rows block (Reduce (Map (*) Hole)) (Input A)`` (each row's reduce of its
+products with x). Rules rewrite the tree; each holds in real arithmetic for
+the associative + with identity 0:
 
   split(s)       Reduce (Map f X)          -> Reduce (Each (Reduce (Map f Hole)) (Split s X))
-  columns(T, m)  Each (Reduce (Map f Hole)) C
-                                           -> Each (Reduce (Each (Reduce (Map f Hole))
-                                                                 (Columns T m Hole))) C
-  vectorize(V)   ... Split s (Input xs)     -> ... Split (s/V) (Vec V (Input xs)), the map and
-                 the column folds then run lane-wise on num<V>, and each thread's V lane
-                 results join the partials
+  columns(T, m)  Reduce (Map f Hole), per chunk (or per row)
+                                           -> Reduce (Each (Reduce (Map f Hole)) (Columns T m Hole))
+  vectorize(V)   ... Split s (Input xs)     -> ... Split (s/V) (Vec V (Input xs)) (a row: Vec V);
+                 the map and the column folds then run lane-wise on num<V>
+  tree           Reduce (Each ... (Columns ..)) -> Tree (Each ... (Columns ..)): a chunk's (or a
+                 row's) column results reduced by the halving tree (lane trees within warps,
+                 then over the warp sums) instead of a fold
+  second(k, T2)  Reduce (Each (Tree ..) (Split s X)) -> Last k T2 (Each (Tree ..) (Split s X)):
+                 the chunk results reduced in the same kernel by the last work-group to finish
+                 (k = seq: a fold in chunk order; tree: T2 strided folds, then the tree)
+  rows(l)        Rows block B A -> Rows l B A: a GEMV's rows mapped to work-groups (block) or to
+                 the warps of a work-group (warp; its columns are then the 32 lanes)
+  fuse_maps      Reduce (Map f (Map g X)) -> Reduce (Map (f . g) X): the inner map's result is
+                 never written out
+                 (one kernel instead of two; the value of every element is the same)
   fuse, lower    Reduce (Map f col) -> reduceSeq (lambda (x, a). a + f x) 0 col; the Each
-                 over Split -> mapWorkgroup, the Each over Columns -> mapLocal; the
-                 outermost Reduce over the per-thread partials becomes folding kernels
-                 (it reads what other blocks wrote: a kernel boundary)
+                 over Split -> mapWorkgroup, the Each over Columns -> mapLocal (mapLane for rows
+                 at warp level); an outermost Reduce over the per-thread partials becomes folding
+                 kernels (it reads what other blocks wrote: a kernel boundary), a Last becomes
+                 the second level in the last work-group of the same kernel
 
 ``derivations`` enumerates rule sequences over parameter grids, ``rewrite``
 applies one to the start expression (each rule checks the shape it rewrites),
 and ``lower`` turns the resulting tree into kernel phrases. Each derivation's
-result is exact for its own tree; different derivations round differently.
+result is exact for its own tree; different derivations round differently
+(except fuse_maps, which changes no value).
 """
 from __future__ import annotations
 
@@ -34,6 +48,8 @@ from dataclasses import dataclass, field
 from . import phrase as P
 from . import programs as PR
 
+SCALE = 1.5  # the a of asum_scal (the bandwidth workload's scal factor)
+
 # ---------------------------------------------------------------------------
 # the strategy-free grammar
 # ---------------------------------------------------------------------------
@@ -41,7 +57,7 @@ from . import programs as PR
 
 @dataclass(frozen=True)
 class Input:
-    name: str            # "dot" (zip x y) or "asum" (x)
+    name: str            # "dot" (zip x y), "asum" / "asum_scal" (x), "gemv" (A)
 
 
 @dataclass(frozen=True)
@@ -51,7 +67,7 @@ class Hole:
 
 @dataclass(frozen=True)
 class Map:
-    f: str               # "mul" (fst * snd) or "abs"
+    f: str               # "mul" (fst * snd), "abs", "scale" (a *), or "abs.scale" (fused)
     e: object
 
 
@@ -85,11 +101,34 @@ class Vec:
     e: object
 
 
+@dataclass(frozen=True)
+class Tree:
+    e: object
+
+
+@dataclass(frozen=True)
+class Last:
+    kind: str            # "seq" or "tree"
+    T2: int
+    e: object
+
+
+@dataclass(frozen=True)
+class Rows:
+    level: str           # "block" or "warp"
+    body: object
+    e: object
+
+
 HOLE = Hole()
 
 
 def start(kind: str):
-    """Reduce (Map f (Input xs)) for kind in {"dot", "asum"}."""
+    """The strategy-free expression of kind "dot", "asum", "asum_scal" or "gemv"."""
+    if kind == "gemv":
+        return Rows("block", Reduce(Map("mul", HOLE)), Input("gemv"))
+    if kind == "asum_scal":
+        return Reduce(Map("abs", Map("scale", Input(kind))))
     return Reduce(Map({"dot": "mul", "asum": "abs"}[kind], Input(kind)))
 
 
@@ -102,24 +141,41 @@ class RuleError(ValueError):
 # ---------------------------------------------------------------------------
 
 
+def _is_stream(x) -> bool:
+    """An input, or a map of one that is written out by a kernel of its own."""
+    return isinstance(x, Input) or (isinstance(x, Map) and isinstance(x.e, Input))
+
+
 def r_split(e, s: int):
-    if not (isinstance(e, Reduce) and isinstance(e.e, Map) and isinstance(e.e.e, Input)):
+    if not (isinstance(e, Reduce) and isinstance(e.e, Map) and _is_stream(e.e.e)):
         raise RuleError("split rewrites Reduce (Map f (Input xs))")
     return Reduce(Each(Reduce(Map(e.e.f, HOLE)), Split(s, e.e.e)))
 
 
+def _columns_of(body, T: int, m: str):
+    if not (isinstance(body, Reduce) and isinstance(body.e, Map) and body.e.e == HOLE):
+        raise RuleError("columns rewrites a per-chunk (or per-row) Reduce (Map f Hole)")
+    return Reduce(Each(Reduce(Map(body.e.f, HOLE)), Columns(T, m, HOLE)))
+
+
 def r_columns(e, T: int, m: str):
-    ok = (isinstance(e, Reduce) and isinstance(e.e, Each) and isinstance(e.e.body, Reduce)
-          and isinstance(e.e.body.e, Map) and e.e.body.e.e == HOLE)
-    if not ok:
+    if isinstance(e, Rows):
+        if e.level == "warp" and (T, m) != (P.WARP, "interleaved"):
+            raise RuleError("a row at warp level has the warp's 32 lanes as its interleaved columns")
+        return Rows(e.level, _columns_of(e.body, T, m), e.e)
+    if not (isinstance(e, Reduce) and isinstance(e.e, Each)):
         raise RuleError("columns rewrites the per-chunk Reduce (Map f Hole)")
-    f = e.e.body.e.f
-    return Reduce(Each(Reduce(Each(Reduce(Map(f, HOLE)), Columns(T, m, HOLE))), e.e.e))
+    return Reduce(Each(_columns_of(e.e.body, T, m), e.e.e))
 
 
 def r_vectorize(e, V: int):
+    if isinstance(e, Rows):
+        if not isinstance(e.e, Input):
+            raise RuleError("vectorize applies once")
+        return Rows(e.level, e.body, Vec(V, e.e))
+
     def go(x):
-        if isinstance(x, Split) and isinstance(x.e, Input):
+        if isinstance(x, Split) and _is_stream(x.e):
             if x.s % V:
                 raise RuleError(f"split {x.s} is not a multiple of the width {V}")
             return Split(x.s // V, Vec(V, x.e))
@@ -131,7 +187,42 @@ def r_vectorize(e, V: int):
     return go(e)
 
 
-RULES = {"split": r_split, "columns": r_columns, "vectorize": r_vectorize}
+def _tree_of(body):
+    if not (isinstance(body, Reduce) and isinstance(body.e, Each) and isinstance(body.e.e, Columns)):
+        raise RuleError("tree rewrites the Reduce over a chunk's (or row's) columns")
+    return Tree(body.e)
+
+
+def r_tree(e):
+    if isinstance(e, Rows):
+        return Rows(e.level, _tree_of(e.body), e.e)
+    if not (isinstance(e, Reduce) and isinstance(e.e, Each)):
+        raise RuleError("tree rewrites the Reduce over a chunk's columns")
+    return Reduce(Each(_tree_of(e.e.body), e.e.e))
+
+
+def r_second(e, kind: str, T2: int):
+    if not (isinstance(e, Reduce) and isinstance(e.e, Each) and isinstance(e.e.body, Tree)):
+        raise RuleError("second rewrites the Reduce over the chunks' tree results")
+    if kind not in ("seq", "tree"):
+        raise RuleError(f"second level {kind}: seq or tree")
+    return Last(kind, T2, e.e)
+
+
+def r_rows(e, level: str):
+    if not isinstance(e, Rows) or level not in ("block", "warp"):
+        raise RuleError("rows rewrites a GEMV's row map to block or warp level")
+    return Rows(level, e.body, e.e)
+
+
+def r_fuse_maps(e):
+    if not (isinstance(e, Reduce) and isinstance(e.e, Map) and isinstance(e.e.e, Map)):
+        raise RuleError("fuse_maps rewrites Reduce (Map f (Map g X))")
+    return Reduce(Map(f"{e.e.f}.{e.e.e.f}", e.e.e.e))
+
+
+RULES = {"split": r_split, "columns": r_columns, "vectorize": r_vectorize, "tree": r_tree, "second": r_second,
+         "rows": r_rows, "fuse_maps": r_fuse_maps}
 
 
 @dataclass(frozen=True)
@@ -166,20 +257,44 @@ def rewrite(kind: str, d: Derivation):
 # ---------------------------------------------------------------------------
 
 
-def _elem_fn(f: str):
+def _elem_fn(f: str, V: int = 1):
+    """The per-item function of a map: mul (fst * snd), abs, or abs of (a *)."""
     if f == "mul":
         return lambda x: P.mul(P.fst(x), P.snd(x))
-    return lambda x: P.abs_(x)
+    if f == "abs":
+        return lambda x: P.abs_(x)
+    if f == "abs.scale":
+        a = P.lit(SCALE) if V == 1 else P.vlit(SCALE, V)
+        return lambda x: P.abs_(P.mul(a, x))
+    raise RuleError(f"no element function {f}")
 
 
-def lower(kind: str, d: Derivation, n: int):
-    """Kernel phrases for a derivation: [(name, phrase, inputs), ...]: the
-    per-thread partials, then folding kernels down to one number."""
+def _stream(kind: str, n: int, V: int, materialized: bool):
+    """(inputs, the item stream) of a reduction: zip x y for dot, x otherwise (y,
+    the output of the map kernel before it, when the inner map is written out)."""
+    if kind == "dot":
+        x, y = P.inp("x", P.arr(n, P.F32)), P.inp("y", P.arr(n, P.F32))
+        return [x, y], (P.zip_(x, y) if V == 1 else P.zip_(P.asVector(V, x), P.asVector(V, y)))
+    x = P.inp("y" if materialized else "x", P.arr(n, P.F32))
+    return [x], (x if V == 1 else P.asVector(V, x))
+
+
+def lower(kind: str, d: Derivation, n: int, M: int = 0):
+    """Kernel phrases for a derivation: [(name, phrase, inputs), ...], run in
+    order, each reading the previous one's output. Reductions: the per-thread
+    partials and then folding kernels down to one number (the paper's form), or
+    one kernel when the chunk results are reduced in the last work-group (a
+    materialized inner map adds a kernel in front). GEMV (n = columns, M rows):
+    one kernel, or partials and row folds."""
     e = rewrite(kind, d)
-    # expected shape: Reduce (Each (Reduce (Each (Reduce (Map f Hole)) (Columns T m Hole))) (Split s S))
+    if kind == "gemv":
+        return _lower_gemv(e, M, n)
+    kernels = []
+    top = e
     try:
-        chunk_each = e.e
-        col_each = chunk_each.body.e
+        chunk_each = top.e
+        body = chunk_each.body
+        col_each = body.e
         f = col_each.body.e.f
         T, m = col_each.e.T, col_each.e.m
         sp = chunk_each.e
@@ -187,21 +302,30 @@ def lower(kind: str, d: Derivation, n: int):
     except AttributeError as exc:
         raise RuleError(f"derivation {d} does not reach the lowerable shape") from exc
     V = stream.V if isinstance(stream, Vec) else 1
-    if kind == "dot":
-        x, y = P.inp("x", P.arr(n, P.F32)), P.inp("y", P.arr(n, P.F32))
-        ins = [x, y]
-        xs = P.zip_(x, y) if V == 1 else P.zip_(P.asVector(V, x), P.asVector(V, y))
-    else:
-        x = P.inp("x", P.arr(n, P.F32))
-        ins = [x]
-        xs = x if V == 1 else P.asVector(V, x)
-    g = _elem_fn(f)
+    base = stream.e if isinstance(stream, Vec) else stream
+    materialized = isinstance(base, Map)
+    if materialized:  # the inner map is a kernel of its own that writes its result out
+        ph, ins = PR.scal(n, SCALE, V=V)
+        kernels.append(("map_scale", ph, ins))
+    ins, xs = _stream(kind, n, V, materialized)
+    g = _elem_fn(f, V)
     zero = P.lit(0.0) if V == 1 else P.vlit(0.0, V)
+    if isinstance(top, Last):
+        if not isinstance(body, Tree):
+            raise RuleError("the second level needs the chunks' tree results")
+        step = lambda v, a: P.add(a, g(v))
+        s_items = s * V  # the split counted in numbers (s counts the stream's vectors)
+        T2 = min(top.T2, n // s_items) if top.kind == "tree" else 1
+        ph = PR._reduce_R(xs, n, s_items, T, m, V, top.kind, T2, step)
+        kernels.append(("one_kernel", ph, ins))
+        return kernels
+    if isinstance(body, Tree):
+        raise RuleError("a chunk tree needs the second level in the same kernel (second)")
     first = P.join(P.mapWorkgroup(
         lambda chunk: P.mapLocal(lambda col: P.reduceSeq(lambda v, a: P.add(a, g(v)), zero, col),
                                  PR.columns(chunk, T, m)),
         P.split(s, xs)))
-    kernels = [("partials", first, ins)]
+    kernels.append(("partials", first, ins))
     left = n // (s * V) * T * V
     for grp in fold_plan(left):
         if grp == left:
@@ -212,6 +336,28 @@ def lower(kind: str, d: Derivation, n: int):
             kernels.append((f"fold{grp}", ph, i2))
         left //= grp
     return kernels
+
+
+def _lower_gemv(e, M: int, N: int):
+    try:
+        level, body, src = e.level, e.body, e.e
+        V = src.V if isinstance(src, Vec) else 1
+        col_each = body.e
+        T, m = col_each.e.T, col_each.e.m
+    except AttributeError as exc:
+        raise RuleError("a GEMV derivation needs its columns") from exc
+    if level == "warp":
+        if not isinstance(body, Tree):
+            raise RuleError("rows at warp level reduce their lanes by the tree")
+        rpb = next(r for r in (8, 4, 2, 1) if M % r == 0)
+        ph, ins = PR.gemv_R_warp(M, N, rpb, V)
+        return [("one_kernel", ph, ins)]
+    if isinstance(body, Tree):
+        ph, ins = PR.gemv_R(M, N, T, V, m)
+        return [("one_kernel", ph, ins)]
+    ph, ins = PR.gemv_partials(M, N, T, m, V)
+    ph2, i2 = PR.fold_rows(M, T * V)
+    return [("partials", ph, ins), ("rows", ph2, i2)]
 
 
 def fold_plan(m: int) -> list:
@@ -230,17 +376,40 @@ def fold_plan(m: int) -> list:
 
 
 def derivations(n: int, splits=(1 << 14, 1 << 15, 1 << 16), threads=(128, 256, 512),
-                maps=("interleaved", "contig"), widths=(1, 4)):
-    """Every derivation over the parameter grids whose rules apply."""
+                maps=("interleaved", "contig"), widths=(1, 4), forms=("paper",), kind: str = "dot"):
+    """Every derivation over the parameter grids whose rules apply. forms:
+    "paper" (per-thread partials, then folding kernels) and/or "single" (the
+    chunk's tree and the second level in the last work-group: one kernel); for
+    asum_scal each derivation comes with and without fuse_maps."""
     out = []
-    for s, T, m, V in itertools.product(splits, threads, maps, widths):
+    fuse_opts = (False, True) if kind == "asum_scal" else (False,)
+    for s, T, m, V, form, fm in itertools.product(splits, threads, maps, widths, forms, fuse_opts):
         if n % s or (s // V) % T or s % V:
             continue
-        rules = [Rule("split", (s,)), Rule("columns", (T, m))]
+        rules = ([Rule("fuse_maps")] if fm else []) + [Rule("split", (s,)), Rule("columns", (T, m))]
         if V > 1:
             rules.append(Rule("vectorize", (V,)))
+        if form == "single":
+            rules += [Rule("tree"), Rule("second", ("tree", min(256, T, n // s)))]
         rules += [Rule("fuse"), Rule("lower")]
         out.append(Derivation(rules))
+    return out
+
+
+def gemv_derivations(M: int, N: int, threads=(64, 128, 256), widths=(1, 4)):
+    """GEMV derivations: rows at block level (T columns, interleaved or contig,
+    the row's tree in one kernel or partials and row folds) and at warp level."""
+    out = []
+    for T, m, V, tree in itertools.product(threads, ("interleaved", "contig"), widths, (True, False)):
+        if N % (T * V):
+            continue
+        rules = [Rule("columns", (T, m))] + ([Rule("vectorize", (V,))] if V > 1 else [])
+        out.append(Derivation(rules + ([Rule("tree")] if tree else []) + [Rule("fuse"), Rule("lower")]))
+    for V in widths:
+        if N % (P.WARP * V) == 0:
+            out.append(Derivation([Rule("rows", ("warp",)), Rule("columns", (P.WARP, "interleaved"))]
+                                  + ([Rule("vectorize", (V,))] if V > 1 else []) + [Rule("tree"), Rule("fuse"),
+                                                                                     Rule("lower")]))
     return out
 
 
@@ -249,14 +418,16 @@ def derivations(n: int, splits=(1 << 14, 1 << 15, 1 << 16), threads=(128, 256, 5
 # ---------------------------------------------------------------------------
 
 
-def compile_pipeline(kind: str, d: Derivation, n: int):
+def compile_pipeline(kind: str, d: Derivation, n: int, M: int = 0):
     """CUDA kernels of a derivation with their launch shapes: [(kernel, grid, block)]."""
     from .build import compile_cuda
 
     out = []
-    for name, ph, ins in lower(kind, d, n):
-        tag = f"{kind}_{name}_" + "_".join(str(a) for r in d.rules for a in r.args)
-        k = compile_cuda(("x" + tag).replace("-", "_"), ph, ins, unroll=4 if name == "partials" else 64)
+    for name, ph, ins in lower(kind, d, n, M):
+        tag = f"{kind}_{name}_" + "_".join(str(a) for r in d.rules for a in r.args) + \
+            ("_fm" if any(r.name == "fuse_maps" for r in d.rules) else "")
+        k = compile_cuda(("x" + tag).replace("-", "_").replace(".", "_").replace(",", "_").replace(" ", ""),
+                         ph, ins, unroll=4 if name in ("partials", "one_kernel") else 64)
         grid, block = k.default_launch()
         if name.startswith("fold") and name != "partials":  # a thread per group, blocks of 64 over many SMs
             rows = ph.type.n if isinstance(ph.type, P.Arr) else 1
@@ -280,13 +451,20 @@ def run_pipeline(pipe, inputs, device="cuda"):
     return out
 
 
-def explore(kind: str, inputs, n: int, derivs=None, reps: int = 5):
-    """Time every derivation's pipeline on the inputs; return [(ms, derivation)] fastest first."""
+def explore(kind: str, inputs, n: int, derivs=None, reps: int = 5, M: int = 0):
+    """Time every derivation's pipeline on the inputs; return [(ms, derivation)]
+    fastest first. The pipelines are compiled first, on several host threads."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
     from ..tune import time_call
 
+    derivs = derivs or (gemv_derivations(M, n) if kind == "gemv" else derivations(n, kind=kind))
+    workers = max(1, min(16, len(os.sched_getaffinity(0))))
+    with ThreadPoolExecutor(workers) as pool:
+        pipes = list(pool.map(lambda d: compile_pipeline(kind, d, n, M), derivs))
     results = []
-    for d in derivs or derivations(n):
-        pipe = compile_pipeline(kind, d, n)
+    for d, pipe in zip(derivs, pipes):
         results.append((time_call(lambda: run_pipeline(pipe, inputs), reps=reps, warmup=2), d))
     results.sort(key=lambda t: t[0])
     return results

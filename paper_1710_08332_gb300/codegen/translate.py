@@ -14,9 +14,13 @@ private accumulator, its initialisation, a sequential for loop and the
 continuation applied to the accumulator.
 
 The result is a command tree of ``New`` (a temporary in an address space),
-``For`` (a loop at a level), ``Assign`` (acceptor := expression) and ``Seq``.
+``For`` (a loop at a level), ``Assign`` (acceptor := expression) and ``Seq``,
+plus ``TreeReduce`` (a lane tree: each lane's element written into a
+buffer, then the halving tree over it) and ``LastBlock`` (a command run by
+the last work-group to finish the kernel's work-group loop: the second level).
 Nested maps must run at strictly finer levels (workgroup > local > seq;
-global > seq), the legality rule the paper's conclusion asks for.
+workgroup > warp > lane > seq; global > seq), the legality rule the paper's
+conclusion asks for.
 """
 from __future__ import annotations
 
@@ -111,6 +115,7 @@ class Temp:
     type: object
     space: str
     hoist: list = field(default_factory=list)  # [(loop variable, trip count)] outermost first
+    lanes: bool = False  # a lane tree's buffer: element l belongs to lane l of the warp
 
 
 class Acc:
@@ -196,6 +201,27 @@ class For(Comm):
     body: Comm
 
 
+@dataclass(eq=False)
+class TreeReduce(Comm):
+    """fill writes element l of buf (an L-array, L a power of two <= 32) at
+    level ``level``; then, while L > 1, buf[l] := f(buf[l], buf[l + L/2]) for
+    l < L/2 and L := L/2; finally res := buf[0]."""
+    level: str
+    buf: Temp
+    fill: Comm
+    f: object  # P.Lam of two elements
+    res: Temp
+
+
+@dataclass(eq=False)
+class LastBlock(Comm):
+    """body runs once, in the last work-group to finish everything before it
+    (every work-group takes a ticket from the counter ``ticket``; the one that
+    draws the last runs body and puts the counter back to zero)."""
+    body: Comm
+    ticket: Temp
+
+
 class TranslationError(Exception):
     pass
 
@@ -204,7 +230,8 @@ class TranslationError(Exception):
 # Stage I + II
 # ---------------------------------------------------------------------------
 
-_RANK = {"global": 0, "workgroup": 0, "local": 1, "seq": 2}
+# the levels a parallel map at each level may contain (sequential maps nest anywhere)
+FINER = {"workgroup": ("local", "warp"), "warp": ("lane",)}
 
 
 class Translator:
@@ -223,12 +250,15 @@ class Translator:
 
     @staticmethod
     def check_nesting(outer: list, level: str):
-        if not outer:
-            return
-        last = outer[-1]
         if level == "seq":
             return
-        if last in ("global", "local", "seq") or (last == "workgroup" and level != "local"):
+        if not outer:
+            if level in ("warp", "lane"):
+                raise TranslationError(f"illegal nesting: a {level} map outside a "
+                                       f"{'workgroup' if level == 'warp' else 'warp'} map")
+            return
+        last = outer[-1]
+        if level not in FINER.get(last, ()):
             raise TranslationError(f"illegal nesting: a {level} map inside a {last} map "
                                    f"(a nested map must run at a strictly finer level)")
 
@@ -246,6 +276,8 @@ class Translator:
             return self.C(e.e, body, levels)
         if isinstance(e, P.Reduce):
             return self.C(e, lambda v: self.assign(out, v, levels), levels)
+        if isinstance(e, P.SecondLevel):
+            return self.second_level(e, out, levels)
         if isinstance(e, P.Split):
             return self.A(e.e, ASplit(e.n, out), levels)
         if isinstance(e, P.Join):
@@ -284,6 +316,43 @@ class Translator:
             raise TranslationError(f"cannot copy a value of type {v.type}")
         i = self.ivar()
         return For(i, v.type.n, "seq", self.copy(P.Idx(v, i), AIdx(out, i), levels + ["seq"]))
+
+    def second_level(self, e: P.SecondLevel, out: Acc, levels: list) -> Comm:
+        """The work-groups write their parts into a global temporary; the last
+        to finish applies f to it in one work-group (levels: inside a
+        work-group), writing the kernel's output."""
+        if levels:
+            raise TranslationError("the second level closes a kernel: it must be the kernel's whole expression")
+        g = self.temp(e.parts.type, "global")
+        gv = P.Ident(g.name, g.type, temp="global")
+        ticket = self.temp(P.I32, "global")
+        first = self.A(e.parts, AOut(g.name, g.type, g), [])
+        body = self.A(P.apply(e.f, gv), out, ["workgroup"])
+        return New(g, New(ticket, Seq([first, LastBlock(body, ticket)])))
+
+    def tree(self, e: P.ReduceTree, k, levels: list) -> Comm:
+        """reduceTree lane: inside a warp map, lane l holds element l of the
+        array (a lane map fills it directly), then the halving tree."""
+        if not levels or levels[-1] != "warp":
+            raise TranslationError("a lane tree runs directly inside a warp map")
+        L = e.e.type.n
+        buf = self.temp(e.e.type, "private")
+        buf.lanes = True
+        res = self.temp(e.type, "private")
+        bacc = AOut(buf.name, buf.type, buf)
+        src = e.e
+        if isinstance(src, P.Map) and src.level == "lane":
+            fill = self.A(src, bacc, levels)
+        elif not src.computes():
+            i = self.ivar("l")
+            fill = For(i, L, "lane", self.A(P.Idx(src, i), AIdx(bacc, i), levels + ["lane"]))
+        else:
+            def copy_in(v):
+                i = self.ivar("l")
+                return For(i, L, "lane", self.A(P.Idx(v, i), AIdx(bacc, i), levels + ["lane"]))
+            fill = self.C(src, copy_in, levels)
+        rv = P.Ident(res.name, res.type, temp="private")
+        return New(res, Seq([TreeReduce("lane", buf, fill, e.f, res), k(rv)]))
 
     # -- C: continuation-passing --------------------------------------------
 
@@ -344,6 +413,12 @@ class Translator:
             return self.C(e.e, lambda v: k(P.AsVector(e.n, v)), levels)
         if isinstance(e, P.AsScalar):
             return self.C(e.e, lambda v: k(P.AsScalar(v)), levels)
+        if isinstance(e, P.Lanes):
+            return self.C(e.e, lambda v: k(P.Lanes(v)), levels)
+        if isinstance(e, P.ReduceTree):
+            return self.tree(e, k, levels)
+        if isinstance(e, P.SecondLevel):
+            raise TranslationError("the second level's value is the kernel's output, not an operand")
         raise TranslationError(f"cannot translate {type(e).__name__}")
 
 
@@ -373,4 +448,9 @@ def hoist(c: Comm, loops=()) -> list:
         found += hoist(c.body, loops)
     elif isinstance(c, For):
         found += hoist(c.body, loops + ((c.var, c.n, c.level),))
+    elif isinstance(c, TreeReduce):
+        found += [c.buf, c.res]
+        found += hoist(c.fill, loops)
+    elif isinstance(c, LastBlock):
+        found += hoist(c.body, ())
     return found

@@ -18,15 +18,18 @@ index, written or read, is bounded by the length of the array it indexes
 (a loop's trip count may not exceed it). Further:
 the body may not read a temporary that the same parallel loop writes (the
 acceptor of a variable and its expression would interfere), and parallel
-loops nest at strictly finer levels (workgroup > local; global and local
-hold only sequential loops; nothing parallel inside a sequential loop).
+loops nest at strictly finer levels (workgroup > local; workgroup > warp >
+lane; global, local and lane hold only sequential loops; nothing parallel
+inside a sequential loop). A lane tree's fill is a lane loop writing its own
+element of the tree's buffer, and its function combines two elements into
+one; the last block's second level is checked as the body of one work-group.
 """
 from __future__ import annotations
 
 from . import phrase as P
 from . import translate as T
 
-PARALLEL = ("global", "workgroup", "local")
+PARALLEL = ("global", "workgroup", "warp", "lane", "local")
 
 
 class TypeCheckError(Exception):
@@ -169,6 +172,10 @@ def _reads(c: T.Comm, out: set):
         _reads(c.body, out)
     elif isinstance(c, T.Assign):
         _temps_read(c.e, out)
+    elif isinstance(c, T.TreeReduce):
+        _reads(c.fill, out)
+    elif isinstance(c, T.LastBlock):
+        _reads(c.body, out)
 
 
 # ---------------------------------------------------------------------------
@@ -203,9 +210,12 @@ def _check(c: T.Comm, frames: list, levels: list, trips: dict, out: T.AOut | Non
             raise TypeCheckError(f"loop over {c.var.name} at unknown level {c.level}")
         if c.level in PARALLEL and levels:
             last = levels[-1]
-            if last in ("global", "local", "seq") or (last == "workgroup" and c.level != "local"):
+            if c.level not in T.FINER.get(last, ()):
                 raise TypeCheckError(f"a {c.level} loop inside a {last} loop (parallel loops nest at "
                                      f"strictly finer levels, never inside a sequential loop)")
+        if c.level in ("warp", "lane") and (not levels or levels[-1] != {"warp": "workgroup",
+                                                                         "lane": "warp"}[c.level]):
+            raise TypeCheckError(f"a {c.level} loop outside a {'workgroup' if c.level == 'warp' else 'warp'} loop")
         inner = {**trips, c.var.name: c.n}
         if c.level in PARALLEL:
             f = _Frame(c.var, c.level)
@@ -239,6 +249,22 @@ def _check(c: T.Comm, frames: list, levels: list, trips: dict, out: T.AOut | Non
         for f in frames:  # temporaries declared outside a loop and written inside it
             if root.temp is not None and root.name not in f.local:
                 f.written.add(root.name)
+    elif isinstance(c, T.TreeReduce):
+        t = c.buf.type
+        if not (isinstance(t, P.Arr) and t.n & (t.n - 1) == 0 and t.n <= P.WARP and c.res.type == t.elem):
+            raise TypeCheckError(f"lane tree over acc[{t}] into {c.res.type}")
+        ps = c.f.params
+        if len(ps) != 2 or any(p.type != t.elem for p in ps) or c.f.body.type != t.elem:
+            raise TypeCheckError("a lane tree's function combines two elements into one")
+        if not levels or levels[-1] != "warp":
+            raise TypeCheckError("a lane tree runs directly inside a warp loop")
+        for f in frames:  # the buffer and the result belong to this iteration
+            f.local.update((c.buf.name, c.res.name))
+        _check(c.fill, frames, levels, trips, out)
+    elif isinstance(c, T.LastBlock):
+        if frames or levels:
+            raise TypeCheckError("the last block's second level runs outside every loop")
+        _check(c.body, [], ["workgroup"], trips, out)
     else:
         raise TypeCheckError(f"unknown command {type(c).__name__}")
 

@@ -48,7 +48,7 @@ def oracle_fold(p):
 
 @pytest.mark.parametrize("thread_map", ["interleaved", "contig"])
 @pytest.mark.parametrize("n,s,Tn", [(4096, 512, 32), (6144, 2048, 64), (256, 256, 1)])
-def test_dot_two_kernels_match_oracle(n, s, Tn, thread_map):
+def test_dot_two_kernels_match_oracle(c_build, n, s, Tn, thread_map):
     x, y = uniform(n, 1), uniform(n, 2)
     e, ins = PR.dot_partials(n, s, Tn, thread_map)
     part = np.zeros(n // s * Tn, np.float32)
@@ -61,7 +61,7 @@ def test_dot_two_kernels_match_oracle(n, s, Tn, thread_map):
     assert bits(out)[0] == bits([oracle_fold(want)])[0]
 
 
-def test_dot_K1_is_the_sequential_loop():
+def test_dot_K1_is_the_sequential_loop(c_build):
     x, y = uniform(1000, 3), uniform(1000, 4)
     e, ins = PR.dot_K1(1000)
     out = np.zeros(1, np.float32)
@@ -72,7 +72,7 @@ def test_dot_K1_is_the_sequential_loop():
     assert bits(out)[0] == bits([acc])[0]
 
 
-def test_asum_scal_gemv_match_oracle():
+def test_asum_scal_gemv_match_oracle(c_build):
     n, s, Tn = 8192, 1024, 64
     x = uniform(n, 5)
     x[::7] = -x[::7]
@@ -107,7 +107,7 @@ def test_asum_scal_gemv_match_oracle():
 
 
 @pytest.mark.parametrize("space", ["global", "private", "local"])
-def test_temporaries_in_each_address_space(space):
+def test_temporaries_in_each_address_space(c_build, space):
     """A map's output consumed inside a workgroup loop becomes a temporary in
     the annotated space; a global one is hoisted out of the parallel loop with
     one slice per iteration (Section 6.4)."""
@@ -131,15 +131,29 @@ def test_temporaries_in_each_address_space(space):
     assert np.array_equal(bits(out), bits(want))
 
 
-def test_openmp_outer_loop_gives_the_same_bits():
-    n, s, Tn = 1 << 16, 4096, 128
-    x, y = uniform(n, 10), uniform(n, 11)
-    e, ins = PR.dot_partials(n, s, Tn)
-    a = np.zeros(n // s * Tn, np.float32)
-    b = np.zeros_like(a)
-    G.compile_c("dotp", e, ins).run(x, y, a)
-    G.compile_c("dotp", e, ins, openmp=True).run(x, y, b)
-    assert np.array_equal(bits(a), bits(b))
+@pytest.fixture(params=["serial", "openmp"])
+def c_build(request, monkeypatch):
+    """Run a test's host builds serially and again with the outermost parallel
+    loop on OpenMP threads (the paper's multicore target): both must equal the
+    oracle."""
+    if request.param == "openmp":
+        orig = G.compile_c
+        monkeypatch.setattr(G, "compile_c", lambda *a, **k: orig(*a, **{**k, "openmp": True}))
+    return request.param
+
+
+def test_openmp_marks_only_parallel_loops():
+    """Only the outermost work-group or global loop runs on OpenMP threads: a
+    program whose top loop is a sequential fold (or the second level after the
+    work-group loop) keeps it on one thread."""
+    e, ins = PR.dot_partials(1 << 12, 512, 32)
+    assert G.compile_c("dotp", e, ins, openmp=True).source.count("#pragma omp parallel for") == 1
+    e, ins = PR.fold_all(256)
+    assert "#pragma omp" not in G.compile_c("fold", e, ins, openmp=True).source
+    e, ins = PR.dot_R(1 << 12, 512, 32, 4, "interleaved", "tree", 8)
+    src = G.compile_c("dR", e, ins, openmp=True).source
+    assert src.count("#pragma omp parallel for") == 1
+    assert src.index("#pragma omp") < src.index("for (long long i")
 
 
 def test_loop_nest_levels_follow_the_strategy():
@@ -223,7 +237,7 @@ def oracle_dot_partials_vec(x, y, s, Tn, thread_map, V=4):
 
 
 @pytest.mark.parametrize("thread_map", ["interleaved", "contig"])
-def test_vector_dot_scal_gemv_match_oracle(thread_map):
+def test_vector_dot_scal_gemv_match_oracle(c_build, thread_map):
     """asVector 4 streams, lane-wise folds, un-reduced lane partials (Section 6's float4 kernel)."""
     n, s, Tn = 8192, 2048, 64
     x, y = uniform(n, 12), uniform(n, 13)
@@ -342,7 +356,7 @@ def test_rewrite_rules_check_their_shapes():
 
 @pytest.mark.parametrize("kind", ["dot", "asum"])
 @pytest.mark.parametrize("tm,V", [("interleaved", 1), ("contig", 4)])
-def test_derived_pipelines_match_oracle(kind, tm, V):
+def test_derived_pipelines_match_oracle(c_build, kind, tm, V):
     """Every kernel of a derivation, run on the host, equals the oracle's
     evaluation of the same tree: per-thread folds (lanes with V), then the
     folding stages in order."""
@@ -378,7 +392,7 @@ def test_derived_pipelines_match_oracle(kind, tm, V):
     assert RW.fold_plan(1 << 21) == [128, 128, 128] and RW.fold_plan(3 * 257) == [3 * 257]
 
 
-def test_gemv_backward_programs_match_the_library_trees():
+def test_gemv_backward_programs_match_the_library_trees(c_build):
     """The generated dx (row chunks of R, then the chunk fold) computes the same
     tree as the library's dx kernel: equal to the loop-nest oracle of that
     kernel; dA = dy x^T exactly."""
@@ -416,7 +430,7 @@ def test_input_names_must_not_clash_with_generated_names():
             E.generate("k", G.mapGlobal(lambda v: G.mul(v, v), X), [X], "cuda")
 
 
-def test_random_dot_strategies_match_oracle():
+def test_random_dot_strategies_match_oracle(c_build):
     """Thirty random derivations (split, threads, thread map, width) on random
     lengths: every generated pipeline equals the oracle's evaluation of its tree."""
     rng = np.random.default_rng(60)
@@ -442,7 +456,7 @@ def test_random_dot_strategies_match_oracle():
 
 
 @pytest.mark.parametrize("tm", ["interleaved", "contig"])
-def test_compensated_pipeline_matches_oracle(tm):
+def test_compensated_pipeline_matches_oracle(c_build, tm):
     """Kahan pairs as the fold's accumulator: per-thread compensated sums, then
     group merges and the final merge, each equal to the oracle's kahan_step /
     kahan_combine evaluation of the same tree."""
@@ -470,7 +484,7 @@ def test_compensated_pipeline_matches_oracle(tm):
 
 
 @pytest.mark.parametrize("rows,g", [(1, 7), (5, 128), (64, 3), (300, 32)])
-def test_fold_cols_folds_strided_groups_in_order(rows, g):
+def test_fold_cols_folds_strided_groups_in_order(c_build, rows, g):
     """fold_cols(rows, g): output j is the sequential f32 fold of p[j],
     p[rows + j], ..., p[(g - 1) rows + j] from +0 -- the transpose of split
     rows -- and its threads' reads are p[i], p[i + 1], ... for consecutive j."""
@@ -487,3 +501,195 @@ def test_fold_cols_folds_strided_groups_in_order(rows, g):
     assert out.tobytes() == want.tobytes()
     src = B.cuda_source(E.generate("fcols", e, ins, backend="cuda"))
     assert "blockIdx" in src and "__global__" in src
+
+
+# --------------------------------------------------------------------------
+# the whole strategy in one kernel: lane trees, the block tree, the second
+# level in the last work-group
+# --------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("n,s,T,V,tm,second,T2", [
+    (1 << 14, 2048, 64, 4, "interleaved", "tree", 8), (1 << 14, 1024, 32, 1, "contig", "seq", 1),
+    (1 << 15, 4096, 128, 4, "contig", "tree", 8), (4096, 512, 128, 4, "interleaved", "seq", 1),
+    (1 << 13, 1024, 256, 2, "interleaved", "tree", 4), (1 << 12, 256, 8, 4, "interleaved", "tree", 16)])
+def test_single_launch_reductions_match_oracle(c_build, n, s, T, V, tm, second, T2):
+    """dot_R and asum_R (thread folds, lane trees within warps and over the warp
+    sums, the second level) run as C equal the oracle's loop nest of the same
+    strategy bit for bit."""
+    from oracle import loopnest
+
+    x, y = uniform(n, 80 + T), uniform(n, 81 + V)
+    st = c1.Strategy(s=s, T=T, V=V, thread_map=tm, second=second, T2=max(T2, 1))
+    e, ins = PR.dot_R(n, s, T, V, tm, second, T2)
+    f = G.compile_c("dR", e, ins)
+    out = np.zeros(1, np.float32)
+    f.run(x, y, out, *f.temps_like())
+    assert bits(out)[0] == bits([loopnest.dot_f32(x, y, st)])[0]
+    e, ins = PR.asum_R(n, s, T, V, tm, second, T2)
+    f = G.compile_c("aR", e, ins)
+    f.run(x, out, *f.temps_like())
+    assert bits(out)[0] == bits([loopnest.asum_f32(x, st)])[0]
+
+
+def test_single_launch_gemv_matches_oracle(c_build):
+    from oracle import loopnest
+
+    rng = np.random.default_rng(90)
+    M, N = 37, 1024
+    A = rng.standard_normal((M, N)).astype(np.float32)
+    xv = uniform(N, 91)
+    for T, V in ((64, 4), (256, 1), (32, 4)):
+        e, ins = PR.gemv_R(M, N, T, V)
+        f = G.compile_c("gR", e, ins)
+        y = np.zeros(M, np.float32)
+        f.run(A.ravel().copy(), xv, y, *f.temps_like())
+        assert np.array_equal(bits(y), bits(loopnest.gemv_f32(A, xv, c1.Strategy(s=N, T=T, V=V))))
+    A2 = rng.standard_normal((40, N)).astype(np.float32)
+    e, ins = PR.gemv_R_warp(40, N, 8, 4)
+    f = G.compile_c("gRw", e, ins)
+    y = np.zeros(40, np.float32)
+    f.run(A2.ravel().copy(), xv, y, *f.temps_like())
+    assert np.array_equal(bits(y), bits(loopnest.gemv_f32(A2, xv, c1.Strategy(s=N, T=32, V=4))))
+
+
+def test_lane_trees_and_second_level_are_checked():
+    """A lane tree needs a warp map around it, a warp map a work-group map, and
+    the second level is a kernel's whole expression."""
+    x = G.inp("x", G.arr(1024, G.F32))
+    plus = lambda a, b: G.add(a, b)
+    with pytest.raises(T.TranslationError, match="warp map"):
+        T.translate(G.mapWorkgroup(lambda ch: G.reduceTree(plus, ch), G.split(32, x)))
+    with pytest.raises(T.TranslationError, match="illegal nesting"):
+        T.translate(G.mapWarp(lambda ch: G.reduceTree(plus, ch), G.split(32, x)))
+    with pytest.raises(T.TranslationError, match="illegal nesting"):
+        T.translate(G.mapWorkgroup(lambda ch: G.mapLane(lambda v: v, ch), G.split(32, x)))
+    with pytest.raises(TypeError, match="power-of-two"):
+        G.reduceTree(plus, G.inp("z", G.arr(24, G.F32)))
+    parts = G.join(G.mapWorkgroup(lambda ch: G.mapWarp(lambda g: G.reduceTree(plus, g), G.split(32, ch)),
+                                  G.split(64, x)))
+    sl = G.secondLevel(parts, lambda p: G.reduceSeq(lambda v, a: G.add(a, v), 0.0, p))
+    with pytest.raises(T.TranslationError, match="second level"):
+        T.translate(G.add(sl, sl))
+    comm, out = T.translate(sl)
+    CK.check(comm)
+    from paper_1710_08332_gb300.codegen import typecheck as TC
+
+    TC.typecheck(comm, out)
+
+
+@pytest.mark.skipif(not shutil.which("nvcc"), reason="nvcc not installed")
+def test_single_launch_sources_compile_for_sm103a(tmp_path):
+    progs = {"dotR": PR.dot_R(1 << 20, 8192, 256, 4, "interleaved", "tree", 128),
+             "asumR": PR.asum_R(1 << 20, 8192, 256, 4, "contig", "seq", 1),
+             "gemvR": PR.gemv_R(512, 1024, 128, 4), "gemvRw": PR.gemv_R_warp(512, 1024, 8, 4)}
+    for name, (e, ins) in progs.items():
+        src = B.cuda_source(E.generate(name, e, ins, "cuda", unroll=4))
+        assert "__shfl_down_sync" in src
+        path = tmp_path / f"{name}.cu"
+        path.write_text(src)
+        r = subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-fmad=false", "-c",
+                            str(path), "-o", str(tmp_path / f"{name}.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+
+
+# --------------------------------------------------------------------------
+# exploration beyond the reduce family: the one-kernel form, GEMV's row map,
+# map fusion across kernels
+# --------------------------------------------------------------------------
+
+
+def _oracle_of_derivation(kind, d, x, y=None, A=None):
+    """The oracle's value of a derivation's tree: c2 for the strategy's first
+    level (or the whole one-kernel strategy), c1 for the folding stages."""
+    from oracle import loopnest
+
+    args = {r.name: r.args for r in d.rules}
+    if kind == "gemv":
+        if "rows" in args:  # a warp per row: 32 interleaved lanes, then the lane tree
+            return loopnest.gemv_f32(A, x, c1.Strategy(s=A.shape[1], T=32, V=args.get("vectorize", (1,))[0]))
+        T, tm = args["columns"]
+        V = args.get("vectorize", (1,))[0]
+        st = c1.Strategy(s=A.shape[1], T=T, V=V, thread_map=tm)
+        if "tree" in args:
+            return loopnest.gemv_f32(A, x, st)
+        return np.array([oracle_fold(list(loopnest.lane_partials_f32("dot", row, x, st))) for row in A], np.float32)
+    s, (T, tm), V = args["split"][0], args["columns"], args.get("vectorize", (1,))[0]
+    src = loopnest.scal_f32(RW.SCALE, x) if kind == "asum_scal" else x
+    k = "dot" if kind == "dot" else "asum"
+    if "second" in args:
+        kind2, T2 = args["second"]
+        return np.float32((loopnest.dot_f32(src, y, c1.Strategy(s=s, T=T, V=V, thread_map=tm, second=kind2, T2=T2))
+                           if k == "dot" else
+                           loopnest.asum_f32(src, c1.Strategy(s=s, T=T, V=V, thread_map=tm, second=kind2, T2=T2))))
+    vals = list(loopnest.lane_partials_f32(k, src, y, c1.Strategy(s=s, T=T, V=V, thread_map=tm)))
+    for grp in RW.fold_plan(len(vals)):
+        rows = len(vals) // grp
+        vals = [oracle_fold(vals[j::rows]) for j in range(rows)]
+    return np.float32(vals[0])
+
+
+def _run_host(kind, d, inputs, n, M=0):
+    cur = list(inputs)
+    for name, ph, ins in RW.lower(kind, d, n, M):
+        f = G.compile_c("h_" + name, ph, ins)
+        count = next(c for (_, _, c, role) in f.params if role == "out")
+        out = np.zeros(count, np.float32)
+        f.run(*cur, out, *f.temps_like())
+        cur = [out]
+    return cur[0]
+
+
+def test_rewrite_rules_for_one_kernel_rows_and_fusion():
+    with pytest.raises(RW.RuleError, match="tree results"):
+        RW.rewrite("dot", RW.Derivation([RW.Rule("split", (512,)), RW.Rule("columns", (32, "contig")),
+                                         RW.Rule("second", ("tree", 8))]))
+    with pytest.raises(RW.RuleError, match="Map f \\(Map g X\\)"):
+        RW.rewrite("dot", RW.Derivation([RW.Rule("fuse_maps")]))
+    with pytest.raises(RW.RuleError, match="32 lanes"):
+        RW.rewrite("gemv", RW.Derivation([RW.Rule("rows", ("warp",)), RW.Rule("columns", (64, "interleaved"))]))
+    e = RW.rewrite("asum_scal", RW.Derivation([RW.Rule("fuse_maps"), RW.Rule("split", (512,)),
+                                               RW.Rule("columns", (32, "interleaved")), RW.Rule("tree"),
+                                               RW.Rule("second", ("seq", 1))]))
+    assert e == RW.Last("seq", 1, RW.Each(RW.Tree(RW.Each(RW.Reduce(RW.Map("abs.scale", RW.HOLE)),
+                                                           RW.Columns(32, "interleaved", RW.HOLE))),
+                                          RW.Split(512, RW.Input("asum_scal"))))
+    n = 1 << 14
+    d_un = RW.Derivation([RW.Rule("split", (1024,)), RW.Rule("columns", (64, "interleaved")), RW.Rule("tree"),
+                          RW.Rule("second", ("tree", 16))])
+    d_fu = RW.Derivation([RW.Rule("fuse_maps")] + d_un.rules)
+    assert [k for k, _, _ in RW.lower("asum_scal", d_un, n)] == ["map_scale", "one_kernel"]
+    assert [k for k, _, _ in RW.lower("asum_scal", d_fu, n)] == ["one_kernel"]
+    assert len(RW.derivations(n, splits=(1024,), threads=(64,), maps=("contig",), widths=(4,),
+                              forms=("paper", "single"), kind="asum_scal")) == 4
+
+
+@pytest.mark.parametrize("form", ["paper", "single"])
+def test_dot_and_asum_scal_derivations_match_oracle(c_build, form):
+    """Every derivation (both thread maps, widths 1 and 4; for asum_scal with and
+    without fuse_maps) equals the oracle's evaluation of its tree; fusing the
+    maps changes no bit."""
+    n = 1 << 14
+    x, y = uniform(n, 400), uniform(n, 401)
+    for kind in ("dot", "asum_scal"):
+        got = {}
+        for d in RW.derivations(n, splits=(2048,), threads=(64,), maps=("interleaved", "contig"), widths=(1, 4),
+                                forms=(form,), kind=kind):
+            v = _run_host(kind, d, [x, y] if kind == "dot" else [x], n)
+            assert bits(v)[0] == bits([_oracle_of_derivation(kind, d, x, y)])[0], str(d)
+            got.setdefault(str(d).replace("fuse_maps ; ", ""), set()).add(bits(v)[0])
+        assert all(len(b) == 1 for b in got.values())
+
+
+def test_gemv_derivations_match_oracle(c_build):
+    """Rows at block level (one kernel with the row's tree, or partials and row
+    folds) and at warp level, each equal to the oracle's evaluation of its tree."""
+    rng = np.random.default_rng(402)
+    M, N = 24, 512
+    A = rng.standard_normal((M, N)).astype(np.float32)
+    xv = uniform(N, 403)
+    ds = RW.gemv_derivations(M, N, threads=(32, 128), widths=(1, 4))
+    assert any(r.name == "rows" for d in ds for r in d.rules)
+    for d in ds:
+        got = _run_host("gemv", d, [A.ravel().copy(), xv], N, M)
+        assert np.array_equal(bits(got), bits(_oracle_of_derivation("gemv", d, xv, A=A))), str(d)

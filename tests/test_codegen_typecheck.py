@@ -31,6 +31,11 @@ PROGRAMS = {
     "dot_partials_kahan": lambda: PR.dot_partials_kahan(1 << 12, 1 << 10, 64),
     "fold_pairs_rows": lambda: PR.fold_pairs_rows(16, 8),
     "fold_pairs_all": lambda: PR.fold_pairs_all(16),
+    "dot_R": lambda: PR.dot_R(1 << 14, 1 << 11, 128, 4, "interleaved", "tree", 8),
+    "dot_R_seq_contig": lambda: PR.dot_R(1 << 13, 1 << 10, 64, 1, "contig", "seq", 1),
+    "asum_R": lambda: PR.asum_R(1 << 14, 1 << 11, 256, 4, "interleaved", "tree", 8),
+    "gemv_R": lambda: PR.gemv_R(16, 512, 64, 4),
+    "gemv_R_warp": lambda: PR.gemv_R_warp(16, 512, 4, 4),
 }
 
 
@@ -180,6 +185,10 @@ def _parallel_writes(c, par=(), out=None):
             _parallel_writes(x, par, out)
     elif isinstance(c, T.New):
         _parallel_writes(c.body, par, out)
+    elif isinstance(c, T.TreeReduce):
+        _parallel_writes(c.fill, par, out)
+    elif isinstance(c, T.LastBlock):
+        _parallel_writes(c.body, (), out)
     elif isinstance(c, T.For):
         _parallel_writes(c.body, par + ((c.var.name,) if c.level != "seq" else ()), out)
     elif isinstance(c, T.Assign):

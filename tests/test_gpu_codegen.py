@@ -160,34 +160,65 @@ def test_vector_kernels(cuda_device, thread_map):
     assert np.array_equal(bits(part), bits(want))
 
 
-def test_exploration_ranks_derivations_and_each_is_exact_for_its_tree(cuda_device):
-    """The explored derivations are ranked by time; the fastest and slowest
-    each equal the oracle's evaluation of their own tree -- c2's lane partials
-    for the split / columns / vectorize part, then c1's strided folds of the
-    fold plan -- and lie within the normwise bound of the exact dot."""
-    from oracle import loopnest, naive64
-    from oracle import patterns as P_
+@pytest.mark.parametrize("kind", ["dot", "asum_scal"])
+def test_exploration_ranks_derivations_and_each_is_exact_for_its_tree(cuda_device, kind):
+    """The explored derivations -- the paper's form (partials, then folding
+    kernels) and the one-kernel form (the chunk tree and the second level in
+    the last block), for asum_scal with and without fusing the maps -- are
+    ranked by time; the fastest three and slowest two each equal the oracle's
+    evaluation of their own tree and lie within the normwise bound of the exact
+    result. One-kernel derivations are faster than the paper's form with the
+    same split, columns and width, and fused maps faster than unfused."""
+    from oracle import naive64
     from paper_1710_08332_gb300.codegen import rewrite as RW
+    from tests.test_codegen_host import _oracle_of_derivation
 
-    n = 1 << 20
+    n = 1 << 22
     x, y = uniform(n, 42), uniform(n, 43)
     dx, dy = dev(x), dev(y)
-    derivs = RW.derivations(n, splits=(1 << 14, 1 << 15), threads=(128, 256), maps=("interleaved", "contig"),
-                            widths=(1, 4))
-    ranked = RW.explore("dot", [dx, dy], n, derivs, reps=3)
+    ins = [dx, dy] if kind == "dot" else [dx]
+    derivs = RW.derivations(n, splits=(1 << 14, 1 << 15), threads=(128, 256),
+                            maps=("interleaved", "contig"), widths=(1, 4), forms=("paper", "single"), kind=kind)
+    ranked = RW.explore(kind, ins, n, derivs, reps=3)
     assert len(ranked) == len(derivs) and ranked[0][0] <= ranked[-1][0]
-    exact, bound = naive64.dot_exact(x, y), 1e-5 * naive64.abs_dot_f64(x, y)
+    if kind == "dot":
+        exact, scale = naive64.dot_exact(x, y), naive64.abs_dot_f64(x, y)
+    else:
+        xs = np.float32(RW.SCALE) * x
+        exact, scale = naive64.asum_exact(xs), naive64.asum_exact(xs)
     for _, d in ranked[:3] + ranked[-2:]:
-        got = RW.run_pipeline(RW.compile_pipeline("dot", d, n), [dx, dy])
+        got = RW.run_pipeline(RW.compile_pipeline(kind, d, n), ins)
         torch.cuda.synchronize()
-        args = {r.name: r.args for r in d.rules}
-        s, (Tn, tm), V = args["split"][0], args["columns"], args.get("vectorize", (1,))[0]
-        vals = list(loopnest.lane_partials_f32("dot", x, y, P_.Strategy(s=s, T=Tn, V=V, thread_map=tm)))
-        for grp in RW.fold_plan(len(vals)):
-            rows = len(vals) // grp
-            vals = [oracle_fold(vals[j::rows]) for j in range(rows)]
-        assert bits(got.cpu().numpy())[0] == bits(vals)[0], str(d)
-        assert abs(float(vals[0]) - exact) <= bound
+        want = _oracle_of_derivation(kind, d, x, y)
+        assert bits(got.cpu().numpy())[0] == bits([want])[0], str(d)
+        assert abs(float(want) - exact) <= 1e-5 * scale
+    t = {str(d): ms for ms, d in ranked}
+    for d in derivs:
+        k = str(d)
+        if "second" in k and "fuse_maps" not in k:
+            paper = k.replace(" ; tree ; second(tree, 128)", "").replace(" ; tree ; second(tree, 256)", "")
+            assert t[k] < t[paper], (k, t[k], t[paper])
+        if kind == "asum_scal" and "fuse_maps" in k:
+            assert t[k] < t[k.replace("fuse_maps ; ", "")], k
+
+
+def test_gemv_exploration_each_is_exact_for_its_tree(cuda_device):
+    """GEMV derivations (rows at block level, one kernel or partials and row
+    folds; rows at warp level) ranked on 8192 x 8192; the fastest and the
+    slowest equal the oracle's evaluation of their trees on every row."""
+    from paper_1710_08332_gb300.codegen import rewrite as RW
+    from synth import workloads as W
+    from tests.test_codegen_host import _oracle_of_derivation
+
+    A, xv, _ = W.gemv("cuda")
+    M, N = A.shape
+    derivs = RW.gemv_derivations(M, N, threads=(128, 256), widths=(4,))
+    ranked = RW.explore("gemv", [A, xv], N, derivs, reps=3, M=M)
+    hA, hx = A.cpu().numpy(), xv.cpu().numpy()
+    for _, d in ranked[:2] + ranked[-1:]:
+        got = RW.run_pipeline(RW.compile_pipeline("gemv", d, N, M), [A, xv])
+        torch.cuda.synchronize()
+        assert np.array_equal(bits(got.cpu().numpy()), bits(_oracle_of_derivation("gemv", d, hx, A=hA))), str(d)
 
 
 def test_generated_gemv_backward(cuda_device):
@@ -222,3 +253,80 @@ def test_generated_compensated_dot(cuda_device):
     out = run(G.compile_cuda("kf", e, ins), dev(part), out_count=1)
     final = c1.reduce_(lambda pr, a: c1.kahan_combine(F, a, pr), (F.zero, F.zero), want)
     assert bits(out)[0] == bits([final[0]])[0]
+
+
+# --------------------------------------------------------------------------
+# the whole strategy in one generated kernel
+# --------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("n,s,T,V,tm,second,T2", [
+    (1 << 20, 8192, 256, 4, "interleaved", "tree", 128), (1 << 20, 8192, 256, 4, "interleaved", "seq", 1),
+    (1 << 20, 16384, 512, 4, "contig", "tree", 64), (1 << 18, 4096, 1024, 1, "interleaved", "tree", 64),
+    (1 << 18, 2048, 64, 2, "contig", "seq", 1), (1 << 16, 512, 32, 4, "interleaved", "tree", 128)])
+def test_single_launch_reductions_match_oracle_gpu(cuda_device, n, s, T, V, tm, second, T2):
+    """dot_R / asum_R generated as one kernel each (thread folds, lane trees,
+    the second level in the last block) equal the oracle's loop nest of the
+    same strategy bit for bit, on consecutive launches (the ticket counter is
+    back at zero after each) and under a smaller persistent grid."""
+    from oracle import loopnest
+    from oracle import patterns as P_
+
+    x, y = uniform(n, 300 + T), uniform(n, 301 + V)
+    st = P_.Strategy(s=s, T=T, V=V, thread_map=tm, second=second, T2=max(T2, 1))
+    want_d, want_a = loopnest.dot_f32(x, y, st), loopnest.asum_f32(x, st)
+    e, ins = PR.dot_R(n, s, T, V, tm, second, T2)
+    kd = G.compile_cuda("dotR", e, ins, unroll=4)
+    e, ins = PR.asum_R(n, s, T, V, tm, second, T2)
+    ka = G.compile_cuda("asumR", e, ins, unroll=4)
+    dx, dy = dev(x), dev(y)
+    temps_d, temps_a = kd.temps_like(), ka.temps_like()
+    for grid in (None, None, 37):
+        out = torch.full((1,), float("nan"), device="cuda")
+        kd.run(dx, dy, out, *temps_d, grid=grid)
+        torch.cuda.synchronize()
+        assert bits(out.cpu().numpy())[0] == bits([want_d])[0], grid
+        ka.run(dx, out, *temps_a, grid=grid)
+        torch.cuda.synchronize()
+        assert bits(out.cpu().numpy())[0] == bits([want_a])[0], grid
+    assert int(temps_d[-1].item()) == 0 and int(temps_a[-1].item()) == 0
+
+
+def test_single_launch_dot_at_size_matches_oracle(cuda_device):
+    """The bandwidth workload's dot (n = 2^26) as one generated kernel with the
+    strategy the library's tuner picks most often (split 65536, 256 threads,
+    float4 lanes, a tree second level over the 1024 chunk results): bit for
+    bit the oracle's dot of the same strategy."""
+    from oracle import loopnest
+    from oracle import patterns as P_
+    from synth import workloads as W
+
+    x, y = W.bandwidth("cuda")
+    n, s, T, V, T2 = x.numel(), 65536, 256, 4, 256
+    e, ins = PR.dot_R(n, s, T, V, "interleaved", "tree", T2)
+    k = G.compile_cuda("dotR26", e, ins, unroll=4)
+    out = torch.empty(1, device="cuda")
+    k.run(x, y, out, *k.temps_like())
+    torch.cuda.synchronize()
+    want = loopnest.dot_f32(x.cpu().numpy(), y.cpu().numpy(), P_.Strategy(s=s, T=T, V=V, second="tree", T2=T2))
+    assert bits(out.cpu().numpy())[0] == bits([want])[0]
+
+
+@pytest.mark.parametrize("M,N,T,V", [(8192, 8192, 128, 4), (300, 1024, 256, 1), (64, 4096, 1024, 4)])
+def test_single_launch_gemv_matches_oracle_gpu(cuda_device, M, N, T, V):
+    """gemv_R (a block per row) and gemv_R_warp (a warp per row) against the
+    oracle's GEMV of the same strategy, every row."""
+    from oracle import loopnest
+    from oracle import patterns as P_
+
+    rng = np.random.default_rng(M + N)
+    A = (rng.standard_normal((M, N)) / np.sqrt(N)).astype(np.float32)
+    xv = uniform(N, 310)
+    dA, dxv = dev(A.ravel()), dev(xv)
+    e, ins = PR.gemv_R(M, N, T, V)
+    got = run(G.compile_cuda("gemvR", e, ins, unroll=4), dA, dxv, out_count=M)
+    assert np.array_equal(bits(got), bits(loopnest.gemv_f32(A, xv, P_.Strategy(s=N, T=T, V=V))))
+    if M % 8 == 0:
+        e, ins = PR.gemv_R_warp(M, N, 8, 4)
+        got = run(G.compile_cuda("gemvRw", e, ins, unroll=4), dA, dxv, out_count=M)
+        assert np.array_equal(bits(got), bits(loopnest.gemv_f32(A, xv, P_.Strategy(s=N, T=32, V=4))))
