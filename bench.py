@@ -84,6 +84,17 @@ def barrier(dist, device=None):
 # ---------------------------------------------------------------------------
 
 
+def max_sm_mhz(clk=None) -> float:
+    """The maximum SM clock: from the sampled clocks, else MEASURED_PEAKS.json, else 2070 MHz."""
+    if clk and clk.get("sm_max_mhz"):
+        return float(clk["sm_max_mhz"])
+    try:
+        with open(PEAKS_PATH) as f:
+            return float(json.load(f).get("sm_max_mhz") or 2070.0)
+    except (OSError, ValueError):
+        return 2070.0
+
+
 def peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -117,6 +128,33 @@ class ClockSampler:
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.time()  # nvidia-smi takes a moment to start: wait for its first sample (at most 3 s)
+        while self.count() < 1 and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.02)
+
+    def count(self) -> int:
+        """Samples written so far."""
+        if self.proc is None or not self.path:
+            return 0
+        try:
+            with open(self.path) as f:
+                return sum(1 for line in f if line.count(",") >= 8)
+        except OSError:
+            return 0
+
+    def warm(self, step, min_samples: int = 3, max_s: float = 2.0):
+        """Run more untimed warm-up steps until min_samples samples were taken
+        since now (at most max_s seconds), so the clock record covers the GPU
+        under this workload's load and not only its idle start."""
+        if self.proc is None:
+            return
+        import torch
+
+        target, t0 = self.count() + min_samples, time.time()
+        while self.count() < target and time.time() - t0 < max_s:
+            step()
+            torch.cuda.synchronize()
 
     def stop(self):
         if self.proc is None:
@@ -142,7 +180,7 @@ class ClockSampler:
         load = [v for v in sm if mx and v > 0.5 * max(mx)] or sm
         return {"sm_mhz": statistics.median(load) if load else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
-                "window": "warm-up + timed steps"}
+                "window": "warm-up (extended until three samples were taken under load) + timed steps"}
 
 
 def source_digest(paths):
@@ -351,6 +389,7 @@ def bandwidth_workload(args, device, dist):
     clocks.start()
     for _ in range(args.warmup):
         step()
+    clocks.warm(step)
     torch.cuda.synchronize(device)
     barrier(dist, device)
     torch.cuda.synchronize(device)
@@ -471,6 +510,7 @@ def timed_steps(args, device, dist, names, step, flush=None):
         if flush:
             flush()
         step(None)
+    clocks.warm(lambda: (flush() if flush else None, step(None)))
     torch.cuda.synchronize(device)
     barrier(dist, device)
     tl = Timeline(names, stream)
@@ -690,13 +730,13 @@ def gemm_workload(args, device, dist):
         e1.synchronize()
         f32_ms.append(e0.elapsed_time(e1))
     f32 = min(f32_ms)
-    sm_mhz = (clk or {}).get("sm_mhz") or 1900.0
+    sm_max = max_sm_mhz(clk)
     sms = torch.cuda.get_device_properties(device).multi_processor_count
-    fma_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    fma_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
     kern["f32_fold_fwd"] = {"avg_us": round(f32 * 1e3, 1), "flops": fl, "TFLOP_s": round(fl / f32 / 1e9, 2),
                             "bound": "alu", "peak_TFLOP_s": round(fma_peak, 1),
-                            "peak_source": f"{sms} SMs x 128 FP32 FMA lanes x 2 flops x {sm_mhz:.0f} MHz (median "
-                                           "clock under load)", "frac": round(fl / f32 / 1e9 / fma_peak, 4)}
+                            "peak_source": f"{sms} SMs x 128 FP32 FMA lanes x 2 flops x {sm_max:.0f} MHz (the "
+                                           "maximum SM clock)", "frac": round(fl / f32 / 1e9 / fma_peak, 4)}
     # each launch alone (L2 flushed before it): one CTA per 256-row tile (cta_group::1), CTA pairs
     # (cta_group::2) on 256-row and 512-row tiles, and cuBLAS (torch.matmul, bf16 out) on the same shape
     flush = L2Flush(device)
@@ -885,14 +925,69 @@ def batched_workload(args, device, dist):
     return line
 
 
+def generated_single_launch(device, x, y, A, xv, sms: int, reps: int = 20):
+    """The generated one-kernel reductions (thread folds, lane trees, the second
+    level in the last block) on the bandwidth inputs and the GEMV matrix, each
+    beside the library's kernel with the same strategy, timed alone (back to
+    back launches). The dot takes the faster of two splits."""
+    import torch
+
+    import paper_1710_08332_gb300 as dpia
+    from paper_1710_08332_gb300 import codegen as G
+    from paper_1710_08332_gb300 import tune
+    from paper_1710_08332_gb300.codegen import programs as PR
+
+    n = x.numel()
+    M, N = A.shape
+    out = torch.empty(1, device=device)
+    yv = torch.empty(M, device=device)
+    res, best = {}, None
+    for s_, T, V, T2 in ((16384, 256, 4, 256), (32768, 256, 4, 256)):
+        C = n // s_
+        kd = G.compile_cuda(f"gen_dot_R_s{s_}_T{T}", *PR.dot_R(n, s_, T, V, "interleaved", "tree", min(T2, C)),
+                            unroll=4)
+        td = kd.temps_like(device)
+        st = dpia.ReduceStrategy(split=s_, threads=T, vec=V, second="tree", threads2=min(T2, C))
+        ws = dpia.workspace(dpia.dpia_dot_workspace_size(n, st), device)
+        g_ms = tune.time_call(lambda: kd.run(x, y, out, *td), reps=reps)
+        l_ms = tune.time_call(lambda: dpia.dpia_dot_f32(x, y, n, st, out, ws), reps=reps)
+        label = f"dot_R s={s_} T={T} V={V} tree {min(T2, C)}"
+        res[label] = {"generated_us": round(g_ms * 1e3, 2), "library_us": round(l_ms * 1e3, 2),
+                      "generated_GB_s": round(8 * n / g_ms / 1e6, 1), "library_GB_s": round(8 * n / l_ms / 1e6, 1),
+                      "generated_over_library_time": round(l_ms / g_ms, 3)}
+        if best is None or g_ms < best[1]:
+            best = (label, g_ms, l_ms, kd, td, st)
+    label, g_ms, l_ms, kd, td, st = best
+    ka = G.compile_cuda("gen_asum_R", *PR.asum_R(n, st.split, st.threads, st.vec, "interleaved", "tree",
+                                                 st.threads2), unroll=4)
+    ta = ka.temps_like(device)
+    ws = dpia.workspace(dpia.dpia_dot_workspace_size(n, st), device)
+    ga = tune.time_call(lambda: ka.run(x, out, *ta), reps=reps)
+    la = tune.time_call(lambda: dpia.dpia_asum_f32(x, n, st, out, ws), reps=reps)
+    res["asum_R (the dot's strategy)"] = {"generated_us": round(ga * 1e3, 2), "library_us": round(la * 1e3, 2),
+                                          "generated_GB_s": round(4 * n / ga / 1e6, 1),
+                                          "generated_over_library_time": round(la / ga, 3)}
+    kg = G.compile_cuda("gen_gemv_R", *PR.gemv_R(M, N, 128, 4), unroll=4)
+    stg = dpia.ReduceStrategy(split=N, threads=128, vec=4)
+    gg = tune.time_call(lambda: kg.run(A, xv, yv), reps=reps)
+    lg = tune.time_call(lambda: dpia.dpia_gemv_f32(A, M, N, N, xv, yv, stg), reps=reps)
+    gb = 4 * M * N + 4 * (M + N)
+    res["gemv_R (a block of 128 per row, float4)"] = {
+        "generated_us": round(gg * 1e3, 2), "library_us": round(lg * 1e3, 2),
+        "generated_GB_s": round(gb / gg / 1e6, 1), "generated_over_library_time": round(lg / gg, 3)}
+    return res, best
+
+
 def codegen_workload(args, device, dist):
     """Kernels produced by the code generator from the paper's phrases, on the
-    bandwidth inputs (n = 2^26) and the GEMV 8192^2 inputs, all reading their
-    streams as asVector 4 (GEMV: scalar): the dot as four generated kernels
-    (per-thread lane partials over 2048 chunks of 2^15 with 256 threads, then
-    the folding stages of the rewrite lowering's fold plan), the
-    asum partials, scal, and the GEMV partials with the per-row fold; beside
-    them the library's hand-written dot and asum on the same inputs."""
+    bandwidth inputs (n = 2^26) and the GEMV 8192^2 inputs. The line's value is
+    the dot generated as ONE kernel with the canonical strategy (per-thread
+    folds on asVector 4, lane trees within warps and over the warp sums, the
+    second level in the last block), beside the library's hand-written dot with
+    the same strategy. Also timed: the same phrases in the paper's own form
+    (per-thread lane partials, then folding kernels), asum, scal, GEMV (one
+    kernel, and partials + row folds) and the GEMV backward, the rewrite
+    exploration, and the host C build of the dot partials (OpenMP)."""
     import torch
 
     import paper_1710_08332_gb300 as dpia
@@ -902,15 +997,20 @@ def codegen_workload(args, device, dist):
 
     n = W.BW_N
     x, y = W.bandwidth(device)
-    # streams read as asVector 4; sequential loops unrolled 4 (the folds 64) so
-    # that loads issue ahead of the dependent steps (a sweep of split, threads,
-    # width and unroll factor chose these)
+    A, xv, _ = W.gemv(device)
+    M, N_ = A.shape
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    single, best = generated_single_launch(device, x, y, A, xv, sms)
+    best_label, _, _, kdR, tdR, st_best = best
+    out1 = torch.empty(1, device=device)
+    # the paper's form: lane partials over 2048 chunks of 2^15 with 256 threads,
+    # then the folding stages of the rewrite lowering's fold plan
     s, Tn, V = 1 << 15, 256, 4
-    m1 = n // s * Tn * V  # lane partials of the first kernel
+    m1 = n // s * Tn * V
     k1 = G.compile_cuda("gen_dot_partials", *PR.dot_partials(n, s, Tn, V=V), unroll=4)
     from paper_1710_08332_gb300.codegen import rewrite as RW
 
-    folds, left = [], m1  # the folding stages of the 2M lane partials
+    folds, left = [], m1
     for grp in RW.fold_plan(m1):
         ph = PR.fold_all(left) if grp == left else PR.fold_cols(left // grp, grp)
         folds.append((G.compile_cuda(f"gen_dot_fold_{left}_{grp}", *ph, unroll=64), left // grp))
@@ -922,10 +1022,7 @@ def codegen_workload(args, device, dist):
         for (k, cnt), dst in zip(folds, fold_bufs):
             k.run(src, dst, grid=max(1, cnt // 64), block=min(64, cnt) if cnt > 1 else 1)
             src = dst
-    ka = G.compile_cuda("gen_asum_partials", *PR.asum_partials(n, s, Tn, V=V), unroll=4)
     ks = G.compile_cuda("gen_scal", *PR.scal(n, W.SCAL_A, V=V))
-    A, xv, _ = W.gemv(device)
-    M, N_ = A.shape
     kg = G.compile_cuda("gen_gemv_partials", *PR.gemv_partials(M, N_, 128))
     kr = G.compile_cuda("gen_gemv_rows", *PR.fold_rows(M, 128), unroll=64)
     R = 32  # dx: row chunks of 32 (256 workgroups), then the fold over the chunks
@@ -940,26 +1037,24 @@ def codegen_workload(args, device, dist):
     ys = torch.empty_like(x)
     gpart = torch.empty(M * 128, device=device)
     yv = torch.empty(M, device=device)
-    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    ws = dpia.workspace(dpia.dpia_dot_workspace_size(n, st_best), device)
+    # step order: each of the two compared dots follows a kernel that leaves no
+    # dirty lines in L2 (the kernels after scal and dA pay for writing theirs back)
     calls = {
-        "gen_dot_partials": lambda: k1.run(x, y, part),
-        "gen_dot_folds": dot_folds,
-        "gen_asum_partials": lambda: ka.run(x, part),
-        "gen_scal": lambda: ks.run(x, ys, grid=sms * 8, block=256),
+        "gen_gemv_dA": lambda: kda.run(dyv, xv, dAm),
         "gen_gemv_partials": lambda: kg.run(A, xv, gpart),
         "gen_gemv_rows": lambda: kr.run(gpart, yv, grid=M // 64, block=64),  # a thread per row over 128 SMs
+        "gen_dot_R": lambda: kdR.run(x, y, out1, *tdR),
+        "library_dot": lambda: dpia.dpia_dot_f32(x, y, n, st_best, out1, ws),
+        "gen_dot_partials": lambda: k1.run(x, y, part),
+        "gen_dot_folds": dot_folds,
+        "gen_scal": lambda: ks.run(x, ys, grid=sms * 8, block=256),
         "gen_gemv_dx_partials": lambda: kdx.run(A, dyv, dxpart),
         "gen_gemv_dx_fold": lambda: kdf.run(dxpart, dxv, grid=N_ // 64, block=64),  # a thread per column
-        "gen_gemv_dA": lambda: kda.run(dyv, xv, dAm),
     }
-    st = dpia.ReduceStrategy(split=16384, threads=256, vec=4, second="tree", threads2=256)
-    ws = dpia.workspace(dpia.dpia_dot_workspace_size(n, st), device)
-    lib_out = torch.empty(1, device=device)
-    calls["library_dot"] = lambda: dpia.dpia_dot_f32(x, y, n, st, lib_out, ws)
-    calls["library_asum"] = lambda: dpia.dpia_asum_f32(x, n, st, lib_out, ws)
-    bytes_ = {"gen_dot_partials": 8 * n, "gen_asum_partials": 4 * n, "gen_scal": 8 * n,
+    bytes_ = {"gen_dot_R": 8 * n, "library_dot": 8 * n, "gen_dot_partials": 8 * n, "gen_scal": 8 * n,
               "gen_gemv_partials": 4 * M * N_ + 4 * N_, "gen_gemv_dx_partials": 4 * M * N_ + 4 * M,
-              "gen_gemv_dA": 4 * M * N_ + 4 * (M + N_), "library_dot": 8 * n, "library_asum": 4 * n}
+              "gen_gemv_dA": 4 * M * N_ + 4 * (M + N_)}
     names = list(calls)
 
     def step(tl):
@@ -967,64 +1062,84 @@ def codegen_workload(args, device, dist):
             calls[name]() if tl is None else tl.call(name, calls[name])
 
     per, step_ms, clk = timed_steps(args, device, dist, names, step)
-    alone = standalone_us({k: calls[k] for k in ("gen_dot_partials", "library_dot", "gen_asum_partials",
-                                                  "library_asum", "gen_scal", "gen_gemv_partials",
-                                                  "gen_gemv_dx_partials", "gen_gemv_dA")}, bytes_)
-    # rewrite-based exploration: every derivation of hreduce (+) 0 (hmap (*) (zip x y)) over
-    # split 2^14..2^16, 128 / 256 threads, both thread maps, widths 1 and 4, timed whole
-    from paper_1710_08332_gb300.codegen import rewrite as RW
+    alone = standalone_us({k: calls[k] for k in ("gen_dot_R", "library_dot", "gen_dot_partials", "gen_scal",
+                                                  "gen_gemv_partials", "gen_gemv_dx_partials", "gen_gemv_dA")},
+                          bytes_)
+    # rewrite-based exploration, every pipeline timed whole: the dot (split 2^14..2^16, 256
+    # threads, both thread maps, widths 1 and 4, the paper's form and the one-kernel form),
+    # sum |1.5 x_i| (with and without fusing scal's map into the reduction) and GEMV rows
+    def summary(ranked, lib_us=None):
+        d = {"candidates": len(ranked),
+             "best": {"derivation": str(ranked[0][1]), "pipeline_us": round(ranked[0][0] * 1e3, 1)},
+             "worst": {"derivation": str(ranked[-1][1]), "pipeline_us": round(ranked[-1][0] * 1e3, 1)},
+             "all_us": {str(dd): round(ms * 1e3, 1) for ms, dd in ranked}}
+        if lib_us is not None:
+            d["library_us"] = lib_us
+        return d
 
-    ranked = RW.explore("dot", [x, y], n, RW.derivations(n, threads=(128, 256)), reps=5)
-    explored = {"candidates": len(ranked),
-                "best": {"derivation": str(ranked[0][1]), "pipeline_us": round(ranked[0][0] * 1e3, 1)},
-                "worst": {"derivation": str(ranked[-1][1]), "pipeline_us": round(ranked[-1][0] * 1e3, 1)},
-                "library_dot_us": alone["library_dot"]["median_us"]}
+    explored = {"dot": summary(RW.explore("dot", [x, y], n, RW.derivations(
+        n, threads=(256,), forms=("paper", "single")), reps=5), alone["library_dot"]["median_us"])}
+    explored["asum_scal"] = summary(RW.explore("asum_scal", [x], n, RW.derivations(
+        n, splits=(1 << 15,), threads=(256,), maps=("interleaved",), widths=(4,), forms=("paper", "single"),
+        kind="asum_scal"), reps=5))
+    explored["gemv"] = summary(RW.explore("gemv", [A, xv], N_, RW.gemv_derivations(M, N_, threads=(128, 256),
+                                                                                  widths=(4,)), reps=5, M=M))
     # the same phrases on the host (the paper's multicore target): C with the
-    # outermost parallel loop on OpenMP threads, on 2^24 elements of the inputs
+    # outermost parallel loop (the work-group map) on OpenMP threads, the whole
+    # dot (first level, trees, second level) on the full n = 2^26 inputs
     import numpy as np
 
-    nh = 1 << 24
-    hx, hy = x[:nh].cpu().numpy(), y[:nh].cpu().numpy()
-    hc = G.compile_c("host_dot_partials", *PR.dot_partials(nh, s, Tn, V=V), openmp=True)
-    hpart = np.zeros(nh // s * Tn * V, np.float32)
-    hc.run(hx, hy, hpart)
+    hx, hy = x.cpu().numpy(), y.cpu().numpy()
+    hc = G.compile_c("host_dot_R", *PR.dot_R(n, st_best.split, st_best.threads, st_best.vec, "interleaved",
+                                             "tree", st_best.threads2), openmp=True)
+    hout = np.zeros(1, np.float32)
+    htemps = hc.temps_like()
+    hc.run(hx, hy, hout, *htemps)
     reps, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < 3.0:
-        hc.run(hx, hy, hpart)
+        hc.run(hx, hy, hout, *htemps)
         reps += 1
     host_s = (time.perf_counter() - t0) / reps
-    host_line = {"kernel": "generated C, outermost parallel loop on OpenMP threads",
-                 "GB_s": round(8 * nh / host_s / 1e9, 2), "n": nh, "threads": os.cpu_count(), "reps": reps}
+    host_line = {"kernel": f"generated C of the one-kernel dot ({best_label}), work-group loop on OpenMP threads",
+                 "GB_s": round(8 * n / host_s / 1e9, 2), "ms": round(host_s * 1e3, 2), "n": n,
+                 "threads": host_cores(), "reps": reps,
+                 "same_bits_as_gpu": bool(hout.tobytes() == out1.cpu().numpy().tobytes())}
     hbm = peaks()[0]
     kern = {k: {"avg_us": round(v * 1e3, 2)} for k, v in per.items()}
     for k, b in bytes_.items():
         kern[k]["GB_s"] = round(b / per[k] / 1e6, 1)
-    dot_ms = per["gen_dot_partials"] + per["gen_dot_folds"]
-    achieved = 8 * n / per["gen_dot_partials"] / 1e6
-    roof = {"bound": "hbm", "kernel": "gen_dot_partials (generated: mapWorkgroup / mapLocal / reduceSeq on "
-                                      "asVector 4)",
+    dot_ms = per["gen_dot_R"]
+    achieved = 8 * n / dot_ms / 1e6
+    roof = {"bound": "hbm", "kernel": f"gen_dot_R (generated, one kernel: {best_label})",
             "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
             "traffic": None, "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": 8 * n,
-            "frac_alone": round(alone["gen_dot_partials"]["GB_s"] / hbm, 4)}
-    cfg = {"workload": "generated kernels: dot n=2^26 (partials + folding kernels), asum partials, scal (a=1.5), GEMV 8192^2 "
-                       "partials + row folds, bandwidth inputs seed 1 / GEMV seed 2, asVector 4 (GEMV scalar), "
-                       "sequential loops unrolled 4 (folds 16); beside them the "
-                       "library's dot and asum (split 16384, tree)",
-           "n": n, "dot_split": s, "threads": Tn, "vec": V, "unroll": 4, "l2": "inputs larger than L2"}
+            "frac_alone": round(alone["gen_dot_R"]["GB_s"] / hbm, 4)}
+    cfg = {"workload": "generated kernels: dot n=2^26 as one kernel (canonical strategy) and in the paper's "
+                       "two-kernel form, scal (a=1.5), GEMV 8192^2 (one kernel; partials + row folds) and its "
+                       "backward, bandwidth inputs seed 1 / GEMV seed 2; beside them the library's kernels with "
+                       "the same strategies", "n": n, "strategy": st_best.as_dict(),
+           "l2": "inputs larger than L2"}
     world = dist.get_world_size() if dist else 1
     return _line(args, dist, round(world * 8 * n / (dot_ms / 1e3) / 1e9, 1), "GB/s", dot_ms, "f32", cfg, kern,
                  roof, clk, len(names) * args.steps,
-                 {"kernels_alone": alone, "explored_dot": explored, "host_generated_dot_partials": host_line,
-                  "generated_dot_vs_library_dot": round(per["library_dot"] / dot_ms, 3)})
+                 {"kernels_alone": alone, "single_launch": single, "explored_dot": explored,
+                  "host_generated_dot": host_line,
+                  "generated_dot_vs_library_dot": round(per["library_dot"] / per["gen_dot_R"], 3),
+                  "paper_form_dot_vs_library_dot": round(per["library_dot"] /
+                                                         (per["gen_dot_partials"] + per["gen_dot_folds"]), 3)})
 
 
 def cpu_baseline_for(workload):
-    """Oracle timings for the secondary workloads (one thread, bounded samples)."""
+    """Oracle timings for the secondary workloads (bounded samples, the oracle's
+    units on every host core)."""
     import numpy as np
 
     from oracle import loopnest
     from oracle import patterns as P
     from synth import workloads as W
+
+    cores = host_cores()
+    loopnest.set_threads(cores)
 
     t0 = time.perf_counter()
     if workload == "dot":
@@ -1034,7 +1149,7 @@ def cpu_baseline_for(workload):
             loopnest.dot_f32(x.numpy(), y.numpy(), P.Strategy(s=8192, T=256, V=4))
             reps += 1
         dt = time.perf_counter() - t0
-        return {"value": round(reps * 8 * x.numel() / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+        return {"value": round(reps * 8 * x.numel() / dt / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
                 "sample": f"oracle dot (same strategy) on the full n=2^20 input, {reps} reps, {dt:.1f} s"}
     if workload == "gemv":
         A, x, dy = W.gemv("cpu", M=1024)
@@ -1047,7 +1162,7 @@ def cpu_baseline_for(workload):
             reps += 1
         dt = time.perf_counter() - t0
         b = 3 * 4 * hA.size
-        return {"value": round(reps * b / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+        return {"value": round(reps * b / dt / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
                 "sample": f"oracle GEMV forward + dx + dA on 1024 of the 8192 rows, {reps} reps, {dt:.1f} s"}
     if workload == "batched":
         import torch
@@ -1063,7 +1178,7 @@ def cpu_baseline_for(workload):
                 loopnest.dot_f32(x, x, st)
             reps += 1
         dt = time.perf_counter() - t0
-        return {"value": round(reps * 8 * sum(lens) / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+        return {"value": round(reps * 8 * sum(lens) / dt / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
                 "sample": f"oracle dots of the first 64 batch instances ({sum(lens)} elements), {reps} passes, "
                           f"{dt:.1f} s"}
     if workload == "gemm":
@@ -1072,7 +1187,7 @@ def cpu_baseline_for(workload):
         cols = np.arange(4096)
         loopnest.gemm_f32_sample(A.numpy(), B.numpy(), False, False, True, rows, cols)
         dt = time.perf_counter() - t0
-        return {"value": round(2 * 64 * 4096 * 4096 / dt / 1e12, 5), "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+        return {"value": round(2 * 64 * 4096 * 4096 / dt / 1e12, 5), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                 "sample": f"oracle FP32 fold (FMA) for 64 of the 4096 rows of C = A B, {dt:.1f} s"}
     return None
 
@@ -1173,10 +1288,9 @@ def e2e_bandwidth(args, device, dist, st_dot, st_asum, hx, hy, step_bytes):
 
 
 def oracle_bandwidth_sample(n_sample: int, reps: int, st_dot=None, st_asum=None):
-    """Time the oracle (C loop nests, one thread) on asum + scal + dot of
-    n_sample elements; returns (GB/s, seconds, description)."""
-    import numpy as np
-
+    """Time the oracle (C loop nests, its units on the thread count set by
+    loopnest.set_threads) on asum + scal + dot of n_sample elements; returns
+    (GB/s, seconds)."""
     from oracle import loopnest
     from oracle import patterns as P
     from synth import workloads as W
@@ -1199,32 +1313,60 @@ def oracle_bandwidth_sample(n_sample: int, reps: int, st_dot=None, st_asum=None)
         loopnest.dot_f32(hx, hy, od)
     dt = time.perf_counter() - t0
     step_bytes = 20 * n_sample
-    return reps * step_bytes / dt / 1e9, dt, np.float32(0)
+    return reps * step_bytes / dt / 1e9, dt
 
 
-def cpu_baseline(st_dot=None, st_asum=None, budget_s: float = 10.0):
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+def cpu_baseline(st_dot=None, st_asum=None, budget_s: float = 8.0):
+    """The oracle on the host: every core this process may run on (the value),
+    and one core beside it, each for about budget_s on n = 2^24."""
+    from oracle import loopnest
+
     n_sample = 1 << 24
-    gbs, dt, _ = oracle_bandwidth_sample(n_sample, 1, st_dot, st_asum)
-    reps = max(1, int(budget_s / max(dt, 1e-3)))
-    gbs, dt, _ = oracle_bandwidth_sample(n_sample, reps, st_dot, st_asum)
-    return {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle loop-nest evaluator (C, -O2 -ffp-contract=off, one thread): asum + scal + dot "
-                      f"on n=2^24 of the same distribution with the GPU's strategies, {reps} rep(s), "
-                      f"{dt:.1f} s", "seconds": round(dt, 2)}
+    res = {}
+    old = loopnest.set_threads(1)
+    try:
+        for cores in (host_cores(), 1):
+            loopnest.set_threads(cores)
+            _, dt = oracle_bandwidth_sample(n_sample, 1, st_dot, st_asum)
+            reps = max(1, int(budget_s / max(dt, 1e-3)))
+            gbs, dt = oracle_bandwidth_sample(n_sample, reps, st_dot, st_asum)
+            res[cores] = (gbs, reps, dt)
+    finally:
+        loopnest.set_threads(old)
+    cores = host_cores()
+    gbs, reps, dt = res[cores]
+    g1, r1, d1 = res[1]
+    return {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle loop-nest evaluator (C, -O2 -ffp-contract=off; chunks, and scal's elements, on "
+                      f"{cores} OpenMP threads, every fold across chunks on one): asum + scal + dot on n=2^24 of "
+                      f"the same distribution with the GPU's strategies, {reps} rep(s), {dt:.1f} s",
+            "seconds": round(dt, 2),
+            "one_core": {"value": round(g1, 3), "unit": "GB/s", "cores": 1, "reps": r1, "seconds": round(d1, 2)}}
 
 
 def reference_arm(args):
+    """The oracle timed as it stands on the host cores: each step asum + scal +
+    dot on a bounded sample (n = 2^22) of the bandwidth workload."""
+    from oracle import loopnest
+
     ws, rank, _ = dist_env()
     if rank != 0:
         return None
+    cores = host_cores()
+    loopnest.set_threads(cores)
     n_sample = 1 << 22
     for _ in range(args.warmup):
         oracle_bandwidth_sample(n_sample, 1)
-    gbs, dt, _ = oracle_bandwidth_sample(n_sample, args.steps)
+    gbs, dt = oracle_bandwidth_sample(n_sample, args.steps)
     step_bytes = 20 * n_sample
     ms_step = dt / args.steps * 1e3
-    cb = {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-          "sample": f"each step: oracle asum + scal + dot on n=2^22 (1/16 of the 2^26 workload), one thread"}
+    cb = {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+          "sample": f"each step: oracle asum + scal + dot on n=2^22 (1/16 of the 2^26 workload), {cores} threads "
+                    f"over chunks"}
     return {"impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -1251,6 +1393,9 @@ def main(argv=None):
                          "(4096 dots + 512 GEMVs of uneven sizes, one launch vs one launch per instance), codegen "
                          "(kernels generated from the paper's phrases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="bandwidth workload: skip the summary of the other workloads (dot 2^20, GEMV, GEMM, "
+                         "batched) in the headline line")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the split autotuner; use the default strategy (split 16384, tree second level)")
     ap.add_argument("--profile", choices=sorted(PROFILE_CASES),
@@ -1285,6 +1430,8 @@ def main(argv=None):
     dist = dist_init("nccl") if world > 1 else None
     if args.workload == "bandwidth":
         line = bandwidth_workload(args, device, dist)
+        if not args.no_workloads:
+            line["workloads"] = secondary_workloads(args, device, dist)
     else:
         line = {"dot": dot_workload, "gemv": gemv_workload, "gemm": gemm_workload,
                 "batched": batched_workload, "codegen": codegen_workload}[args.workload](args, device, dist)
@@ -1298,6 +1445,86 @@ def main(argv=None):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def _pick(d: dict, *keys):
+    return {k: d[k] for k in keys if k in d}
+
+
+def secondary_workloads(args, device, dist):
+    """The other workloads at full size, each timed on its own (K <= 10 steps
+    after W >= 3 warm-ups, its own clock record), summarised for the headline
+    line: the 2^20 dot, GEMV 8192^2 forward and backward, GEMM 4096^3 (BF16
+    forward and backward, FP32 fold), the batched uneven instances, and the
+    reductions generated from phrases as single kernels."""
+    import copy
+
+    import torch
+
+    sub = copy.copy(args)
+    sub.steps, sub.warmup, sub.gemm_ksweep = max(3, min(args.steps, 10)), 3, False
+    out = {}
+    for name, fn in (("dot_n2e20", dot_workload), ("gemv_8192", gemv_workload), ("gemm_4096", gemm_workload),
+                     ("batched", batched_workload)):
+        t0 = time.time()
+        try:
+            line = fn(sub, device, dist)
+        except Exception as exc:  # a failure here must not lose the headline line
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+            continue
+        finally:
+            torch.cuda.empty_cache()
+        k, r = line["kernels"], line["roofline"]
+        if name == "dot_n2e20":
+            d = {"f32_us": k["dot_f32"]["avg_us"], "f32_GB_s": k["dot_f32"]["GB_s"],
+                 "i32_us": k["dot_i32"]["avg_us"], "i32_GB_s": k["dot_i32"]["GB_s"], "frac": r["frac"],
+                 "empty_launch_us": line["context"]["empty_launch_floor"]["median_us"],
+                 "cublas_dot_us": line["context"]["torch_dot_cublas"]["median_us"]}
+        elif name == "gemv_8192":
+            a = line["kernels_alone"]
+            d = {kk: {"GB_s": k[kk]["GB_s"], "frac": round(k[kk]["GB_s"] / r["peak"], 4),
+                      "alone_GB_s": a[kk]["GB_s"], "alone_frac": round(a[kk]["GB_s"] / r["peak"], 4)}
+                 for kk in ("gemv_fwd", "gemv_bwd_dx", "gemv_bwd_dA")}
+        elif name == "gemm_4096":
+            d = {kk: {"TFLOP_s": k[kk]["TFLOP_s"], "frac": r["frac_per_launch"][kk]}
+                 for kk in ("bf16_fwd", "bf16_bwd_dA", "bf16_bwd_dB")}
+            d["bf16_alone_512row_pairs"] = k["alone_by_cluster"]["2x512"]
+            d["cublas_bf16_TFLOP_s"] = k["cublas_same_shape"]["TFLOP_s"]
+            d["f32_fold_fwd"] = _pick(k["f32_fold_fwd"], "TFLOP_s", "frac", "peak_TFLOP_s", "peak_source")
+            d["cublas_f32_TFLOP_s"] = k["f32_fold_fwd"]["cublas_same_shape"]["TFLOP_s"]
+        else:
+            d = {"fwd_ms": k["batched_fwd"]["avg_ms"], "bwd_ms": k["batched_bwd"]["avg_ms"],
+                 "fwd_GB_s": k["batched_fwd"]["GB_s"], "bwd_GB_s": k["batched_bwd"]["GB_s"],
+                 "fwd_frac": r["frac"], "bwd_frac": r["bwd_frac"],
+                 "speedup_vs_per_launch": line["value"], "speedup_unit": line["unit"],
+                 "policy": line["config"]["policy"]}
+        d["value"], d["unit"], d["ms_per_step"] = line["value"], line["unit"], line["ms_per_step"]
+        d["roofline"] = _pick(r, "bound", "kernel", "achieved", "peak", "unit", "frac", "traffic")
+        d["steps"], d["warmup"], d["clocks"], d["wall_s"] = sub.steps, sub.warmup, line["clocks"], \
+            round(time.time() - t0, 1)
+        out[name] = d
+    # kernels generated from phrases as one launch each, beside the library's
+    t0 = time.time()
+    clocks = ClockSampler(device.index)
+    clocks.start()
+    try:
+        from synth import workloads as W
+
+        x, y = W.bandwidth(device)
+        A, xv, _ = W.gemv(device)
+        sms = torch.cuda.get_device_properties(device).multi_processor_count
+        single, best = generated_single_launch(device, x, y, A, xv, sms, reps=10)
+        out["codegen_single_launch"] = {
+            "kernels": single, "best_dot": best[0],
+            "generated_dot_over_library_dot_time": round(best[2] / best[1], 3),
+            "note": "each kernel timed alone, back-to-back launches; the library's kernel runs the same strategy"}
+    except Exception as exc:
+        out["codegen_single_launch"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+    finally:
+        out.setdefault("codegen_single_launch", {})["clocks"] = clocks.stop()
+        out["codegen_single_launch"]["wall_s"] = round(time.time() - t0, 1)
+        torch.cuda.empty_cache()
+    return out
 
 
 def _strategy(line, op):
