@@ -407,11 +407,18 @@ dpia_status dpia_batch_backward_f32(const void *plan_dev, const void *plan_host,
  * strategy, same bits) but takes no workspace: its scratch (the per-chunk
  * partials and the completion counter) is a static device array of
  * DPIA_NOALLOC_SCRATCH_BYTES (1 MiB) that every GPU loading the library keeps
- * until the process exits, so at most (1 MiB - 128) / 8 = 131056 chunks
- * (n / split, rounded up) are allowed; larger requests return
- * DPIA_ERR_WORKSPACE with an explanation and enqueue nothing.
+ * until the process exits. Its layout is that of dpia_dot_f32's workspace: a
+ * 128-byte counter, then 8 bytes per chunk whatever the strategy (room for a
+ * Kahan pair), so at most (1 MiB - 128) / 8 = 131056 chunks (n / split,
+ * rounded up) are allowed; larger requests return DPIA_ERR_WORKSPACE with an
+ * explanation and enqueue nothing.
  *   - The first call on a device (with that device current) looks up the
  *     array's device address; make that first call before any stream capture.
+ *   - The address is kept for the life of the process. cudaDeviceReset (or
+ *     any reset of the device's primary context) unloads the library's device
+ *     code together with the array, so this entry point must not be called
+ *     on a device after it has been reset; the entries that take a caller
+ *     workspace are not affected.
  *   - Every call clears the array's counter (an asynchronous memset on
  *     `stream`) and then reuses the array: calls whose executions overlap on
  *     the GPU race on it and must be ordered by the caller.

@@ -11,7 +11,10 @@
 // may not pass the array's name to a kernel (on the host it is only a stand-in
 // symbol), so the first call on each device, with that device current, looks
 // up its device address with cudaGetSymbolAddress and caches it. That first
-// call should therefore come before any stream capture on that device.
+// call should therefore come before any stream capture on that device. The
+// cached address stays valid only as long as the device's context: after
+// cudaDeviceReset the array is unloaded with the rest of the device code, so
+// the entry must not be used on a device that has been reset.
 //
 // All calls share the one array: calls that overlap on the GPU (on different
 // streams, or from several host threads without ordering) race on it. The
@@ -76,7 +79,8 @@ extern "C" dpia_status dpia_dot_f32_noalloc(const float *x, const float *y, int6
   if (need > kNoAllocScratchBytes) {
     dpia::set_last_error(
         "dpia_dot_f32_noalloc: this n and split need %zu bytes of scratch, more than the %zu-byte "
-        "static scratch (at most %zu chunks); use a larger split or dpia_dot_f32 with a workspace",
+        "static scratch (8 bytes per chunk after a 128-byte counter: at most %zu chunks); use a larger "
+        "split or dpia_dot_f32 with a workspace",
         need, kNoAllocScratchBytes, (kNoAllocScratchBytes - 128) / 8);
     return DPIA_ERR_WORKSPACE;
   }
