@@ -215,6 +215,43 @@ __device__ __forceinline__ typename A::acc_t thread_fold(const typename E::in_t 
         for (int v = 0; v < V; ++v)
           acc[v] = A::step(acc[v], E::elem(xv[u][v], E::kTwo ? yv[u][v] : xv[u][v]));
     }
+    // what is left of the column in a half and a quarter batch (a short column,
+    // e.g. a narrow GEMV row's, keeps its loads in flight together), then singly;
+    // the vectors are still folded in r order
+    if constexpr (U >= 4) {
+      constexpr int H = U / 2;
+      if (r + H <= Rc) {
+        in_t xv[H][V], yv[H][V];
+#pragma unroll
+        for (int u = 0; u < H; ++u) {
+          load_vec<V, false>(x + base + (r + u) * step, xv[u]);
+          if constexpr (E::kTwo) load_vec<V, CACHE_Y>(y + base + (r + u) * step, yv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < H; ++u)
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+            acc[v] = A::step(acc[v], E::elem(xv[u][v], E::kTwo ? yv[u][v] : xv[u][v]));
+        r += H;
+      }
+    }
+    if constexpr (U >= 8) {
+      constexpr int Q = U / 4;
+      if (r + Q <= Rc) {
+        in_t xv[Q][V], yv[Q][V];
+#pragma unroll
+        for (int u = 0; u < Q; ++u) {
+          load_vec<V, false>(x + base + (r + u) * step, xv[u]);
+          if constexpr (E::kTwo) load_vec<V, CACHE_Y>(y + base + (r + u) * step, yv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < Q; ++u)
+#pragma unroll
+          for (int v = 0; v < V; ++v)
+            acc[v] = A::step(acc[v], E::elem(xv[u][v], E::kTwo ? yv[u][v] : xv[u][v]));
+        r += Q;
+      }
+    }
     for (; r < Rc; ++r) {
       in_t xv[V], yv[V];
       load_vec<V, false>(x + base + r * step, xv);
