@@ -213,30 +213,38 @@ def _plus(a, b):
     return P.add(a, b)
 
 
-def block_tree(parts):
-    """The block's tree over its T thread results (T a power of two, 1..1024):
-    a lane tree over each group of min(32, T) consecutive results, then a lane
-    tree over the group sums -- a one-element array (the work-group's result).
-    Each stage's input is a local temporary: other threads wrote it."""
-    T = parts.type.n
+def block_tree(cols, column):
+    """The block's tree over its T thread results, T = len(cols) a power of two
+    (1..1024), thread t's result being column(cols[t]): the columns are split
+    into groups of min(32, T), a warp per group; lane l computes its column's
+    result straight into its register of a lane tree over the group, and a lane
+    tree over the group sums (a local temporary: other warps wrote it) gives the
+    one-element array of the work-group's result. The same tree as a halving
+    tree within each group of 32 consecutive thread results, then over the
+    group sums."""
+    T = cols.type.n
     L = min(P.WARP, T)
-    sums = P.mapWarp(lambda g: P.reduceTree(_plus, g), P.split(L, P.to_local(parts)))
+    sums = P.mapWarp(lambda g: P.reduceTree(_plus, P.mapLane(column, g)), P.split(L, cols))
     W = T // L
     if W == 1:
         return sums
     return P.mapWarp(lambda g: P.reduceTree(_plus, g), P.split(W, P.to_local(sums)))
 
 
-def thread_results(chunk, T: int, thread_map: str, V: int, step, zero_lane=0.0):
-    """mapLocal over the chunk's T columns: each thread folds its column from
-    +0 with ``step`` (lane-wise on num<V>), then folds its V lanes in lane order
-    from +0."""
+def column_result(V: int, step):
+    """A thread's result: its column folded from +0 with ``step`` (lane-wise on
+    num<V>), then its V lanes folded in lane order from +0."""
     def column(col):
         acc = P.reduceSeq(step, _zero(V), col)
         if V == 1:
             return acc
-        return P.reduceSeq(lambda v, a: P.add(a, v), P.lit(zero_lane), P.lanes(acc))
-    return P.mapLocal(column, columns(chunk, T, thread_map))
+        return P.reduceSeq(lambda v, a: P.add(a, v), P.lit(0.0), P.lanes(acc))
+    return column
+
+
+def chunk_result(chunk, T: int, thread_map: str, V: int, step):
+    """The chunk's first level: T thread folds of its columns, then the block tree."""
+    return block_tree(columns(chunk, T, thread_map), column_result(V, step))
 
 
 def second_level(parts, second: str, T2: int):
@@ -248,15 +256,14 @@ def second_level(parts, second: str, T2: int):
         return P.reduceSeq(lambda v, a: P.add(a, v), 0.0, parts)
     if C % T2:
         raise ValueError(f"a tree second level over {C} results needs a thread count dividing it, not {T2}")
-    cols = P.mapLocal(lambda col: P.reduceSeq(lambda v, a: P.add(a, v), 0.0, col), P.transpose(P.split(T2, parts)))
-    return block_tree(cols)
+    return block_tree(P.transpose(P.split(T2, parts)), lambda col: P.reduceSeq(lambda v, a: P.add(a, v), 0.0, col))
 
 
 def _reduce_R(items, n_items: int, s: int, T: int, thread_map: str, V: int, second: str, T2: int, step):
     if s % (T * V) or n_items % s:
         raise ValueError(f"split {s} over {T} threads x {V} lanes does not divide {n_items} items")
     chunks = P.split(s // V, items)
-    parts = P.join(P.mapWorkgroup(lambda ch: block_tree(thread_results(ch, T, thread_map, V, step)), chunks))
+    parts = P.join(P.mapWorkgroup(lambda ch: chunk_result(ch, T, thread_map, V, step), chunks))
     return P.secondLevel(parts, lambda p: second_level(p, second, T2))
 
 
@@ -287,7 +294,7 @@ def gemv_R(M: int, N: int, T: int, V: int = 4, thread_map: str = "interleaved"):
     A, x = P.inp("A", P.arr(M, N, P.F32)), P.inp("x", P.arr(N, P.F32))
     step = lambda p, acc: P.add(acc, P.mul(P.fst(p), P.snd(p)))
     e = P.join(P.mapWorkgroup(
-        lambda row: block_tree(thread_results(P.zip_(_vec(row, V), _vec(x, V)), T, thread_map, V, step)), A))
+        lambda row: chunk_result(P.zip_(_vec(row, V), _vec(x, V)), T, thread_map, V, step), A))
     return e, [A, x]
 
 
