@@ -27,8 +27,13 @@ def _store(op, trans):
 
 @pytest.mark.parametrize("contract", ["fma", "off"])
 @pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0), (1, 1)])
-@pytest.mark.parametrize("M,N,K", [(256, 384, 80), (300, 257, 70), (1, 129, 3), (128, 128, 16)])
+@pytest.mark.parametrize("M,N,K", [(256, 384, 80), (300, 257, 70), (1, 129, 3), (128, 128, 16), (260, 132, 84),
+                                   (200, 264, 36), (384, 256, 4)])
 def test_gemm_f32_bits(cuda_device, contract, tA, tB, M, N, K):
+    """Every layout and both contractions; shapes whose rows are 16-byte multiples
+    (with the declared contraction and B not transposed: the TMA-staged kernel,
+    including ragged M and N and a k tail) and shapes that are not (the
+    register-staged kernel)."""
     g = torch.Generator().manual_seed(M * 7 + N + K)
     opA = torch.randn(M, K, generator=g).numpy()
     opB = torch.randn(K, N, generator=g).numpy()
