@@ -973,8 +973,9 @@ def generated_single_launch(device, x, y, A, xv, sms: int, reps: int = 20):
         if best is None or g_ms < best[1]:
             best = (label, g_ms, l_ms, kd, td, st)
     label, g_ms, l_ms, kd, td, st = best
+    # one operand: twice the unroll of the dot, the same bytes of loads in flight per thread
     ka = G.compile_cuda("gen_asum_R", *PR.asum_R(n, st.split, st.threads, st.vec, "interleaved", "tree",
-                                                 st.threads2), unroll=4)
+                                                 st.threads2), unroll=8)
     ta = ka.temps_like(device)
     ws = dpia.workspace(dpia.dpia_dot_workspace_size(n, st), device)
     ga = tune.time_call(lambda: ka.run(x, out, *ta), reps=reps)
