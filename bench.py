@@ -191,15 +191,16 @@ def source_digest(paths):
     return h.hexdigest()[:16]
 
 
-def profile_traffic(summary: str, sources):
-    """Per-launch DRAM bytes recorded in a profiles/ summary, if it was taken on
-    the current kernel sources (its 'source_digest' matches); else None."""
+def profile_traffic(summary: str, sources, key="traffic_bytes_per_launch"):
+    """Per-launch DRAM bytes (or another figure named by key) recorded in a
+    profiles/ summary, if it was taken on the current kernel sources (its
+    'source_digest' matches); else None."""
     path = os.path.join(PROFILES, summary)
     try:
         text = open(path).read()
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m = re.search(key + r":\s*([0-9.eE+]+)", text)
     d = re.search(r"source_digest:\s*([0-9a-f]+)", text)
     if not m or not d or d.group(1) != source_digest(sources):
         return None
@@ -210,6 +211,7 @@ REDUCE_SOURCES = ["paper_1710_08332_gb300/csrc/k_reduce.cu", "paper_1710_08332_g
 GEMV_SOURCES = ["paper_1710_08332_gb300/csrc/k_gemv.cu", "paper_1710_08332_gb300/csrc/device_common.cuh",
                 "paper_1710_08332_gb300/csrc/k_maps.cu"]
 GEMM_SOURCES = ["paper_1710_08332_gb300/csrc/k_gemm_bf16.cu"]
+BATCH_SOURCES = ["paper_1710_08332_gb300/csrc/k_batched.cu", "paper_1710_08332_gb300/csrc/device_common.cuh"]
 CODEGEN_SOURCES = ["paper_1710_08332_gb300/codegen/phrase.py", "paper_1710_08332_gb300/codegen/translate.py",
                    "paper_1710_08332_gb300/codegen/emit.py", "paper_1710_08332_gb300/codegen/programs.py"]
 
@@ -328,6 +330,9 @@ def profile_case(args):
         def fn():
             b.forward(xs, ys, dot_out, As, gx, gy)
             b.backward(xs, ys, dot_g, dxs, dys, As, gx, gdy, dAs, dgx)
+        n_dot = int(sum(b.dot_lengths))
+        mn = int(sum(m * k for m, k in zip(rows.tolist()[:16], cols.tolist()[:16])))
+        print(f"algorithmic bytes: forward {8 * n_dot + 4 * mn}, backward {16 * n_dot + 8 * mn}", flush=True)
     elif args.profile == "gen_dot":  # the generated dot partials kernel (asVector 4, split 2^15, 256 threads)
         from paper_1710_08332_gb300 import codegen as G
         from paper_1710_08332_gb300.codegen import programs as PR
@@ -917,8 +922,13 @@ def batched_workload(args, device, dist):
     speed_graph = (per["graph_per_launch_fwd"] + per["graph_per_launch_bwd"]) / \
         (per["graph_batched_fwd"] + per["graph_batched_bwd"])
     achieved = fwd_bytes / per["batched_fwd"] / 1e6
+    ratio = profile_traffic("batch_kernels_4096dots_512gemvs.md", BATCH_SOURCES,
+                            key="traffic_bytes_per_algorithmic_byte")
+    traffic = round(ratio * fwd_bytes) if ratio is not None else None
     roof = {"bound": "hbm", "kernel": "batch_fwd_kernel (dpia_batch_forward_f32)", "achieved": round(achieved, 1),
-            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
+            "traffic_note": "DRAM bytes per algorithmic byte of the forward kernel on a small case of the same "
+                            "batch (ncu), times this launch's algorithmic bytes",
             "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": fwd_bytes,
             "bwd_frac": round(bwd_bytes / per["batched_bwd"] / 1e6 / hbm, 4)}
     cfg = {"workload": "batched uneven instances: 4096 f32 dots (lengths log-uniform [256, 65536]) + 512 GEMVs "

@@ -64,7 +64,7 @@ struct GemvDesc {
   int64_t s, Crow, Rc, step, tstride;  // forward row strategy (a warp per row)
   int64_t Rs, Cr, Npad, part_base;     // backward dx: rows per chunk, chunks, padded width, partial offset
   int32_t tiles, tile_cnt;             // dx column tiles (kDxTile columns each), index of the first tile's counter
-  int32_t da_rows, fwd_rows;           // rows of a dA item; rows of a forward item (all warps of a block)
+  int32_t da_rows, pad0;               // rows of a dA item
 };
 
 struct Item {
@@ -122,16 +122,6 @@ constexpr int kDaMaxRows = 64;
 constexpr int64_t kDaItemBytes = 64 * 1024;
 constexpr int64_t kDxTile = 128;
 
-// Rows each warp of a forward GEMV item folds, one after another: at least 4,
-// and enough (a power of two, at most 32) that the warp reads about 32 KiB, so
-// the item's fixed cost (fetching the item and its instance's descriptor) is
-// spread over enough bytes for narrow rows too.
-int64_t fwd_rows_per_warp(int64_t N) {
-  int64_t r = 4;
-  while (r < 32 && r * N * 4 < 32 * 1024) r *= 2;
-  return r;
-}
-
 int64_t da_rows_for(int64_t N) {
   int64_t r = 1;
   while (r < kDaMaxRows && r * N * 4 < kDaItemBytes) r *= 2;
@@ -169,7 +159,7 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
   h.n_dots = nd;
   h.n_gemvs = ng;
   h.schedule = opt->schedule;
-  h.rows_per_item = T / 32 * 4;  // a warp per row, at least four rows per warp (fwd_rows_per_warp)
+  h.rows_per_item = T / 32 * 4;  // a warp per row, four rows per warp
   h.da_rows_per_item = kDaMaxRows;
   h.bwd_elems_per_item = kDotBwdElems;
   std::vector<std::pair<int64_t, Item>> fwd, bwd;  // (cost, item)
@@ -252,7 +242,6 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
     g.part_base = h.dx_partials;
     g.tiles = (int32_t)((in.N + kDxTile - 1) / kDxTile);
     g.da_rows = (int32_t)da_rows_for(in.N);
-    g.fwd_rows = (int32_t)(T / 32 * fwd_rows_per_warp(in.N));
     g.tile_cnt = (int32_t)h.dx_tiles;
     h.dx_partials += g.Cr * g.Npad;
     h.dx_tiles += g.tiles;
@@ -260,8 +249,8 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
     h.gx_extent = std::max(h.gx_extent, in.x_off + in.N);
     h.gy_extent = std::max(h.gy_extent, in.y_off + in.M);
     b.gemvs.push_back(g);
-    for (int64_t r = 0; r < in.M; r += g.fwd_rows)
-      fwd.push_back({4 * std::min<int64_t>(g.fwd_rows, in.M - r) * in.N, Item{GEMV_ROWS, i, r}});
+    for (int64_t r = 0; r < in.M; r += h.rows_per_item)
+      fwd.push_back({4 * std::min<int64_t>(h.rows_per_item, in.M - r) * in.N, Item{GEMV_ROWS, i, r}});
     for (int64_t r = 0; r < in.M; r += g.da_rows)
       bwd.push_back({4 * std::min<int64_t>(g.da_rows, in.M - r) * in.N, Item{GEMV_DA, i, r}});
     for (int64_t t = 0; t < g.tiles; ++t)
@@ -427,7 +416,7 @@ __global__ void __launch_bounds__(256, 3) batch_fwd_kernel(const FwdArgs a) {
       __syncthreads();
     } else {  // GEMV_ROWS: a warp per row, the row's chunks folded in order
       const int64_t warps = blockDim.x >> 5;
-      const int64_t r_end = w.a + g.fwd_rows < g.M ? w.a + g.fwd_rows : g.M;
+      const int64_t r_end = w.a + h->rows_per_item < g.M ? w.a + h->rows_per_item : g.M;
       const float *x = a.gx + g.x_off;
       for (int64_t r = w.a + warp; r < r_end; r += warps) {
         const float *row = a.As + g.a_off + r * g.lda;
