@@ -11,7 +11,7 @@ from .build import CFunction, CudaKernel, compile_c, compile_cuda
 from .emit import EmitError, generate
 from .phrase import (F32, I32, I64, Arr, Num, PairT, VecT, abs_, add, arr, asScalar, asVector, fst, inp, join,
                      lanes, lit, mapGlobal, mapLane, mapLocal, mapSeq, mapWarp, mapWorkgroup, mul, reduceSeq,
-                     reduceTree, secondLevel, snd, split, sub, to_global, to_local, to_private, transpose, vlit, zip_)
+                     reduceTree, secondLevel, snd, splat, split, sub, to_global, to_local, to_private, transpose, vlit, zip_)
 from .translate import TranslationError
 from .typecheck import TypeCheckError
 

@@ -68,6 +68,8 @@ __device__ __forceinline__ float dpia_lane4(float4 v, long long l) {
 __device__ __forceinline__ float dpia_lane2(float2 v, long long l) { return l == 0 ? v.x : v.y; }
 __device__ __forceinline__ float4 dpia_vabs4(float4 a) { return make_float4(fabsf(a.x), fabsf(a.y), fabsf(a.z), fabsf(a.w)); }
 __device__ __forceinline__ float2 dpia_vabs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float4 dpia_splat4(float v) { return make_float4(v, v, v, v); }
+__device__ __forceinline__ float2 dpia_splat2(float v) { return make_float2(v, v); }
 """
 
 THREADED = ("local", "warp", "lane")  # levels whose loops spread over the threads of a block
@@ -91,6 +93,8 @@ static inline float dpia_lane4(float4 v, long long l) { return l == 0 ? v.x : l 
 static inline float dpia_lane2(float2 v, long long l) { return l == 0 ? v.x : v.y; }
 static inline float4 dpia_vabs4(float4 a) { return make_float4(fabsf(a.x), fabsf(a.y), fabsf(a.z), fabsf(a.w)); }
 static inline float2 dpia_vabs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+static inline float4 dpia_splat4(float v) { return make_float4(v, v, v, v); }
+static inline float2 dpia_splat2(float v) { return make_float2(v, v); }
 """
 
 
@@ -221,6 +225,10 @@ class Emitter:
                 raise EmitError("index into a number")
             a, b = self.access(e.a, []), self.access(e.b, [])
             return self.binop(e.op, a, b, e.type)
+        if isinstance(e, P.Splat):
+            if path:  # a lane of the vector: the number itself
+                return self.access(e.a, [])
+            return f"dpia_splat{e.n}({self.access(e.a, [])})"
         if isinstance(e, P.Abs):
             if isinstance(e.type, P.VecT):
                 return f"dpia_vabs{e.type.n}({self.access(e.a, [])})"

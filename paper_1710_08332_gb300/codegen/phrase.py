@@ -210,6 +210,23 @@ class Abs(Phrase):
 
 
 @dataclass(eq=False)
+class Splat(Phrase):
+    """splat V e: the vector num<V> whose V lanes are all the number e (the
+    widening of a number to a vector in vector arithmetic, Section 6.2)."""
+    n: int
+    a: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        if self.a.type != F32:
+            raise TypeError(f"splat of a {self.a.type} (f32 numbers only)")
+        self.type = VecT(self.n, self.a.type)
+
+    def children(self):
+        return (self.a,)
+
+
+@dataclass(eq=False)
 class Lam:
     """A function of one or two phrases (the body refers to the parameters)."""
     params: tuple
@@ -596,6 +613,11 @@ def vlit(v, n=4):
     return Lit(v, VecT(n, F32))
 
 
+def splat(n, e):
+    """The vector of n copies of the number e."""
+    return Splat(n, e)
+
+
 def to_private(e):
     return To("private", e)
 
@@ -648,6 +670,8 @@ def subst(p: Phrase, env: dict) -> Phrase:
         return Bin(p.op, subst(p.a, env), subst(p.b, env))
     if isinstance(p, Abs):
         return Abs(subst(p.a, env))
+    if isinstance(p, Splat):
+        return Splat(p.n, subst(p.a, env))
     if isinstance(p, Map):
         return Map(p.level, Lam(p.f.params, subst(p.f.body, env)), subst(p.e, env))
     if isinstance(p, Reduce):

@@ -8,6 +8,9 @@ is one or two kernels, the second folding the first one's partial results.
     asum  the same with map abs
     scal  mapGlobal (lambda v. a * v) x
     dA    mapWorkgroup (lambda d. mapLocal (lambda v. d * v) x) dy
+    dot dx = mapGlobal (lambda v. g * v) y
+    gemm  mapWorkgroup (lambda a. mapLocal (lambda b. reduceSeq (+) 0
+                       (map (*) (zip a b))) (transpose B)) A
     dx    partials = mapWorkgroup (lambda (rows, dys). mapLocal (lambda col.
                        reduceSeq (+) 0 (map (*) (zip col dys))) (transpose rows))
                        (zip (split R A) (split R dy));  dx = mapGlobal fold (columns of partials)
@@ -142,6 +145,54 @@ def gemv_bwd_dx_fold(C: int, N: int):
     p = P.inp("p", P.arr(C * N, P.F32))
     return P.mapGlobal(lambda col: P.reduceSeq(lambda v, acc: P.add(acc, v), 0.0, col),
                        P.transpose(P.split(N, p))), [p]
+
+
+def dot_bwd(n: int, V: int = 1):
+    """One half of the dot's backward pass: map (lambda v. g * v) over y gives dx
+    (and over x gives dy) -- the adjoint of the reduce broadcasts the incoming
+    gradient g, the adjoint of the zip-map multiplies pointwise. g is a
+    one-element input (the gradient as the autodiff leaves it, in memory)."""
+    from .translate import IConst
+
+    g, v = P.inp("g", P.arr(1, P.F32)), P.inp("v", P.arr(n, P.F32))
+    gv = P.Idx(g, IConst(0))
+    if V == 1:
+        return P.mapGlobal(lambda e: P.mul(gv, e), v), [g, v]
+    return P.asScalar(P.mapGlobal(lambda e: P.mul(P.splat(V, gv), e), P.asVector(V, v))), [g, v]
+
+
+def gemm(M: int, N: int, K: int, V: int = 1, transA: bool = False, transB: bool = False):
+    """C = map (lambda a. map (lambda b. reduceSeq (+) 0 (map (*) (zip a b)))
+    (transpose B)) A: a workgroup per row of C, the row's columns over the
+    workgroup's threads, each C_ij one sequential fold over k from +0 (the
+    product and the sum rounded separately). op(A) is A (M x K) or, with
+    transA, the transpose of a stored K x M matrix; op(B) is B (K x N) or,
+    with transB, the transpose of a stored N x K matrix -- transposes are
+    views, so the backward products dA = dC B^T and dB = A^T dC are the same
+    phrase. With V > 1 (B not transposed) a thread folds V adjacent columns
+    as one num<V>: a_ik widened to a vector times the V entries of row k of
+    B, each lane its own fold, in the same order."""
+    A = P.inp("A", P.arr(K, M, P.F32) if transA else P.arr(M, K, P.F32))
+    B = P.inp("B", P.arr(N, K, P.F32) if transB else P.arr(K, N, P.F32))
+    rows = P.transpose(A) if transA else A
+    if V == 1:
+        cols = B if transB else P.transpose(B)
+        e = P.mapWorkgroup(
+            lambda a: P.mapLocal(
+                lambda b: P.reduceSeq(lambda p, acc: P.add(acc, P.mul(P.fst(p), P.snd(p))), 0.0, P.zip_(a, b)),
+                cols),
+            rows)
+        return e, [A, B]
+    if transB or N % V:
+        raise ValueError("vector columns need B stored K x N with N a multiple of V")
+    cols = P.transpose(P.split(N // V, P.asVector(V, P.join(B))))  # (N/V) x K of num<V>
+    e = P.mapWorkgroup(
+        lambda a: P.asScalar(P.mapLocal(
+            lambda b: P.reduceSeq(lambda p, acc: P.add(acc, P.mul(P.splat(V, P.fst(p)), P.snd(p))),
+                                  P.vlit(0.0, V), P.zip_(a, b)),
+            cols)),
+        rows)
+    return e, [A, B]
 
 
 # ---------------------------------------------------------------------------

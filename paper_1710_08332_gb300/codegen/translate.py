@@ -57,6 +57,10 @@ def iadd(a, b):
         return a
     if isinstance(a, IConst) and isinstance(b, IConst):
         return IConst(a.v + b.v)
+    # (x / n) * n + x % n = x for the non-negative x of an index (a join of a split)
+    if (isinstance(a, IOp) and a.op == "*" and isinstance(a.a, IOp) and a.a.op == "/" and a.a.b == a.b
+            and isinstance(b, IOp) and b.op == "%" and b.b == a.b and b.a == a.a.a):
+        return b.a
     return IOp("+", a, b)
 
 
@@ -395,6 +399,8 @@ class Translator:
             return self.C(e.a, lambda a: self.C(e.b, lambda b: k(P.Bin(e.op, a, b)), levels), levels)
         if isinstance(e, P.Abs):
             return self.C(e.a, lambda a: k(P.Abs(a)), levels)
+        if isinstance(e, P.Splat):
+            return self.C(e.a, lambda a: k(P.Splat(e.n, a)), levels)
         if isinstance(e, P.Zip):
             return self.C(e.a, lambda a: self.C(e.b, lambda b: k(P.Zip(a, b)), levels), levels)
         if isinstance(e, P.Proj):

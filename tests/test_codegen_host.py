@@ -209,7 +209,8 @@ def test_type_errors():
 def test_cuda_sources_compile_for_sm103a(tmp_path):
     progs = {"dotp": PR.dot_partials(1 << 20, 8192, 256), "asump": PR.asum_partials(1 << 20, 8192, 256, "contig"),
              "fold": PR.fold_all(4096), "scal": PR.scal(1 << 20, 1.5), "gemvp": PR.gemv_partials(512, 1024, 128),
-             "rows": PR.fold_rows(512, 128), "k1": PR.dot_K1(4096)}
+             "rows": PR.fold_rows(512, 128), "k1": PR.dot_K1(4096), "gemm4": PR.gemm(256, 512, 128, 4),
+             "gemm_tt": PR.gemm(256, 512, 128, 1, True, True), "dotbwd4": PR.dot_bwd(1 << 20, 4)}
     for name, (e, ins) in progs.items():
         src = B.cuda_source(E.generate(name, e, ins, "cuda"))
         assert "__fadd_rn" in src or "__fmul_rn" in src
@@ -412,6 +413,52 @@ def test_gemv_backward_programs_match_the_library_trees(c_build):
     dA = np.zeros(M * N, np.float32)
     G.compile_c("dA", e, ins).run(dy, x, dA)
     assert np.array_equal(bits(dA.reshape(M, N)), bits(loopnest.gemv_bwd_dA_f32(x, dy)))
+
+
+@pytest.mark.parametrize("transA,transB,V", [(False, False, 1), (False, False, 4), (True, False, 4),
+                                          (False, True, 1), (True, True, 1), (False, False, 2)])
+@pytest.mark.parametrize("M,N,K", [(5, 12, 7), (33, 40, 65), (1, 4, 1)])
+def test_gemm_matches_oracle(c_build, M, N, K, transA, transB, V):
+    """The generated GEMM (a workgroup per row of C, columns over its threads,
+    V adjacent columns per thread as a vector) folds every C_ij over k in
+    order from +0, the product and the sum rounded separately: equal to the
+    loop-nest oracle with contraction off, in all four operand layouts."""
+    from oracle import loopnest
+
+    rng = np.random.default_rng(60 + M + K)
+    A = rng.uniform(-1, 1, (K, M) if transA else (M, K)).astype(np.float32)
+    B = rng.uniform(-1, 1, (N, K) if transB else (K, N)).astype(np.float32)
+    e, ins = PR.gemm(M, N, K, V, transA, transB)
+    C = np.zeros((M, N), np.float32)
+    G.compile_c(f"gemm_{M}_{N}_{K}_{int(transA)}{int(transB)}{V}", e, ins).run(A, B, C)
+    want = loopnest.gemm_f32(A, B, transA, transB, contract_fma=False)
+    assert np.array_equal(bits(C), bits(want))
+
+
+def test_gemm_vector_columns_need_a_row_major_B():
+    with pytest.raises(ValueError):
+        PR.gemm(8, 16, 8, 4, False, True)
+    with pytest.raises(ValueError):
+        PR.gemm(8, 18, 8, 4)
+    with pytest.raises(TypeError):
+        G.splat(4, G.vlit(1.0, 4))
+
+
+@pytest.mark.parametrize("V", [1, 4])
+def test_dot_backward_matches_oracle(c_build, V):
+    """dx = g y and dy = g x, the generated map applied to each stream."""
+    from oracle import loopnest
+
+    n = 4096 + 8
+    x, y = uniform(n, 70), uniform(n, 71)
+    g = np.array([-0.8125], np.float32)
+    e, ins = PR.dot_bwd(n, V)
+    f = G.compile_c(f"dot_bwd_{V}", e, ins)
+    dx, dy = np.zeros(n, np.float32), np.zeros(n, np.float32)
+    f.run(g, y, dx)
+    f.run(g, x, dy)
+    wx, wy = loopnest.dot_bwd_f32(x, y, float(g[0]))
+    assert np.array_equal(bits(dx), bits(wx)) and np.array_equal(bits(dy), bits(wy))
 
 
 def test_local_temporaries_are_bounded():

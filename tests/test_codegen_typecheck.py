@@ -36,6 +36,12 @@ PROGRAMS = {
     "asum_R": lambda: PR.asum_R(1 << 14, 1 << 11, 256, 4, "interleaved", "tree", 8),
     "gemv_R": lambda: PR.gemv_R(16, 512, 64, 4),
     "gemv_R_warp": lambda: PR.gemv_R_warp(16, 512, 4, 4),
+    "dot_bwd": lambda: PR.dot_bwd(1024),
+    "dot_bwd_V4": lambda: PR.dot_bwd(1024, 4),
+    "gemm": lambda: PR.gemm(24, 40, 12),
+    "gemm_V4": lambda: PR.gemm(24, 40, 12, 4),
+    "gemm_tA_tB": lambda: PR.gemm(24, 40, 12, 1, True, True),
+    "gemm_tA_V4": lambda: PR.gemm(24, 40, 12, 4, True, False),
 }
 
 

@@ -322,3 +322,68 @@ def test_single_launch_gemv_matches_oracle_gpu(cuda_device, M, N, T, V):
         e, ins = PR.gemv_R_warp(M, N, 8, 4)
         got = run(G.compile_cuda("gemvRw", e, ins, unroll=4), dA, dxv, out_count=M)
         assert np.array_equal(bits(got), bits(loopnest.gemv_f32(A, xv, P_.Strategy(s=N, T=32, V=4))))
+
+
+@pytest.mark.parametrize("transA,transB,V", [(False, False, 4), (True, False, 4), (False, True, 1),
+                                          (True, True, 1), (False, False, 1)])
+def test_generated_gemm_matches_oracle(cuda_device, transA, transB, V):
+    """The generated GEMM, every C_ij one fold over k from +0 (product and sum
+    rounded separately), in all four operand layouts: equal to the loop-nest
+    oracle with contraction off, under the default launch and smaller grids
+    and blocks (row and column loops stride over what the launch covers)."""
+    from oracle import loopnest
+
+    M, N, K = 130, 264, 77
+    rng = np.random.default_rng(80 + 2 * transA + transB)
+    A = rng.standard_normal((K, M) if transA else (M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K) if transB else (K, N)).astype(np.float32)
+    k = G.compile_cuda(f"gemm_{int(transA)}{int(transB)}_{V}", *PR.gemm(M, N, K, V, transA, transB), unroll=4)
+    want = loopnest.gemm_f32(A, B, transA, transB, contract_fma=False)
+    for grid, block in ((None, None), (7, 64), (200, 32)):
+        got = run(k, dev(A), dev(B), out_count=M * N, grid=grid, block=block).reshape(M, N)
+        assert np.array_equal(bits(got), bits(want)), (grid, block)
+
+
+def test_generated_gemm_4096(cuda_device):
+    """At 4096^3 (float4 columns): every element equal to the library's FP32
+    fold with contraction off (the same fold per element), and 96 full rows
+    equal to the oracle's fold."""
+    from oracle import loopnest
+    from synth import workloads as W
+    from tests.test_gpu_gemm import _f32_rows_4096
+
+    import paper_1710_08332_gb300 as dpia
+
+    n = W.GEMM_MNK
+    A, B, _ = W.gemm("cuda")
+    k = G.compile_cuda("gemm_4096_v4", *PR.gemm(n, n, n, 4), unroll=4)
+    C = torch.empty(n * n, device="cuda")
+    k.run(A, B, C)
+    lib = torch.empty(n, n, device="cuda")
+    dpia.dpia_gemm_f32(A, B, lib, n, n, n, n, n, n, 0, 0, "off")
+    torch.cuda.synchronize()
+    got = C.view(n, n)
+    assert torch.equal(got.view(torch.int32), lib.view(torch.int32))
+    rows = _f32_rows_4096(n)
+    want = loopnest.gemm_f32_sample(A.cpu().numpy(), B.cpu().numpy(), False, False, False, rows, np.arange(n))
+    assert np.array_equal(bits(got.cpu().numpy()[rows]), bits(want))
+
+
+@pytest.mark.parametrize("V", [1, 4])
+def test_generated_dot_backward(cuda_device, V):
+    """dx = g y, dy = g x from the generated map: equal to the oracle and to the
+    library's dot backward."""
+    from oracle import loopnest
+
+    import paper_1710_08332_gb300 as dpia
+
+    n = (1 << 20) + 4 * 7
+    x, y = uniform(n, 90), uniform(n, 91)
+    g = np.array([1.375], np.float32)
+    k = G.compile_cuda(f"dot_bwd_{V}", *PR.dot_bwd(n, V))
+    dx = run(k, dev(g), dev(y), out_count=n)
+    dy = run(k, dev(g), dev(x), out_count=n)
+    wx, wy = loopnest.dot_bwd_f32(x, y, float(g[0]))
+    assert np.array_equal(bits(dx), bits(wx)) and np.array_equal(bits(dy), bits(wy))
+    lx, ly = dpia.dot_bwd(dev(x), dev(y), dev(g))
+    assert np.array_equal(bits(lx.cpu().numpy()), bits(dx)) and np.array_equal(bits(ly.cpu().numpy()), bits(dy))
