@@ -500,24 +500,24 @@ __global__ void __launch_bounds__(256, 4) batch_bwd_kernel(const BwdArgs a) {
       const float *x = a.gx + g.x_off;
       const float *dyv = a.gdy + g.y_off;
       const int64_t r0 = w.a, r1 = w.a + g.da_rows < g.M ? w.a + g.da_rows : g.M;
+      const int nr = (int)(r1 - r0);  // at most kDaMaxRows = 64
+      // the item's dy values, two per lane, handed to the store loop by shuffles:
+      // no load waits between the stores
+      const float dlo = lane < nr ? __ldg(dyv + r0 + lane) : 0.0f;
+      const float dhi = lane + 32 < nr ? __ldg(dyv + r0 + 32 + lane) : 0.0f;
       const int64_t cgv = g.N / 4;  // full column groups
       float *base = a.dAs + g.a_off;
-      for (int64_t j = lane; j < cgv; j += 32) {
-        const float4 xv = ld_cached_v4(x + 4 * j);  // loaded once, stored scaled into every row
-        int64_t r = r0;
-        for (; r + 4 <= r1; r += 4) {
-          float dv[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) dv[u] = __ldg(dyv + r + u);
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            st_stream_v4(base + (r + u) * g.lda + 4 * j, make_float4(__fmul_rn(dv[u], xv.x), __fmul_rn(dv[u], xv.y),
-                                                                    __fmul_rn(dv[u], xv.z), __fmul_rn(dv[u], xv.w)));
-        }
-        for (; r < r1; ++r) {
-          const float dv = __ldg(dyv + r);
-          st_stream_v4(base + r * g.lda + 4 * j, make_float4(__fmul_rn(dv, xv.x), __fmul_rn(dv, xv.y),
-                                                            __fmul_rn(dv, xv.z), __fmul_rn(dv, xv.w)));
+      float *rows = base + r0 * g.lda;
+      for (int64_t jb = 0; jb < cgv; jb += 32) {  // every lane runs every trip (the shuffles)
+        const int64_t j = jb + lane;
+        const bool on = j < cgv;
+        const float4 xv = on ? ld_cached_v4(x + 4 * j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 4
+        for (int r = 0; r < nr; ++r) {
+          const float dv = __shfl_sync(0xffffffffu, r < 32 ? dlo : dhi, r & 31);
+          if (on)
+            st_stream_v4(rows + r * g.lda + 4 * j, make_float4(__fmul_rn(dv, xv.x), __fmul_rn(dv, xv.y),
+                                                              __fmul_rn(dv, xv.z), __fmul_rn(dv, xv.w)));
         }
       }
       if (4 * cgv < g.N)  // the ragged last columns, element by element
