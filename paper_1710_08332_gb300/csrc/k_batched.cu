@@ -346,6 +346,68 @@ constexpr int kSeqStage = 1024;
 // rows keep 32 items per lane in flight, which measured faster than 4 blocks
 // with 16 (64 registers). The backward kernel keeps 4 blocks (64 registers).
 
+// Rows of an interleaved GEMV whose one chunk gives each lane at most RC
+// vectors (N <= 128 RC): the warp takes 8 / RC of its rows at once, so that up
+// to eight 128-bit loads per lane are in flight as for wider rows, then folds
+// each row exactly as thread_fold does (lane vectors in r order, items at or
+// past N as the identity (0, 0), the lane's four sums from zero in lane
+// order), the warp tree, and the row's one chunk added to zero.
+template <int RC>
+__device__ __forceinline__ void gemv_rows_narrow(const float *A, int64_t lda, const float *x, float *y, int64_t N,
+                                                 int64_t r0, int64_t r_end, int64_t stride, int lane) {
+  constexpr int G = 8 / RC;
+  float4 xv[RC];
+#pragma unroll
+  for (int q = 0; q < RC; ++q) {
+    const int64_t e0 = 4 * lane + 128 * q;
+    if (e0 + 4 <= N) {
+      xv[q] = ld_cached_v4(x + e0);
+    } else {
+      xv[q].x = e0 < N ? x[e0] : 0.0f;
+      xv[q].y = e0 + 1 < N ? x[e0 + 1] : 0.0f;
+      xv[q].z = e0 + 2 < N ? x[e0 + 2] : 0.0f;
+      xv[q].w = e0 + 3 < N ? x[e0 + 3] : 0.0f;
+    }
+  }
+  for (int64_t r = r0; r < r_end; r += stride * G) {
+    float4 av[G][RC];
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      const int64_t row = r + k * stride;
+      const float *p = A + (row < r_end ? row : r0) * lda;
+#pragma unroll
+      for (int q = 0; q < RC; ++q) {
+        const int64_t e0 = 4 * lane + 128 * q;
+        if (e0 + 4 <= N) {
+          av[k][q] = ld_stream_v4(p + e0);
+        } else {
+          av[k][q].x = e0 < N ? p[e0] : 0.0f;
+          av[k][q].y = e0 + 1 < N ? p[e0 + 1] : 0.0f;
+          av[k][q].z = e0 + 2 < N ? p[e0 + 2] : 0.0f;
+          av[k][q].w = e0 + 3 < N ? p[e0 + 3] : 0.0f;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      float acc[4] = {SumF32::zero(), SumF32::zero(), SumF32::zero(), SumF32::zero()};
+#pragma unroll
+      for (int q = 0; q < RC; ++q) {
+        acc[0] = SumF32::step(acc[0], DotF32::elem(av[k][q].x, xv[q].x));
+        acc[1] = SumF32::step(acc[1], DotF32::elem(av[k][q].y, xv[q].y));
+        acc[2] = SumF32::step(acc[2], DotF32::elem(av[k][q].z, xv[q].z));
+        acc[3] = SumF32::step(acc[3], DotF32::elem(av[k][q].w, xv[q].w));
+      }
+      float t = SumF32::zero();
+#pragma unroll
+      for (int v = 0; v < 4; ++v) t = SumF32::combine(t, acc[v]);
+      t = warp_tree<SumF32>(t, 32);
+      const int64_t row = r + k * stride;
+      if (lane == 0 && row < r_end) y[row] = __fadd_rn(0.0f, t);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256, 3) batch_fwd_kernel(const FwdArgs a) {
   __shared__ float sm[32];
   __shared__ float stage[kSeqStage];
@@ -418,6 +480,13 @@ __global__ void __launch_bounds__(256, 3) batch_fwd_kernel(const FwdArgs a) {
       const int64_t warps = blockDim.x >> 5;
       const int64_t r_end = w.a + h->rows_per_item < g.M ? w.a + h->rows_per_item : g.M;
       const float *x = a.gx + g.x_off;
+      if (g.Crow == 1 && g.Rc >= 2 && g.Rc <= 4 && g.step == 32 * V) {
+        const float *A0 = a.As + g.a_off;
+        float *y = a.gy + g.y_off;
+        // two or three vectors fold as four: the others lie past N, identity items
+        // (+0 added to a sum that starts at +0 and so is never -0: the same bits)
+        gemv_rows_narrow<4>(A0, g.lda, x, y, g.N, w.a + warp, r_end, warps, lane);
+      } else
       for (int64_t r = w.a + warp; r < r_end; r += warps) {
         const float *row = a.As + g.a_off + r * g.lda;
         float acc = 0.0f;
