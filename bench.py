@@ -1014,17 +1014,19 @@ def generated_single_launch(device, x, y, A, xv, sms: int, reps: int = 20):
     res["gemv_R (a block of 128 per row, float4)"] = {
         "generated_us": round(gg * 1e3, 2), "library_us": round(lg * 1e3, 2),
         "generated_GB_s": round(gb / gg / 1e6, 1), "generated_over_library_time": round(lg / gg, 3)}
-    res["gemm (4096^3 FP32, a workgroup per row, float4 columns)"] = generated_gemm(device, reps=max(3, reps // 4))
+    res["gemm (4096^3 FP32)"] = generated_gemm(device, reps=max(3, reps // 4))
     return res, best
 
 
 def generated_gemm(device, reps: int = 5):
-    """The generated FP32 GEMM at 4096^3 (map of maps of a fold over k; a
-    workgroup per row of C, each thread four adjacent columns as one float4
-    fold), beside the library's register-tiled FP32 fold with contraction off
-    (the same fold of every element), both on the GEMM inputs; L2 is flushed
-    before every launch (A and B fit in it). The block size of the generated
-    kernel is the fastest of 256, 512 and 1024 threads."""
+    """The generated FP32 GEMM at 4096^3 in two forms of the same map of maps of
+    a fold over k: a workgroup per row with four adjacent columns per thread as
+    one float4 fold, and the register-tiled form (a workgroup per 8 rows, each
+    thread an 8 x 8 block of C accumulated in a private array, A read along k
+    as float4); beside them the library's register-tiled FP32 fold with
+    contraction off (the same fold of every element), all on the GEMM inputs,
+    L2 flushed before every launch (A and B fit in it). Each form takes the
+    fastest of its block sizes."""
     import torch
 
     import paper_1710_08332_gb300 as dpia
@@ -1036,7 +1038,6 @@ def generated_gemm(device, reps: int = 5):
     A, B, _ = W.gemm(device)
     C = torch.empty(n, n, device=device)
     flush = torch.empty(64 << 20, device=device)
-    k = G.compile_cuda("gen_gemm_4096_v4", *PR.gemm(n, n, n, 4), unroll=4)
 
     def timed(fn):
         ts = []
@@ -1050,16 +1051,21 @@ def generated_gemm(device, reps: int = 5):
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts[1:])
 
-    by_block = {b: timed(lambda: k.run(A, B, C, block=b)) for b in (256, 512, 1024)}
-    blk = min(by_block, key=by_block.get)
-    lib = timed(lambda: dpia.dpia_gemm_f32(A, B, C, n, n, n, n, n, n, 0, 0, "off"))
     fl = 2.0 * n ** 3
-    return {"generated_ms": round(by_block[blk], 3), "generated_TFLOP_s": round(fl / by_block[blk] / 1e9, 2),
-            "block": blk, "by_block_ms": {str(b): round(v, 3) for b, v in by_block.items()},
-            "library_fold_off_ms": round(lib, 3), "library_TFLOP_s": round(fl / lib / 1e9, 2),
-            "generated_over_library_time": round(lib / by_block[blk], 3),
-            "note": "every element equal to the library's (tests); no register tiling in the phrase: each "
-                    "thread folds its own four columns, B is re-read from L2 for every row"}
+    lib = timed(lambda: dpia.dpia_gemm_f32(A, B, C, n, n, n, n, n, n, 0, 0, "off"))
+    out = {"library_fold_off_ms": round(lib, 3), "library_TFLOP_s": round(fl / lib / 1e9, 2)}
+    forms = {"columns (a workgroup per row, float4 columns)":
+             (G.compile_cuda("gen_gemm_4096_v4", *PR.gemm(n, n, n, 4), unroll=4), (256, 512, 1024)),
+             "tiled (8 x 8 per thread in a private array, A along k as float4)":
+             (G.compile_cuda("gen_gemm_4096_tiled", *PR.gemm_tiled(n, n, n, 8, 8, 4, 4)), (128, 256))}
+    for label, (k, blocks) in forms.items():
+        by_block = {b: timed(lambda: k.run(A, B, C, block=b)) for b in blocks}
+        blk = min(by_block, key=by_block.get)
+        out[label] = {"ms": round(by_block[blk], 3), "TFLOP_s": round(fl / by_block[blk] / 1e9, 2), "block": blk,
+                      "by_block_ms": {str(b): round(v, 3) for b, v in by_block.items()},
+                      "over_library_time": round(lib / by_block[blk], 3)}
+    out["note"] = "every element of both forms equal to the library's (tests)"
+    return out
 
 
 def codegen_workload(args, device, dist):

@@ -41,6 +41,8 @@ the phrase denotes.
 """
 from __future__ import annotations
 
+import math
+
 from . import phrase as P
 from . import translate as T
 
@@ -96,6 +98,31 @@ static inline float2 dpia_vabs2(float2 a) { return make_float2(fabsf(a.x), fabsf
 static inline float4 dpia_splat4(float v) { return make_float4(v, v, v, v); }
 static inline float2 dpia_splat2(float v) { return make_float2(v, v); }
 """
+
+
+def _acc_root(a):
+    while not isinstance(a, T.AOut):
+        a = a.acc
+    return a
+
+
+def _reads_private_array(e) -> bool:
+    if isinstance(e, P.Ident):
+        return e.temp == "private" and isinstance(e.type, P.Arr)
+    return any(_reads_private_array(x) for x in e.children())
+
+
+def _private_array_loop(c) -> bool:
+    """The command writes or reads an element of a private array temporary."""
+    if isinstance(c, T.Assign):
+        r = _acc_root(c.acc)
+        return (r.temp is not None and r.temp.space == "private" and isinstance(r.temp.type, P.Arr)) or \
+            _reads_private_array(c.e)
+    if isinstance(c, T.Seq):
+        return any(_private_array_loop(x) for x in c.cs)
+    if isinstance(c, (T.New, T.For)):
+        return _private_array_loop(c.body)
+    return False
 
 
 def divisible(i, V: int) -> bool:
@@ -219,6 +246,8 @@ class Emitter:
         if isinstance(e, Shuffle):
             return f"__shfl_down_sync(0xffffffffu, {self.access(e.e, path)}, {e.offset})"
         if isinstance(e, P.Lit):
+            if isinstance(e.type, P.Arr):  # every element of an array literal is its value
+                return self.literal(P.Lit(e.value, P.base_elem(e.type)))
             return self.literal(e)
         if isinstance(e, P.Bin):
             if path:
@@ -410,8 +439,8 @@ class Emitter:
             t = c.temp
             if t.space != "private":
                 self.sync[-1] = True
-            if isinstance(P.base_elem(t.type), P.VecT) and (dims(t.type) or t.space != "private"):
-                raise EmitError("vector temporaries are private scalars only")
+            if isinstance(P.base_elem(t.type), P.VecT) and t.space != "private":
+                raise EmitError("vector temporaries are private only")
             if isinstance(t.type, P.PairT):
                 if t.space != "private":
                     raise EmitError("pair temporaries are private scalars only")
@@ -428,8 +457,8 @@ class Emitter:
                 shape = dims(t.type)
                 par = sum(1 for l in ctx if l != "seq")
                 self.private_ctx[t.name] = (par, _per_thread(ctx))
-                if shape:
-                    self.lines.append(f"{pad}{ct} {t.name}[{P.scalar_count(t.type)}];")
+                if shape:  # one entry per element (a number or a vector)
+                    self.lines.append(f"{pad}{ct} {t.name}[{math.prod(shape)}];")
                 else:
                     self.lines.append(f"{pad}{ct} {t.name};")
             elif t.space == "local" and self.backend == "cuda":
@@ -462,7 +491,11 @@ class Emitter:
                     self.lines.append(f"{pad}  }}")
                     self.lines.append(f"{pad}}}")
                     return
-                if self.backend == "cuda" and self.unroll > 1 and c.level == "seq" and n > self.unroll:
+                if self.backend == "cuda" and c.level == "seq" and n <= 16 and _private_array_loop(c.body):
+                    # a short loop over a private array (e.g. a thread's tile of
+                    # accumulators): unrolled whole, so that the array lives in registers
+                    self.lines.append(f"{pad}#pragma unroll")
+                elif self.backend == "cuda" and self.unroll > 1 and c.level == "seq" and n > self.unroll:
                     # a sequential loop's iterations stay in order; unrolling only
                     # lets their loads be issued ahead of the dependent steps
                     self.lines.append(f"{pad}#pragma unroll {self.unroll}")

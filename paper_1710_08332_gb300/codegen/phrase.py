@@ -99,6 +99,11 @@ def is_value(t) -> bool:
     return is_scalar(t) or (isinstance(t, PairT) and is_scalar(t.a) and is_scalar(t.b))
 
 
+def is_num_array(t) -> bool:
+    """An array (of arrays ...) of numbers or of vectors of numbers."""
+    return isinstance(t, Arr) and isinstance(base_elem(t), (Num, VecT))
+
+
 def arr(*dims_and_elem):
     """arr(n, m, F32) is the type n.m.f32."""
     *dims, elem = dims_and_elem
@@ -264,7 +269,9 @@ class Map(Phrase):
 
 @dataclass(eq=False)
 class Reduce(Phrase):
-    """reduceSeq f init e: a left fold, f(element, accumulator) (Section 4.2's reduceI)."""
+    """reduceSeq f init e: a left fold, f(element, accumulator) (Section 4.2's reduceI).
+    The accumulator is a number, a vector, a pair of them, or an array of
+    numbers (a private array: e.g. a thread's tile of C in a GEMM)."""
     f: Lam
     init: Phrase
     e: Phrase
@@ -273,8 +280,8 @@ class Reduce(Phrase):
     def __post_init__(self):
         if not isinstance(self.e.type, Arr):
             raise TypeError(f"reduce over a non-array {self.e.type}")
-        if not is_value(self.init.type):
-            raise TypeError("reduce accumulates numbers, vectors or pairs of them")
+        if not (is_value(self.init.type) or is_num_array(self.init.type)):
+            raise TypeError("reduce accumulates numbers, vectors, pairs of them or arrays of numbers")
         ps = self.f.params
         if len(ps) != 2 or ps[0].type != self.e.type.elem or ps[1].type != self.init.type:
             raise TypeError("reduce function must take (element, accumulator)")
@@ -606,6 +613,13 @@ def asVector(n, e):
 
 def asScalar(e):
     return AsScalar(e)
+
+
+def alit(v, t):
+    """The array of type t (of numbers) with every element v."""
+    if not is_num_array(t):
+        raise TypeError(f"an array literal of {t}: arrays of numbers or vectors only")
+    return Lit(v, t)
 
 
 def vlit(v, n=4):

@@ -195,6 +195,69 @@ def gemm(M: int, N: int, K: int, V: int = 1, transA: bool = False, transB: bool 
     return e, [A, B]
 
 
+def gemm_tiled(M: int, N: int, K: int, R: int = 8, Cn: int = 8, V: int = 4, KV: int = 1, transA: bool = False,
+               transB: bool = False):
+    """The GEMM with a register tile per thread: a workgroup per block of R rows
+    of C, its threads over blocks of Cn columns, each thread's R x Cn block of C
+    one fold over k whose accumulator is a private array (Cn/V vectors per row):
+
+        join (mapWorkgroup (lambda rows. transpose (mapLocal (lambda cols.
+          reduceSeq (lambda (a, b) acc. mapSeq (lambda (a_r, acc_r). mapSeq
+            (lambda (b_q, c). c + splat a_r * b_q) (zip b acc_r)) (zip a acc))
+            0 (zip (transpose rows) cols)) colblocks)) (split R op(A)))
+
+    a is column k of the row block (R numbers), b row k of the column block
+    (Cn/V vectors of B, read with V-wide loads). With KV > 1 the fold runs over
+    groups of KV consecutive k: the row block's A is read as vectors along k
+    (asVector KV, one load per row for KV steps), their lanes staged in a
+    private array, and the group's KV steps folded in k order by an inner
+    reduceSeq whose initial value is the outer accumulator. Every element of C
+    is still one sequential fold over k from +0, product and sum rounded
+    separately, so the result equals the plain fold (and the untiled gemm) bit
+    for bit; the tile only keeps each loaded value in registers for several
+    products. The transposes are views; V > 1 needs B stored K x N and KV > 1
+    needs A stored M x K (the adjacent numbers a vector load reads)."""
+    if M % R or N % Cn or Cn % V or K % KV:
+        raise ValueError("R must divide M, Cn must divide N, V must divide Cn and KV must divide K")
+    if (V > 1 and transB) or (KV > 1 and transA):
+        raise ValueError("vector loads need B stored K x N (V > 1) and A stored M x K (KV > 1)")
+    A = P.inp("A", P.arr(K, M, P.F32) if transA else P.arr(M, K, P.F32))
+    B = P.inp("B", P.arr(N, K, P.F32) if transB else P.arr(K, N, P.F32))
+    if KV > 1:
+        rows = P.split(R, P.split(K // KV, P.asVector(KV, P.join(A))))  # (M/R) x R x (K/KV) vectors
+    else:
+        rows = P.split(R, P.transpose(A) if transA else A)  # (M/R) x R x K
+    if transB:
+        colblocks, col_view = P.split(Cn, B), P.transpose  # (N/Cn) x Cn x K, each viewed K x Cn
+    elif V == 1:
+        colblocks, col_view = P.transpose(P.split(N // Cn, P.split(Cn, P.join(B)))), (lambda c: c)
+    else:
+        colblocks = P.transpose(P.split(N // Cn, P.split(Cn // V, P.asVector(V, P.join(B)))))
+        col_view = lambda c: c  # noqa: E731  (N/Cn) x K x (Cn/V) vectors
+    elt = P.F32 if V == 1 else P.VecT(V, P.F32)
+    zero = P.alit(0.0, P.arr(R, Cn // V, elt))
+
+    def step(p, acc):  # one k: a (R numbers), b (Cn/V numbers or vectors)
+        a, b = P.fst(p), P.snd(p)
+        return P.mapSeq(lambda q: P.mapSeq(
+            lambda s: P.add(P.snd(s), P.mul(P.fst(q) if V == 1 else P.splat(V, P.fst(q)), P.fst(s))),
+            P.zip_(b, P.snd(q))), P.zip_(a, acc))
+
+    def group(p, acc):  # KV consecutive k: R vectors of A along k, KV rows of the column block
+        ak = P.transpose(P.to_private(P.mapSeq(lambda v: P.lanes(v), P.fst(p))))  # KV x R numbers
+        return P.reduceSeq(step, acc, P.zip_(ak, P.snd(p)))
+
+    def fold(rb, cb):
+        if KV == 1:
+            return P.reduceSeq(step, zero, P.zip_(P.transpose(rb), col_view(cb)))
+        return P.reduceSeq(group, zero, P.zip_(P.transpose(rb), P.split(KV, col_view(cb))))
+
+    e = P.join(P.mapWorkgroup(lambda rb: P.transpose(P.mapLocal(lambda cb: fold(rb, cb), colblocks)), rows))
+    if V > 1:
+        e = P.asScalar(P.join(P.join(e)))
+    return e, [A, B]
+
+
 # ---------------------------------------------------------------------------
 # compensated (Kahan) folds: the accumulator is a pair (s, c)
 # ---------------------------------------------------------------------------

@@ -371,12 +371,12 @@ class Translator:
                 acc = AOut(t.name, t.type, t)
                 i = self.ivar("r")
                 init = self.A(e.init, acc, levels)
-                if not isinstance(e.type, P.PairT):
+                if not isinstance(e.type, (P.PairT, P.Arr)):
                     step = self.A(P.apply(e.f, P.Idx(x, i), tv), acc, levels + ["seq"])
                 else:
-                    # a pair is written component by component: the step goes to a
-                    # fresh pair first, so that its second component still reads
-                    # the old accumulator, then replaces the accumulator
+                    # a pair (or an array) is written component by component: the
+                    # step goes to a fresh one first, so that every component still
+                    # reads the old accumulator, then replaces the accumulator
                     nt = self.temp(e.type, "private")
                     nv = P.Ident(nt.name, nt.type, temp="private")
                     step = New(nt, Seq([self.A(P.apply(e.f, P.Idx(x, i), tv), AOut(nt.name, nt.type, nt),

@@ -435,6 +435,44 @@ def test_gemm_matches_oracle(c_build, M, N, K, transA, transB, V):
     assert np.array_equal(bits(C), bits(want))
 
 
+@pytest.mark.parametrize("R,Cn,V,KV,transA,transB", [
+    (4, 8, 4, 1, False, False), (8, 8, 4, 4, False, False), (2, 8, 2, 2, False, False),
+    (4, 4, 1, 4, False, True), (8, 4, 4, 1, True, False), (4, 4, 1, 1, True, True), (1, 4, 4, 4, False, False)])
+def test_gemm_tiled_matches_oracle(c_build, R, Cn, V, KV, transA, transB):
+    """The register-tiled GEMM (a private R x Cn accumulator array per thread,
+    A read as vectors along k when KV > 1, the group's KV steps an inner fold)
+    still folds every C_ij over k in order from +0: equal to the loop-nest
+    oracle with contraction off."""
+    from oracle import loopnest
+
+    M, N, K = 24, 40, 36
+    rng = np.random.default_rng(100 + R + Cn + KV)
+    A = rng.uniform(-1, 1, (K, M) if transA else (M, K)).astype(np.float32)
+    B = rng.uniform(-1, 1, (N, K) if transB else (K, N)).astype(np.float32)
+    e, ins = PR.gemm_tiled(M, N, K, R, Cn, V, KV, transA, transB)
+    C = np.zeros(M * N, np.float32)
+    G.compile_c(f"gemm_tiled_{R}{Cn}{V}{KV}{int(transA)}{int(transB)}", e, ins).run(A, B, C)
+    want = loopnest.gemm_f32(A, B, transA, transB, contract_fma=False)
+    assert np.array_equal(bits(C.reshape(M, N)), bits(want))
+
+
+def test_array_accumulators_are_checked():
+    """A reduce may accumulate an array of numbers (or vectors) only; the tiled
+    GEMM rejects shapes that do not divide and vector loads across a transpose."""
+    x = G.inp("x", G.arr(16, G.F32))
+    with pytest.raises(TypeError):
+        G.alit(0.0, G.F32)
+    with pytest.raises(TypeError):  # the step must return the accumulator's type
+        G.reduceSeq(lambda v, acc: v, G.alit(0.0, G.arr(4, G.F32)), x)
+    for bad in ((24, 40, 36, 5, 8, 4, 1), (24, 40, 36, 4, 8, 3, 1), (24, 40, 36, 4, 8, 4, 5)):
+        with pytest.raises(ValueError):
+            PR.gemm_tiled(*bad)
+    with pytest.raises(ValueError):
+        PR.gemm_tiled(24, 40, 36, 4, 8, 4, 4, True, False)
+    with pytest.raises(ValueError):
+        PR.gemm_tiled(24, 40, 36, 4, 8, 4, 1, False, True)
+
+
 def test_gemm_vector_columns_need_a_row_major_B():
     with pytest.raises(ValueError):
         PR.gemm(8, 16, 8, 4, False, True)

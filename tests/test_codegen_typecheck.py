@@ -42,6 +42,9 @@ PROGRAMS = {
     "gemm_V4": lambda: PR.gemm(24, 40, 12, 4),
     "gemm_tA_tB": lambda: PR.gemm(24, 40, 12, 1, True, True),
     "gemm_tA_V4": lambda: PR.gemm(24, 40, 12, 4, True, False),
+    "gemm_tiled": lambda: PR.gemm_tiled(16, 32, 12, 4, 8, 4),
+    "gemm_tiled_KV4": lambda: PR.gemm_tiled(16, 32, 12, 4, 8, 4, 4),
+    "gemm_tiled_tA_tB": lambda: PR.gemm_tiled(16, 32, 12, 4, 4, 1, 1, True, True),
 }
 
 

@@ -344,10 +344,33 @@ def test_generated_gemm_matches_oracle(cuda_device, transA, transB, V):
         assert np.array_equal(bits(got), bits(want)), (grid, block)
 
 
-def test_generated_gemm_4096(cuda_device):
-    """At 4096^3 (float4 columns): every element equal to the library's FP32
-    fold with contraction off (the same fold per element), and 96 full rows
-    equal to the oracle's fold."""
+@pytest.mark.parametrize("R,Cn,V,KV,transA,transB", [(4, 8, 4, 1, False, False), (8, 8, 4, 4, False, False),
+                                                   (4, 4, 1, 4, False, True), (8, 4, 4, 1, True, False),
+                                                   (4, 4, 1, 1, True, True)])
+def test_generated_tiled_gemm_matches_oracle(cuda_device, R, Cn, V, KV, transA, transB):
+    """The register-tiled GEMM (private accumulator arrays, A read along k as
+    vectors when KV > 1) in every operand layout, under the default launch and
+    smaller ones: equal to the loop-nest oracle with contraction off."""
+    from oracle import loopnest
+
+    M, N, K = 136, 264, 76
+    rng = np.random.default_rng(120 + R + KV)
+    A = rng.standard_normal((K, M) if transA else (M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K) if transB else (K, N)).astype(np.float32)
+    k = G.compile_cuda(f"gemm_tiled_{R}{Cn}{V}{KV}{int(transA)}{int(transB)}",
+                       *PR.gemm_tiled(M, N, K, R, Cn, V, KV, transA, transB))
+    want = loopnest.gemm_f32(A, B, transA, transB, contract_fma=False)
+    for grid, block in ((None, None), (5, 32), (40, 128)):
+        got = run(k, dev(A), dev(B), out_count=M * N, grid=grid, block=block).reshape(M, N)
+        assert np.array_equal(bits(got), bits(want)), (grid, block)
+
+
+@pytest.mark.parametrize("form", ["columns", "tiled"])
+def test_generated_gemm_4096(cuda_device, form):
+    """At 4096^3 (the float4-column form, and the register-tiled form with 8 x 8
+    tiles and A read along k): every element equal to the library's FP32 fold
+    with contraction off (the same fold per element), and 96 full rows equal to
+    the oracle's fold."""
     from oracle import loopnest
     from synth import workloads as W
     from tests.test_gpu_gemm import _f32_rows_4096
@@ -356,9 +379,12 @@ def test_generated_gemm_4096(cuda_device):
 
     n = W.GEMM_MNK
     A, B, _ = W.gemm("cuda")
-    k = G.compile_cuda("gemm_4096_v4", *PR.gemm(n, n, n, 4), unroll=4)
+    if form == "columns":
+        k, block = G.compile_cuda("gemm_4096_v4", *PR.gemm(n, n, n, 4), unroll=4), None
+    else:
+        k, block = G.compile_cuda("gemm_4096_tiled", *PR.gemm_tiled(n, n, n, 8, 8, 4, 4)), 128
     C = torch.empty(n * n, device="cuda")
-    k.run(A, B, C)
+    k.run(A, B, C, block=block)
     lib = torch.empty(n, n, device="cuda")
     dpia.dpia_gemm_f32(A, B, lib, n, n, n, n, n, n, 0, 0, "off")
     torch.cuda.synchronize()
