@@ -9,7 +9,7 @@ results are bit-identical to any other evaluation of the same phrase.
 """
 from .build import CFunction, CudaKernel, compile_c, compile_cuda
 from .emit import EmitError, generate
-from .phrase import (F32, I32, I64, Arr, Num, PairT, VecT, abs_, add, alit, arr, asScalar, asVector, fst, inp, join,
+from .phrase import (F32, I32, I64, Arr, Num, PairT, VecT, abs_, add, alit, arr, fma, asScalar, asVector, fst, inp, join,
                      lanes, lit, mapGlobal, mapLane, mapLocal, mapSeq, mapWarp, mapWorkgroup, mul, reduceSeq,
                      reduceTree, secondLevel, snd, splat, split, sub, to_global, to_local, to_private, transpose, vlit, zip_)
 from .translate import TranslationError

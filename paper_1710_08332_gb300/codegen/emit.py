@@ -72,6 +72,11 @@ __device__ __forceinline__ float4 dpia_vabs4(float4 a) { return make_float4(fabs
 __device__ __forceinline__ float2 dpia_vabs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 __device__ __forceinline__ float4 dpia_splat4(float v) { return make_float4(v, v, v, v); }
 __device__ __forceinline__ float2 dpia_splat2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float4 dpia_vfma4(float4 a, float4 b, float4 c) {
+  return make_float4(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y), __fmaf_rn(a.z, b.z, c.z),
+                     __fmaf_rn(a.w, b.w, c.w)); }
+__device__ __forceinline__ float2 dpia_vfma2(float2 a, float2 b, float2 c) {
+  return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y)); }
 """
 
 THREADED = ("local", "warp", "lane")  # levels whose loops spread over the threads of a block
@@ -97,6 +102,10 @@ static inline float4 dpia_vabs4(float4 a) { return make_float4(fabsf(a.x), fabsf
 static inline float2 dpia_vabs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 static inline float4 dpia_splat4(float v) { return make_float4(v, v, v, v); }
 static inline float2 dpia_splat2(float v) { return make_float2(v, v); }
+static inline float4 dpia_vfma4(float4 a, float4 b, float4 c) {
+  return make_float4(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y), fmaf(a.z, b.z, c.z), fmaf(a.w, b.w, c.w)); }
+static inline float2 dpia_vfma2(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)); }
 """
 
 
@@ -254,6 +263,13 @@ class Emitter:
                 raise EmitError("index into a number")
             a, b = self.access(e.a, []), self.access(e.b, [])
             return self.binop(e.op, a, b, e.type)
+        if isinstance(e, P.Fma):
+            if path:
+                raise EmitError("index into a number")
+            a, b, c = self.access(e.a, []), self.access(e.b, []), self.access(e.c, [])
+            if isinstance(e.type, P.VecT):
+                return f"dpia_vfma{e.type.n}({a}, {b}, {c})"
+            return f"__fmaf_rn({a}, {b}, {c})" if self.backend == "cuda" else f"fmaf({a}, {b}, {c})"
         if isinstance(e, P.Splat):
             if path:  # a lane of the vector: the number itself
                 return self.access(e.a, [])

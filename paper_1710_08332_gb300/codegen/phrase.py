@@ -201,6 +201,26 @@ class Bin(Phrase):
 
 
 @dataclass(eq=False)
+class Fma(Phrase):
+    """fma a b c: a * b + c rounded once (the contraction a strategy may
+    declare), on numbers or lane by lane on vectors."""
+    a: Phrase
+    b: Phrase
+    c: Phrase
+    type: object = field(init=False)
+
+    def __post_init__(self):
+        t = self.a.type
+        if not (t == F32 or (isinstance(t, VecT) and t.num == F32)) or self.b.type != t or self.c.type != t:
+            raise TypeError(f"fma needs three f32 numbers (or vectors) of one type, not "
+                            f"{self.a.type}, {self.b.type}, {self.c.type}")
+        self.type = t
+
+    def children(self):
+        return (self.a, self.b, self.c)
+
+
+@dataclass(eq=False)
 class Abs(Phrase):
     a: Phrase
     type: object = field(init=False)
@@ -660,6 +680,11 @@ def sub(a, b):
     return Bin("-", a, b)
 
 
+def fma(a, b, c):
+    """a * b + c with one rounding."""
+    return Fma(a, b, c)
+
+
 def abs_(a):
     return Abs(a)
 
@@ -686,6 +711,8 @@ def subst(p: Phrase, env: dict) -> Phrase:
         return Abs(subst(p.a, env))
     if isinstance(p, Splat):
         return Splat(p.n, subst(p.a, env))
+    if isinstance(p, Fma):
+        return Fma(subst(p.a, env), subst(p.b, env), subst(p.c, env))
     if isinstance(p, Map):
         return Map(p.level, Lam(p.f.params, subst(p.f.body, env)), subst(p.e, env))
     if isinstance(p, Reduce):

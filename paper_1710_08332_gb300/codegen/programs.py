@@ -196,7 +196,7 @@ def gemm(M: int, N: int, K: int, V: int = 1, transA: bool = False, transB: bool 
 
 
 def gemm_tiled(M: int, N: int, K: int, R: int = 8, Cn: int = 8, V: int = 4, KV: int = 1, transA: bool = False,
-               transB: bool = False):
+               transB: bool = False, contract: str = "off"):
     """The GEMM with a register tile per thread: a workgroup per block of R rows
     of C, its threads over blocks of Cn columns, each thread's R x Cn block of C
     one fold over k whose accumulator is a private array (Cn/V vectors per row):
@@ -216,7 +216,11 @@ def gemm_tiled(M: int, N: int, K: int, R: int = 8, Cn: int = 8, V: int = 4, KV: 
     separately, so the result equals the plain fold (and the untiled gemm) bit
     for bit; the tile only keeps each loaded value in registers for several
     products. The transposes are views; V > 1 needs B stored K x N and KV > 1
-    needs A stored M x K (the adjacent numbers a vector load reads)."""
+    needs A stored M x K (the adjacent numbers a vector load reads). With
+    contract = "fma" each step is fma(a_r, b_q, c), one rounding (the
+    contraction the library's FP32 fold declares by default)."""
+    if contract not in ("off", "fma"):
+        raise ValueError(f"contract {contract!r}: off or fma")
     if M % R or N % Cn or Cn % V or K % KV:
         raise ValueError("R must divide M, Cn must divide N, V must divide Cn and KV must divide K")
     if (V > 1 and transB) or (KV > 1 and transA):
@@ -237,11 +241,14 @@ def gemm_tiled(M: int, N: int, K: int, R: int = 8, Cn: int = 8, V: int = 4, KV: 
     elt = P.F32 if V == 1 else P.VecT(V, P.F32)
     zero = P.alit(0.0, P.arr(R, Cn // V, elt))
 
+    def madd(a_r, b_q, c):
+        a_r = a_r if V == 1 else P.splat(V, a_r)
+        return P.fma(a_r, b_q, c) if contract == "fma" else P.add(c, P.mul(a_r, b_q))
+
     def step(p, acc):  # one k: a (R numbers), b (Cn/V numbers or vectors)
         a, b = P.fst(p), P.snd(p)
-        return P.mapSeq(lambda q: P.mapSeq(
-            lambda s: P.add(P.snd(s), P.mul(P.fst(q) if V == 1 else P.splat(V, P.fst(q)), P.fst(s))),
-            P.zip_(b, P.snd(q))), P.zip_(a, acc))
+        return P.mapSeq(lambda q: P.mapSeq(lambda s: madd(P.fst(q), P.fst(s), P.snd(s)),
+                                           P.zip_(b, P.snd(q))), P.zip_(a, acc))
 
     def group(p, acc):  # KV consecutive k: R vectors of A along k, KV rows of the column block
         ak = P.transpose(P.to_private(P.mapSeq(lambda v: P.lanes(v), P.fst(p))))  # KV x R numbers

@@ -401,6 +401,9 @@ class Translator:
             return self.C(e.a, lambda a: k(P.Abs(a)), levels)
         if isinstance(e, P.Splat):
             return self.C(e.a, lambda a: k(P.Splat(e.n, a)), levels)
+        if isinstance(e, P.Fma):
+            return self.C(e.a, lambda a: self.C(e.b, lambda b: self.C(e.c, lambda c: k(P.Fma(a, b, c)), levels),
+                                                levels), levels)
         if isinstance(e, P.Zip):
             return self.C(e.a, lambda a: self.C(e.b, lambda b: k(P.Zip(a, b)), levels), levels)
         if isinstance(e, P.Proj):

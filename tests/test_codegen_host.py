@@ -456,6 +456,40 @@ def test_gemm_tiled_matches_oracle(c_build, R, Cn, V, KV, transA, transB):
     assert np.array_equal(bits(C.reshape(M, N)), bits(want))
 
 
+@pytest.mark.parametrize("R,Cn,V,KV,transA,transB", [(8, 8, 4, 4, False, False), (4, 4, 1, 1, True, True),
+                                                   (4, 8, 4, 1, True, False), (2, 4, 1, 2, False, True)])
+def test_gemm_tiled_fma_matches_oracle(c_build, R, Cn, V, KV, transA, transB):
+    """With the contraction declared, every step is fma(a_ik, b_kj, c_ij) (one
+    rounding, fmaf on the host): equal to the oracle's fold with fmaf, and not
+    to the fold that rounds the product and the sum separately."""
+    from oracle import loopnest
+
+    M, N, K = 24, 40, 36
+    rng = np.random.default_rng(140 + R + KV)
+    A = rng.uniform(-1, 1, (K, M) if transA else (M, K)).astype(np.float32)
+    B = rng.uniform(-1, 1, (N, K) if transB else (K, N)).astype(np.float32)
+    e, ins = PR.gemm_tiled(M, N, K, R, Cn, V, KV, transA, transB, "fma")
+    C = np.zeros(M * N, np.float32)
+    G.compile_c(f"gemm_tiled_fma_{R}{Cn}{V}{KV}{int(transA)}{int(transB)}", e, ins).run(A, B, C)
+    want = loopnest.gemm_f32(A, B, transA, transB, contract_fma=True)
+    assert np.array_equal(bits(C.reshape(M, N)), bits(want))
+    assert not np.array_equal(bits(C.reshape(M, N)), bits(loopnest.gemm_f32(A, B, transA, transB, contract_fma=False)))
+
+
+def test_fma_phrase_types():
+    x = G.inp("x", G.arr(8, G.F32))
+    with pytest.raises(TypeError):
+        G.fma(G.lit(1.0), G.vlit(1.0, 4), G.lit(0.0))
+    with pytest.raises(ValueError):
+        PR.gemm_tiled(8, 8, 8, 4, 4, 1, 1, False, False, "fast")
+    e = G.mapGlobal(lambda v: G.fma(v, v, G.lit(1.0)), x)
+    out = np.zeros(8, np.float32)
+    xs = (np.arange(-4, 4) * 0.75).astype(np.float32)  # v * v + 1 exact: one rounding or two agree
+    G.compile_c("fma_map", e, [x]).run(xs, out)
+    want = (xs.astype(np.float64) ** 2 + 1.0).astype(np.float32)
+    assert np.array_equal(bits(out), bits(want))
+
+
 def test_array_accumulators_are_checked():
     """A reduce may accumulate an array of numbers (or vectors) only; the tiled
     GEMM rejects shapes that do not divide and vector loads across a transpose."""

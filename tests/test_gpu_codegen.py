@@ -344,10 +344,11 @@ def test_generated_gemm_matches_oracle(cuda_device, transA, transB, V):
         assert np.array_equal(bits(got), bits(want)), (grid, block)
 
 
-@pytest.mark.parametrize("R,Cn,V,KV,transA,transB", [(4, 8, 4, 1, False, False), (8, 8, 4, 4, False, False),
-                                                   (4, 4, 1, 4, False, True), (8, 4, 4, 1, True, False),
-                                                   (4, 4, 1, 1, True, True)])
-def test_generated_tiled_gemm_matches_oracle(cuda_device, R, Cn, V, KV, transA, transB):
+@pytest.mark.parametrize("R,Cn,V,KV,transA,transB,contract", [
+    (4, 8, 4, 1, False, False, "off"), (8, 8, 4, 4, False, False, "off"), (4, 4, 1, 4, False, True, "off"),
+    (8, 4, 4, 1, True, False, "off"), (4, 4, 1, 1, True, True, "off"), (8, 8, 4, 4, False, False, "fma"),
+    (4, 4, 1, 1, True, True, "fma")])
+def test_generated_tiled_gemm_matches_oracle(cuda_device, R, Cn, V, KV, transA, transB, contract):
     """The register-tiled GEMM (private accumulator arrays, A read along k as
     vectors when KV > 1) in every operand layout, under the default launch and
     smaller ones: equal to the loop-nest oracle with contraction off."""
@@ -357,20 +358,21 @@ def test_generated_tiled_gemm_matches_oracle(cuda_device, R, Cn, V, KV, transA, 
     rng = np.random.default_rng(120 + R + KV)
     A = rng.standard_normal((K, M) if transA else (M, K)).astype(np.float32)
     B = rng.standard_normal((N, K) if transB else (K, N)).astype(np.float32)
-    k = G.compile_cuda(f"gemm_tiled_{R}{Cn}{V}{KV}{int(transA)}{int(transB)}",
-                       *PR.gemm_tiled(M, N, K, R, Cn, V, KV, transA, transB))
-    want = loopnest.gemm_f32(A, B, transA, transB, contract_fma=False)
+    k = G.compile_cuda(f"gemm_tiled_{R}{Cn}{V}{KV}{int(transA)}{int(transB)}_{contract}",
+                       *PR.gemm_tiled(M, N, K, R, Cn, V, KV, transA, transB, contract))
+    want = loopnest.gemm_f32(A, B, transA, transB, contract_fma=contract == "fma")
     for grid, block in ((None, None), (5, 32), (40, 128)):
         got = run(k, dev(A), dev(B), out_count=M * N, grid=grid, block=block).reshape(M, N)
         assert np.array_equal(bits(got), bits(want)), (grid, block)
 
 
-@pytest.mark.parametrize("form", ["columns", "tiled"])
+@pytest.mark.parametrize("form", ["columns", "tiled", "tiled_fma"])
 def test_generated_gemm_4096(cuda_device, form):
-    """At 4096^3 (the float4-column form, and the register-tiled form with 8 x 8
-    tiles and A read along k): every element equal to the library's FP32 fold
-    with contraction off (the same fold per element), and 96 full rows equal to
-    the oracle's fold."""
+    """At 4096^3 (the float4-column form, the register-tiled form with 8 x 8
+    tiles and A read along k, and a 16 x 8 tiled form with the contraction
+    declared): every element equal to the library's FP32 fold with the same
+    contraction (the same fold per element), and 96 full rows equal to the
+    oracle's fold."""
     from oracle import loopnest
     from synth import workloads as W
     from tests.test_gpu_gemm import _f32_rows_4096
@@ -379,19 +381,23 @@ def test_generated_gemm_4096(cuda_device, form):
 
     n = W.GEMM_MNK
     A, B, _ = W.gemm("cuda")
+    contract = "fma" if form == "tiled_fma" else "off"
     if form == "columns":
         k, block = G.compile_cuda("gemm_4096_v4", *PR.gemm(n, n, n, 4), unroll=4), None
-    else:
+    elif form == "tiled":
         k, block = G.compile_cuda("gemm_4096_tiled", *PR.gemm_tiled(n, n, n, 8, 8, 4, 4)), 128
+    else:
+        k, block = G.compile_cuda("gemm_4096_tiled_fma", *PR.gemm_tiled(n, n, n, 16, 8, 4, 4, contract="fma")), 128
     C = torch.empty(n * n, device="cuda")
     k.run(A, B, C, block=block)
     lib = torch.empty(n, n, device="cuda")
-    dpia.dpia_gemm_f32(A, B, lib, n, n, n, n, n, n, 0, 0, "off")
+    dpia.dpia_gemm_f32(A, B, lib, n, n, n, n, n, n, 0, 0, contract)
     torch.cuda.synchronize()
     got = C.view(n, n)
     assert torch.equal(got.view(torch.int32), lib.view(torch.int32))
     rows = _f32_rows_4096(n)
-    want = loopnest.gemm_f32_sample(A.cpu().numpy(), B.cpu().numpy(), False, False, False, rows, np.arange(n))
+    want = loopnest.gemm_f32_sample(A.cpu().numpy(), B.cpu().numpy(), False, False, contract == "fma", rows,
+                                    np.arange(n))
     assert np.array_equal(bits(got.cpu().numpy()[rows]), bits(want))
 
 
