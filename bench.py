@@ -1179,6 +1179,18 @@ def codegen_workload(args, device, dist):
         kind="asum_scal"), reps=5))
     explored["gemv"] = summary(RW.explore("gemv", [A, xv], N_, RW.gemv_derivations(M, N_, threads=(128, 256),
                                                                                   widths=(4,)), reps=5, M=M))
+    # GEMM 4096^3: the plain map of maps and the register tiles (every derivation the same bits)
+    gA, gB, _ = W.gemm(device)
+    gk = W.GEMM_MNK
+    ranked_g = RW.explore_gemm(gA, gB, gk, gk, gk, reps=3)
+    explored["gemm"] = {"candidates": len(ranked_g),
+                        "best": {"derivation": str(ranked_g[0][1]) or "plain", "block": ranked_g[0][2],
+                                 "ms": round(ranked_g[0][0], 3),
+                                 "TFLOP_s": round(2 * gk ** 3 / ranked_g[0][0] / 1e9, 2)},
+                        "worst": {"derivation": str(ranked_g[-1][1]) or "plain", "block": ranked_g[-1][2],
+                                  "ms": round(ranked_g[-1][0], 3)},
+                        "all_ms": {f"{str(d) or 'plain'} @ {blk}": round(ms, 3) for ms, d, blk in ranked_g}}
+    del gA, gB
     # the same phrases on the host (the paper's multicore target): C with the
     # outermost parallel loop (the work-group map) on OpenMP threads, the whole
     # dot (first level, trees, second level) on the full n = 2^26 inputs

@@ -34,6 +34,19 @@ the associative + with identity 0:
                  kernels (it reads what other blocks wrote: a kernel boundary), a Last becomes
                  the second level in the last work-group of the same kernel
 
+GEMM, the map of maps of a fold over k (``Map (Map (Reduce (Map (*) (zip a b))))``), has
+rules of its own; each keeps every C_ij the same fold over k in order, so all GEMM
+derivations give the same bits:
+
+  vectorize(V)   the column map over groups of V adjacent columns, each group one num<V> fold
+                 (the map of a fold over vectors = the vector of the folds)
+  tile(R, Cn)    the row map split by R and the column map by Cn, the R x Cn maps moved
+                 inside the fold (map-reduce interchange): one fold over k whose accumulator
+                 is the R x Cn array
+  vectorize_k(KV) the fold over k split into groups of KV (a left fold over k is the fold
+                 over groups, each group folded in order from the running value), A read as
+                 num<KV> along k
+
 ``derivations`` enumerates rule sequences over parameter grids, ``rewrite``
 applies one to the start expression (each rule checks the shape it rewrites),
 and ``lower`` turns the resulting tree into kernel phrases. Each derivation's
@@ -411,6 +424,72 @@ def gemv_derivations(M: int, N: int, threads=(64, 128, 256), widths=(1, 4)):
                                   + ([Rule("vectorize", (V,))] if V > 1 else []) + [Rule("tree"), Rule("fuse"),
                                                                                      Rule("lower")]))
     return out
+
+
+def gemm_derivations(M: int, N: int, K: int, tiles=((1, 1), (4, 8), (8, 4), (8, 8), (16, 8)), widths=(1, 4),
+                     kwidths=(1, 4)):
+    """GEMM derivations: the plain map of maps (vector columns or not) and the
+    register tiles, with and without A read along k; only those whose rules'
+    shapes divide (M, N, K)."""
+    out = []
+    for (R, Cn), V, KV in itertools.product(tiles, widths, kwidths):
+        if (R, Cn) == (1, 1):
+            if KV == 1 and N % V == 0:
+                out.append(Derivation([Rule("vectorize", (V,))] if V > 1 else []))
+            continue
+        if M % R or N % Cn or Cn % V or K % KV:
+            continue
+        out.append(Derivation([Rule("tile", (R, Cn))] + ([Rule("vectorize", (V,))] if V > 1 else [])
+                              + ([Rule("vectorize_k", (KV,))] if KV > 1 else [])))
+    return out
+
+
+def lower_gemm(d: Derivation, M: int, N: int, K: int, contract: str = "off"):
+    """The GEMM phrase of a derivation (programs.gemm or programs.gemm_tiled)."""
+    args = {r.name: r.args for r in d.rules}
+    unknown = set(args) - {"tile", "vectorize", "vectorize_k"}
+    if unknown:
+        raise RuleError(f"no GEMM rule {sorted(unknown)}")
+    R, Cn = args.get("tile", (1, 1))
+    V = args.get("vectorize", (1,))[0]
+    KV = args.get("vectorize_k", (1,))[0]
+    if (R, Cn) == (1, 1):
+        if KV > 1 or contract != "off":
+            raise RuleError("vectorize_k and fma apply to tiled GEMMs")
+        return PR.gemm(M, N, K, V)
+    return PR.gemm_tiled(M, N, K, R, Cn, V, KV, contract=contract)
+
+
+def explore_gemm(A, B, M: int, N: int, K: int, derivs=None, blocks=(128, 256), reps: int = 3):
+    """Time every GEMM derivation (at each block size; the plain maps at their
+    default launch) on A (M x K) and B (K x N); return [(ms, derivation, block)]
+    fastest first."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+
+    from ..tune import time_call
+    from .build import compile_cuda
+
+    derivs = derivs or gemm_derivations(M, N, K)
+
+    def build(d):
+        tag = "_".join(str(a) for r in d.rules for a in r.args) or "plain"
+        return compile_cuda(f"xgemm_{M}_{N}_{K}_{tag}", *lower_gemm(d, M, N, K), unroll=1 if any(
+            r.name == "tile" for r in d.rules) else 4)
+
+    workers = max(1, min(16, len(os.sched_getaffinity(0))))
+    with ThreadPoolExecutor(workers) as pool:
+        kernels = list(pool.map(build, derivs))
+    C = torch.empty(M * N, device=A.device)
+    results = []
+    for d, k in zip(derivs, kernels):
+        tiled = any(r.name == "tile" for r in d.rules)
+        for blk in (blocks if tiled else (None,)):
+            results.append((time_call(lambda: k.run(A, B, C, block=blk), reps=reps, warmup=1), d, blk))
+    results.sort(key=lambda t: t[0])
+    return results
 
 
 # ---------------------------------------------------------------------------

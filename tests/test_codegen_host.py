@@ -490,6 +490,30 @@ def test_fma_phrase_types():
     assert np.array_equal(bits(out), bits(want))
 
 
+def test_gemm_derivations_match_oracle(c_build):
+    """Every GEMM derivation (vector columns, register tiles, A along k) keeps
+    each C_ij the same fold over k: all of them equal the oracle's fold."""
+    from oracle import loopnest
+    from paper_1710_08332_gb300.codegen import rewrite as RW
+
+    M, N, K = 32, 32, 16
+    rng = np.random.default_rng(160)
+    A = rng.uniform(-1, 1, (M, K)).astype(np.float32)
+    B = rng.uniform(-1, 1, (K, N)).astype(np.float32)
+    want = bits(loopnest.gemm_f32(A, B, False, False, contract_fma=False))
+    ds = RW.gemm_derivations(M, N, K)
+    assert len(ds) >= 12 and any("tile" in str(d) and "vectorize_k" in str(d) for d in ds)
+    for d in ds:
+        C = np.zeros(M * N, np.float32)
+        tag = "_".join(str(a) for r in d.rules for a in r.args) or "plain"
+        G.compile_c(f"gemm_deriv_{tag}", *RW.lower_gemm(d, M, N, K)).run(A, B, C)
+        assert np.array_equal(bits(C.reshape(M, N)), want), str(d)
+    with pytest.raises(RW.RuleError):
+        RW.lower_gemm(RW.Derivation([RW.Rule("vectorize_k", (4,))]), M, N, K)
+    with pytest.raises(RW.RuleError):
+        RW.lower_gemm(RW.Derivation([RW.Rule("split", (4,))]), M, N, K)
+
+
 def test_array_accumulators_are_checked():
     """A reduce may accumulate an array of numbers (or vectors) only; the tiled
     GEMM rejects shapes that do not divide and vector loads across a transpose."""

@@ -419,3 +419,27 @@ def test_generated_dot_backward(cuda_device, V):
     assert np.array_equal(bits(dx), bits(wx)) and np.array_equal(bits(dy), bits(wy))
     lx, ly = dpia.dot_bwd(dev(x), dev(y), dev(g))
     assert np.array_equal(bits(lx.cpu().numpy()), bits(dx)) and np.array_equal(bits(ly.cpu().numpy()), bits(dy))
+
+
+def test_gemm_exploration_ranks_derivations_that_match_oracle(cuda_device):
+    """The GEMM derivations on the GPU at 512^3: each one's output equals the
+    oracle's fold, and the exploration ranks every (derivation, block) pair."""
+    from oracle import loopnest
+    from paper_1710_08332_gb300.codegen import rewrite as RW
+
+    n = 512
+    rng = np.random.default_rng(170)
+    hA = rng.standard_normal((n, n)).astype(np.float32)
+    hB = rng.standard_normal((n, n)).astype(np.float32)
+    want = bits(loopnest.gemm_f32(hA, hB, False, False, contract_fma=False))
+    A, B = dev(hA), dev(hB)
+    ds = RW.gemm_derivations(n, n, n)
+    for d in ds:
+        tag = "_".join(str(a) for r in d.rules for a in r.args) or "plain"
+        k = G.compile_cuda(f"xgemm_{n}_{n}_{n}_{tag}", *RW.lower_gemm(d, n, n, n),
+                           unroll=1 if "tile" in str(d) else 4)
+        got = run(k, A, B, out_count=n * n, block=128 if "tile" in str(d) else None)
+        assert np.array_equal(bits(got.reshape(n, n)), want), str(d)
+    ranked = RW.explore_gemm(A, B, n, n, n, ds, reps=2)
+    assert len(ranked) == sum(2 if "tile" in str(d) else 1 for d in ds)
+    assert [t[0] for t in ranked] == sorted(t[0] for t in ranked)
