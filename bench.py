@@ -212,7 +212,8 @@ REDUCE_SOURCES = ["paper_1710_08332_gb300/csrc/k_reduce.cu", "paper_1710_08332_g
 GEMV_SOURCES = ["paper_1710_08332_gb300/csrc/k_gemv.cu", "paper_1710_08332_gb300/csrc/device_common.cuh",
                 "paper_1710_08332_gb300/csrc/k_maps.cu"]
 GEMM_SOURCES = ["paper_1710_08332_gb300/csrc/k_gemm_bf16.cu"]
-BATCH_SOURCES = ["paper_1710_08332_gb300/csrc/k_batched.cu", "paper_1710_08332_gb300/csrc/device_common.cuh"]
+BATCH_SOURCES = ["paper_1710_08332_gb300/csrc/k_batched.cu", "paper_1710_08332_gb300/csrc/device_common.cuh",
+                 "paper_1710_08332_gb300/batch.py"]  # the kernels and the packer's layout
 
 
 def generated_dot_R_digest() -> str:
@@ -945,7 +946,7 @@ def batched_workload(args, device, dist):
             "peak_source": "measured hbm_gbs (copy, burst)", "algorithmic_bytes_per_launch": fwd_bytes,
             "bwd_frac": round(bwd_bytes / per["batched_bwd"] / 1e6 / hbm, 4)}
     cfg = {"workload": "batched uneven instances: 4096 f32 dots (lengths log-uniform [256, 65536]) + 512 GEMVs "
-                       "(rows log-uniform [256, 65536], cols [256, 4096]), seed 3, packed with offsets, forward + "
+                       "(rows log-uniform [256, 65536], cols [256, 4096]), seed 3, packed with offsets (matrix rows padded to 128-byte lines), forward + "
                        "backward; one persistent launch per direction vs one launch per instance",
            "dots": len(dots), "gemvs": len(gemvs), "dot_elements": n_dot, "gemv_elements": mn,
            "policy": b.policy.__dict__, "tuned_ms": tune_ms,

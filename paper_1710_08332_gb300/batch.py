@@ -48,7 +48,14 @@ class BatchPolicy:
 
 
 class Batch:
-    def __init__(self, dot_lengths, gemv_shapes, device="cuda", policy: BatchPolicy | None = None):
+    def __init__(self, dot_lengths, gemv_shapes, device="cuda", policy: BatchPolicy | None = None,
+                 row_align: int = 32):
+        """row_align: each GEMV matrix's rows start every round_up(N, row_align) floats
+        (32, the default: rows on 128-byte lines, so that no two pieces of a row that
+        different items read share a line; 4: 16-byte rows, the least the vector loads
+        need)."""
+        if row_align < 4 or row_align % 4:
+            raise ValueError("row_align must be a positive multiple of 4 floats")
         self.device = torch.device(device)
         self.policy = policy or BatchPolicy()
         P = self.policy
@@ -63,7 +70,7 @@ class Batch:
         self.a_offs, self.gx_offs, self.gy_offs, self.ldas = [], [], [], []
         aoff = xoff = yoff = 0
         for M, N_ in self.gemv_shapes:
-            lda = _round(N_, 4)
+            lda = _round(N_, row_align)
             self.a_offs.append(aoff)
             self.gx_offs.append(xoff)
             self.gy_offs.append(yoff)
