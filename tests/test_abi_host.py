@@ -186,3 +186,13 @@ def test_gemm_strategy_validation():
     assert call(tile_m=512) == N.ERR_UNSUPPORTED
     assert L.dpia_gemm_bf16(p(0x10000), p(0x20000), p(0x30000), 512, 512, 512, 512, 512, 512, 0, 0, None,
                             None) == N.ERR_NULL
+
+
+def test_batch_row_alignment_is_checked():
+    """The packer's row alignment is a positive multiple of 4 floats (the vector
+    loads need 16-byte rows); it is checked before anything is planned."""
+    from paper_1710_08332_gb300.batch import Batch
+
+    for bad in (0, 3, 6, -4):
+        with pytest.raises(ValueError):
+            Batch([16], [(4, 8)], "cpu", row_align=bad)
