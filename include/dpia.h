@@ -351,7 +351,11 @@ typedef struct {
  *   threads       -- block size (a power of two, 32..256);
  *   schedule      -- 0: items sorted longest first and dealt to the blocks
  *                    round robin; 1: items in instance order, each block takes
- *                    the contiguous run whose byte costs make up its equal share.
+ *                    the contiguous run whose byte costs make up its equal share;
+ *                    2: items sorted longest first, dealt round robin in the
+ *                    forward, and in the backward each warp takes the next one
+ *                    from a counter in the workspace when it is free (launches
+ *                    sharing a workspace must not overlap: run them on one stream).
  */
 typedef struct {
   int32_t threads;

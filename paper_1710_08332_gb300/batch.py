@@ -34,7 +34,9 @@ class BatchPolicy:
     dot_second: str = "tree"
     gemv_split_cap: int = 4096     # GEMV row split = N rounded up to 128, capped
     row_split: int = 256           # backward dx rows per chunk
-    schedule: int = 0              # 0: longest first, round robin; 1: contiguous equal-cost runs
+    schedule: int = 0              # 0: longest first, round robin; 1: contiguous equal-cost runs;
+    #                                2: longest first, forward round robin, each backward warp
+    #                                   takes the next item when it is free
 
     def dot_strategy(self, n: int) -> ReduceStrategy:
         q = self.threads * 4

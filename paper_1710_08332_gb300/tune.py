@@ -205,6 +205,8 @@ def batch_candidates():
     out = [BatchPolicy(threads=256, dot_split_cap=8192, row_split=128, schedule=1)]
     for T, cap, rs in ((256, 8192, 128), (128, 8192, 128), (256, 16384, 256), (256, 4096, 64), (256, 8192, 512)):
         out.append(BatchPolicy(threads=T, dot_split_cap=cap, row_split=rs))
+    for rs in (256, 512):  # items taken from a counter by whichever block or warp is free
+        out.append(BatchPolicy(threads=256, dot_split_cap=8192, row_split=rs, schedule=2))
     return out
 
 

@@ -196,3 +196,19 @@ def test_batch_row_alignment_is_checked():
     for bad in (0, 3, 6, -4):
         with pytest.raises(ValueError):
             Batch([16], [(4, 8)], "cpu", row_align=bad)
+
+
+def test_batch_schedule_values():
+    """Schedules 0 (longest first, round robin), 1 (equal-cost runs) and 2
+    (longest first, taken from a counter) plan; anything else is refused."""
+    from paper_1710_08332_gb300.batch import BatchPolicy
+
+    L = N.lib()
+    d = (N.DotInstanceC * 1)()
+    d[0] = N.DotInstanceC(0, 4096, BatchPolicy().dot_strategy(4096).to_c())
+    g = (N.GemvInstanceC * 1)()
+    for sched in (0, 1, 2):
+        assert L.dpia_batch_plan_size(1, d, 0, g, ctypes.byref(N.BatchOptionsC(256, sched))) > 0
+    for sched in (-1, 3):
+        assert L.dpia_batch_plan_size(1, d, 0, g, ctypes.byref(N.BatchOptionsC(256, sched))) == 0
+        assert "schedule" in dpia.dpia_last_error_message()

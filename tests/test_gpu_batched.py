@@ -78,8 +78,9 @@ SMALL_GEMVS = [(1, 1), (3, 5), (100, 257), (300, 1000), (50, 4096), (2000, 128),
 @pytest.mark.parametrize("policy", [BatchPolicy(), BatchPolicy(threads=128, dot_split_cap=2048, dot_second="seq",
                                                                 gemv_split_cap=256, row_split=100),
                                     BatchPolicy(schedule=1),
-                                    BatchPolicy(threads=64, schedule=1, row_split=37)],
-                         ids=["default", "small-splits", "contiguous", "contiguous-64"])
+                                    BatchPolicy(threads=64, schedule=1, row_split=37),
+                                    BatchPolicy(schedule=2), BatchPolicy(threads=64, schedule=2, row_split=37)],
+                         ids=["default", "small-splits", "contiguous", "contiguous-64", "dynamic", "dynamic-64"])
 def test_batch_bits_against_oracle(cuda_device, policy):
     rng = np.random.default_rng(11)
     dots = SMALL_DOTS + [int(v) for v in np.exp(rng.uniform(np.log(256), np.log(20000), 150))]
@@ -93,12 +94,17 @@ def test_batch_bits_against_oracle(cuda_device, policy):
     b.backward(xs, ys, dot_g, dxs, dys, As, gx, gdy, dAs, dgx)
     torch.cuda.synchronize()
     _check_against_oracle(b, xs, ys, As, gx, dot_g, gdy, dot_out, gy, dxs, dys, dAs, dgx)
-    # the per-instance counters are back at zero, so a second launch gives the same bits
-    assert not host(b.ws)[128:128 + 4 * len(dots)].view(np.uint32).any()
+    # the per-instance counters (and the dynamic schedule's) are back at zero, so a
+    # second launch gives the same bits
+    assert not host(b.ws)[:128 + 4 * len(dots)].view(np.uint32).any()
     dot2, gy2 = _outputs(b)
     b.forward(xs, ys, dot2, As, gx, gy2)
+    dxs2, dys2, dAs2, dgx2 = _bwd_outputs(b)
+    b.backward(xs, ys, dot_g, dxs2, dys2, As, gx, gdy, dAs2, dgx2)
     torch.cuda.synchronize()
-    assert host(dot2).tobytes() == host(dot_out).tobytes()
+    assert host(dot2).tobytes() == host(dot_out).tobytes() and host(gy2).tobytes() == host(gy).tobytes()
+    assert host(dgx2).tobytes() == host(dgx).tobytes() and host(dAs2).tobytes() == host(dAs).tobytes()
+    assert not host(b.ws)[:128].view(np.uint32).any()
 
 
 def test_batch_equals_per_launch_and_graph(cuda_device):
