@@ -361,18 +361,24 @@ template <int RC>
 __device__ __forceinline__ void gemv_rows_narrow(const float *A, int64_t lda, const float *x, float *y, int64_t N,
                                                  int64_t r0, int64_t r_end, int64_t stride, int lane) {
   constexpr int G = 8 / RC;
-  float4 xv[RC];
-#pragma unroll
-  for (int q = 0; q < RC; ++q) {
+  constexpr bool HOLD_X = RC <= 4;  // wider rows re-read x (cached) inside the fold: fewer registers
+  auto x_at = [&](int q) {
     const int64_t e0 = 4 * lane + 128 * q;
+    float4 v;
     if (e0 + 4 <= N) {
-      xv[q] = ld_cached_v4(x + e0);
+      v = ld_cached_v4(x + e0);
     } else {
-      xv[q].x = e0 < N ? x[e0] : 0.0f;
-      xv[q].y = e0 + 1 < N ? x[e0 + 1] : 0.0f;
-      xv[q].z = e0 + 2 < N ? x[e0 + 2] : 0.0f;
-      xv[q].w = e0 + 3 < N ? x[e0 + 3] : 0.0f;
+      v.x = e0 < N ? x[e0] : 0.0f;
+      v.y = e0 + 1 < N ? x[e0 + 1] : 0.0f;
+      v.z = e0 + 2 < N ? x[e0 + 2] : 0.0f;
+      v.w = e0 + 3 < N ? x[e0 + 3] : 0.0f;
     }
+    return v;
+  };
+  float4 xv[HOLD_X ? RC : 1];
+  if constexpr (HOLD_X) {
+#pragma unroll
+    for (int q = 0; q < RC; ++q) xv[q] = x_at(q);
   }
   for (int64_t r = r0; r < r_end; r += stride * G) {
     float4 av[G][RC];
@@ -398,10 +404,11 @@ __device__ __forceinline__ void gemv_rows_narrow(const float *A, int64_t lda, co
       float acc[4] = {SumF32::zero(), SumF32::zero(), SumF32::zero(), SumF32::zero()};
 #pragma unroll
       for (int q = 0; q < RC; ++q) {
-        acc[0] = SumF32::step(acc[0], DotF32::elem(av[k][q].x, xv[q].x));
-        acc[1] = SumF32::step(acc[1], DotF32::elem(av[k][q].y, xv[q].y));
-        acc[2] = SumF32::step(acc[2], DotF32::elem(av[k][q].z, xv[q].z));
-        acc[3] = SumF32::step(acc[3], DotF32::elem(av[k][q].w, xv[q].w));
+        const float4 xq = HOLD_X ? xv[HOLD_X ? q : 0] : x_at(q);
+        acc[0] = SumF32::step(acc[0], DotF32::elem(av[k][q].x, xq.x));
+        acc[1] = SumF32::step(acc[1], DotF32::elem(av[k][q].y, xq.y));
+        acc[2] = SumF32::step(acc[2], DotF32::elem(av[k][q].z, xq.z));
+        acc[3] = SumF32::step(acc[3], DotF32::elem(av[k][q].w, xq.w));
       }
       float t = SumF32::zero();
 #pragma unroll
@@ -488,12 +495,13 @@ __global__ void __launch_bounds__(256, 3) batch_fwd_kernel(const FwdArgs a) {
       const int64_t warps = blockDim.x >> 5;
       const int64_t r_end = w.a + h->rows_per_item < g.M ? w.a + h->rows_per_item : g.M;
       const float *x = a.gx + g.x_off;
-      if (g.Crow == 1 && g.Rc >= 2 && g.Rc <= 4 && g.step == 32 * V) {
+      if (g.Crow == 1 && g.Rc >= 2 && g.Rc <= 8 && g.step == 32 * V) {
         const float *A0 = a.As + g.a_off;
         float *y = a.gy + g.y_off;
-        // two or three vectors fold as four: the others lie past N, identity items
+        // fewer vectors fold as four (or eight): the others lie past N, identity items
         // (+0 added to a sum that starts at +0 and so is never -0: the same bits)
-        gemv_rows_narrow<4>(A0, g.lda, x, y, g.N, w.a + warp, r_end, warps, lane);
+        if (g.Rc <= 4) gemv_rows_narrow<4>(A0, g.lda, x, y, g.N, w.a + warp, r_end, warps, lane);
+        else gemv_rows_narrow<8>(A0, g.lda, x, y, g.N, w.a + warp, r_end, warps, lane);
       } else
       for (int64_t r = w.a + warp; r < r_end; r += warps) {
         const float *row = a.As + g.a_off + r * g.lda;
