@@ -70,9 +70,10 @@ def _check_against_oracle(b, xs, ys, As, gx, dot_g, gdy, dot_out, gy, dxs, dys, 
 
 SMALL_DOTS = [0, 1, 3, 100, 1023, 1024, 1025, 5000, 8192, 8193, 20000, 70001]
 # (64, 256), (17, 384), (33, 511), (5, 129): two, three and four vectors a lane, whole and ragged,
-# on the forward path that takes narrow rows two at a time
+# on the forward path that takes narrow rows two at a time; (9, 640), (3, 513), (12, 1024):
+# five to eight vectors a lane, loaded at once
 SMALL_GEMVS = [(1, 1), (3, 5), (100, 257), (300, 1000), (50, 4096), (2000, 128), (0, 64), (257, 4100),
-               (64, 256), (17, 384), (33, 511), (5, 129)]
+               (64, 256), (17, 384), (33, 511), (5, 129), (9, 640), (3, 513), (12, 1024)]
 
 
 @pytest.mark.parametrize("policy", [BatchPolicy(), BatchPolicy(threads=128, dot_split_cap=2048, dot_second="seq",
