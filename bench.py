@@ -331,7 +331,11 @@ def profile_case(args):
         from paper_1710_08332_gb300.batch import Batch
 
         dl, rows, cols = W.batched_shapes()
-        b = Batch(dl.tolist()[:512], list(zip(rows.tolist()[:16], cols.tolist()[:16])), dev)
+        from paper_1710_08332_gb300.batch import BatchPolicy
+
+        # the policy the autotuner picks on the whole batch: backward items taken by free warps
+        b = Batch(dl.tolist()[:512], list(zip(rows.tolist()[:16], cols.tolist()[:16])), dev,
+                  policy=BatchPolicy(row_split=256, schedule=2))
         xs = torch.rand(b.xs_len, device=dev)
         ys = torch.rand(b.xs_len, device=dev)
         As = torch.randn(b.as_len, device=dev)
