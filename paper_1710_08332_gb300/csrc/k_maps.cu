@@ -53,6 +53,40 @@ __global__ void __launch_bounds__(256) scal_kernel(float a, const float *x, floa
   for (int64_t e = nv * V + g0; e < n; e += ng) y[e] = __fmul_rn(a, x[e]);
 }
 
+// The same map over contiguous chunks of 256 * U vectors: a block takes chunks
+// blockIdx.x, + gridDim.x, ...; in a chunk thread t loads vectors t, t + 256, ...
+// (all U loads in flight before the stores), so each block streams one
+// contiguous 32 KiB (V = 4, U = 8) piece at a time. A ragged end is left to
+// the grid-stride kernel's tail loops (vectors, then scalars).
+template <int V, int U>
+__global__ void __launch_bounds__(256) scal_chunk_kernel(float a, const float *x, float *y, int64_t n) {
+  const int64_t nv = n / V;
+  const int64_t chunks = nv / (256 * U);
+  for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+    const int64_t base = c * (256 * U) + threadIdx.x;
+    float r[U][V];
+#pragma unroll
+    for (int u = 0; u < U; ++u) load_vec<V, false>(x + (base + u * 256) * V, r[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) r[u][v] = __fmul_rn(a, r[u][v]);
+      store_vec<V>(y + (base + u * 256) * V, r[u]);
+    }
+  }
+  // the vectors past the last whole chunk, then the scalar tail
+  const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ng = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = chunks * (256 * U) + g0; i < nv; i += ng) {
+    float r[V];
+    load_vec<V, false>(x + i * V, r);
+#pragma unroll
+    for (int v = 0; v < V; ++v) r[v] = __fmul_rn(a, r[v]);
+    store_vec<V>(y + i * V, r);
+  }
+  for (int64_t e = nv * V + g0; e < n; e += ng) y[e] = __fmul_rn(a, x[e]);
+}
+
 // dx = g*y, dy = g*x with g read from device memory.
 __global__ void __launch_bounds__(256) dot_bwd_kernel(const float *x, const float *y, const float *g,
                                                       int64_t n, float *dx, float *dy) {
@@ -108,7 +142,7 @@ cudaError_t launch_scal(float a, const float *x, float *y, int64_t n, int V, cud
   switch (V) {
     case 1: k = (const void *)scal_kernel<1>; break;
     case 2: k = (const void *)scal_kernel<2>; break;
-    case 4: k = (const void *)scal_kernel<4>; break;
+    case 4: k = (const void *)scal_chunk_kernel<4, 8>; break;
     case 8: k = (const void *)scal_kernel<8>; break;
     case 16: k = (const void *)scal_kernel<16>; break;
     default: return cudaErrorInvalidValue;
