@@ -355,7 +355,8 @@ typedef struct {
  *                    2: items sorted longest first, dealt round robin in the
  *                    forward, and in the backward each warp takes the next one
  *                    from a counter in the workspace when it is free (launches
- *                    sharing a workspace must not overlap: run them on one stream).
+ *                    sharing a workspace must not overlap: run them on one stream;
+ *                    at most 2^30 backward items, else DPIA_ERR_SHAPE).
  */
 typedef struct {
   int32_t threads;

@@ -289,6 +289,10 @@ dpia_status build_plan(int32_t nd, const dpia_dot_instance *dots, int32_t ng, co
   h.bwd_total = acc;
   h.n_fwd = (int64_t)b.fwd.size();
   h.n_bwd = (int64_t)b.bwd.size();
+  if (h.schedule == 2 && h.n_bwd > (int64_t)1 << 30) {  // the 32-bit counter also counts every warp's last grab
+    set_last_error("dpia_batch_plan: schedule 2 takes at most 2^30 backward items (%lld)", (long long)h.n_bwd);
+    return DPIA_ERR_SHAPE;
+  }
   int64_t off = round_up(sizeof(PlanHeader), 128);
   h.dots_off = off;
   off += round_up((int64_t)b.dots.size() * sizeof(DotDesc), 128);
