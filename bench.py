@@ -1011,6 +1011,25 @@ def generated_single_launch(device, x, y, A, xv, sms: int, reps: int = 20):
     res["asum_R (the dot's strategy)"] = {"generated_us": round(ga * 1e3, 2), "library_us": round(la * 1e3, 2),
                                           "generated_GB_s": round(4 * n / ga / 1e6, 1),
                                           "generated_over_library_time": round(la / ga, 3)}
+    # compensated (Kahan at every level): lane pairs, trees over (s, c) by shuffles; the
+    # faster of two splits (the folds not unrolled: measured fastest for this chain)
+    kbest = None
+    for s_ in (16384, 32768):
+        C = n // s_
+        kk = G.compile_cuda(f"gen_dot_R_kahan_s{s_}", *PR.dot_R_kahan(n, s_, 256, 4, "interleaved", "tree",
+                                                                     min(256, C)), unroll=1)
+        tk = kk.temps_like(device)
+        stk = dpia.ReduceStrategy(split=s_, threads=256, vec=4, second="tree", threads2=min(256, C),
+                                  compensated=True)
+        wsk = dpia.workspace(dpia.dpia_dot_workspace_size(n, stk), device)
+        gk = tune.time_call(lambda: kk.run(x, y, out, *tk), reps=reps)
+        lk = tune.time_call(lambda: dpia.dpia_dot_f32(x, y, n, stk, out, wsk), reps=reps)
+        if kbest is None or gk < kbest[1]:
+            kbest = (s_, gk, lk)
+    s_, gk, lk = kbest
+    res[f"dot_R compensated (Kahan) s={s_} T=256 V=4 tree"] = {
+        "generated_us": round(gk * 1e3, 2), "library_us": round(lk * 1e3, 2),
+        "generated_GB_s": round(8 * n / gk / 1e6, 1), "generated_over_library_time": round(lk / gk, 3)}
     kg = G.compile_cuda("gen_gemv_R", *PR.gemv_R(M, N, 128, 4), unroll=4)
     stg = dpia.ReduceStrategy(split=N, threads=128, vec=4)
     gg = tune.time_call(lambda: kg.run(A, xv, yv), reps=reps)

@@ -151,6 +151,8 @@ def place_size(acc) -> int:
         acc = acc.acc
     if not isinstance(acc.type, (P.Arr, P.PairT)) and not P.is_scalar(acc.type):
         raise RaceError(f"cannot size {acc.name} of type {acc.type}")
+    if isinstance(acc.type, P.PairT):  # a private pair (of numbers or vectors): one place per component
+        return 2
     n = P.scalar_count(acc.type) if not isinstance(acc.type, P.VecT) else 1
     if isinstance(P.base_elem(acc.type), P.VecT):
         n = max(1, n // P.base_elem(acc.type).n)  # vector outputs are addressed by vector

@@ -116,8 +116,12 @@ def _acc_root(a):
 
 
 def _reads_private_array(e) -> bool:
+    """The expression reads an element of a private array temporary, or a lane of
+    a vector (unrolled, a lane index is a constant: a register, not a select)."""
     if isinstance(e, P.Ident):
         return e.temp == "private" and isinstance(e.type, P.Arr)
+    if isinstance(e, P.Lanes):
+        return True
     return any(_reads_private_array(x) for x in e.children())
 
 
@@ -244,10 +248,17 @@ class Emitter:
                 return f"({v}).{LANES[lane.v]}"
             return f"dpia_lane{V}({v}, {render_index(lane)})"
         if isinstance(e, P.Lanes):
-            V = e.e.type.n
-            if len(path) != 1 or path[0][0] != "i":
-                raise EmitError("lanes read must select one lane")
-            v = self.access(e.e, [])
+            if isinstance(e.e.type, P.PairT):  # lane v of a pair of vectors: component k's lane v
+                V = e.e.type.a.n
+                if len(path) != 2 or path[0][0] != "i" or path[1][0] != "p":
+                    raise EmitError("lanes of a pair: select one lane, then a component")
+                v = self.access(e.e, [path[1]])
+                path = path[:1]
+            else:
+                V = e.e.type.n
+                if len(path) != 1 or path[0][0] != "i":
+                    raise EmitError("lanes read must select one lane")
+                v = self.access(e.e, [])
             lane = path[0][1]
             if isinstance(lane, T.IConst):
                 return f"({v}).{LANES[lane.v]}"
@@ -315,6 +326,14 @@ class Emitter:
             if len(path) != 1 or path[0][0] != "p":
                 raise EmitError("a pair temporary is read one component at a time")
             return f"{e.name}_{path[0][1]}"
+        if e.temp is not None and isinstance(P.base_elem(e.type), P.PairT) and path and path[-1][0] == "p":
+            # a component of an element of an array of pairs
+            if any(s[0] != "i" for s in path[:-1]):
+                raise EmitError("an array of pairs is indexed, then projected")
+            ref = self.temp_pair_ref(self.temps[e.name], [s[1] for s in path[:-1]], path[-1][1])
+            if self.in_last and self.temps[e.name].space == "global" and self.backend == "cuda":
+                return f"__ldcg(&{ref})"
+            return ref
         idx = [s[1] for s in path]
         if any(s[0] != "i" for s in path):
             raise EmitError("projection of a non-pair")
@@ -329,6 +348,19 @@ class Emitter:
         if self.in_last and t.space == "global" and self.backend == "cuda":
             return f"__ldcg(&{ref})"  # written by other blocks: read through L2, not a stale L1 line
         return ref
+
+    def temp_pair_ref(self, t: T.Temp, idx: list, k: int) -> str:
+        """Component k of element idx of a temporary array of pairs (stored as
+        two numbers per element); a lane tree's buffer of pairs is two registers."""
+        if t.lanes and self.backend == "cuda":
+            return f"{t.name}_{k}"
+        shape = dims(t.type)
+        off = T.iadd(T.imul(linear(idx, shape), 2), T.IConst(k)) if shape else T.IConst(k)
+        if t.space == "global" and t.hoist:
+            size = P.scalar_count(t.type)
+            h = linear([v for v, _ in t.hoist], [n for _, n in t.hoist])
+            off = T.iadd(T.imul(h, size), off)
+        return f"{t.name}[{render_index(off)}]"
 
     def temp_ref(self, t: T.Temp, idx: list) -> str:
         shape = dims(t.type)
@@ -428,9 +460,9 @@ class Emitter:
                 raise EmitError(f"pair component through a {type(acc).__name__}")
             acc = acc.acc
         if acc.temp is not None:
-            if acc.temp.space != "private" or dims(acc.temp.type):
-                raise EmitError("pair temporaries are private scalars only")
-            return f"{acc.name}_{k}"
+            if isinstance(acc.temp.type, P.PairT):  # a private pair: two variables
+                return f"{acc.name}_{k}"
+            return self.temp_pair_ref(acc.temp, path, k)
         if not isinstance(P.base_elem(acc.type), P.PairT):
             raise EmitError("pair component of a non-pair output")
         off = linear(path, dims(acc.type)) if dims(acc.type) else T.IConst(0)
@@ -466,8 +498,13 @@ class Emitter:
                 self.lines.append(f"{pad}{ctype(t.type.b)} {t.name}_1;")
                 self.emit(c.body, ind, ctx)
                 return
-            if isinstance(P.base_elem(t.type), P.PairT):
-                raise EmitError("arrays of pairs are outputs only")
+            if isinstance(P.base_elem(t.type), P.PairT) and t.space == "private":
+                # an array of pairs: element j's components at 2j and 2j + 1
+                par = sum(1 for l in ctx if l != "seq")
+                self.private_ctx[t.name] = (par, _per_thread(ctx))
+                self.lines.append(f"{pad}{ctype(P.base_num(t.type))} {t.name}[{P.scalar_count(t.type)}];")
+                self.emit(c.body, ind, ctx)
+                return
             if t.space == "private":
                 ct = ctype(P.base_elem(t.type))
                 shape = dims(t.type)
@@ -551,6 +588,8 @@ class Emitter:
             self.lines.append(f"{pad}__syncthreads();")
 
     def emit_tree(self, c: T.TreeReduce, ind: int, ctx: tuple):
+        if isinstance(c.buf.type.elem, P.PairT):
+            return self.emit_pair_tree(c, ind, ctx)
         pad = "  " * ind
         L = c.buf.type.n
         et = c.buf.type.elem
@@ -582,6 +621,56 @@ class Emitter:
                               f"{c.buf.name}[dpia_l] = {self.access(step, [])};")
             h //= 2
         self.lines.append(f"{pad}{c.res.name} = {c.buf.name}[0];")
+
+    def emit_pair_tree(self, c: T.TreeReduce, ind: int, ctx: tuple):
+        """The halving tree over pairs (e.g. compensated sums (s, c)): each step
+        computes both components of f(x_l, x_{l+h}) before either replaces x_l
+        (the second component may read the first's old value)."""
+        pad = "  " * ind
+        L = c.buf.type.n
+        et = c.buf.type.elem
+        ct = ctype(et.a)
+        zero = self.literal(P.Lit(0.0, et.a))
+        self.private_ctx[c.buf.name] = (sum(1 for l in ctx if l != "seq"), _per_thread(ctx))
+        if isinstance(c.res.type, P.PairT):
+            res = [f"{c.res.name}_0", f"{c.res.name}_1"]
+        else:
+            raise EmitError("a tree over pairs gives a pair")
+        if self.backend == "cuda":
+            if "warp" not in ctx or "lane" in ctx:
+                raise EmitError("a lane tree runs directly inside a warp loop")
+            # lane l keeps element l in two registers; lanes past L hold zeros
+            self.lines.append(f"{pad}{ct} {c.buf.name}_0 = {zero};")
+            self.lines.append(f"{pad}{ct} {c.buf.name}_1 = {zero};")
+            self.emit(c.fill, ind, ctx)
+            reg = P.Ident(c.buf.name, et, temp="private")
+            other = P.Ident("dpia_o", et, temp="private")  # lane l + h's pair, shuffled once
+            h = L // 2
+            while h >= 1:
+                step = P.apply(c.f, reg, other)
+                a0, a1 = self.access(step, [("p", 0)]), self.access(step, [("p", 1)])
+                self.lines.append(f"{pad}{{ const {ct} dpia_o_0 = __shfl_down_sync(0xffffffffu, {c.buf.name}_0, {h}); "
+                                  f"const {ct} dpia_o_1 = __shfl_down_sync(0xffffffffu, {c.buf.name}_1, {h});")
+                self.lines.append(f"{pad}  const {ct} dpia_n0 = {a0}; const {ct} dpia_n1 = {a1}; "
+                                  f"{c.buf.name}_0 = dpia_n0; {c.buf.name}_1 = dpia_n1; }}")
+                h //= 2
+            self.lines.append(f"{pad}{res[0]} = {c.buf.name}_0;  // the tree's value, in lane 0")
+            self.lines.append(f"{pad}{res[1]} = {c.buf.name}_1;")
+            return
+        bufv = P.Ident(c.buf.name, c.buf.type, temp="private")
+        self.lines.append(f"{pad}{ct} {c.buf.name}[{2 * L}];")
+        self.emit(c.fill, ind, ctx)
+        h = L // 2
+        while h >= 1:
+            j = T.IVar("dpia_l")
+            step = P.apply(c.f, P.Idx(bufv, j), P.Idx(bufv, T.iadd(j, T.IConst(h))))
+            a0, a1 = self.access(step, [("p", 0)]), self.access(step, [("p", 1)])
+            self.lines.append(f"{pad}for (long long dpia_l = 0; dpia_l < {h}; ++dpia_l) {{ "
+                              f"const {ct} dpia_n0 = {a0}; const {ct} dpia_n1 = {a1}; "
+                              f"{c.buf.name}[2 * dpia_l] = dpia_n0; {c.buf.name}[2 * dpia_l + 1] = dpia_n1; }}")
+            h //= 2
+        self.lines.append(f"{pad}{res[0]} = {c.buf.name}[0];")
+        self.lines.append(f"{pad}{res[1]} = {c.buf.name}[1];")
 
     def emit_last_block(self, c: T.LastBlock, ind: int, ctx: tuple):
         pad = "  " * ind

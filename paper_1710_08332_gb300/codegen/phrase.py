@@ -99,6 +99,11 @@ def is_value(t) -> bool:
     return is_scalar(t) or (isinstance(t, PairT) and is_scalar(t.a) and is_scalar(t.b))
 
 
+def _num_or_num_pair(t) -> bool:
+    """A number, or a pair of two numbers of one type (a compensated sum's (s, c))."""
+    return isinstance(t, Num) or (isinstance(t, PairT) and isinstance(t.a, Num) and t.a == t.b)
+
+
 def is_num_array(t) -> bool:
     """An array (of arrays ...) of numbers or of vectors of numbers."""
     return isinstance(t, Arr) and isinstance(base_elem(t), (Num, VecT))
@@ -476,14 +481,19 @@ class Idx(Phrase):
 
 @dataclass(eq=False)
 class Lanes(Phrase):
-    """lanes: num<V> -> V.num, the vector's numbers as an array (a view)."""
+    """lanes: num<V> -> V.num, the vector's numbers as an array (a view); of a
+    pair of vectors (num<V> x num<V>) -> V.(num x num), lane v's pair."""
     e: Phrase
     type: object = field(init=False)
 
     def __post_init__(self):
-        if not isinstance(self.e.type, VecT):
-            raise TypeError(f"lanes of a non-vector {self.e.type}")
-        self.type = Arr(self.e.type.n, self.e.type.num)
+        t = self.e.type
+        if isinstance(t, VecT):
+            self.type = Arr(t.n, t.num)
+        elif isinstance(t, PairT) and isinstance(t.a, VecT) and t.a == t.b:
+            self.type = Arr(t.a.n, PairT(t.a.num, t.a.num))
+        else:
+            raise TypeError(f"lanes of a non-vector {t}")
 
     def children(self):
         return (self.e,)
@@ -503,9 +513,10 @@ class ReduceTree(Phrase):
         t = self.e.type
         if self.level != "lane":
             raise TypeError(f"reduceTree at level {self.level}: trees run over the lanes of a warp")
-        if not (isinstance(t, Arr) and isinstance(t.elem, Num) and t.n >= 1 and t.n & (t.n - 1) == 0
+        if not (isinstance(t, Arr) and _num_or_num_pair(t.elem) and t.n >= 1 and t.n & (t.n - 1) == 0
                 and t.n <= WARP):
-            raise TypeError(f"reduceTree over {t}: a power-of-two array of at most {WARP} numbers")
+            raise TypeError(f"reduceTree over {t}: a power-of-two array of at most {WARP} numbers "
+                            f"(or pairs of numbers)")
         ps = self.f.params
         if len(ps) != 2 or ps[0].type != t.elem or ps[1].type != t.elem or self.f.body.type != t.elem:
             raise TypeError("reduceTree's function combines two elements into one")
@@ -527,8 +538,8 @@ class SecondLevel(Phrase):
     type: object = field(init=False)
 
     def __post_init__(self):
-        if not isinstance(self.parts.type, Arr) or not isinstance(base_elem(self.parts.type), Num):
-            raise TypeError(f"second level over {self.parts.type}: an array of numbers")
+        if not isinstance(self.parts.type, Arr) or not _num_or_num_pair(base_elem(self.parts.type)):
+            raise TypeError(f"second level over {self.parts.type}: an array of numbers (or pairs of numbers)")
         if len(self.f.params) != 1 or self.f.params[0].type != self.parts.type:
             raise TypeError("the second level's function takes the array of parts")
         self.type = self.f.body.type

@@ -334,7 +334,7 @@ def _plus(a, b):
     return P.add(a, b)
 
 
-def block_tree(cols, column):
+def block_tree(cols, column, combine=None):
     """The block's tree over its T thread results, T = len(cols) a power of two
     (1..1024), thread t's result being column(cols[t]): the columns are split
     into groups of min(32, T), a warp per group; lane l computes its column's
@@ -343,13 +343,14 @@ def block_tree(cols, column):
     one-element array of the work-group's result. The same tree as a halving
     tree within each group of 32 consecutive thread results, then over the
     group sums."""
+    combine = combine or _plus
     T = cols.type.n
     L = min(P.WARP, T)
-    sums = P.mapWarp(lambda g: P.reduceTree(_plus, P.mapLane(column, g)), P.split(L, cols))
+    sums = P.mapWarp(lambda g: P.reduceTree(combine, P.mapLane(column, g)), P.split(L, cols))
     W = T // L
     if W == 1:
         return sums
-    return P.mapWarp(lambda g: P.reduceTree(_plus, g), P.split(W, P.to_local(sums)))
+    return P.mapWarp(lambda g: P.reduceTree(combine, g), P.split(W, P.to_local(sums)))
 
 
 def column_result(V: int, step):
@@ -386,6 +387,61 @@ def _reduce_R(items, n_items: int, s: int, T: int, thread_map: str, V: int, seco
     chunks = P.split(s // V, items)
     parts = P.join(P.mapWorkgroup(lambda ch: chunk_result(ch, T, thread_map, V, step), chunks))
     return P.secondLevel(parts, lambda p: second_level(p, second, T2))
+
+
+def _kahan_combine(a, b):
+    """Merge compensated partial b into a: a Kahan step of a with e = b.s - b.c."""
+    return kahan_merge(a, P.fst(b), P.snd(b))
+
+
+def _reduce_R_kahan(items, n_items: int, s: int, T: int, thread_map: str, V: int, second: str, T2: int, elem):
+    """The canonical strategy with every fold step a Kahan step: each lane keeps
+    (s, c) (lane-wise on num<V>), a thread merges its V lane pairs in lane order
+    from (0, 0), the trees and the second level merge pairs, and the result is
+    the final s -- the library's compensated reduction."""
+    if s % (T * V) or n_items % s:
+        raise ValueError(f"split {s} over {T} threads x {V} lanes does not divide {n_items} items")
+
+    def column(col):
+        zero = P.pair(_zero(V), _zero(V))
+        acc = P.reduceSeq(lambda it, a: kahan_step(a, elem(it)), zero, col)
+        if V == 1:
+            return acc
+        lane_pairs = P.lanes(acc)  # lane v's (s, c): the accumulator read once
+        return P.reduceSeq(lambda lp, a: kahan_merge(a, P.fst(lp), P.snd(lp)), _zero_pair(), lane_pairs)
+
+    def fold_pairs(col):
+        return P.reduceSeq(lambda p, a: _kahan_combine(a, p), _zero_pair(), col)
+
+    chunks = P.split(s // V, items)
+    parts = P.join(P.mapWorkgroup(
+        lambda ch: block_tree(columns(ch, T, thread_map), column, _kahan_combine), chunks))
+
+    def second_level_kahan(p):
+        C = p.type.n
+        if second == "seq":
+            return P.fst(fold_pairs(p))
+        if C % T2:
+            raise ValueError(f"a tree second level over {C} results needs a thread count dividing it, not {T2}")
+        return P.mapSeq(lambda r: P.fst(r), block_tree(P.transpose(P.split(T2, p)), fold_pairs, _kahan_combine))
+
+    return P.secondLevel(parts, second_level_kahan)
+
+
+def dot_R_kahan(n: int, s: int, T: int, V: int = 4, thread_map: str = "interleaved", second: str = "tree",
+                T2: int = 256):
+    """x . y in one kernel with the canonical strategy, compensated (Kahan) at
+    every level: the library's dot with compensated = 1."""
+    x, y = P.inp("x", P.arr(n, P.F32)), P.inp("y", P.arr(n, P.F32))
+    return _reduce_R_kahan(P.zip_(_vec(x, V), _vec(y, V)), n, s, T, thread_map, V, second, T2,
+                           lambda p: P.mul(P.fst(p), P.snd(p))), [x, y]
+
+
+def asum_R_kahan(n: int, s: int, T: int, V: int = 4, thread_map: str = "interleaved", second: str = "tree",
+                 T2: int = 256):
+    """sum |x_i| in one kernel, compensated at every level."""
+    x = P.inp("x", P.arr(n, P.F32))
+    return _reduce_R_kahan(_vec(x, V), n, s, T, thread_map, V, second, T2, P.abs_), [x]
 
 
 def dot_R(n: int, s: int, T: int, V: int = 4, thread_map: str = "interleaved", second: str = "tree",

@@ -722,8 +722,32 @@ def test_lane_trees_and_second_level_are_checked():
 
 
 @pytest.mark.skipif(not shutil.which("nvcc"), reason="nvcc not installed")
+@pytest.mark.parametrize("n,s,T,V,tm,second,T2", [
+    (1 << 14, 2048, 128, 4, "interleaved", "tree", 8), (1 << 14, 2048, 128, 4, "contig", "seq", 1),
+    (1 << 13, 1024, 64, 1, "interleaved", "tree", 8), (1 << 12, 512, 32, 2, "interleaved", "seq", 1),
+    (1 << 12, 256, 8, 4, "interleaved", "tree", 16)])
+def test_compensated_single_launch_matches_oracle(c_build, n, s, T, V, tm, second, T2):
+    """The compensated one-kernel dot and asum (lane-wise Kahan folds, lane pairs
+    merged in lane order, trees and second level over (s, c) pairs, the final s)
+    equal the oracle's compensated loop nest of the same strategy, and differ
+    from the plain one."""
+    from oracle import loopnest
+
+    x, y = uniform(n, 90 + T), uniform(n, 91 + V)
+    st = c1.Strategy(s=s, T=T, V=V, thread_map=tm, second=second, T2=max(T2, 1), compensated=True)
+    out = np.zeros(1, np.float32)
+    f = G.compile_c(f"dRk_{n}_{s}_{T}_{V}_{tm}_{second}", *PR.dot_R_kahan(n, s, T, V, tm, second, T2))
+    f.run(x, y, out, *f.temps_like())
+    assert bits(out)[0] == bits([loopnest.dot_f32(x, y, st)])[0]
+    f = G.compile_c(f"aRk_{n}_{s}_{T}_{V}_{tm}_{second}", *PR.asum_R_kahan(n, s, T, V, tm, second, T2))
+    f.run(x, out, *f.temps_like())
+    assert bits(out)[0] == bits([loopnest.asum_f32(x, st)])[0]
+
+
 def test_single_launch_sources_compile_for_sm103a(tmp_path):
     progs = {"dotR": PR.dot_R(1 << 20, 8192, 256, 4, "interleaved", "tree", 128),
+             "dotRk": PR.dot_R_kahan(1 << 20, 8192, 256, 4, "interleaved", "tree", 128),
+             "asumRk": PR.asum_R_kahan(1 << 20, 8192, 256, 4, "contig", "seq", 1),
              "asumR": PR.asum_R(1 << 20, 8192, 256, 4, "contig", "seq", 1),
              "gemvR": PR.gemv_R(512, 1024, 128, 4), "gemvRw": PR.gemv_R_warp(512, 1024, 8, 4)}
     for name, (e, ins) in progs.items():

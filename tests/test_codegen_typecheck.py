@@ -42,6 +42,8 @@ PROGRAMS = {
     "gemm_V4": lambda: PR.gemm(24, 40, 12, 4),
     "gemm_tA_tB": lambda: PR.gemm(24, 40, 12, 1, True, True),
     "gemm_tA_V4": lambda: PR.gemm(24, 40, 12, 4, True, False),
+    "dot_R_kahan": lambda: PR.dot_R_kahan(1 << 14, 1 << 11, 128, 4, "interleaved", "tree", 8),
+    "asum_R_kahan_seq": lambda: PR.asum_R_kahan(1 << 13, 1 << 10, 64, 1, "contig", "seq", 1),
     "gemm_tiled": lambda: PR.gemm_tiled(16, 32, 12, 4, 8, 4),
     "gemm_tiled_KV4": lambda: PR.gemm_tiled(16, 32, 12, 4, 8, 4, 4),
     "gemm_tiled_tA_tB": lambda: PR.gemm_tiled(16, 32, 12, 4, 4, 1, 1, True, True),

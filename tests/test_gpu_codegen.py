@@ -443,3 +443,34 @@ def test_gemm_exploration_ranks_derivations_that_match_oracle(cuda_device):
     ranked = RW.explore_gemm(A, B, n, n, n, ds, reps=2)
     assert len(ranked) == sum(2 if "tile" in str(d) else 1 for d in ds)
     assert [t[0] for t in ranked] == sorted(t[0] for t in ranked)
+
+
+@pytest.mark.parametrize("n,s,second,T2", [(1 << 20, 8192, "seq", 1), (1 << 22, 16384, "tree", 256),
+                                           (1 << 26, 16384, "tree", 256)])
+def test_generated_compensated_dot_matches_oracle_and_library(cuda_device, n, s, second, T2):
+    """The compensated one-kernel dot (Kahan at every level, trees over (s, c)
+    pairs by shuffles) equals the oracle's compensated loop nest and the
+    library's compensated dot, on two consecutive launches (the ticket resets)."""
+    from oracle import loopnest
+    from synth import workloads as W
+
+    import paper_1710_08332_gb300 as dpia
+
+    x, y = W.bandwidth("cuda", n=n)
+    k = G.compile_cuda(f"dot_R_kahan_{n}_{s}_{second}", *PR.dot_R_kahan(n, s, 256, 4, "interleaved", second, T2),
+                       unroll=4)
+    temps = k.temps_like()
+    outs = []
+    for _ in range(2):
+        out = torch.full((1,), float("nan"), device="cuda")
+        k.run(x, y, out, *temps)
+        outs.append(out)
+    st = dpia.ReduceStrategy(split=s, threads=256, vec=4, second=second, threads2=T2, compensated=True)
+    lib = torch.empty(1, device="cuda")
+    dpia.dpia_dot_f32(x, y, n, st, lib, dpia.workspace(dpia.dpia_dot_workspace_size(n, st), "cuda"))
+    torch.cuda.synchronize()
+    want = loopnest.dot_f32(x.cpu().numpy(), y.cpu().numpy(),
+                            c1.Strategy(s=s, T=256, V=4, second=second, T2=T2, compensated=True))
+    for out in outs:
+        assert bits(out.cpu().numpy())[0] == bits([want])[0]
+    assert bits(lib.cpu().numpy())[0] == bits([want])[0]
