@@ -1203,6 +1203,7 @@ def codegen_workload(args, device, dist):
         kind="asum_scal"), reps=5))
     explored["gemv"] = summary(RW.explore("gemv", [A, xv], N_, RW.gemv_derivations(M, N_, threads=(128, 256),
                                                                                   widths=(4,)), reps=5, M=M))
+    explored["gemv_dx"] = summary(RW.explore("gemv_dx", [A, dyv], N_, RW.gemv_dx_derivations(M, N_), reps=5, M=M))
     # GEMM 4096^3: the plain map of maps and the register tiles (every derivation the same bits)
     gA, gB, _ = W.gemm(device)
     gk = W.GEMM_MNK

@@ -126,17 +126,30 @@ def gemv_bwd_dA(M: int, N: int):
     return P.mapWorkgroup(lambda d: P.mapLocal(lambda v: P.mul(d, v), x), dy), [dy, x]
 
 
-def gemv_bwd_dx_partials(M: int, N: int, R: int):
+def gemv_bwd_dx_partials(M: int, N: int, R: int, V: int = 1):
     """The first kernel of dx = A^T dy split over rows: for each chunk of R rows
     (a workgroup) and each column (the workgroup's threads), the column's fold
-    over the chunk's rows in row order -- (M/R) x N partials."""
+    over the chunk's rows in row order -- (M/R) x N partials. With V > 1 a
+    thread folds V adjacent columns as one num<V> (dy_r widened), each lane its
+    own column's fold in the same order."""
     A, dy = P.inp("A", P.arr(M, N, P.F32)), P.inp("dy", P.arr(M, P.F32))
+    if V == 1:
+        e = P.mapWorkgroup(
+            lambda c: P.mapLocal(
+                lambda col: P.reduceSeq(lambda q, acc: P.add(acc, P.mul(P.fst(q), P.snd(q))), 0.0,
+                                        P.zip_(col, P.snd(c))),
+                P.transpose(P.fst(c))),
+            P.zip_(P.split(R, A), P.split(R, dy)))
+        return e, [A, dy]
+    if N % V:
+        raise ValueError("vector columns need N a multiple of V")
+    rows = P.split(R, P.split(N // V, P.asVector(V, P.join(A))))  # (M/R) x R x (N/V) vectors
     e = P.mapWorkgroup(
-        lambda c: P.mapLocal(
-            lambda col: P.reduceSeq(lambda q, acc: P.add(acc, P.mul(P.fst(q), P.snd(q))), 0.0,
-                                    P.zip_(col, P.snd(c))),
-            P.transpose(P.fst(c))),
-        P.zip_(P.split(R, A), P.split(R, dy)))
+        lambda c: P.asScalar(P.mapLocal(
+            lambda col: P.reduceSeq(lambda q, acc: P.add(acc, P.mul(P.fst(q), P.splat(V, P.snd(q)))),
+                                    P.vlit(0.0, V), P.zip_(col, P.snd(c))),
+            P.transpose(P.fst(c)))),
+        P.zip_(rows, P.split(R, dy)))
     return e, [A, dy]
 
 

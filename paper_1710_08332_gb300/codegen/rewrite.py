@@ -47,6 +47,11 @@ derivations give the same bits:
                  over groups, each group folded in order from the running value), A read as
                  num<KV> along k
 
+GEMV's backward dx = A^T dy (a map over columns of a fold over rows): split_rows(R) splits
+each column's fold into chunks of R rows, a work-group per chunk, then a fold of the chunk
+results in chunk order (each R its own tree); vectorize(V) folds V adjacent columns as one
+num<V> (no value changes).
+
 ``derivations`` enumerates rule sequences over parameter grids, ``rewrite``
 applies one to the start expression (each rule checks the shape it rewrites),
 and ``lower`` turns the resulting tree into kernel phrases. Each derivation's
@@ -299,6 +304,8 @@ def lower(kind: str, d: Derivation, n: int, M: int = 0):
     one kernel when the chunk results are reduced in the last work-group (a
     materialized inner map adds a kernel in front). GEMV (n = columns, M rows):
     one kernel, or partials and row folds."""
+    if kind == "gemv_dx":
+        return lower_gemv_dx(d, M, n)
     e = rewrite(kind, d)
     if kind == "gemv":
         return _lower_gemv(e, M, n)
@@ -426,6 +433,30 @@ def gemv_derivations(M: int, N: int, threads=(64, 128, 256), widths=(1, 4)):
     return out
 
 
+def gemv_dx_derivations(M: int, N: int, row_splits=(16, 32, 64, 128, 256, 512), widths=(1, 4)):
+    """GEMV backward dx = A^T dy (a map over columns of a fold over rows):
+    split_rows(R) splits each column's fold into chunks of R rows (a
+    work-group per chunk, then a fold of the chunk partials in chunk order),
+    vectorize(V) folds V adjacent columns as one num<V>. Each R is its own tree
+    (a different association); V changes no bit."""
+    out = []
+    for R, V in itertools.product(row_splits, widths):
+        if M % R or N % V:
+            continue
+        out.append(Derivation([Rule("split_rows", (R,))] + ([Rule("vectorize", (V,))] if V > 1 else [])))
+    return out
+
+
+def lower_gemv_dx(d: Derivation, M: int, N: int):
+    """The two kernels of a dx derivation: the chunk partials and their fold."""
+    args = {r.name: r.args for r in d.rules}
+    if "split_rows" not in args or set(args) - {"split_rows", "vectorize"}:
+        raise RuleError(f"a dx derivation is split_rows(R) [; vectorize(V)], not {d}")
+    R = args["split_rows"][0]
+    V = args.get("vectorize", (1,))[0]
+    return [("partials", *PR.gemv_bwd_dx_partials(M, N, R, V)), ("fold", *PR.gemv_bwd_dx_fold(M // R, N))]
+
+
 def gemm_derivations(M: int, N: int, K: int, tiles=((1, 1), (4, 8), (8, 4), (8, 8), (16, 8)), widths=(1, 4),
                      kwidths=(1, 4)):
     """GEMM derivations: the plain map of maps (vector columns or not) and the
@@ -549,7 +580,8 @@ def explore(kind: str, inputs, n: int, derivs=None, reps: int = 5, M: int = 0):
 
     from ..tune import time_call
 
-    derivs = derivs or (gemv_derivations(M, n) if kind == "gemv" else derivations(n, kind=kind))
+    derivs = derivs or (gemv_derivations(M, n) if kind == "gemv" else
+                        gemv_dx_derivations(M, n) if kind == "gemv_dx" else derivations(n, kind=kind))
     workers = max(1, min(16, len(os.sched_getaffinity(0))))
     with ThreadPoolExecutor(workers) as pool:
         pipes = list(pool.map(lambda d: compile_pipeline(kind, d, n, M), derivs))

@@ -514,6 +514,36 @@ def test_gemm_derivations_match_oracle(c_build):
         RW.lower_gemm(RW.Derivation([RW.Rule("split", (4,))]), M, N, K)
 
 
+def test_gemv_dx_derivations_match_oracle(c_build):
+    """Every dx derivation (row chunks of R, columns as vectors or not) equals the
+    oracle's dx for its own R: the chunk partials folded in chunk order."""
+    from oracle import loopnest
+    from paper_1710_08332_gb300.codegen import rewrite as RW
+
+    M, N = 128, 72
+    A = np.random.default_rng(180).standard_normal((M, N)).astype(np.float32)
+    dy = uniform(M, 181)
+    ds = RW.gemv_dx_derivations(M, N, row_splits=(16, 32, 64), widths=(1, 4))
+    assert len(ds) == 6
+    for d in ds:
+        R = d.rules[0].args[0]
+        cur = [A.ravel().copy(), dy]
+        for name, ph, ins in RW.lower("gemv_dx", d, N, M):
+            out = np.zeros(P_count(ph), np.float32)
+            tag = "_".join(str(a) for r in d.rules for a in r.args)
+            G.compile_c(f"dx_{name}_{tag}", ph, ins).run(*cur, out)
+            cur = [out]
+        assert np.array_equal(bits(cur[0]), bits(loopnest.gemv_bwd_dx_f32(A, dy, R))), str(d)
+    with pytest.raises(RW.RuleError):
+        RW.lower_gemv_dx(RW.Derivation([RW.Rule("vectorize", (4,))]), M, N)
+
+
+def P_count(ph):
+    from paper_1710_08332_gb300.codegen import phrase as PP
+
+    return PP.scalar_count(ph.type) if isinstance(ph.type, PP.Arr) else 1
+
+
 def test_array_accumulators_are_checked():
     """A reduce may accumulate an array of numbers (or vectors) only; the tiled
     GEMM rejects shapes that do not divide and vector loads across a transpose."""

@@ -474,3 +474,23 @@ def test_generated_compensated_dot_matches_oracle_and_library(cuda_device, n, s,
     for out in outs:
         assert bits(out.cpu().numpy())[0] == bits([want])[0]
     assert bits(lib.cpu().numpy())[0] == bits([want])[0]
+
+
+def test_gemv_dx_exploration_matches_oracle(cuda_device):
+    """GEMV dx derivations at 8192^2 on the GPU: the ranked pipelines, each run
+    again, equal the oracle's dx for their own row split."""
+    from oracle import loopnest
+    from paper_1710_08332_gb300.codegen import rewrite as RW
+    from synth import workloads as W
+
+    A, _, dy = W.gemv("cuda")
+    M, N = A.shape
+    hA, hdy = A.cpu().numpy(), dy.cpu().numpy()
+    ranked = RW.explore("gemv_dx", [A, dy], N, RW.gemv_dx_derivations(M, N), reps=2, M=M)
+    assert len(ranked) == 12 and [t[0] for t in ranked] == sorted(t[0] for t in ranked)
+    for _, d in (ranked[0], ranked[-1]):
+        R = d.rules[0].args[0]
+        pipe = RW.compile_pipeline("gemv_dx", d, N, M)
+        got = RW.run_pipeline(pipe, [A, dy])
+        torch.cuda.synchronize()
+        assert np.array_equal(bits(got.cpu().numpy()), bits(loopnest.gemv_bwd_dx_f32(hA, hdy, R))), str(d)
