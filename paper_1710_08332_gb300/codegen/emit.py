@@ -115,26 +115,27 @@ def _acc_root(a):
     return a
 
 
-def _reads_private_array(e) -> bool:
+def _reads_lane_or_private_element(e) -> bool:
     """The expression reads an element of a private array temporary, or a lane of
     a vector (unrolled, a lane index is a constant: a register, not a select)."""
     if isinstance(e, P.Ident):
         return e.temp == "private" and isinstance(e.type, P.Arr)
     if isinstance(e, P.Lanes):
         return True
-    return any(_reads_private_array(x) for x in e.children())
+    return any(_reads_lane_or_private_element(x) for x in e.children())
 
 
-def _private_array_loop(c) -> bool:
-    """The command writes or reads an element of a private array temporary."""
+def _indexes_registers(c) -> bool:
+    """The command writes or reads an element of a private array temporary, or
+    reads a lane of a vector: indices that unrolling turns into constants."""
     if isinstance(c, T.Assign):
         r = _acc_root(c.acc)
         return (r.temp is not None and r.temp.space == "private" and isinstance(r.temp.type, P.Arr)) or \
-            _reads_private_array(c.e)
+            _reads_lane_or_private_element(c.e)
     if isinstance(c, T.Seq):
-        return any(_private_array_loop(x) for x in c.cs)
+        return any(_indexes_registers(x) for x in c.cs)
     if isinstance(c, (T.New, T.For)):
-        return _private_array_loop(c.body)
+        return _indexes_registers(c.body)
     return False
 
 
@@ -544,9 +545,10 @@ class Emitter:
                     self.lines.append(f"{pad}  }}")
                     self.lines.append(f"{pad}}}")
                     return
-                if self.backend == "cuda" and c.level == "seq" and n <= 16 and _private_array_loop(c.body):
+                if self.backend == "cuda" and c.level == "seq" and n <= 16 and _indexes_registers(c.body):
                     # a short loop over a private array (e.g. a thread's tile of
-                    # accumulators): unrolled whole, so that the array lives in registers
+                    # accumulators) or over a vector's lanes: unrolled whole, so that the
+                    # array lives in registers and a lane is a register, not a select
                     self.lines.append(f"{pad}#pragma unroll")
                 elif self.backend == "cuda" and self.unroll > 1 and c.level == "seq" and n > self.unroll:
                     # a sequential loop's iterations stay in order; unrolling only
