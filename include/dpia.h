@@ -251,6 +251,18 @@ enum { DPIA_CONTRACT_OFF = 0, DPIA_CONTRACT_FMA = 1 };
  * tiles when M >= 512 and pairs fit on the device, else one CTA. cluster = 2
  * where no CTA pair fits returns DPIA_ERR_CUDA. The value of C does not
  * depend on it. The FP32 fold ignores grid and cluster.
+ * schedule (FP32 fold only; BF16 ignores it): how the tiles of a last wave
+ * that 128 x 128 tiles leave partly empty are spread over the SMs. 1: every
+ * tile a CTA, one launch. 2: the tile rows of a last wave at most half full
+ * as 64 x 128 tiles in a second launch (else as 1). 3: k-range pieces over
+ * two launches: the (tile, k-slice) units cut into one equal range per
+ * resident CTA; the first launch folds the low-k part of every cut tile and
+ * leaves its accumulators in C, the second continues those folds from C
+ * (needs at least two tiles' k-slices per CTA of the device, else
+ * DPIA_ERR_STRATEGY). 0: 3 where it fits and the last wave gives some SM
+ * two tiles while more than 8% of the launch's tile slots stay empty, else
+ * 1. Every schedule runs each C_ij's one sequential fold: C is the same bits
+ * under all of them. Outside 0..3: DPIA_ERR_STRATEGY.
  */
 typedef struct {
   int32_t contract;
@@ -259,6 +271,7 @@ typedef struct {
   int32_t tile_k;
   int32_t grid;
   int32_t cluster;
+  int32_t schedule;
 } dpia_gemm_strategy;
 
 /*

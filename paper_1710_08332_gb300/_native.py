@@ -36,7 +36,8 @@ class DPIAError(RuntimeError):
 
 class GemmStrategyC(ctypes.Structure):
     _fields_ = [("contract", ctypes.c_int32), ("tile_m", ctypes.c_int32), ("tile_n", ctypes.c_int32),
-                ("tile_k", ctypes.c_int32), ("grid", ctypes.c_int32), ("cluster", ctypes.c_int32)]
+                ("tile_k", ctypes.c_int32), ("grid", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("schedule", ctypes.c_int32)]
 
 
 class ReduceStrategyC(ctypes.Structure):

@@ -10,7 +10,8 @@
 namespace dpia {
 cudaError_t launch_gemm_f32(const float *A, const float *B, float *C, int64_t M, int64_t N, int64_t K,
                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int fma, int vec_ok,
-                            cudaStream_t stream);
+                            int schedule, cudaStream_t stream);
+bool gemm_f32_pieces_fit(int64_t M, int64_t N, int64_t K, int fma);
 cudaError_t launch_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,
                              int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int grid, int tile_m,
                              int tile_n, int cluster, int vec_ok, cudaStream_t stream);
@@ -119,18 +120,28 @@ dpia_status dpia_gemm_f32(const float *A, const float *B, float *C, int64_t M, i
     set_last_error("%s: only 128 x 128 x 16 tiles are implemented for the FP32 fold", fn);
     return DPIA_ERR_UNSUPPORTED;
   }
+  if (st->schedule < 0 || st->schedule > 3) {
+    set_last_error("%s: schedule=%d (0 automatic, 1 tiles, 2 half-height tail tiles, 3 k-range pieces)", fn,
+                   st->schedule);
+    return DPIA_ERR_STRATEGY;
+  }
   int64_t ab = 0, bb = 0;
   dpia_status rc = check_gemm(fn, A, B, C, M, N, K, lda, ldb, ldc, transA, transB, 4, &ab, &bb);
   if (rc || M == 0 || N == 0) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (K == 0) return cuda_status(cudaMemset2DAsync(C, ldc * 4, 0, N * 4, M, s), fn);
+  if (st->schedule == 3 && !gemm_f32_pieces_fit(M, N, K, st->contract)) {
+    set_last_error("%s: schedule 3 needs at least two tiles' k-slices per CTA of the device", fn);
+    return DPIA_ERR_STRATEGY;
+  }
   if (!aligned(A, 4) || !aligned(B, 4)) {
     set_last_error("%s: A and B must be 4-byte aligned", fn);
     return DPIA_ERR_ALIGN;
   }
   const int vec_ok = aligned(A, 16) && aligned(B, 16) && aligned(C, 16) && lda % 4 == 0 && ldb % 4 == 0 &&
                      ldc % 4 == 0;
-  return cuda_status(launch_gemm_f32(A, B, C, M, N, K, lda, ldb, ldc, transA, transB, st->contract, vec_ok, s), fn);
+  return cuda_status(
+      launch_gemm_f32(A, B, C, M, N, K, lda, ldb, ldc, transA, transB, st->contract, vec_ok, st->schedule, s), fn);
 }
 
 dpia_status dpia_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int64_t M, int64_t N, int64_t K,

@@ -101,6 +101,118 @@ __device__ __forceinline__ void store_slices(float (*As)[BM], float (*Bs)[BN], c
   }
 }
 
+// Element (i, j) of a thread's 8 x 8 micro-tile: row m0 + ty*4 + i (i < 4) or
+// m0 + 64 + ty*4 + (i-4); column n0 + h*64 + tx*4 + jj for j = 4h + jj.
+__device__ __forceinline__ void load_c(const GemmArgs &g, int vec_ok, int64_t m0, int64_t n0, float (&acc)[8][8]) {
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t n = n0 + h * 64 + tx * 4;
+      if (m < g.M && vec_ok && n + 4 <= g.N) {
+        const float4 v = __ldcg(reinterpret_cast<const float4 *>(g.C + m * g.ldc + n));
+        acc[i][4 * h] = v.x; acc[i][4 * h + 1] = v.y; acc[i][4 * h + 2] = v.z; acc[i][4 * h + 3] = v.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][4 * h + j] = m < g.M && n + j < g.N ? __ldcg(g.C + m * g.ldc + n + j) : 0.0f;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void store_c(const GemmArgs &g, int vec_ok, int64_t m0, int64_t n0,
+                                        const float (&acc)[8][8]) {
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (m >= g.M) continue;
+    float *crow = g.C + m * g.ldc;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t n = n0 + h * 64 + tx * 4;
+      if (vec_ok && n + 4 <= g.N) {
+        *reinterpret_cast<float4 *>(crow + n) =
+            make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (n + j < g.N) crow[n + j] = acc[i][4 * h + j];
+      }
+    }
+  }
+}
+
+// Slices kt0 .. kt1-1 (kt1 > kt0) of the fold of the 128 x 128 tile at (m0, n0):
+// the accumulators start at +0 (from_c false) or at the values C holds (a fold
+// that an earlier launch carried up to slice kt0), and are written to C at the
+// end. A fold cut into such pieces runs the same chain of roundings as one
+// pass over all slices, so the bits of C do not depend on the cut.
+template <bool TA, bool TB, bool FMA>
+__device__ __forceinline__ void fold_tile(const GemmArgs &g, int vec_ok, float (*As)[BK][BM], float (*Bs)[BK][BN],
+                                          int64_t m0, int64_t n0, int64_t kt0, int64_t kt1, bool from_c) {
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const bool interior_mn = m0 + BM <= g.M && n0 + BN <= g.N;
+  float acc[8][8];
+  if (from_c) {
+    load_c(g, vec_ok, m0, n0, acc);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+  }
+
+  float ra[8], rb[8];
+  load_slices<TA, TB>(g, m0, n0, kt0 * BK, vec_ok && interior_mn && kt0 * BK + BK <= g.K, ra, rb);
+  store_slices<TA, TB>(As[0], Bs[0], ra, rb);
+  __syncthreads();
+  for (int64_t kt = kt0; kt < kt1; ++kt) {
+    const int buf = (int)(kt - kt0) & 1;
+    const int64_t k0 = kt * BK;
+    if (kt + 1 < kt1) {
+      const int64_t k1 = k0 + BK;
+      load_slices<TA, TB>(g, m0, n0, k1, vec_ok && interior_mn && k1 + BK <= g.K, ra, rb);
+    }
+    const int kcount = g.K - k0 < BK ? (int)(g.K - k0) : BK;
+    if (kcount == BK) {
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+        float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+        float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+        float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = madd<FMA>(a[i], b[j], acc[i][j]);
+      }
+    } else {
+      for (int kk = 0; kk < kcount; ++kk) {  // k tail: exactly K terms, no padded ones
+        float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+        float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+        float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+        float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = madd<FMA>(a[i], b[j], acc[i][j]);
+      }
+    }
+    if (kt + 1 < kt1) {
+      store_slices<TA, TB>(As[buf ^ 1], Bs[buf ^ 1], ra, rb);
+    }
+    __syncthreads();
+  }
+  store_c(g, vec_ok, m0, n0, acc);
+}
+
 template <bool TA, bool TB, bool FMA>
 __global__ void __launch_bounds__(NT, FMA ? 2 : 1) sgemm_fold_kernel(const GemmArgs g, int vec_ok) {
   __shared__ __align__(16) float As[2][BK][BM];
@@ -182,9 +294,76 @@ __global__ void __launch_bounds__(NT, FMA ? 2 : 1) sgemm_fold_kernel(const GemmA
 }
 
 // ---------------------------------------------------------------------------
-// Tiles of 64 x 128 for the last rows of C: when the 128 x 128 tiles leave a
-// last wave less than half full, those rows are computed as half-height tiles
-// by a second launch. Same fold, same bits, same 8 x 8 elements per thread as
+// The fold cut into k-range pieces over two launches (a stream-k schedule that
+// keeps every fold sequential). The work is the list of (tile, k-slice) units
+// in tile-major order, W = tiles x S units with S = ceil(K / 16), cut into P
+// equal ranges, one per CTA. CTA c's range [u0, u1) holds the high-k part of
+// the tile it shares with CTA c-1 (L_c slices), whole tiles, and the low-k part
+// of the tile it shares with CTA c+1. The first launch folds the whole tiles
+// and the low-k parts and leaves the accumulators in C; the second folds the
+// high-k parts, starting from what C holds. Every CTA's second-launch share is
+// D = max_c L_c slices: its own L_c plus the last D - L_c slices of its last
+// whole tile (which it then stops short of in the first launch), so both
+// launches are balanced. The host requires floor(W / P) >= 2 S, so that every
+// range holds at least one whole tile and every tile is cut at most once
+// between two CTAs.
+// ---------------------------------------------------------------------------
+
+struct PieceArgs {
+  int64_t W, P, S, tn, D;
+};
+
+template <bool TA, bool TB, bool FMA>
+__global__ void __launch_bounds__(NT, FMA ? 2 : 1) sgemm_fold_pieces_kernel(const GemmArgs g, int vec_ok,
+                                                                            const PieceArgs p, int phase) {
+  __shared__ __align__(16) float As[2][BK][BM];
+  __shared__ __align__(16) float Bs[2][BK][BN];
+  // this CTA's pieces in this launch: (tile, first slice, end slice) each;
+  // read from shared memory at the start of every piece so that none of the
+  // plan stays in registers across a fold
+  __shared__ int64_t plan[3][3];
+  __shared__ int64_t whole[2];  // phase 0: first whole tile, count of whole tiles before the last
+  __shared__ int npieces;
+  if (threadIdx.x == 0) {
+    const int64_t c = blockIdx.x;
+    const int64_t u0 = c * p.W / p.P, u1 = (c + 1) * p.W / p.P;
+    const int64_t t_first = ceil_div(u0, p.S), t_last = u1 / p.S;  // whole tiles [t_first, t_last)
+    const int64_t L = t_first * p.S - u0, T = u1 - t_last * p.S, E = p.D - L;
+    int n = 0;
+    auto add = [&](int64_t t, int64_t kt0, int64_t kt1) {
+      plan[n][0] = t; plan[n][1] = kt0; plan[n][2] = kt1; ++n;
+    };
+    if (phase == 0) {
+      whole[0] = t_first;
+      whole[1] = t_last - 1 - t_first;  // whole tiles folded over every slice
+      add(t_last - 1, 0, p.S - E);      // the last whole tile, short of its E top slices
+      if (T > 0) add(t_last, 0, T);     // the low-k part of the tile shared with CTA c+1
+    } else {
+      whole[0] = 0;
+      whole[1] = 0;
+      if (E > 0) add(t_last - 1, p.S - E, p.S);
+      if (L > 0) add(t_first - 1, p.S - L, p.S);  // the high-k part of the tile shared with CTA c-1
+    }
+    npieces = n;
+  }
+  __syncthreads();
+  const volatile int64_t *vw = whole;
+  for (int64_t i = 0; i < vw[1]; ++i) {
+    const int64_t t = vw[0] + i;
+    fold_tile<TA, TB, FMA>(g, vec_ok, As, Bs, (t / p.tn) * BM, (t % p.tn) * BN, 0, p.S, false);
+  }
+  const volatile int *vn = &npieces;
+  for (int j = 0; j < *vn; ++j) {
+    const volatile int64_t *q = plan[j];
+    const int64_t t = q[0], kt0 = q[1];
+    fold_tile<TA, TB, FMA>(g, vec_ok, As, Bs, (t / p.tn) * BM, (t % p.tn) * BN, kt0, q[2], kt0 > 0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tiles of 64 x 128 for the last rows of C (schedule 2): when the 128 x 128
+// tiles leave a last wave less than half full, those rows are computed as
+// half-height tiles by a second launch. Same fold, same bits, same 8 x 8 elements per thread as
 // the full tile (rows ty*4 + i and 32 + ty*4 + i, columns as above), on 128
 // threads, so that four blocks share an SM.
 // ---------------------------------------------------------------------------
@@ -320,18 +499,73 @@ const void *pick(int ta, int tb) {
 
 }  // namespace
 
+namespace {
+
+template <bool FMA>
+const void *pick_pieces(int ta, int tb) {
+  if (!ta && !tb) return (const void *)sgemm_fold_pieces_kernel<false, false, FMA>;
+  if (!ta && tb) return (const void *)sgemm_fold_pieces_kernel<false, true, FMA>;
+  if (ta && !tb) return (const void *)sgemm_fold_pieces_kernel<true, false, FMA>;
+  return (const void *)sgemm_fold_pieces_kernel<true, true, FMA>;
+}
+
+// The piece schedule over P CTAs (two per SM with the declared FMA): W units
+// of (tile, k-slice), D the second launch's share.
+bool piece_plan(int64_t M, int64_t N, int64_t K, int fma, PieceArgs *p) {
+  const int64_t tn = ceil_div(N, BN), tm = ceil_div(M, BM), S = ceil_div(K, BK);
+  const void *k = fma ? pick_pieces<true>(0, 0) : pick_pieces<false>(0, 0);
+  const int64_t P = (int64_t)sm_count() * resident_blocks(k, NT);
+  if (S < 1 || P < 1) return false;
+  const int64_t W = tn * tm * S;
+  if (W / P < 2 * S) return false;
+  int64_t D = 0;
+  for (int64_t c = 0; c < P; ++c) {
+    const int64_t u0 = c * W / P, L = ceil_div(u0, S) * S - u0;
+    if (L > D) D = L;
+  }
+  *p = PieceArgs{W, P, S, tn, D};
+  return true;
+}
+
+}  // namespace
+
+bool gemm_f32_pieces_fit(int64_t M, int64_t N, int64_t K, int fma) {
+  PieceArgs p;
+  return piece_plan(M, N, K, fma, &p);
+}
+
 cudaError_t launch_gemm_f32(const float *A, const float *B, float *C, int64_t M, int64_t N, int64_t K,
                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int fma,
-                            int vec_ok, cudaStream_t stream) {
+                            int vec_ok, int schedule, cudaStream_t stream) {
   GemmArgs g{A, B, C, M, N, K, lda, ldb, ldc};
   const void *k = fma ? pick<true>(transA, transB) : pick<false>(transA, transB);
   const int64_t tn = ceil_div(N, BN), tm = ceil_div(M, BM);
-  // a last wave of 128 x 128 tiles less than half full: its rows go to the
-  // half-height kernel, which finishes them in half a wave's time
   const int64_t slots = (int64_t)sm_count() * resident_blocks(k, NT);
   const int64_t total = tn * tm, rem = total % slots;
+  // automatic: one launch, unless the last wave leaves some SM two tiles and
+  // more than 8% of all the two-tile slots of the launch's waves empty; then
+  // the k-range pieces where they fit. A last wave of at most one tile per SM
+  // costs about half a wave, since a tile alone on an SM runs faster than one
+  // of two (4096^3: one launch 2.63 ms, pieces 2.73, half-height tail tiles
+  // 2.73); the pieces cost about 8% of the run in all (3584 x 3584 x 4096:
+  // 2.12 ms against 2.21 in one launch; 6144 x 6144 x 2048: 3.02 against 2.96).
+  const int64_t sms = sm_count();
+  const bool pieces_pay = total > slots && rem > sms && (slots - rem) * 100 > 8 * slots * (total / slots + 1);
+  PieceArgs p;
+  if ((schedule == 0 && pieces_pay) || schedule == 3) {
+    if (piece_plan(M, N, K, fma, &p)) {
+      const void *kp = fma ? pick_pieces<true>(transA, transB) : pick_pieces<false>(transA, transB);
+      for (int phase = 0; phase < 2; ++phase) {
+        void *pargs[] = {&g, &vec_ok, &p, &phase};
+        cudaError_t e = cudaLaunchKernel(kp, dim3((unsigned)p.P), dim3(NT), pargs, 0, stream);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+    if (schedule == 3) return cudaErrorInvalidValue;  // refused on the host before this call
+  }
   int64_t tail = 0;  // tile rows computed as half tiles
-  if (total > slots && rem > 0 && rem <= slots / 2) tail = ceil_div(rem, tn);
+  if (schedule == 2 && total > slots && rem > 0 && rem <= slots / 2) tail = ceil_div(rem, tn);
   if (tail >= tm) tail = 0;
   void *args[] = {&g, &vec_ok};
   cudaError_t e = cudaLaunchKernel(k, dim3((unsigned)tn, (unsigned)(tm - tail)), dim3(NT), args, 0, stream);

@@ -105,16 +105,18 @@ def dpia_gemv_bwd_f32(A, M, N_, lda, x, dy, dx, dA, ldda, row_split, ws, stream=
                                       _stream(stream)), "dpia_gemv_bwd_f32")
 
 
-def _gst(contract="fma", grid=0, tile_n=0, cluster=0, tile_m=0):
+def _gst(contract="fma", grid=0, tile_n=0, cluster=0, tile_m=0, schedule=0):
     return ctypes.byref(N.GemmStrategyC(1 if contract == "fma" else 0, int(tile_m), int(tile_n), 0, int(grid),
-                                        int(cluster)))
+                                        int(cluster), int(schedule)))
 
 
-def dpia_gemm_f32(A, B, C, M, N_, K, lda, ldb, ldc, transA=0, transB=0, contract="fma", stream=None):
+def dpia_gemm_f32(A, B, C, M, N_, K, lda, ldb, ldc, transA=0, transB=0, contract="fma", schedule=0, stream=None):
+    """schedule: 0 automatic, 1 one launch of 128 x 128 tiles, 2 half-height tiles
+    for a last wave at most half full, 3 k-range pieces over two launches."""
     _need_cuda(A, B, C)
     N.check(N.lib().dpia_gemm_f32(_ptr(A), _ptr(B), _ptr(C), int(M), int(N_), int(K), int(lda), int(ldb),
-                                  int(ldc), int(transA), int(transB), _gst(contract), _stream(stream)),
-            "dpia_gemm_f32")
+                                  int(ldc), int(transA), int(transB), _gst(contract, schedule=schedule),
+                                  _stream(stream)), "dpia_gemm_f32")
 
 
 def dpia_gemm_bf16(A, B, C, M, N_, K, lda, ldb, ldc, transA=0, transB=0, grid=0, tile_n=0, cluster=0,

@@ -170,11 +170,11 @@ def test_gemm_strategy_validation():
 
     def call(**kw):
         st = N.GemmStrategyC(1, kw.get("tile_m", 0), kw.get("tile_n", 0), kw.get("tile_k", 0), kw.get("grid", 0),
-                             kw.get("cluster", 0))
+                             kw.get("cluster", 0), kw.get("schedule", 0))
         return L.dpia_gemm_bf16(p(0x10000), p(0x20000), p(0x30000), 512, 512, 512, 512, 512, 512, 0, 0,
                                 ctypes.byref(st), None)
 
-    assert ctypes.sizeof(N.GemmStrategyC) == 6 * 4
+    assert ctypes.sizeof(N.GemmStrategyC) == 7 * 4
     for c in (3, 4, 8, -1):
         assert call(cluster=c) == N.ERR_STRATEGY
         assert "cluster" in dpia.dpia_last_error_message()
@@ -186,6 +186,18 @@ def test_gemm_strategy_validation():
     assert call(tile_m=512) == N.ERR_UNSUPPORTED
     assert L.dpia_gemm_bf16(p(0x10000), p(0x20000), p(0x30000), 512, 512, 512, 512, 512, 512, 0, 0, None,
                             None) == N.ERR_NULL
+
+
+def test_gemm_f32_schedule_values():
+    """The FP32 fold's schedules are 0..3; any other value is refused before any
+    CUDA call (schedule 3 that does not fit the device is refused on a GPU)."""
+    L = N.lib()
+    p = ctypes.c_void_p
+    for sched, want in ((-1, N.ERR_STRATEGY), (4, N.ERR_STRATEGY), (7, N.ERR_STRATEGY)):
+        st = N.GemmStrategyC(1, 0, 0, 0, 0, 0, sched)
+        assert L.dpia_gemm_f32(p(0x10000), p(0x20000), p(0x30000), 512, 512, 512, 512, 512, 512, 0, 0,
+                               ctypes.byref(st), None) == want
+        assert "schedule" in dpia.dpia_last_error_message()
 
 
 def test_batch_row_alignment_is_checked():

@@ -64,8 +64,8 @@ def gemm_inputs():
 
 def _f32_rows_4096(n):
     """Rows of C checked at 4096^3: two in every 128-row tile row (at offsets that
-    vary from tile to tile) and every 16th row of the last 512, whose tiles run
-    as 64-row half tiles in the second launch -- 96 rows, all columns."""
+    vary from tile to tile) and every 16th row of the last 512 -- 96 rows, all
+    columns."""
     rows = set()
     for t in range(n // 128):
         rows.add(t * 128 + (t * 41) % 128)
@@ -75,13 +75,19 @@ def _f32_rows_4096(n):
 
 
 def test_gemm_f32_4096_rows(cuda_device, gemm_inputs):
-    """The FP32 fold at 4096^3 against the oracle's fold, bit for bit, on 96 full
-    rows of C (every tile row, both launches), and within the summation bound
-    of FP64 there."""
+    """The FP32 fold at 4096^3 (the automatic schedule: one launch) against the
+    oracle's fold, bit for bit, on 96 full rows of C (every tile row), and
+    within the summation bound of FP64 there; all of C is the same bits under
+    the half-tile and k-range piece schedules."""
     A, B, _ = gemm_inputs
     n = W.GEMM_MNK
     C = torch.empty(n, n, device="cuda")
     dpia.dpia_gemm_f32(A, B, C, n, n, n, n, n, n, 0, 0, "fma")
+    for sched in (2, 3):
+        C2 = torch.empty(n, n, device="cuda")
+        dpia.dpia_gemm_f32(A, B, C2, n, n, n, n, n, n, 0, 0, "fma", schedule=sched)
+        assert torch.equal(C2.view(torch.int32), C.view(torch.int32)), f"schedule {sched}"
+        del C2
     rows = _f32_rows_4096(n)
     assert rows.size >= 64
     hA, hB = host(A), host(B)
@@ -273,7 +279,7 @@ def test_gemm_validation(cuda_device):
 
 @pytest.mark.parametrize("tA,tB", [(0, 0), (1, 0), (0, 1)])
 def test_gemm_f32_tail_rows_as_half_tiles(cuda_device, tA, tB):
-    """2560 x 2048 tiles fill more than the SMs hold with a small last wave: the
+    """Schedule 2: 2560 x 2048 tiles fill more than the SMs hold with a small last wave: the
     last tile row runs as half-height tiles in a second launch; every element
     is still the oracle's fold."""
     M, N, K = 2560, 2048, 64
@@ -281,8 +287,53 @@ def test_gemm_f32_tail_rows_as_half_tiles(cuda_device, tA, tB):
     B = (torch.randn(N, K) if tB else torch.randn(K, N)).numpy()
     C = torch.full((M, N), float("nan"), device="cuda")
     dpia.dpia_gemm_f32(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, M, N, K, A.shape[1], B.shape[1],
-                       N, tA, tB, "fma")
+                       N, tA, tB, "fma", schedule=2)
     torch.cuda.synchronize()
     rows = np.r_[0:8, 2300:2560]
     want = loopnest.gemm_f32_sample(A, B, bool(tA), bool(tB), True, rows, np.arange(N))
     assert_bits_equal(host(C)[rows], want, f"tail tA={tA} tB={tB}")
+
+
+def _two_rows_per_tile_row(M):
+    rows = set()
+    for t in range((M + 127) // 128):
+        lo, hi = t * 128, min(M, t * 128 + 128)
+        rows.add(lo + (t * 37) % (hi - lo))
+        rows.add(hi - 1 - (t * 11) % (hi - lo))
+    return np.array(sorted(rows))
+
+
+@pytest.mark.parametrize("contract", ["fma", "off"])
+@pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("M,N,K", [(3500, 3490, 300), (3584, 3584, 40)])
+def test_gemm_f32_pieces_bits(cuda_device, contract, tA, tB, M, N, K):
+    """k-range pieces (schedule 3): 784 tiles, each CTA's range cut at k-slices
+    that differ from tile to tile (ragged M and N, a k tail of 12 or 8), the
+    cut tiles' folds carried through C from the first launch to the second.
+    All of C is the same bits under schedules 1, 2, 3 and 0, and two rows of
+    every tile row are the oracle's fold."""
+    g = torch.Generator().manual_seed(M + 3 * N + K)
+    opA = torch.randn(M, K, generator=g).numpy()
+    opB = torch.randn(K, N, generator=g).numpy()
+    A, B = _store(opA, tA), _store(opB, tB)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    out = {}
+    for sched in (3, 1, 2, 0):
+        C = torch.full((M, N), float("nan"), device="cuda")
+        dpia.dpia_gemm_f32(Ad, Bd, C, M, N, K, A.shape[1], B.shape[1], N, tA, tB, contract, schedule=sched)
+        out[sched] = C
+    torch.cuda.synchronize()
+    for sched in (1, 2, 0):
+        assert torch.equal(out[sched].view(torch.int32), out[3].view(torch.int32)), f"schedule {sched} vs 3"
+    rows = _two_rows_per_tile_row(M)
+    want = loopnest.gemm_f32_sample(A, B, bool(tA), bool(tB), contract == "fma", rows, np.arange(N))
+    assert_bits_equal(host(out[3])[rows], want, f"pieces {contract} tA={tA} tB={tB} {M}x{N}x{K}")
+
+
+def test_gemm_f32_pieces_refused_when_they_do_not_fit(cuda_device):
+    """Schedule 3 needs at least two tiles' k-slices per resident CTA: 4 x 4
+    tiles are refused with a strategy error, before any launch."""
+    A = torch.zeros(512, 512, device="cuda")
+    C = torch.zeros(512, 512, device="cuda")
+    with pytest.raises(dpia.DPIAError, match="STRATEGY"):
+        dpia.dpia_gemm_f32(A, A.clone(), C, 512, 512, 512, 512, 512, 512, 0, 0, "fma", schedule=3)
