@@ -324,7 +324,7 @@ def profile_case(args):
 
         def fn():
             dpia.dpia_gemm_bf16(Ab, Bb, C, m, m, m, m, m, m, 0, 0, cluster=args.cluster, tile_m=args.tile_m)
-            dpia.dpia_gemm_f32(A, B, C, m, m, m, m, m, m, 0, 0, "fma")
+            dpia.dpia_gemm_f32(A, B, C, m, m, m, m, m, m, 0, 0, "fma", schedule=args.schedule)
     elif args.profile == "batched":  # the first 512 dots and 16 GEMVs of the batched workload
         import math
 
@@ -758,23 +758,33 @@ def gemm_workload(args, device, dist):
     fl = 2 * n ** 3
     _, bf16_peak, bf16_sust, src = peaks()
     kern = {k: {"avg_us": round(v * 1e3, 2), "flops": fl, "TFLOP_s": round(fl / v / 1e9, 1)} for k, v in per.items()}
-    # FP32 fold forward, a few launches (it runs on the FMA pipes, not the tensor cores)
-    f32_ms = []
-    for _ in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        dpia.dpia_gemm_f32(A, B, Cf, n, n, n, n, n, n, 0, 0, "fma")
-        e1.record()
-        e1.synchronize()
-        f32_ms.append(e0.elapsed_time(e1))
-    f32 = min(f32_ms)
+    # FP32 fold forward, a few launches of each schedule, L2 flushed before each
+    # (it runs on the FMA pipes, not the tensor cores)
+    fl2 = L2Flush(device)
+
+    def f32_median(schedule):
+        ms = []
+        for _ in range(5):
+            fl2()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            dpia.dpia_gemm_f32(A, B, Cf, n, n, n, n, n, n, 0, 0, "fma", schedule=schedule)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return sorted(ms)[len(ms) // 2]
+
+    f32 = f32_median(0)
+    f32_sched = {name: round(f32_median(sc) * 1e3, 1) for name, sc in
+                 (("one_launch", 1), ("half_height_tail_tiles", 2), ("k_range_pieces", 3))}
     sm_max = max_sm_mhz(clk)
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     fma_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
-    kern["f32_fold_fwd"] = {"avg_us": round(f32 * 1e3, 1), "flops": fl, "TFLOP_s": round(fl / f32 / 1e9, 2),
+    kern["f32_fold_fwd"] = {"median_us": round(f32 * 1e3, 1), "flops": fl, "TFLOP_s": round(fl / f32 / 1e9, 2),
                             "bound": "alu", "peak_TFLOP_s": round(fma_peak, 1),
                             "peak_source": f"{sms} SMs x 128 FP32 FMA lanes x 2 flops x {sm_max:.0f} MHz (the "
-                                           "maximum SM clock)", "frac": round(fl / f32 / 1e9 / fma_peak, 4)}
+                                           "maximum SM clock)", "frac": round(fl / f32 / 1e9 / fma_peak, 4),
+                            "schedules_median_us": f32_sched}
     # each launch alone (L2 flushed before it): one CTA per 256-row tile (cta_group::1), CTA pairs
     # (cta_group::2) on 256-row and 512-row tiles, and cuBLAS (torch.matmul, bf16 out) on the same shape
     flush = L2Flush(device)
@@ -1537,6 +1547,9 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2],
                     help="CTAs per tile of the BF16 GEMM in the gemm --profile case (0 = one)")
+    ap.add_argument("--schedule", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="FP32 fold schedule in the gemm --profile case (0 automatic, 1 one launch, 2 half-height "
+                         "tail tiles, 3 k-range pieces over two launches)")
     ap.add_argument("--gemm-ksweep", action="store_true",
                     help="gemm workload: also time the forward at K = 512..8192 (M = N = 4096)")
     ap.add_argument("--tile-m", type=int, default=0, choices=[0, 256, 512],
@@ -1623,7 +1636,8 @@ def secondary_workloads(args, device, dist):
                  for kk in ("bf16_fwd", "bf16_bwd_dA", "bf16_bwd_dB")}
             d["bf16_alone_512row_pairs"] = k["alone_by_cluster"]["2x512"]
             d["cublas_bf16_TFLOP_s"] = k["cublas_same_shape"]["TFLOP_s"]
-            d["f32_fold_fwd"] = _pick(k["f32_fold_fwd"], "TFLOP_s", "frac", "peak_TFLOP_s", "peak_source")
+            d["f32_fold_fwd"] = _pick(k["f32_fold_fwd"], "TFLOP_s", "frac", "peak_TFLOP_s", "peak_source",
+                                      "schedules_median_us")
             d["cublas_f32_TFLOP_s"] = k["f32_fold_fwd"]["cublas_same_shape"]["TFLOP_s"]
         else:
             d = {"fwd_ms": k["batched_fwd"]["avg_ms"], "bwd_ms": k["batched_bwd"]["avg_ms"],
