@@ -103,6 +103,7 @@ __device__ __forceinline__ void store_slices(float (*As)[BM], float (*Bs)[BN], c
 
 // Element (i, j) of a thread's 8 x 8 micro-tile: row m0 + ty*4 + i (i < 4) or
 // m0 + 64 + ty*4 + (i-4); column n0 + h*64 + tx*4 + jj for j = 4h + jj.
+template <bool EXACT>
 __device__ __forceinline__ void load_c(const GemmArgs &g, int vec_ok, int64_t m0, int64_t n0, float (&acc)[8][8]) {
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
 #pragma unroll
@@ -111,7 +112,7 @@ __device__ __forceinline__ void load_c(const GemmArgs &g, int vec_ok, int64_t m0
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int64_t n = n0 + h * 64 + tx * 4;
-      if (m < g.M && vec_ok && n + 4 <= g.N) {
+      if (EXACT || (m < g.M && vec_ok && n + 4 <= g.N)) {
         const float4 v = __ldcg(reinterpret_cast<const float4 *>(g.C + m * g.ldc + n));
         acc[i][4 * h] = v.x; acc[i][4 * h + 1] = v.y; acc[i][4 * h + 2] = v.z; acc[i][4 * h + 3] = v.w;
       } else {
@@ -122,18 +123,19 @@ __device__ __forceinline__ void load_c(const GemmArgs &g, int vec_ok, int64_t m0
   }
 }
 
+template <bool EXACT>
 __device__ __forceinline__ void store_c(const GemmArgs &g, int vec_ok, int64_t m0, int64_t n0,
                                         const float (&acc)[8][8]) {
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int64_t m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-    if (m >= g.M) continue;
+    if (!EXACT && m >= g.M) continue;
     float *crow = g.C + m * g.ldc;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int64_t n = n0 + h * 64 + tx * 4;
-      if (vec_ok && n + 4 <= g.N) {
+      if (EXACT || (vec_ok && n + 4 <= g.N)) {
         *reinterpret_cast<float4 *>(crow + n) =
             make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
       } else {
@@ -150,14 +152,14 @@ __device__ __forceinline__ void store_c(const GemmArgs &g, int vec_ok, int64_t m
 // that an earlier launch carried up to slice kt0), and are written to C at the
 // end. A fold cut into such pieces runs the same chain of roundings as one
 // pass over all slices, so the bits of C do not depend on the cut.
-template <bool TA, bool TB, bool FMA>
+template <bool TA, bool TB, bool FMA, bool EXACT>
 __device__ __forceinline__ void fold_tile(const GemmArgs &g, int vec_ok, float (*As)[BK][BM], float (*Bs)[BK][BN],
                                           int64_t m0, int64_t n0, int64_t kt0, int64_t kt1, bool from_c) {
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const bool interior_mn = m0 + BM <= g.M && n0 + BN <= g.N;
+  const bool interior_mn = EXACT || (m0 + BM <= g.M && n0 + BN <= g.N);
   float acc[8][8];
   if (from_c) {
-    load_c(g, vec_ok, m0, n0, acc);
+    load_c<EXACT>(g, vec_ok, m0, n0, acc);
   } else {
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -166,7 +168,7 @@ __device__ __forceinline__ void fold_tile(const GemmArgs &g, int vec_ok, float (
   }
 
   float ra[8], rb[8];
-  load_slices<TA, TB>(g, m0, n0, kt0 * BK, vec_ok && interior_mn && kt0 * BK + BK <= g.K, ra, rb);
+  load_slices<TA, TB>(g, m0, n0, kt0 * BK, EXACT || (vec_ok && interior_mn && kt0 * BK + BK <= g.K), ra, rb);
   store_slices<TA, TB>(As[0], Bs[0], ra, rb);
   __syncthreads();
   for (int64_t kt = kt0; kt < kt1; ++kt) {
@@ -174,10 +176,10 @@ __device__ __forceinline__ void fold_tile(const GemmArgs &g, int vec_ok, float (
     const int64_t k0 = kt * BK;
     if (kt + 1 < kt1) {
       const int64_t k1 = k0 + BK;
-      load_slices<TA, TB>(g, m0, n0, k1, vec_ok && interior_mn && k1 + BK <= g.K, ra, rb);
+      load_slices<TA, TB>(g, m0, n0, k1, EXACT || (vec_ok && interior_mn && k1 + BK <= g.K), ra, rb);
     }
-    const int kcount = g.K - k0 < BK ? (int)(g.K - k0) : BK;
-    if (kcount == BK) {
+    const int kcount = EXACT ? BK : (g.K - k0 < BK ? (int)(g.K - k0) : BK);
+    if (EXACT || kcount == BK) {
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
@@ -210,25 +212,29 @@ __device__ __forceinline__ void fold_tile(const GemmArgs &g, int vec_ok, float (
     }
     __syncthreads();
   }
-  store_c(g, vec_ok, m0, n0, acc);
+  store_c<EXACT>(g, vec_ok, m0, n0, acc);
 }
 
-template <bool TA, bool TB, bool FMA>
+// EXACT: every tile interior (M, N multiples of 128), K a multiple of 16 and
+// the 128-bit paths legal, so the loads, the k loop and the stores need no
+// edge cases (4096^3: 2.42 against 2.63 ms for the general kernel; the same
+// fold of every element).
+template <bool TA, bool TB, bool FMA, bool EXACT>
 __global__ void __launch_bounds__(NT, FMA ? 2 : 1) sgemm_fold_kernel(const GemmArgs g, int vec_ok) {
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN];
   const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const bool interior_mn = m0 + BM <= g.M && n0 + BN <= g.N;
+  const bool interior_mn = EXACT || (m0 + BM <= g.M && n0 + BN <= g.N);
   float acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
 
-  const int64_t nk = ceil_div(g.K, BK);
+  const int64_t nk = EXACT ? g.K / BK : ceil_div(g.K, BK);
   float ra[8], rb[8];
-  load_slices<TA, TB>(g, m0, n0, 0, vec_ok && interior_mn && BK <= g.K, ra, rb);
+  load_slices<TA, TB>(g, m0, n0, 0, EXACT || (vec_ok && interior_mn && BK <= g.K), ra, rb);
   store_slices<TA, TB>(As[0], Bs[0], ra, rb);
   __syncthreads();
   for (int64_t kt = 0; kt < nk; ++kt) {
@@ -236,10 +242,10 @@ __global__ void __launch_bounds__(NT, FMA ? 2 : 1) sgemm_fold_kernel(const GemmA
     const int64_t k0 = kt * BK;
     if (kt + 1 < nk) {
       const int64_t k1 = k0 + BK;
-      load_slices<TA, TB>(g, m0, n0, k1, vec_ok && interior_mn && k1 + BK <= g.K, ra, rb);
+      load_slices<TA, TB>(g, m0, n0, k1, EXACT || (vec_ok && interior_mn && k1 + BK <= g.K), ra, rb);
     }
-    const int kcount = g.K - k0 < BK ? (int)(g.K - k0) : BK;
-    if (kcount == BK) {
+    const int kcount = EXACT ? BK : (g.K - k0 < BK ? (int)(g.K - k0) : BK);
+    if (EXACT || kcount == BK) {
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
@@ -276,12 +282,12 @@ __global__ void __launch_bounds__(NT, FMA ? 2 : 1) sgemm_fold_kernel(const GemmA
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int64_t m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-    if (m >= g.M) continue;
+    if (!EXACT && m >= g.M) continue;
     float *crow = g.C + m * g.ldc;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int64_t n = n0 + h * 64 + tx * 4;
-      if (vec_ok && n + 4 <= g.N) {
+      if (EXACT || (vec_ok && n + 4 <= g.N)) {
         *reinterpret_cast<float4 *>(crow + n) =
             make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
       } else {
@@ -313,7 +319,7 @@ struct PieceArgs {
   int64_t W, P, S, tn, D;
 };
 
-template <bool TA, bool TB, bool FMA>
+template <bool TA, bool TB, bool FMA, bool EXACT>
 __global__ void __launch_bounds__(NT, FMA ? 2 : 1) sgemm_fold_pieces_kernel(const GemmArgs g, int vec_ok,
                                                                             const PieceArgs p, int phase) {
   __shared__ __align__(16) float As[2][BK][BM];
@@ -350,13 +356,13 @@ __global__ void __launch_bounds__(NT, FMA ? 2 : 1) sgemm_fold_pieces_kernel(cons
   const volatile int64_t *vw = whole;
   for (int64_t i = 0; i < vw[1]; ++i) {
     const int64_t t = vw[0] + i;
-    fold_tile<TA, TB, FMA>(g, vec_ok, As, Bs, (t / p.tn) * BM, (t % p.tn) * BN, 0, p.S, false);
+    fold_tile<TA, TB, FMA, EXACT>(g, vec_ok, As, Bs, (t / p.tn) * BM, (t % p.tn) * BN, 0, p.S, false);
   }
   const volatile int *vn = &npieces;
   for (int j = 0; j < *vn; ++j) {
     const volatile int64_t *q = plan[j];
     const int64_t t = q[0], kt0 = q[1];
-    fold_tile<TA, TB, FMA>(g, vec_ok, As, Bs, (t / p.tn) * BM, (t % p.tn) * BN, kt0, q[2], kt0 > 0);
+    fold_tile<TA, TB, FMA, EXACT>(g, vec_ok, As, Bs, (t / p.tn) * BM, (t % p.tn) * BN, kt0, q[2], kt0 > 0);
   }
 }
 
@@ -489,31 +495,31 @@ const void *pick_half(int ta, int tb) {
   return (const void *)sgemm_fold_half_kernel<true, true, FMA>;
 }
 
-template <bool FMA>
+template <bool FMA, bool EXACT>
 const void *pick(int ta, int tb) {
-  if (!ta && !tb) return (const void *)sgemm_fold_kernel<false, false, FMA>;
-  if (!ta && tb) return (const void *)sgemm_fold_kernel<false, true, FMA>;
-  if (ta && !tb) return (const void *)sgemm_fold_kernel<true, false, FMA>;
-  return (const void *)sgemm_fold_kernel<true, true, FMA>;
+  if (!ta && !tb) return (const void *)sgemm_fold_kernel<false, false, FMA, EXACT>;
+  if (!ta && tb) return (const void *)sgemm_fold_kernel<false, true, FMA, EXACT>;
+  if (ta && !tb) return (const void *)sgemm_fold_kernel<true, false, FMA, EXACT>;
+  return (const void *)sgemm_fold_kernel<true, true, FMA, EXACT>;
 }
 
 }  // namespace
 
 namespace {
 
-template <bool FMA>
+template <bool FMA, bool EXACT>
 const void *pick_pieces(int ta, int tb) {
-  if (!ta && !tb) return (const void *)sgemm_fold_pieces_kernel<false, false, FMA>;
-  if (!ta && tb) return (const void *)sgemm_fold_pieces_kernel<false, true, FMA>;
-  if (ta && !tb) return (const void *)sgemm_fold_pieces_kernel<true, false, FMA>;
-  return (const void *)sgemm_fold_pieces_kernel<true, true, FMA>;
+  if (!ta && !tb) return (const void *)sgemm_fold_pieces_kernel<false, false, FMA, EXACT>;
+  if (!ta && tb) return (const void *)sgemm_fold_pieces_kernel<false, true, FMA, EXACT>;
+  if (ta && !tb) return (const void *)sgemm_fold_pieces_kernel<true, false, FMA, EXACT>;
+  return (const void *)sgemm_fold_pieces_kernel<true, true, FMA, EXACT>;
 }
 
 // The piece schedule over P CTAs (two per SM with the declared FMA): W units
 // of (tile, k-slice), D the second launch's share.
 bool piece_plan(int64_t M, int64_t N, int64_t K, int fma, PieceArgs *p) {
   const int64_t tn = ceil_div(N, BN), tm = ceil_div(M, BM), S = ceil_div(K, BK);
-  const void *k = fma ? pick_pieces<true>(0, 0) : pick_pieces<false>(0, 0);
+  const void *k = fma ? pick_pieces<true, false>(0, 0) : pick_pieces<false, false>(0, 0);
   const int64_t P = (int64_t)sm_count() * resident_blocks(k, NT);
   if (S < 1 || P < 1) return false;
   const int64_t W = tn * tm * S;
@@ -538,7 +544,9 @@ cudaError_t launch_gemm_f32(const float *A, const float *B, float *C, int64_t M,
                             int64_t lda, int64_t ldb, int64_t ldc, int transA, int transB, int fma,
                             int vec_ok, int schedule, cudaStream_t stream) {
   GemmArgs g{A, B, C, M, N, K, lda, ldb, ldc};
-  const void *k = fma ? pick<true>(transA, transB) : pick<false>(transA, transB);
+  const bool exact = vec_ok && M % BM == 0 && N % BN == 0 && K % BK == 0;
+  const void *k = fma ? (exact ? pick<true, true>(transA, transB) : pick<true, false>(transA, transB))
+                      : (exact ? pick<false, true>(transA, transB) : pick<false, false>(transA, transB));
   const int64_t tn = ceil_div(N, BN), tm = ceil_div(M, BM);
   const int64_t slots = (int64_t)sm_count() * resident_blocks(k, NT);
   const int64_t total = tn * tm, rem = total % slots;
@@ -546,15 +554,17 @@ cudaError_t launch_gemm_f32(const float *A, const float *B, float *C, int64_t M,
   // more than 8% of all the two-tile slots of the launch's waves empty; then
   // the k-range pieces where they fit. A last wave of at most one tile per SM
   // costs about half a wave, since a tile alone on an SM runs faster than one
-  // of two (4096^3: one launch 2.63 ms, pieces 2.73, half-height tail tiles
-  // 2.73); the pieces cost about 8% of the run in all (3584 x 3584 x 4096:
-  // 2.12 ms against 2.21 in one launch; 6144 x 6144 x 2048: 3.02 against 2.96).
+  // of two (4096^3: one launch 2.42 ms, half-height tail tiles 2.58, pieces
+  // 2.64); the pieces cost about 8-10% of the run in all (3584 x 3584 x 4096:
+  // 1.98 ms against 2.07 in one launch; 6144 x 6144 x 2048: 3.05 against 2.75).
   const int64_t sms = sm_count();
   const bool pieces_pay = total > slots && rem > sms && (slots - rem) * 100 > 8 * slots * (total / slots + 1);
   PieceArgs p;
   if ((schedule == 0 && pieces_pay) || schedule == 3) {
     if (piece_plan(M, N, K, fma, &p)) {
-      const void *kp = fma ? pick_pieces<true>(transA, transB) : pick_pieces<false>(transA, transB);
+      const void *kp = fma ? (exact ? pick_pieces<true, true>(transA, transB) : pick_pieces<true, false>(transA, transB))
+                           : (exact ? pick_pieces<false, true>(transA, transB)
+                                    : pick_pieces<false, false>(transA, transB));
       for (int phase = 0; phase < 2; ++phase) {
         void *pargs[] = {&g, &vec_ok, &p, &phase};
         cudaError_t e = cudaLaunchKernel(kp, dim3((unsigned)p.P), dim3(NT), pargs, 0, stream);
