@@ -9,6 +9,10 @@
 // shared memory (double-buffered, the next slice prefetched through registers
 // while the current one is consumed). Every element's fold stays one
 // sequential chain in k, so the result is bit-identical to the oracle's loop.
+// Interior-only shapes run an EXACT instance without edge cases. A partly
+// empty last wave of tiles can be run as one launch, as half-height tiles in a
+// second launch, or as k-range pieces over two launches (the cut folds carried
+// through C); every schedule gives the same bits.
 #include "device_common.cuh"
 #include "kernels.h"
 
