@@ -305,10 +305,11 @@ def _two_rows_per_tile_row(M):
 
 @pytest.mark.parametrize("contract", ["fma", "off"])
 @pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0), (1, 1)])
-@pytest.mark.parametrize("M,N,K", [(3500, 3490, 300), (3584, 3584, 40)])
+@pytest.mark.parametrize("M,N,K", [(3500, 3490, 300), (3584, 3584, 40), (3584, 3584, 48)])
 def test_gemm_f32_pieces_bits(cuda_device, contract, tA, tB, M, N, K):
     """k-range pieces (schedule 3): 784 tiles, each CTA's range cut at k-slices
-    that differ from tile to tile (ragged M and N, a k tail of 12 or 8), the
+    that differ from tile to tile (ragged M and N, a k tail of 12 or 8; or
+    every tile interior with K a multiple of 16, the EXACT instances), the
     cut tiles' folds carried through C from the first launch to the second.
     All of C is the same bits under schedules 1, 2, 3 and 0, and two rows of
     every tile row are the oracle's fold."""
